@@ -1,0 +1,328 @@
+"""FP64 CPU oracle for the adaptive-biasing-potential force call.
+
+TEST INFRASTRUCTURE. Only the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package. The CUDA library
+never calls it and shares no code with it; the only things both sides consume
+are the plain-data walker specs and frames made by the seeded input
+generators.
+
+The arithmetic lives in ``abp_oracle.c`` (plain C, double precision, one
+function per step of the method, each citing the paper's equation). This
+module compiles it with gcc, mirrors its structs with ctypes and converts
+walker specs (dicts, see ``paper_1609_09833_gb300.synth``) into them.
+
+Parity status: every function here is pinned by ``tests/test_oracle_*.py``
+(closed forms, finite differences, exactness on multilinear fields, brute
+force on tiny grids, rational arithmetic for the switching function and
+well-tempered convergence on an analytic double well).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "abp_oracle.c")
+_BUILD_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+CV_TYPES = {"com_dist": 0, "dihedral": 1, "coord": 2, "pos_x": 3}
+FLAG_DEPOSIT, FLAG_OOR, FLAG_SINGULAR, FLAG_BADARG = 1, 2, 4, 8
+MAXCV = 3
+
+
+class OrCv(C.Structure):
+    _fields_ = [
+        ("type", C.c_int),
+        ("na", C.c_int),
+        ("nb", C.c_int),
+        ("ia", C.POINTER(C.c_int)),
+        ("ib", C.POINTER(C.c_int)),
+        ("ma", C.POINTER(C.c_double)),
+        ("mb", C.POINTER(C.c_double)),
+        ("r0", C.c_double),
+        ("nn", C.c_int),
+        ("mm", C.c_int),
+        ("pbc", C.c_int),
+        ("box", C.c_double * 3),
+    ]
+
+
+class OrGrid(C.Structure):
+    _fields_ = [
+        ("d", C.c_int),
+        ("n", C.c_int * 3),
+        ("periodic", C.c_int * 3),
+        ("lo", C.c_double * 3),
+        ("hi", C.c_double * 3),
+    ]
+
+
+class OrHill(C.Structure):
+    _fields_ = [
+        ("w", C.c_double),
+        ("sigma", C.c_double * 3),
+        ("cutoff", C.c_double),
+        ("gamma", C.c_double),
+        ("kT", C.c_double),
+        ("stride", C.c_int64),
+    ]
+
+
+class OrWalker(C.Structure):
+    _fields_ = [("g", OrGrid), ("hill", OrHill), ("cv", OrCv * MAXCV), ("natoms", C.c_int)]
+
+
+class OrDeposit(C.Structure):
+    _fields_ = [
+        ("step", C.c_int64),
+        ("walker", C.c_int32),
+        ("ic", C.c_int32 * 3),
+        ("s", C.c_double * 3),
+        ("height", C.c_double),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile abp_oracle.c into oracle/_build/liboracle.so (gcc, -O2, OpenMP)."""
+    with _lock:
+        if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+            return _LIB_PATH
+        os.makedirs(_BUILD_DIR, exist_ok=True)
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True, capture_output=True, text=True)
+        os.replace(tmp, _LIB_PATH)
+        return _LIB_PATH
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = build()
+        L = C.CDLL(path)
+        dp, ip = C.POINTER(C.c_double), C.POINTER(C.c_int)
+        L.or_cv_eval.argtypes = [C.POINTER(OrCv), C.c_int, dp, dp, dp]
+        L.or_cv_eval.restype = C.c_int
+        L.or_switch.argtypes = [C.c_double, C.c_int, C.c_int, dp]
+        L.or_switch.restype = C.c_double
+        L.or_interp.argtypes = [C.POINTER(OrGrid), dp, dp, dp, dp]
+        L.or_interp.restype = C.c_int
+        L.or_height.argtypes = [C.POINTER(OrHill), C.c_double]
+        L.or_height.restype = C.c_double
+        L.or_deposit_hill.argtypes = [C.POINTER(OrGrid), C.POINTER(OrHill), dp, dp, C.c_double, ip]
+        L.or_deposit_hill.restype = None
+        L.or_grid_nodes.argtypes = [C.POINTER(OrGrid)]
+        L.or_grid_nodes.restype = C.c_long
+        L.or_stencil_halfwidth.argtypes = [C.POINTER(OrGrid), C.POINTER(OrHill), C.c_int]
+        L.or_stencil_halfwidth.restype = C.c_int
+        L.or_check.argtypes = [C.POINTER(OrGrid), C.POINTER(OrHill)]
+        L.or_check.restype = C.c_int
+        L.or_batch_step.argtypes = [
+            C.c_int, C.POINTER(OrWalker), C.POINTER(dp), C.POINTER(dp), C.c_int64,
+            dp, dp, dp, C.POINTER(dp), ip, C.POINTER(OrDeposit),
+        ]
+        L.or_batch_step.restype = C.c_int
+        L.or_run.argtypes = [
+            C.c_int, C.POINTER(OrWalker), C.POINTER(dp), dp, C.POINTER(C.c_int64), C.c_int64,
+            C.c_int64, C.c_int64, dp, dp, dp, dp, ip, C.POINTER(OrDeposit), C.c_int64,
+            C.POINTER(C.c_int64),
+        ]
+        L.or_run.restype = C.c_int
+        L.or_langevin_double_well.argtypes = [
+            C.POINTER(OrWalker), dp, dp, C.c_int64, C.c_double, C.c_double, C.c_double, dp, dp,
+        ]
+        L.or_langevin_double_well.restype = C.c_int
+        L.or_num_threads.argtypes = []
+        L.or_num_threads.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def num_threads() -> int:
+    return int(lib().or_num_threads())
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _iptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+class Walker:
+    """Oracle view of one walker spec (keeps the arrays its struct points at)."""
+
+    def __init__(self, spec: dict):
+        self.spec = spec
+        self._keep = []
+        s = OrWalker()
+        g, hl = spec["grid"], spec["hill"]
+        d = len(g["n"])
+        s.g.d = d
+        for k in range(d):
+            s.g.n[k] = int(g["n"][k])
+            s.g.periodic[k] = int(bool(g["periodic"][k]))
+            s.g.lo[k] = float(g["lo"][k])
+            s.g.hi[k] = float(g["hi"][k])
+        s.hill.w = float(hl["w"])
+        for k in range(d):
+            s.hill.sigma[k] = float(hl["sigma"][k])
+        s.hill.cutoff = float(hl["cutoff"])
+        s.hill.gamma = float(hl["gamma"])
+        s.hill.kT = float(hl["kT"])
+        s.hill.stride = int(hl["stride"])
+        cvs = spec["cvs"]
+        if len(cvs) != d:
+            raise ValueError("one CV per grid axis")
+        for k, cv in enumerate(cvs):
+            c = s.cv[k]
+            c.type = CV_TYPES[cv["type"]]
+            a = np.ascontiguousarray(cv["a"], dtype=np.int32)
+            b = np.ascontiguousarray(cv.get("b", np.zeros(0)), dtype=np.int32)
+            self._keep += [a, b]
+            c.na, c.nb = len(a), len(b)
+            c.ia, c.ib = _iptr(a), _iptr(b)
+            for key, field in (("ma", "ma"), ("mb", "mb")):
+                m = cv.get(key)
+                if m is not None:
+                    m = np.ascontiguousarray(m, dtype=np.float64)
+                    self._keep.append(m)
+                    setattr(c, field, _dptr(m))
+            c.r0 = float(cv.get("r0", 0.4))
+            c.nn = int(cv.get("n", 6))
+            c.mm = int(cv.get("m", 12))
+            c.pbc = int(bool(cv.get("pbc", False)))
+            box = cv.get("box", (0.0, 0.0, 0.0))
+            for q in range(3):
+                c.box[q] = float(box[q])
+        s.natoms = int(spec["natoms"])
+        self.struct = s
+        self.d = d
+        self.nodes = int(np.prod(g["n"]))
+        rc = lib().or_check(C.byref(s.g), C.byref(s.hill))
+        if rc:
+            raise ValueError(f"oracle rejects walker spec (code {rc})")
+
+    def new_field(self) -> np.ndarray:
+        """Zeroed grid: [nodes][1+d], axis 0 fastest."""
+        return np.zeros((self.nodes, 1 + self.d), dtype=np.float64)
+
+    def halfwidth(self, k: int) -> int:
+        return int(lib().or_stencil_halfwidth(C.byref(self.struct.g), C.byref(self.struct.hill), k))
+
+
+# ---------------------------------------------------------------- low level
+
+
+def cv_eval(walker: Walker, k: int, x: np.ndarray):
+    """CV k of the walker at coordinates x (natoms, 3). Returns (s, J, flags)."""
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+    J = np.zeros_like(x)
+    s = C.c_double()
+    fl = lib().or_cv_eval(C.byref(walker.struct.cv[k]), walker.struct.natoms, _dptr(x), C.byref(s), _dptr(J))
+    return s.value, J, fl
+
+
+def switch(x: float, n: int = 6, m: int = 12):
+    d = C.c_double()
+    v = lib().or_switch(float(x), int(n), int(m), C.byref(d))
+    return v, d.value
+
+
+def interp(walker: Walker, field: np.ndarray, s):
+    s3 = np.zeros(3)
+    s3[: walker.d] = s
+    V = C.c_double()
+    dV = np.zeros(3)
+    fl = lib().or_interp(C.byref(walker.struct.g), _dptr(field), _dptr(s3), C.byref(V), _dptr(dV))
+    return V.value, dV[: walker.d].copy(), fl
+
+
+def height(walker: Walker, Vb: float) -> float:
+    return float(lib().or_height(C.byref(walker.struct.hill), float(Vb)))
+
+
+def deposit(walker: Walker, field: np.ndarray, s, h: float):
+    """Deposit one hill of height h at s into field (in place). Returns i_c."""
+    assert field.dtype == np.float64 and field.flags.c_contiguous
+    s3 = np.zeros(3)
+    s3[: walker.d] = s
+    ic = np.zeros(3, dtype=np.int32)
+    lib().or_deposit_hill(C.byref(walker.struct.g), C.byref(walker.struct.hill), _dptr(field), _dptr(s3), float(h), _iptr(ic))
+    return ic[: walker.d].copy()
+
+
+# ---------------------------------------------------------------- replay
+
+
+def run(walkers, frames, atom_offsets, step0: int, T: int, fields=None, record_forces=True,
+        dep_cap: int | None = None):
+    """Open-loop replay of T steps (step0 .. step0+T-1) for a batch of walkers.
+
+    walkers: list of Walker. frames: float array [T, total_atoms, 3] (any
+    float dtype; upcast to float64 exactly). atom_offsets[w]: index of walker
+    w's first atom in a frame. fields: list of per-walker grids (float64
+    [nodes, 1+d]); walkers given the same array object share that grid. New
+    zeroed grids are made when fields is None. Returns a dict with s, V, dV
+    ([T, nw, 3] / [T, nw]), F ([T, total_atoms, 3] or None), flags, the deposit
+    log and the final fields.
+    """
+    nw = len(walkers)
+    frames = np.ascontiguousarray(frames, dtype=np.float64)
+    assert frames.ndim == 3 and frames.shape[0] == T and frames.shape[2] == 3
+    total = frames.shape[1]
+    if fields is None:
+        fields = [w.new_field() for w in walkers]
+    for f in fields:
+        assert f.dtype == np.float64 and f.flags.c_contiguous
+    arr = (OrWalker * nw)(*[w.struct for w in walkers])
+    fptrs = (C.POINTER(C.c_double) * nw)(*[_dptr(f) for f in fields])
+    offs = np.ascontiguousarray(np.asarray(atom_offsets, dtype=np.int64) * 3)
+    s = np.zeros((T, nw, 3))
+    V = np.zeros((T, nw))
+    dV = np.zeros((T, nw, 3))
+    F = np.zeros((T, total, 3)) if record_forces else None
+    flags = np.zeros((T, nw), dtype=np.int32)
+    if dep_cap is None:
+        dep_cap = sum(T // w.struct.hill.stride + 1 for w in walkers)
+    deps = (OrDeposit * max(dep_cap, 1))()
+    nd = C.c_int64()
+    rc = lib().or_run(
+        nw, arr, fptrs, _dptr(frames), offs.ctypes.data_as(C.POINTER(C.c_int64)), total * 3, int(step0), int(T),
+        _dptr(s), _dptr(V), _dptr(dV), _dptr(F) if F is not None else None, _iptr(flags), deps, dep_cap, C.byref(nd),
+    )
+    if rc:
+        raise RuntimeError(f"oracle run failed ({rc})")
+    n = min(nd.value, dep_cap)
+    log = {
+        "step": np.array([deps[i].step for i in range(n)], dtype=np.int64),
+        "walker": np.array([deps[i].walker for i in range(n)], dtype=np.int32),
+        "ic": np.array([list(deps[i].ic) for i in range(n)], dtype=np.int32).reshape(n, 3),
+        "s": np.array([list(deps[i].s) for i in range(n)]).reshape(n, 3),
+        "height": np.array([deps[i].height for i in range(n)]),
+    }
+    return {"s": s, "V": V, "dV": dV, "F": F, "flags": flags, "deposits": log, "fields": fields}
+
+
+def langevin_double_well(walker: Walker, field: np.ndarray, x0: np.ndarray, T: int, dt: float, mu: float,
+                         kw: float, noise: np.ndarray):
+    """Closed-loop overdamped Langevin on U(s) = kw (s^2-1)^2 plus the bias.
+
+    noise: [T, natoms, 3] standard normals. Returns (final x, s history)."""
+    x = np.ascontiguousarray(x0, dtype=np.float64).copy()
+    noise = np.ascontiguousarray(noise, dtype=np.float64)
+    assert noise.shape == (T, walker.struct.natoms, 3)
+    s_hist = np.zeros(T)
+    rc = lib().or_langevin_double_well(C.byref(walker.struct), _dptr(field), _dptr(x), int(T), float(dt), float(mu),
+                                       float(kw), _dptr(noise), _dptr(s_hist))
+    if rc:
+        raise RuntimeError(f"oracle langevin failed ({rc})")
+    return x, s_hist
