@@ -1,0 +1,237 @@
+/*
+ * abp.h -- C ABI of the GB300 adaptive-biasing-potential (ABP) force call.
+ *
+ * The library implements, on one GPU, the per-MD-step bias routine of
+ * Dickson et al., "A fast, open source implementation of adaptive biasing
+ * potentials ..." (arXiv:1609.09833): it receives only the coordinates of
+ * the atoms that enter the collective variables (CVs) and returns the bias
+ * force on those atoms, which the owner adds to its MD force (SI,
+ * "Minimization of Interprocess Communications"). Per walker and MD step:
+ *
+ *   a1  CVs s_k(x): centre-of-mass distance, dihedral, coordination number;
+ *   a2  on a deposit step (step % stride == 0) the well-tempered height
+ *       h = w exp(-V_b(s_t) / ((gamma-1) kT)) from the grid before the
+ *       deposit (one exponential per hill, "Timing of the implementation",
+ *       WTmetaD paragraph);
+ *   a3  deposit of h exp(-|xi - s_t|^2 / 2 sigma^2) and of its derivative
+ *       along each CV on the grid points of a cutoff box around s_t (value
+ *       and derivative fields as in Eq. (histos), updated as in Eq. (update)
+ *       over a neighbourhood of the trajectory as in Eq. (Cupdate));
+ *   a4  V_b(s_t) and dV_b/ds_k(s_t) by multilinear interpolation of the value
+ *       field and of each derivative field (the histogram look-up after
+ *       Eq. (ghill));
+ *   a5  F = - sum_k dV_b/ds_k ds_k/dx on every CV atom.
+ *
+ * Conventions (all calls):
+ *   - Every function returns abp_status: ABP_OK (0) or a negative error
+ *     code; abp_last_error() returns a thread-local message for the last
+ *     failure of the calling thread. No C++ exception, abort or exit crosses
+ *     this boundary.
+ *   - Pointers named *_dev are device pointers on the context's GPU; the
+ *     caller owns them and keeps them valid until the call's work has run on
+ *     the context stream. Descriptor structs and their host arrays are read
+ *     during the call only. Handles (abp_ctx, abp_grid, abp_walker) are owned
+ *     by the library and freed by the matching destroy call.
+ *   - Coordinates and forces are 4-component records per atom
+ *     (x, y, z, pad), float (ABP_F32) or double (ABP_F64), in nm and
+ *     kJ/mol/nm. Walker w's atom i at MD step t of a call is record
+ *     coord_offsets_dev[w] + t * coord_step_stride + i.
+ *   - Compute calls are asynchronous on the context stream; readouts and
+ *     abp_sync wait for it.
+ *   - Units: nm, kJ/mol, rad.
+ */
+#ifndef ABP_H
+#define ABP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int abp_status;
+
+#define ABP_OK 0
+#define ABP_ERR_INVALID_ARG (-1)  /* a bad pointer, size, descriptor or mix of walkers */
+#define ABP_ERR_CUDA (-2)         /* a CUDA runtime call failed (message says which) */
+#define ABP_ERR_OOM (-3)          /* device allocation failed */
+#define ABP_ERR_ADMISSION (-4)    /* the allocation would exceed the context's HBM budget */
+#define ABP_ERR_NONFINITE (-5)    /* non-finite coordinates were seen; those walkers were left unchanged */
+#define ABP_ERR_TIMEOUT (-6)      /* a bounded device or host wait ran out */
+#define ABP_ERR_UNSUPPORTED (-7)  /* a combination this build does not implement */
+
+/* CV types (step a1). */
+#define ABP_CV_COM_DIST 0 /* |R_B - R_A|, R_G the mass-weighted centre of group G */
+#define ABP_CV_DIHEDRAL 1 /* IUPAC dihedral of idx_a[0..3], in [-pi, pi] */
+#define ABP_CV_COORD 2    /* sum over A x B of (1 - (r/r0)^n) / (1 - (r/r0)^m); n = 6, m = 12 */
+
+/* Grid precision. */
+#define ABP_PREC_FP32_COMP 0 /* FP32 fields with a two-sum compensation term per field */
+#define ABP_PREC_FP64 1      /* FP64 fields (and FP64 CV arithmetic, FP64 coordinates) */
+
+/* Element types for coordinate, force and readout buffers. */
+#define ABP_F32 0
+#define ABP_F64 1
+
+/* Force delivery modes. */
+#define ABP_FORCES_ACCUMULATE 0 /* forces[i] += bias force (the owner's MD force array) */
+#define ABP_FORCES_OVERWRITE 1  /* forces[i]  = bias force */
+
+/* Walker flags reported by abp_walker_readout. */
+#define ABP_WFLAG_DEPOSIT 1   /* this step deposited a hill */
+#define ABP_WFLAG_OOR 2       /* a CV was outside a non-periodic grid range (clamped) */
+#define ABP_WFLAG_SINGULAR 4  /* a CV Jacobian was undefined; its gradient was set to 0 */
+#define ABP_WFLAG_NONFINITE 8 /* non-finite coordinates: step skipped, state unchanged */
+
+typedef struct abp_ctx abp_ctx;
+typedef struct abp_grid abp_grid;
+typedef struct abp_walker abp_walker;
+
+/* Grid over ncv = 1..3 CVs. Nodes: non-periodic axis xi_i = lo + i D,
+ * D = (hi - lo) / (n - 1), i = 0..n-1; periodic axis D = (hi - lo) / n with
+ * wrap-around. Fields per node: V and dV/dxi_k for k < ncv. Node index
+ * i0 + n0 (i1 + n1 i2) (axis 0 fastest). */
+typedef struct {
+  int ncv;
+  int n[3];
+  int periodic[3];
+  double lo[3];
+  double hi[3];
+  int precision; /* ABP_PREC_* */
+} abp_grid_desc;
+
+/* One CV over the walker's own block of natoms atoms. Index arrays are
+ * host arrays of atom indices in [0, natoms). */
+typedef struct {
+  int type;              /* ABP_CV_* */
+  int n_a, n_b;          /* COM: group sizes; DIHEDRAL: n_a = 4, n_b = 0; COORD: |A|, |B| */
+  const int32_t *idx_a;  /* COM group A, the 4 dihedral atoms, or CN group A */
+  const int32_t *idx_b;  /* COM group B or CN group B (NULL when n_b = 0) */
+  const double *mass_a;  /* COM masses (NULL = unit masses); ignored otherwise */
+  const double *mass_b;
+  double r0;             /* COORD switching radius (nm) */
+  int nn, mm;            /* COORD exponents; this build supports nn = 6, mm = 12 */
+  int pbc;               /* minimum image on difference vectors (orthorhombic box) */
+  double box[3];
+} abp_cv_desc;
+
+/* A walker: its atoms, one CV per grid axis and its well-tempered hills. */
+typedef struct {
+  int natoms;
+  abp_cv_desc cv[3];     /* cv[k] drives grid axis k; the grid's ncv are used */
+  double w;              /* initial hill height (kJ/mol) */
+  double sigma[3];       /* Gaussian width per CV */
+  double cutoff;         /* half-width R_k = ceil(cutoff sigma_k / D_k) of the stencil box, in sigma */
+  double gamma;          /* bias factor (> 1) */
+  double kT;             /* thermal energy (kJ/mol) */
+  int64_t stride;        /* deposit when step % stride == 0 */
+} abp_walker_desc;
+
+/* One deposited hill (the deposit log). */
+typedef struct {
+  int64_t step;
+  int32_t walker_id;     /* abp_walker_id() of the walker */
+  int32_t ic[3];         /* centre node index per axis, floor(u + 1/2) wrapped on periodic axes */
+  double s[3];           /* s_t as computed on the device */
+  double height;         /* h (FP64) */
+} abp_deposit_rec;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Creates a context on `device`, issuing work on `cuda_stream` (a
+ * cudaStream_t; NULL = the legacy default stream). hbm_budget_bytes caps the
+ * bytes the context may allocate for grids and walkers (0 = no cap): an
+ * allocation beyond it fails with ABP_ERR_ADMISSION. */
+abp_status abp_ctx_create(abp_ctx **out, int device, void *cuda_stream, size_t hbm_budget_bytes);
+abp_status abp_ctx_set_stream(abp_ctx *ctx, void *cuda_stream);
+/* Bytes currently allocated against the budget. */
+abp_status abp_ctx_bytes(const abp_ctx *ctx, size_t *used, size_t *budget);
+void abp_ctx_destroy(abp_ctx *ctx);
+
+/* ---- grids and walkers ---------------------------------------------------- */
+
+/* Allocates a zeroed bias grid (V = 0 everywhere, the paper's initial
+ * condition after Eq. (update)). Grid points must number >= 2 per axis. */
+abp_status abp_create_grid(abp_ctx *ctx, const abp_grid_desc *desc, abp_grid **out);
+void abp_grid_destroy(abp_grid *grid);
+/* Zeroes every field again. */
+abp_status abp_grid_clear(abp_ctx *ctx, abp_grid *grid);
+
+/* Creates a walker depositing into `grid` (several walkers may share one
+ * grid; see abp_step for the ordering). Rejects a periodic stencil box wider
+ * than its axis (2R+1 > n), indices outside [0, natoms), and unsupported CV
+ * parameters, with ABP_ERR_INVALID_ARG. */
+abp_status abp_walker_create(abp_ctx *ctx, abp_grid *grid, const abp_walker_desc *desc, abp_walker **out);
+void abp_walker_destroy(abp_walker *walker);
+int32_t abp_walker_id(const abp_walker *walker);
+
+/* ---- the force call --------------------------------------------------------- */
+
+/* One MD step `step` for n walkers (steps a1..a5). The bias force of each
+ * walker is kept in a library-owned buffer until abp_forces delivers it.
+ * coords_dev: 4-component records (dtype ABP_F32 for FP32_COMP grids,
+ * ABP_F64 for FP64 grids); coord_offsets_dev: n device int64 record offsets.
+ * All walkers of one call must have grids of the same precision. Walkers that
+ * share a grid take their heights from the grid before any deposit of the
+ * step and read V_b after all of them, deposits being applied in list order
+ * (Jacobi order); walkers with their own grids are independent. */
+abp_status abp_step(abp_ctx *ctx, abp_walker *const *walkers, int n, const void *coords_dev, int coords_dtype,
+                    const int64_t *coord_offsets_dev, int64_t step);
+
+/* Delivers the forces of the last abp_step of each walker into forces_dev
+ * (records at force_offsets_dev[w] + i, dtype as coords), by mode. */
+abp_status abp_forces(abp_ctx *ctx, abp_walker *const *walkers, int n, void *forces_dev, int forces_dtype,
+                      const int64_t *force_offsets_dev, int mode);
+
+/* The fused batched form: nsteps consecutive MD steps step0..step0+nsteps-1
+ * of n walkers with their own grids in one launch, equal per step and walker
+ * to abp_step followed by abp_forces. Coordinates of step t at record
+ * coord_offsets_dev[w] + t * coord_step_stride + i; forces written (by mode)
+ * at force_offsets_dev[w] + t * force_step_stride + i. Walkers that share a
+ * grid are rejected (use abp_step). */
+abp_status abp_run(abp_ctx *ctx, abp_walker *const *walkers, int n, const void *coords_dev, int coords_dtype,
+                   const int64_t *coord_offsets_dev, int64_t coord_step_stride, void *forces_dev,
+                   const int64_t *force_offsets_dev, int64_t force_step_stride, int mode, int64_t step0, int nsteps);
+
+/* The plain one-walker-per-launch form of abp_step + abp_forces: for every
+ * walker, separate CV, deposit and interpolation/force kernel launches from a
+ * host loop (the comparison point for the batched form). Same arguments and
+ * results as one step of abp_run. */
+abp_status abp_step_plain(abp_ctx *ctx, abp_walker *const *walkers, int n, const void *coords_dev,
+                          int coords_dtype, const int64_t *coord_offsets_dev, void *forces_dev,
+                          const int64_t *force_offsets_dev, int mode, int64_t step);
+
+/* ---- readouts ------------------------------------------------------------ */
+
+/* Copies the grid's fields, [nodes][1 + ncv] (V then dV/dxi_k), to dst as
+ * ABP_F32 or ABP_F64 (FP32_COMP grids return sum + compensation). Syncs. */
+abp_status abp_bias_readout(abp_ctx *ctx, const abp_grid *grid, void *dst, int dst_is_device, int dtype);
+/* Replaces the grid's fields by src ([nodes][1 + ncv], ABP_F32 or ABP_F64);
+ * an FP64 source is split exactly into value + compensation on FP32_COMP
+ * grids. Syncs. */
+abp_status abp_bias_upload(abp_ctx *ctx, abp_grid *grid, const void *src, int src_is_device, int dtype);
+/* s_t[3], V_b(s_t), dV_b/ds[3] and flags of the walker's last step. Syncs.
+ * Returns ABP_ERR_NONFINITE if that step saw non-finite coordinates. */
+abp_status abp_walker_readout(abp_ctx *ctx, const abp_walker *walker, double *s, double *V, double *dV,
+                              int *flags);
+
+/* Deposit log: when enabled with a capacity, every deposit appends one
+ * abp_deposit_rec (records beyond the capacity are counted, not stored).
+ * Readout syncs and returns the stored records in device order per call. */
+abp_status abp_deposit_log_enable(abp_ctx *ctx, size_t capacity);
+abp_status abp_deposit_log_readout(abp_ctx *ctx, abp_deposit_rec *dst, size_t cap, size_t *n_out,
+                                   size_t *n_total);
+abp_status abp_deposit_log_clear(abp_ctx *ctx);
+
+/* Waits for the context stream; returns ABP_ERR_NONFINITE if any walker
+ * stepped since the last sync saw non-finite coordinates. */
+abp_status abp_sync(abp_ctx *ctx);
+const char *abp_last_error(void);
+/* Library version string. */
+const char *abp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ABP_H */

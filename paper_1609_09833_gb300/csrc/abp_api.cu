@@ -1,0 +1,819 @@
+// abp_api.cu -- host implementation of the C ABI declared in include/abp.h.
+// Owns every device allocation (grids, walker descriptors, force buffers,
+// deposit log), validates arguments, and launches the kernels of
+// abp_kernels.cu on the context stream. No exception leaves this file.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "abp.h"
+#include "abp_internal.cuh"
+#include "abp_launch.h"
+
+using namespace abp;
+
+namespace {
+
+thread_local std::string g_err;
+
+abp_status fail(abp_status code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CUDA_TRY(call)                                                                       \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess) return fail(ABP_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+struct TableCache {
+  std::vector<TableEntry> key;
+  TableEntry *dev = nullptr;
+  size_t cap = 0;
+  unsigned long long last_use = 0;
+};
+
+}  // namespace
+
+struct abp_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  size_t budget = 0;
+  size_t used = 0;
+  DevCounters *ctr = nullptr;
+  DepositLog log{nullptr, nullptr, 0};
+  TableCache tables[4];
+  unsigned long long use_clock = 0;
+  int next_id = 0;
+  std::mutex mu;
+};
+
+struct abp_grid {
+  abp_ctx *ctx = nullptr;
+  GridDev g{};
+  abp_grid_desc desc{};
+  size_t bytes = 0;
+};
+
+struct abp_walker {
+  abp_ctx *ctx = nullptr;
+  abp_grid *grid = nullptr;
+  WalkerDev hd{};
+  WalkerDev *dd = nullptr;
+  std::vector<std::pair<void *, size_t>> allocs;
+  bool has_cn = false;
+  long long cost = 0;  // rough work estimate used to order batched launches
+};
+
+namespace {
+
+abp_status set_device(const abp_ctx *ctx) {
+  int cur = -1;
+  CUDA_TRY(cudaGetDevice(&cur));
+  if (cur != ctx->device) CUDA_TRY(cudaSetDevice(ctx->device));
+  return ABP_OK;
+}
+
+abp_status dev_alloc(abp_ctx *ctx, size_t bytes, void **out) {
+  *out = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (ctx->budget && ctx->used + bytes > ctx->budget)
+    return fail(ABP_ERR_ADMISSION, "allocation of %zu bytes exceeds the HBM budget (%zu of %zu used)", bytes,
+                ctx->used, ctx->budget);
+  cudaError_t e = cudaMalloc(out, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *out = nullptr;
+    return fail(ABP_ERR_OOM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+  }
+  ctx->used += bytes;
+  return ABP_OK;
+}
+
+void dev_free(abp_ctx *ctx, void *p, size_t bytes) {
+  if (!p) return;
+  cudaFree(p);
+  if (bytes == 0) bytes = 16;
+  ctx->used -= std::min(ctx->used, bytes);
+}
+
+int rec_bytes(int prec, int d) {
+  (void)prec;
+  return d == 1 ? 16 : 32;
+}
+
+double spacing(const abp_grid_desc &d, int k) {
+  return d.periodic[k] ? (d.hi[k] - d.lo[k]) / d.n[k] : (d.hi[k] - d.lo[k]) / (d.n[k] - 1);
+}
+
+int walker_fp64(const abp_walker *w) { return w->grid->desc.precision == ABP_PREC_FP64; }
+
+int dyn_bytes(const abp_walker *w, int nwarps) {
+  return group_dyn_bytes(w->hd.natoms, w->hd.cv, w->hd.g.d, nwarps, walker_fp64(w) ? 32 : 16);
+}
+
+// Common validation of a walker list. Returns the precision (0/1) via *fp64.
+abp_status check_list(abp_ctx *ctx, abp_walker *const *walkers, int n, int *fp64, bool *shared) {
+  if (n < 0) return fail(ABP_ERR_INVALID_ARG, "negative walker count");
+  if (n > 0 && !walkers) return fail(ABP_ERR_INVALID_ARG, "walker list is NULL");
+  int prec = -1;
+  std::set<const abp_grid *> grids;
+  *shared = false;
+  for (int i = 0; i < n; ++i) {
+    const abp_walker *w = walkers[i];
+    if (!w) return fail(ABP_ERR_INVALID_ARG, "walker %d is NULL", i);
+    if (w->ctx != ctx) return fail(ABP_ERR_INVALID_ARG, "walker %d belongs to another context", i);
+    int p = walker_fp64(w);
+    if (prec >= 0 && p != prec) return fail(ABP_ERR_INVALID_ARG, "walkers of one call must share a grid precision");
+    prec = p;
+    if (!grids.insert(w->grid).second) *shared = true;
+  }
+  *fp64 = prec < 0 ? 0 : prec;
+  return ABP_OK;
+}
+
+// Device table for a walker list (cached: a small LRU of recent lists).
+abp_status get_table(abp_ctx *ctx, abp_walker *const *walkers, int n, bool sort_by_cost, const TableEntry **out) {
+  std::vector<TableEntry> key(n);
+  for (int i = 0; i < n; ++i) key[i] = TableEntry{walkers[i]->dd, i, 0};
+  if (sort_by_cost) {
+    std::vector<long long> cost(n);
+    for (int i = 0; i < n; ++i) cost[i] = walkers[i]->cost;
+    std::stable_sort(key.begin(), key.end(),
+                     [&](const TableEntry &a, const TableEntry &b) { return cost[a.idx] > cost[b.idx]; });
+  }
+  ++ctx->use_clock;
+  TableCache *victim = &ctx->tables[0];
+  for (auto &t : ctx->tables) {
+    if (t.dev && t.key.size() == key.size() &&
+        std::memcmp(t.key.data(), key.data(), key.size() * sizeof(TableEntry)) == 0) {
+      t.last_use = ctx->use_clock;
+      *out = t.dev;
+      return ABP_OK;
+    }
+    if (t.last_use < victim->last_use) victim = &t;
+  }
+  size_t need = std::max<size_t>(1, key.size()) * sizeof(TableEntry);
+  if (victim->cap < need) {
+    if (victim->dev) cudaFree(victim->dev);
+    victim->dev = nullptr;
+    victim->cap = 0;
+    CUDA_TRY(cudaMalloc(&victim->dev, need));
+    victim->cap = need;
+  }
+  // pageable source: the runtime stages it before returning, so `key` may die
+  CUDA_TRY(cudaMemcpyAsync(victim->dev, key.data(), key.size() * sizeof(TableEntry), cudaMemcpyHostToDevice,
+                           ctx->stream));
+  victim->key = std::move(key);
+  victim->last_use = ctx->use_clock;
+  *out = victim->dev;
+  return ABP_OK;
+}
+
+// Launch shape for a batch: a group of G threads per walker, several
+// groups per CTA, as shared memory allows.
+abp_status pick_shape(abp_walker *const *walkers, int n, int fp64, int *G, int *gpc, int *group_bytes) {
+  bool cn = false;
+  for (int i = 0; i < n; ++i) cn = cn || walkers[i]->has_cn;
+  int g = cn ? 128 : 32;
+  int fixed = group_fixed_bytes(fp64);
+  int dyn = 0;
+  for (int i = 0; i < n; ++i) dyn = std::max(dyn, dyn_bytes(walkers[i], g / 32));
+  int gb = (fixed + dyn + 31) & ~31;
+  const int smem_max = 227 * 1024;
+  if (gb > smem_max) return fail(ABP_ERR_UNSUPPORTED, "a walker needs %d bytes of shared memory (max %d)", gb, smem_max);
+  int per = cn ? 2 : 4;
+  while (per > 1 && per * gb > 100 * 1024) --per;
+  *G = g;
+  *gpc = per;
+  *group_bytes = gb;
+  return ABP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *abp_last_error(void) { return g_err.c_str(); }
+const char *abp_version(void) { return "abp-gb300 0.1 (sm_103a)"; }
+
+abp_status abp_ctx_create(abp_ctx **out, int device, void *cuda_stream, size_t hbm_budget_bytes) {
+  if (!out) return fail(ABP_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  int ndev = 0;
+  CUDA_TRY(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return fail(ABP_ERR_INVALID_ARG, "device %d out of range (%d devices)", device, ndev);
+  abp_ctx *c = new (std::nothrow) abp_ctx();
+  if (!c) return fail(ABP_ERR_OOM, "host allocation failed");
+  c->device = device;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  c->budget = hbm_budget_bytes;
+  abp_status st = set_device(c);
+  if (st == ABP_OK) {
+    cudaError_t e = cudaMalloc(&c->ctr, sizeof(DevCounters));
+    if (e == cudaSuccess) e = cudaMemset(c->ctr, 0, sizeof(DevCounters));
+    if (e != cudaSuccess) st = fail(ABP_ERR_CUDA, "counter allocation: %s", cudaGetErrorString(e));
+  }
+  if (st != ABP_OK) {
+    if (c->ctr) cudaFree(c->ctr);
+    delete c;
+    return st;
+  }
+  *out = c;
+  return ABP_OK;
+}
+
+abp_status abp_ctx_set_stream(abp_ctx *ctx, void *cuda_stream) {
+  if (!ctx) return fail(ABP_ERR_INVALID_ARG, "ctx is NULL");
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  return ABP_OK;
+}
+
+abp_status abp_ctx_bytes(const abp_ctx *ctx, size_t *used, size_t *budget) {
+  if (!ctx) return fail(ABP_ERR_INVALID_ARG, "ctx is NULL");
+  if (used) *used = ctx->used;
+  if (budget) *budget = ctx->budget;
+  return ABP_OK;
+}
+
+void abp_ctx_destroy(abp_ctx *ctx) {
+  if (!ctx) return;
+  set_device(ctx);
+  cudaStreamSynchronize(ctx->stream);
+  for (auto &t : ctx->tables)
+    if (t.dev) cudaFree(t.dev);
+  if (ctx->log.rec) cudaFree(ctx->log.rec);
+  if (ctx->log.count) cudaFree(ctx->log.count);
+  if (ctx->ctr) cudaFree(ctx->ctr);
+  delete ctx;
+}
+
+// ---------------------------------------------------------------- grids
+
+abp_status abp_create_grid(abp_ctx *ctx, const abp_grid_desc *d, abp_grid **out) {
+  if (!ctx || !d || !out) return fail(ABP_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  if (d->ncv < 1 || d->ncv > 3) return fail(ABP_ERR_INVALID_ARG, "ncv must be 1..3 (got %d)", d->ncv);
+  if (d->precision != ABP_PREC_FP32_COMP && d->precision != ABP_PREC_FP64)
+    return fail(ABP_ERR_INVALID_ARG, "unknown precision %d", d->precision);
+  long long nodes = 1;
+  for (int k = 0; k < d->ncv; ++k) {
+    if (d->n[k] < 2) return fail(ABP_ERR_INVALID_ARG, "axis %d needs >= 2 grid points", k);
+    if (!(d->hi[k] > d->lo[k]) || !std::isfinite(d->lo[k]) || !std::isfinite(d->hi[k]))
+      return fail(ABP_ERR_INVALID_ARG, "axis %d needs finite lo < hi", k);
+    nodes *= d->n[k];
+    if (nodes > (1ll << 34)) return fail(ABP_ERR_INVALID_ARG, "grid too large");
+  }
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  abp_status st = set_device(ctx);
+  if (st) return st;
+  abp_grid *g = new (std::nothrow) abp_grid();
+  if (!g) return fail(ABP_ERR_OOM, "host allocation failed");
+  g->ctx = ctx;
+  g->desc = *d;
+  GridDev &gd = g->g;
+  gd.d = d->ncv;
+  for (int k = 0; k < 3; ++k) {
+    bool on = k < d->ncv;
+    gd.n[k] = on ? d->n[k] : 1;
+    gd.periodic[k] = on ? (d->periodic[k] != 0) : 0;
+    gd.lo[k] = on ? d->lo[k] : 0.0;
+    gd.D[k] = on ? spacing(*d, k) : 1.0;
+    gd.invD[k] = 1.0 / gd.D[k];
+    gd.L[k] = on ? d->hi[k] - d->lo[k] : 1.0;
+  }
+  gd.prec = d->precision;
+  gd.rec_bytes = rec_bytes(d->precision, d->ncv);
+  gd.nodes = nodes;
+  g->bytes = (size_t)nodes * gd.rec_bytes;
+  st = dev_alloc(ctx, g->bytes, &gd.rec);
+  if (st) {
+    delete g;
+    return st;
+  }
+  cudaError_t e = cudaMemsetAsync(gd.rec, 0, g->bytes, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) {
+    dev_free(ctx, gd.rec, g->bytes);
+    delete g;
+    return fail(ABP_ERR_CUDA, "grid clear: %s", cudaGetErrorString(e));
+  }
+  *out = g;
+  return ABP_OK;
+}
+
+void abp_grid_destroy(abp_grid *g) {
+  if (!g) return;
+  std::lock_guard<std::mutex> lk(g->ctx->mu);
+  set_device(g->ctx);
+  cudaStreamSynchronize(g->ctx->stream);
+  dev_free(g->ctx, g->g.rec, g->bytes);
+  delete g;
+}
+
+abp_status abp_grid_clear(abp_ctx *ctx, abp_grid *g) {
+  if (!ctx || !g || g->ctx != ctx) return fail(ABP_ERR_INVALID_ARG, "bad grid");
+  abp_status st = set_device(ctx);
+  if (st) return st;
+  CUDA_TRY(cudaMemsetAsync(g->g.rec, 0, g->bytes, ctx->stream));
+  return ABP_OK;
+}
+
+// ---------------------------------------------------------------- walkers
+
+namespace {
+
+abp_status walker_alloc(abp_walker *w, size_t bytes, void **p) {
+  abp_status st = dev_alloc(w->ctx, bytes, p);
+  if (st == ABP_OK) w->allocs.push_back({*p, bytes});
+  return st;
+}
+
+abp_status upload(abp_walker *w, const void *src, size_t bytes, void **dst) {
+  abp_status st = walker_alloc(w, bytes, dst);
+  if (st) return st;
+  if (bytes) CUDA_TRY(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
+  return ABP_OK;
+}
+
+void walker_free(abp_walker *w) {
+  for (auto &a : w->allocs) dev_free(w->ctx, a.first, a.second);
+  w->allocs.clear();
+}
+
+abp_status check_indices(const int32_t *idx, int n, int natoms, const char *what, int k) {
+  if (n > 0 && !idx) return fail(ABP_ERR_INVALID_ARG, "CV %d: %s index list is NULL", k, what);
+  std::vector<int32_t> v(idx, idx + n);
+  for (int i = 0; i < n; ++i)
+    if (v[i] < 0 || v[i] >= natoms)
+      return fail(ABP_ERR_INVALID_ARG, "CV %d: %s index %d out of range [0, %d)", k, what, v[i], natoms);
+  std::sort(v.begin(), v.end());
+  if (std::adjacent_find(v.begin(), v.end()) != v.end())
+    return fail(ABP_ERR_INVALID_ARG, "CV %d: %s index list has duplicates", k, what);
+  return ABP_OK;
+}
+
+abp_status build_cv(abp_walker *w, const abp_cv_desc &c, int k, int natoms, CvDev *out) {
+  CvDev cv{};
+  cv.type = c.type;
+  cv.na = c.n_a;
+  cv.nb = c.n_b;
+  abp_status st;
+  switch (c.type) {
+    case ABP_CV_COM_DIST:
+      if (c.n_a < 1 || c.n_b < 1) return fail(ABP_ERR_INVALID_ARG, "CV %d: COM groups must be non-empty", k);
+      break;
+    case ABP_CV_DIHEDRAL:
+      if (c.n_a != 4) return fail(ABP_ERR_INVALID_ARG, "CV %d: a dihedral needs 4 atoms", k);
+      cv.nb = 0;
+      break;
+    case ABP_CV_COORD:
+      if (c.n_a < 1 || c.n_b < 1) return fail(ABP_ERR_INVALID_ARG, "CV %d: CN groups must be non-empty", k);
+      if (c.nn != 6 || c.mm != 12)
+        return fail(ABP_ERR_UNSUPPORTED, "CV %d: only the n = 6, m = 12 switching function is built", k);
+      if (!(c.r0 > 0) || !std::isfinite(c.r0)) return fail(ABP_ERR_INVALID_ARG, "CV %d: r0 must be > 0", k);
+      cv.inv_r0sq = 1.0 / (c.r0 * c.r0);
+      break;
+    default:
+      return fail(ABP_ERR_INVALID_ARG, "CV %d: unknown type %d", k, c.type);
+  }
+  if ((st = check_indices(c.idx_a, cv.na, natoms, "A", k))) return st;
+  if ((st = check_indices(c.idx_b, cv.nb, natoms, "B", k))) return st;
+  cv.pbc = c.pbc != 0;
+  for (int q = 0; q < 3; ++q) {
+    if (cv.pbc && !(c.box[q] > 0)) return fail(ABP_ERR_INVALID_ARG, "CV %d: pbc needs box edges > 0", k);
+    cv.box[q] = cv.pbc ? c.box[q] : 0.0;
+    cv.inv_box[q] = cv.pbc ? 1.0 / c.box[q] : 0.0;
+  }
+  void *p;
+  if ((st = upload(w, c.idx_a, sizeof(int32_t) * cv.na, &p))) return st;
+  cv.ia = static_cast<const int32_t *>(p);
+  if ((st = upload(w, cv.nb ? c.idx_b : nullptr, sizeof(int32_t) * cv.nb, &p))) return st;
+  cv.ib = static_cast<const int32_t *>(p);
+  if (c.type == ABP_CV_COM_DIST) {
+    // weights m_i / M_group, computed once in FP64
+    for (int grp = 0; grp < 2; ++grp) {
+      int n = grp ? cv.nb : cv.na;
+      const double *m = grp ? c.mass_b : c.mass_a;
+      std::vector<double> wd(n);
+      double M = 0;
+      for (int i = 0; i < n; ++i) {
+        double mi = m ? m[i] : 1.0;
+        if (!(mi > 0) || !std::isfinite(mi)) return fail(ABP_ERR_INVALID_ARG, "CV %d: masses must be > 0", k);
+        wd[i] = mi;
+        M += mi;
+      }
+      std::vector<float> wf(n);
+      for (int i = 0; i < n; ++i) {
+        wd[i] = wd[i] / M;
+        wf[i] = (float)wd[i];
+      }
+      if ((st = upload(w, wf.data(), sizeof(float) * n, &p))) return st;
+      (grp ? cv.wb : cv.wa) = static_cast<const float *>(p);
+      if ((st = upload(w, wd.data(), sizeof(double) * n, &p))) return st;
+      (grp ? cv.wb64 : cv.wa64) = static_cast<const double *>(p);
+    }
+  }
+  *out = cv;
+  return ABP_OK;
+}
+
+}  // namespace
+
+abp_status abp_walker_create(abp_ctx *ctx, abp_grid *grid, const abp_walker_desc *d, abp_walker **out) {
+  if (!ctx || !grid || !d || !out) return fail(ABP_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  if (grid->ctx != ctx) return fail(ABP_ERR_INVALID_ARG, "grid belongs to another context");
+  if (d->natoms < 1) return fail(ABP_ERR_INVALID_ARG, "natoms must be >= 1");
+  if (!(d->gamma > 1) || !(d->kT > 0) || d->stride < 1 || !(d->w >= 0) || !std::isfinite(d->w) ||
+      !std::isfinite(d->gamma) || !std::isfinite(d->kT) || !(d->cutoff > 0))
+    return fail(ABP_ERR_INVALID_ARG, "need gamma > 1, kT > 0, w >= 0, cutoff > 0, stride >= 1");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  abp_status st = set_device(ctx);
+  if (st) return st;
+  abp_walker *w = new (std::nothrow) abp_walker();
+  if (!w) return fail(ABP_ERR_OOM, "host allocation failed");
+  w->ctx = ctx;
+  w->grid = grid;
+  WalkerDev &hd = w->hd;
+  hd.g = grid->g;
+  hd.natoms = d->natoms;
+  const int ncv = grid->desc.ncv;
+  const int fp64 = grid->desc.precision == ABP_PREC_FP64;
+  long long stencil = 1;
+  for (int k = 0; k < ncv; ++k) {
+    double sig = d->sigma[k];
+    if (!(sig > 0) || !std::isfinite(sig)) {
+      delete w;
+      return fail(ABP_ERR_INVALID_ARG, "sigma[%d] must be > 0", k);
+    }
+    double D = spacing(grid->desc, k);
+    double Rd = std::ceil(d->cutoff * sig / D);
+    if (Rd > kRMax) {
+      delete w;
+      return fail(ABP_ERR_UNSUPPORTED, "stencil half-width %g on axis %d exceeds %d nodes", Rd, k, kRMax);
+    }
+    hd.R[k] = (int)Rd;
+    if (grid->desc.periodic[k] && 2 * hd.R[k] + 1 > grid->desc.n[k]) {
+      delete w;
+      return fail(ABP_ERR_INVALID_ARG, "periodic axis %d: stencil box (%d nodes) wider than the axis", k,
+                  2 * hd.R[k] + 1);
+    }
+    hd.sigma[k] = sig;
+    hd.inv2s2[k] = 1.0 / (2.0 * sig * sig);
+    hd.invs2[k] = 1.0 / (sig * sig);
+    stencil *= 2 * hd.R[k] + 1;
+  }
+  hd.w = d->w;
+  hd.inv_dT = 1.0 / ((d->gamma - 1.0) * d->kT);
+  hd.stride = d->stride;
+  for (int k = 0; k < ncv; ++k) {
+    st = build_cv(w, d->cv[k], k, d->natoms, &hd.cv[k]);
+    if (st) {
+      walker_free(w);
+      delete w;
+      return st;
+    }
+    if (d->cv[k].type == ABP_CV_COORD) w->has_cn = true;
+  }
+  int rsz = fp64 ? 32 : 16;
+  void *p;
+  if ((st = walker_alloc(w, (size_t)rsz * d->natoms, &p)) == ABP_OK) {
+    hd.fbuf = p;
+    CUDA_TRY(cudaMemset(p, 0, (size_t)rsz * d->natoms));
+    if ((st = walker_alloc(w, plain_scratch_bytes(fp64, hd.cv, ncv), &p)) == ABP_OK) {
+      hd.jscratch = p;
+      if ((st = walker_alloc(w, sizeof(WalkerState), &p)) == ABP_OK) {
+        hd.state = static_cast<WalkerState *>(p);
+        CUDA_TRY(cudaMemset(p, 0, sizeof(WalkerState)));
+      }
+    }
+  }
+  if (st == ABP_OK) {
+    int need = (group_fixed_bytes(fp64) + dyn_bytes(w, 1) + 31) & ~31;
+    if (need > 227 * 1024) st = fail(ABP_ERR_UNSUPPORTED, "walker of %d atoms needs %d bytes of shared memory", d->natoms, need);
+  }
+  if (st == ABP_OK) {
+    hd.id = ctx->next_id++;
+    if ((st = walker_alloc(w, sizeof(WalkerDev), &p)) == ABP_OK) {
+      w->dd = static_cast<WalkerDev *>(p);
+      CUDA_TRY(cudaMemcpy(w->dd, &hd, sizeof(WalkerDev), cudaMemcpyHostToDevice));
+    }
+  }
+  if (st) {
+    walker_free(w);
+    delete w;
+    return st;
+  }
+  long long pairs = 0;
+  for (int k = 0; k < ncv; ++k)
+    if (hd.cv[k].type == ABP_CV_COORD) pairs += (long long)hd.cv[k].na * hd.cv[k].nb;
+  w->cost = pairs * 4 + d->natoms * 8 + stencil * 4 / d->stride;
+  *out = w;
+  return ABP_OK;
+}
+
+void abp_walker_destroy(abp_walker *w) {
+  if (!w) return;
+  std::lock_guard<std::mutex> lk(w->ctx->mu);
+  set_device(w->ctx);
+  cudaStreamSynchronize(w->ctx->stream);
+  walker_free(w);
+  delete w;
+}
+
+int32_t abp_walker_id(const abp_walker *w) { return w ? w->hd.id : -1; }
+
+// ---------------------------------------------------------------- the force call
+
+static abp_status run_common(abp_ctx *ctx, abp_walker *const *walkers, int n, const void *coords, int cdt,
+                             const int64_t *coff, int64_t cstride, void *forces, const int64_t *foff,
+                             int64_t fstride, int mode, int64_t step0, int nsteps, bool allow_shared_check) {
+  int fp64;
+  bool shared;
+  abp_status st = check_list(ctx, walkers, n, &fp64, &shared);
+  if (st) return st;
+  if (shared && allow_shared_check)
+    return fail(ABP_ERR_UNSUPPORTED, "walkers that share a grid cannot run in the fused form");
+  if (n == 0 || nsteps == 0) return ABP_OK;
+  if (nsteps < 0) return fail(ABP_ERR_INVALID_ARG, "nsteps must be >= 0");
+  if (step0 < 0) return fail(ABP_ERR_INVALID_ARG, "step must be >= 0");
+  if (!coords || !coff) return fail(ABP_ERR_INVALID_ARG, "coordinates or offsets are NULL");
+  if (cdt != (fp64 ? ABP_F64 : ABP_F32))
+    return fail(ABP_ERR_INVALID_ARG, "coordinate dtype must be %s for these walkers", fp64 ? "ABP_F64" : "ABP_F32");
+  if (mode != ABP_FORCES_ACCUMULATE && mode != ABP_FORCES_OVERWRITE) return fail(ABP_ERR_INVALID_ARG, "bad mode");
+  if ((reinterpret_cast<uintptr_t>(coords) & 15) || (forces && (reinterpret_cast<uintptr_t>(forces) & 15)))
+    return fail(ABP_ERR_INVALID_ARG, "coordinate and force buffers must be 16-byte aligned");
+  if (fp64 && ((reinterpret_cast<uintptr_t>(coords) & 31) || (forces && (reinterpret_cast<uintptr_t>(forces) & 31))))
+    return fail(ABP_ERR_INVALID_ARG, "FP64 coordinate and force buffers must be 32-byte aligned");
+  st = set_device(ctx);
+  if (st) return st;
+  RunArgs a{};
+  if ((st = get_table(ctx, walkers, n, true, &a.table))) return st;
+  if ((st = pick_shape(walkers, n, fp64, &a.G, &a.groups_per_cta, &a.group_bytes))) return st;
+  a.nw = n;
+  a.coords = coords;
+  a.coff = reinterpret_cast<const long long *>(coff);
+  a.cstride = cstride;
+  a.forces = forces;
+  a.foff = reinterpret_cast<const long long *>(foff);
+  a.fstride = fstride;
+  a.mode = mode;
+  a.step0 = step0;
+  a.nsteps = nsteps;
+  a.log = ctx->log;
+  a.ctr = ctx->ctr;
+  cudaError_t e = launch_run(a, fp64, ctx->stream);
+  if (e != cudaSuccess) return fail(ABP_ERR_CUDA, "fused launch: %s", cudaGetErrorString(e));
+  return ABP_OK;
+}
+
+abp_status abp_run(abp_ctx *ctx, abp_walker *const *walkers, int n, const void *coords_dev, int coords_dtype,
+                   const int64_t *coord_offsets_dev, int64_t coord_step_stride, void *forces_dev,
+                   const int64_t *force_offsets_dev, int64_t force_step_stride, int mode, int64_t step0, int nsteps) {
+  if (!ctx) return fail(ABP_ERR_INVALID_ARG, "ctx is NULL");
+  if (n > 0 && nsteps > 0 && (!forces_dev || !force_offsets_dev))
+    return fail(ABP_ERR_INVALID_ARG, "forces or force offsets are NULL");
+  return run_common(ctx, walkers, n, coords_dev, coords_dtype, coord_offsets_dev, coord_step_stride, forces_dev,
+                    force_offsets_dev, force_step_stride, mode, step0, nsteps, true);
+}
+
+abp_status abp_step(abp_ctx *ctx, abp_walker *const *walkers, int n, const void *coords_dev, int coords_dtype,
+                    const int64_t *coord_offsets_dev, int64_t step) {
+  if (!ctx) return fail(ABP_ERR_INVALID_ARG, "ctx is NULL");
+  return run_common(ctx, walkers, n, coords_dev, coords_dtype, coord_offsets_dev, 0, nullptr, nullptr, 0,
+                    ABP_FORCES_OVERWRITE, step, 1, true);
+}
+
+abp_status abp_forces(abp_ctx *ctx, abp_walker *const *walkers, int n, void *forces_dev, int forces_dtype,
+                      const int64_t *force_offsets_dev, int mode) {
+  if (!ctx) return fail(ABP_ERR_INVALID_ARG, "ctx is NULL");
+  int fp64;
+  bool shared;
+  abp_status st = check_list(ctx, walkers, n, &fp64, &shared);
+  if (st) return st;
+  if (n == 0) return ABP_OK;
+  if (!forces_dev || !force_offsets_dev) return fail(ABP_ERR_INVALID_ARG, "forces or offsets are NULL");
+  if (forces_dtype != (fp64 ? ABP_F64 : ABP_F32)) return fail(ABP_ERR_INVALID_ARG, "force dtype mismatch");
+  if (mode != ABP_FORCES_ACCUMULATE && mode != ABP_FORCES_OVERWRITE) return fail(ABP_ERR_INVALID_ARG, "bad mode");
+  if ((st = set_device(ctx))) return st;
+  const TableEntry *table;
+  if ((st = get_table(ctx, walkers, n, false, &table))) return st;
+  cudaError_t e = launch_deliver(table, n, forces_dev, reinterpret_cast<const long long *>(force_offsets_dev), mode,
+                                 fp64, ctx->stream);
+  if (e != cudaSuccess) return fail(ABP_ERR_CUDA, "force delivery: %s", cudaGetErrorString(e));
+  return ABP_OK;
+}
+
+abp_status abp_step_plain(abp_ctx *ctx, abp_walker *const *walkers, int n, const void *coords_dev, int coords_dtype,
+                          const int64_t *coord_offsets_dev, void *forces_dev, const int64_t *force_offsets_dev,
+                          int mode, int64_t step) {
+  if (!ctx) return fail(ABP_ERR_INVALID_ARG, "ctx is NULL");
+  int fp64;
+  bool shared;
+  abp_status st = check_list(ctx, walkers, n, &fp64, &shared);
+  if (st) return st;
+  if (shared) return fail(ABP_ERR_UNSUPPORTED, "the plain form takes walkers with their own grids");
+  if (n == 0) return ABP_OK;
+  if (step < 0) return fail(ABP_ERR_INVALID_ARG, "step must be >= 0");
+  if (!coords_dev || !coord_offsets_dev || !forces_dev || !force_offsets_dev)
+    return fail(ABP_ERR_INVALID_ARG, "NULL buffer");
+  if (coords_dtype != (fp64 ? ABP_F64 : ABP_F32)) return fail(ABP_ERR_INVALID_ARG, "coordinate dtype mismatch");
+  if (mode != ABP_FORCES_ACCUMULATE && mode != ABP_FORCES_OVERWRITE) return fail(ABP_ERR_INVALID_ARG, "bad mode");
+  if ((st = set_device(ctx))) return st;
+  std::vector<const WalkerDev *> wd(n);
+  std::vector<int> dyn(n), dep(n);
+  const int threads = 128;
+  for (int i = 0; i < n; ++i) {
+    wd[i] = walkers[i]->dd;
+    dyn[i] = dyn_bytes(walkers[i], threads / 32);
+    dep[i] = (step % walkers[i]->hd.stride) == 0;
+  }
+  PlainArgs a{};
+  a.nw = n;
+  a.wd_dev = wd.data();
+  a.dyn_bytes = dyn.data();
+  a.deposit = dep.data();
+  a.threads = threads;
+  a.coords = coords_dev;
+  a.coff = reinterpret_cast<const long long *>(coord_offsets_dev);
+  a.forces = forces_dev;
+  a.foff = reinterpret_cast<const long long *>(force_offsets_dev);
+  a.mode = mode;
+  a.step = step;
+  a.log = ctx->log;
+  a.ctr = ctx->ctr;
+  cudaError_t e = launch_plain(a, fp64, ctx->stream);
+  if (e != cudaSuccess) return fail(ABP_ERR_CUDA, "plain launch: %s", cudaGetErrorString(e));
+  return ABP_OK;
+}
+
+// ---------------------------------------------------------------- readouts
+
+abp_status abp_bias_readout(abp_ctx *ctx, const abp_grid *g, void *dst, int dst_is_device, int dtype) {
+  if (!ctx || !g || !dst || g->ctx != ctx) return fail(ABP_ERR_INVALID_ARG, "bad argument");
+  if (dtype != ABP_F32 && dtype != ABP_F64) return fail(ABP_ERR_INVALID_ARG, "bad dtype");
+  abp_status st = set_device(ctx);
+  if (st) return st;
+  const GridDev &gd = g->g;
+  const int d = gd.d, nf = 1 + d;
+  std::vector<unsigned char> raw(g->bytes);
+  CUDA_TRY(cudaMemcpyAsync(raw.data(), gd.rec, g->bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  const size_t nvals = (size_t)gd.nodes * nf;
+  std::vector<double> v(nvals);
+  for (long long i = 0; i < gd.nodes; ++i) {
+    for (int q = 0; q < nf; ++q) {
+      double x;
+      if (gd.prec == ABP_PREC_FP32_COMP) {
+        const float *r = reinterpret_cast<const float *>(raw.data() + (size_t)i * gd.rec_bytes);
+        int comp_off = d == 1 ? 2 : 4;
+        x = (double)r[q] + (double)r[comp_off + q];
+      } else {
+        x = reinterpret_cast<const double *>(raw.data() + (size_t)i * gd.rec_bytes)[q];
+      }
+      v[(size_t)i * nf + q] = x;
+    }
+  }
+  const void *src = v.data();
+  std::vector<float> vf;
+  size_t bytes = nvals * sizeof(double);
+  if (dtype == ABP_F32) {
+    vf.resize(nvals);
+    for (size_t i = 0; i < nvals; ++i) vf[i] = (float)v[i];
+    src = vf.data();
+    bytes = nvals * sizeof(float);
+  }
+  if (dst_is_device) {
+    CUDA_TRY(cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice));
+  } else {
+    std::memcpy(dst, src, bytes);
+  }
+  return ABP_OK;
+}
+
+abp_status abp_bias_upload(abp_ctx *ctx, abp_grid *g, const void *src, int src_is_device, int dtype) {
+  if (!ctx || !g || !src || g->ctx != ctx) return fail(ABP_ERR_INVALID_ARG, "bad argument");
+  if (dtype != ABP_F32 && dtype != ABP_F64) return fail(ABP_ERR_INVALID_ARG, "bad dtype");
+  abp_status st = set_device(ctx);
+  if (st) return st;
+  const GridDev &gd = g->g;
+  const int d = gd.d, nf = 1 + d;
+  const size_t nvals = (size_t)gd.nodes * nf;
+  const size_t esz = dtype == ABP_F64 ? 8 : 4;
+  std::vector<unsigned char> in(nvals * esz);
+  if (src_is_device) {
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    CUDA_TRY(cudaMemcpy(in.data(), src, in.size(), cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(in.data(), src, in.size());
+  }
+  std::vector<unsigned char> raw(g->bytes, 0);
+  for (long long i = 0; i < gd.nodes; ++i) {
+    for (int q = 0; q < nf; ++q) {
+      size_t j = (size_t)i * nf + q;
+      double x = dtype == ABP_F64 ? reinterpret_cast<const double *>(in.data())[j]
+                                  : (double)reinterpret_cast<const float *>(in.data())[j];
+      if (gd.prec == ABP_PREC_FP32_COMP) {
+        float *r = reinterpret_cast<float *>(raw.data() + (size_t)i * gd.rec_bytes);
+        int comp_off = d == 1 ? 2 : 4;
+        float hi = (float)x;
+        r[q] = hi;
+        r[comp_off + q] = (float)(x - (double)hi);
+      } else {
+        reinterpret_cast<double *>(raw.data() + (size_t)i * gd.rec_bytes)[q] = x;
+      }
+    }
+  }
+  CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  CUDA_TRY(cudaMemcpy(gd.rec, raw.data(), g->bytes, cudaMemcpyHostToDevice));
+  return ABP_OK;
+}
+
+abp_status abp_walker_readout(abp_ctx *ctx, const abp_walker *w, double *s, double *V, double *dV, int *flags) {
+  if (!ctx || !w || w->ctx != ctx) return fail(ABP_ERR_INVALID_ARG, "bad argument");
+  abp_status st = set_device(ctx);
+  if (st) return st;
+  WalkerState hs;
+  CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  CUDA_TRY(cudaMemcpy(&hs, w->hd.state, sizeof hs, cudaMemcpyDeviceToHost));
+  for (int k = 0; k < 3; ++k) {
+    if (s) s[k] = hs.s[k];
+    if (dV) dV[k] = hs.dV[k];
+  }
+  if (V) *V = hs.V;
+  if (flags) *flags = hs.flags;
+  if (hs.flags & ABP_WFLAG_NONFINITE) return fail(ABP_ERR_NONFINITE, "the walker's last step saw non-finite coordinates");
+  return ABP_OK;
+}
+
+abp_status abp_deposit_log_enable(abp_ctx *ctx, size_t capacity) {
+  if (!ctx) return fail(ABP_ERR_INVALID_ARG, "ctx is NULL");
+  abp_status st = set_device(ctx);
+  if (st) return st;
+  CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  if (ctx->log.rec) cudaFree(ctx->log.rec);
+  if (ctx->log.count) cudaFree(ctx->log.count);
+  ctx->log = DepositLog{nullptr, nullptr, 0};
+  if (capacity == 0) return ABP_OK;
+  CUDA_TRY(cudaMalloc(&ctx->log.rec, capacity * sizeof(abp_deposit_rec)));
+  CUDA_TRY(cudaMalloc(&ctx->log.count, sizeof(unsigned long long)));
+  CUDA_TRY(cudaMemset(ctx->log.count, 0, sizeof(unsigned long long)));
+  ctx->log.cap = capacity;
+  return ABP_OK;
+}
+
+abp_status abp_deposit_log_readout(abp_ctx *ctx, abp_deposit_rec *dst, size_t cap, size_t *n_out, size_t *n_total) {
+  if (!ctx) return fail(ABP_ERR_INVALID_ARG, "ctx is NULL");
+  abp_status st = set_device(ctx);
+  if (st) return st;
+  CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  unsigned long long cnt = 0;
+  if (ctx->log.count) CUDA_TRY(cudaMemcpy(&cnt, ctx->log.count, sizeof cnt, cudaMemcpyDeviceToHost));
+  size_t stored = (size_t)std::min<unsigned long long>(cnt, ctx->log.cap);
+  size_t n = std::min(stored, cap);
+  if (n && !dst) return fail(ABP_ERR_INVALID_ARG, "dst is NULL");
+  if (n) CUDA_TRY(cudaMemcpy(dst, ctx->log.rec, n * sizeof(abp_deposit_rec), cudaMemcpyDeviceToHost));
+  if (n_out) *n_out = n;
+  if (n_total) *n_total = (size_t)cnt;
+  return ABP_OK;
+}
+
+abp_status abp_deposit_log_clear(abp_ctx *ctx) {
+  if (!ctx) return fail(ABP_ERR_INVALID_ARG, "ctx is NULL");
+  abp_status st = set_device(ctx);
+  if (st) return st;
+  if (ctx->log.count) CUDA_TRY(cudaMemsetAsync(ctx->log.count, 0, sizeof(unsigned long long), ctx->stream));
+  return ABP_OK;
+}
+
+abp_status abp_sync(abp_ctx *ctx) {
+  if (!ctx) return fail(ABP_ERR_INVALID_ARG, "ctx is NULL");
+  abp_status st = set_device(ctx);
+  if (st) return st;
+  CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  int nf = 0;
+  CUDA_TRY(cudaMemcpy(&nf, &ctx->ctr->nonfinite, sizeof nf, cudaMemcpyDeviceToHost));
+  if (nf) {
+    CUDA_TRY(cudaMemset(&ctx->ctr->nonfinite, 0, sizeof nf));
+    return fail(ABP_ERR_NONFINITE, "%d walker steps saw non-finite coordinates", nf);
+  }
+  return ABP_OK;
+}
+
+}  // extern "C"

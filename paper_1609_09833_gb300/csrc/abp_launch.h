@@ -1,0 +1,61 @@
+// abp_launch.h -- launch descriptors between the host ABI layer and the
+// kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "abp_internal.cuh"
+
+namespace abp {
+
+// One walker of a batched launch: its device descriptor and its index in
+// the caller's walker list (which selects its coordinate/force offsets).
+struct TableEntry {
+  const WalkerDev *wd;
+  int idx;
+  int pad;
+};
+
+struct RunArgs {
+  const TableEntry *table;
+  int nw;
+  int G;               // threads per walker group
+  int groups_per_cta;
+  int group_bytes;     // shared memory per group (fixed + dynamic part)
+  const void *coords;
+  const long long *coff;
+  long long cstride;   // records between consecutive steps
+  void *forces;        // NULL: write each walker's own force buffer (abp_step)
+  const long long *foff;
+  long long fstride;
+  int mode;
+  long long step0;
+  int nsteps;
+  DepositLog log;
+  DevCounters *ctr;
+};
+
+struct PlainArgs {
+  int nw;
+  const WalkerDev *const *wd_dev;  // host array of device descriptors
+  const int *dyn_bytes;            // host array: dynamic smem per walker
+  const int *deposit;              // host array: deposit this step?
+  int threads;
+  const void *coords;
+  const long long *coff;
+  void *forces;
+  const long long *foff;
+  int mode;
+  long long step;
+  DepositLog log;
+  DevCounters *ctr;
+};
+
+int group_fixed_bytes(int fp64);
+int plain_scratch_bytes(int fp64, const CvDev *cv, int ncv);
+cudaError_t launch_run(const RunArgs &a, int fp64, cudaStream_t st);
+cudaError_t launch_plain(const PlainArgs &a, int fp64, cudaStream_t st);
+cudaError_t launch_deliver(const TableEntry *table, int nw, void *forces, const long long *foff, int mode, int fp64,
+                           cudaStream_t st);
+
+}  // namespace abp
