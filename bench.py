@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--tile", default="auto", choices=["auto", "on", "off"])
+    ap.add_argument("--group-threads", type=int, default=0)
     return ap.parse_args()
 
 
@@ -220,6 +222,8 @@ def main():
     build.build()
     stream = torch.cuda.current_stream()
     ctx = abp.Context(dev, stream.cuda_stream)
+    abp.abp_ctx_tune(ctx.handle, abp.ABP_TUNE_TILE, {"auto": -1, "on": 1, "off": 0}[args.tile])
+    abp.abp_ctx_tune(ctx.handle, abp.ABP_TUNE_GROUP_THREADS, args.group_threads)
     specs, fr = workload(SEED + 7919 * rank)
     walkers = ctx.make_walkers(specs)
     C = args.md_steps

@@ -147,6 +147,23 @@ abp_status abp_ctx_create(abp_ctx **out, int device, void *cuda_stream, size_t h
 abp_status abp_ctx_set_stream(abp_ctx *ctx, void *cuda_stream);
 /* Bytes currently allocated against the budget. */
 abp_status abp_ctx_bytes(const abp_ctx *ctx, size_t *used, size_t *budget);
+
+/* Launch-shape knobs of the batched form, for the autotuner (the paper has
+ * no counterpart: its bias routine runs on one CPU rank). 0 (or -1 for
+ * ABP_TUNE_TILE) restores the library's default choice. Knobs change only
+ * the schedule: results are bit-identical for every tile setting and every
+ * number of groups per CTA; a different group width changes the order of
+ * the CV sums, so results then agree to rounding.
+ *   ABP_TUNE_GROUP_THREADS   threads per walker group: 32, 64, 128 or 256
+ *   ABP_TUNE_GROUPS_PER_CTA  walker groups per CTA: 1..8
+ *   ABP_TUNE_TILE            1 = give groups a shared-memory tile of their
+ *                            grid when it fits (launches of >= 8 steps),
+ *                            0 or -1 = never (the default)
+ * Invalid values return ABP_ERR_INVALID_ARG and leave the knob unchanged. */
+#define ABP_TUNE_GROUP_THREADS 1
+#define ABP_TUNE_GROUPS_PER_CTA 2
+#define ABP_TUNE_TILE 3
+abp_status abp_ctx_tune(abp_ctx *ctx, int knob, int value);
 void abp_ctx_destroy(abp_ctx *ctx);
 
 /* ---- grids and walkers ---------------------------------------------------- */

@@ -63,6 +63,7 @@ _SIGS = {
     "abp_ctx_create": [C.POINTER(_vp), C.c_int, _vp, C.c_size_t],
     "abp_ctx_set_stream": [_vp, _vp],
     "abp_ctx_bytes": [_vp, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)],
+    "abp_ctx_tune": [_vp, C.c_int, C.c_int],
     "abp_ctx_destroy": [_vp],
     "abp_create_grid": [_vp, C.POINTER(GridDesc), C.POINTER(_vp)],
     "abp_grid_destroy": [_vp],
@@ -157,6 +158,13 @@ def abp_ctx_bytes(ctx):
     u, b = C.c_size_t(), C.c_size_t()
     _check(load().abp_ctx_bytes(ctx, C.byref(u), C.byref(b)))
     return u.value, b.value
+
+
+ABP_TUNE_GROUP_THREADS, ABP_TUNE_GROUPS_PER_CTA, ABP_TUNE_TILE = 1, 2, 3
+
+
+def abp_ctx_tune(ctx, knob: int, value: int):
+    _check(load().abp_ctx_tune(ctx, int(knob), int(value)))
 
 
 def abp_ctx_destroy(ctx):

@@ -60,6 +60,8 @@ struct abp_ctx {
   TableCache tables[4];
   unsigned long long use_clock = 0;
   int next_id = 0;
+  int sms = 0;  // multiprocessors of the device
+  int tune_G = 0, tune_gpc = 0, tune_tile = -1;  // tile -1: library default (off; opt in with 1)
   std::mutex mu;
 };
 
@@ -123,8 +125,9 @@ double spacing(const abp_grid_desc &d, int k) {
 
 int walker_fp64(const abp_walker *w) { return w->grid->desc.precision == ABP_PREC_FP64; }
 
+// Dynamic shared bytes of one walker group without a tile.
 int dyn_bytes(const abp_walker *w, int nwarps) {
-  return group_dyn_bytes(w->hd.natoms, w->hd.cv, w->hd.g.d, nwarps, walker_fp64(w) ? 32 : 16);
+  return group_layout(w->hd.natoms, w->hd.cv, w->hd.g, w->hd.R, nwarps, walker_fp64(w) ? 32 : 16, 0).total;
 }
 
 // Common validation of a walker list. Returns the precision (0/1) via *fp64.
@@ -186,22 +189,46 @@ abp_status get_table(abp_ctx *ctx, abp_walker *const *walkers, int n, bool sort_
 }
 
 // Launch shape for a batch: a group of G threads per walker, several
-// groups per CTA, as shared memory allows.
-abp_status pick_shape(abp_walker *const *walkers, int n, int fp64, int *G, int *gpc, int *group_bytes) {
+// groups per CTA, as shared memory allows. Multi-step launches of FP32
+// walkers with few enough walkers per SM also give each group a shared-memory
+// tile of its grid (the rest of ~220 KB / walkers-per-SM).
+abp_status pick_shape(const abp_ctx *ctx, abp_walker *const *walkers, int n, int fp64, int nsteps, int *G, int *gpc,
+                      int *group_bytes, int *tile_budget) {
   bool cn = false;
   for (int i = 0; i < n; ++i) cn = cn || walkers[i]->has_cn;
-  int g = cn ? 128 : 32;
-  int fixed = group_fixed_bytes(fp64);
-  int dyn = 0;
-  for (int i = 0; i < n; ++i) dyn = std::max(dyn, dyn_bytes(walkers[i], g / 32));
-  int gb = (fixed + dyn + 31) & ~31;
+  int g = ctx->tune_G ? ctx->tune_G : (cn ? 128 : 32);
   const int smem_max = 227 * 1024;
+  int fixed = group_fixed_bytes(fp64);
+  int tb = 0;
+  // Measured on the 64-walker workload, one warp per walker: reloading and
+  // indexing the tile cost more than the L2 reads it saves, so tiles are
+  // opt-in (ABP_TUNE_TILE = 1) and need a multi-step launch.
+  bool tile_ok = ctx->tune_tile == 1 && nsteps >= 8;
+  if (!fp64 && tile_ok && ctx->sms > 0) {
+    int per_sm = (n + ctx->sms - 1) / ctx->sms;
+    int avail = (220 * 1024) / per_sm - fixed - 1024;
+    if (avail > 16 * 1024) tb = avail;
+  }
+  int gb = 0;
+  bool any_tile = false;
+  for (int i = 0; i < n; ++i) {
+    int b = run_group_bytes(walkers[i]->hd, fp64, g, tb);
+    gb = std::max(gb, b);
+    if (tb > 0 && b > run_group_bytes(walkers[i]->hd, fp64, g, 0)) any_tile = true;
+  }
+  if (!any_tile) {
+    tb = 0;
+    gb = 0;
+    for (int i = 0; i < n; ++i) gb = std::max(gb, run_group_bytes(walkers[i]->hd, fp64, g, 0));
+  }
   if (gb > smem_max) return fail(ABP_ERR_UNSUPPORTED, "a walker needs %d bytes of shared memory (max %d)", gb, smem_max);
-  int per = cn ? 2 : 4;
-  while (per > 1 && per * gb > 100 * 1024) --per;
+  int per = 1;
+  if (tb == 0) per = ctx->tune_gpc ? ctx->tune_gpc : (cn ? 2 : 4);
+  while (per > 1 && (per * gb > (ctx->tune_gpc ? smem_max : 100 * 1024) || per * g > 256)) --per;
   *G = g;
   *gpc = per;
   *group_bytes = gb;
+  *tile_budget = tb;
   return ABP_OK;
 }
 
@@ -224,6 +251,7 @@ abp_status abp_ctx_create(abp_ctx **out, int device, void *cuda_stream, size_t h
   c->stream = static_cast<cudaStream_t>(cuda_stream);
   c->budget = hbm_budget_bytes;
   abp_status st = set_device(c);
+  if (st == ABP_OK && cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) c->sms = 0;
   if (st == ABP_OK) {
     cudaError_t e = cudaMalloc(&c->ctr, sizeof(DevCounters));
     if (e == cudaSuccess) e = cudaMemset(c->ctr, 0, sizeof(DevCounters));
@@ -242,6 +270,26 @@ abp_status abp_ctx_set_stream(abp_ctx *ctx, void *cuda_stream) {
   if (!ctx) return fail(ABP_ERR_INVALID_ARG, "ctx is NULL");
   ctx->stream = static_cast<cudaStream_t>(cuda_stream);
   return ABP_OK;
+}
+
+abp_status abp_ctx_tune(abp_ctx *ctx, int knob, int value) {
+  if (!ctx) return fail(ABP_ERR_INVALID_ARG, "ctx is NULL");
+  switch (knob) {
+    case ABP_TUNE_GROUP_THREADS:
+      if (value != 0 && value != 32 && value != 64 && value != 128 && value != 256)
+        return fail(ABP_ERR_INVALID_ARG, "group threads must be 32, 64, 128 or 256");
+      ctx->tune_G = value;
+      return ABP_OK;
+    case ABP_TUNE_GROUPS_PER_CTA:
+      if (value < 0 || value > kMaxGroupsPerCta) return fail(ABP_ERR_INVALID_ARG, "groups per CTA must be 0..8");
+      ctx->tune_gpc = value;
+      return ABP_OK;
+    case ABP_TUNE_TILE:
+      if (value < -1 || value > 1) return fail(ABP_ERR_INVALID_ARG, "tile knob must be -1, 0 or 1");
+      ctx->tune_tile = value;
+      return ABP_OK;
+  }
+  return fail(ABP_ERR_INVALID_ARG, "unknown knob %d", knob);
 }
 
 abp_status abp_ctx_bytes(const abp_ctx *ctx, size_t *used, size_t *budget) {
@@ -296,6 +344,12 @@ abp_status abp_create_grid(abp_ctx *ctx, const abp_grid_desc *d, abp_grid **out)
     gd.D[k] = on ? spacing(*d, k) : 1.0;
     gd.invD[k] = 1.0 / gd.D[k];
     gd.L[k] = on ? d->hi[k] - d->lo[k] : 1.0;
+    gd.u0[k] = -gd.lo[k] * gd.invD[k];
+    gd.inv_n[k] = 1.0 / gd.n[k];
+    gd.invD_h[k] = (float)gd.invD[k];
+    gd.invD_l[k] = (float)(gd.invD[k] - (double)gd.invD_h[k]);
+    gd.u0_h[k] = (float)gd.u0[k];
+    gd.u0_l[k] = (float)(gd.u0[k] - (double)gd.u0_h[k]);
   }
   gd.prec = d->precision;
   gd.rec_bytes = rec_bytes(d->precision, d->ncv);
@@ -505,7 +559,7 @@ abp_status abp_walker_create(abp_ctx *ctx, abp_grid *grid, const abp_walker_desc
     }
   }
   if (st == ABP_OK) {
-    int need = (group_fixed_bytes(fp64) + dyn_bytes(w, 1) + 31) & ~31;
+    int need = run_group_bytes(hd, fp64, 32, 0);
     if (need > 227 * 1024) st = fail(ABP_ERR_UNSUPPORTED, "walker of %d atoms needs %d bytes of shared memory", d->natoms, need);
   }
   if (st == ABP_OK) {
@@ -565,7 +619,8 @@ static abp_status run_common(abp_ctx *ctx, abp_walker *const *walkers, int n, co
   if (st) return st;
   RunArgs a{};
   if ((st = get_table(ctx, walkers, n, true, &a.table))) return st;
-  if ((st = pick_shape(walkers, n, fp64, &a.G, &a.groups_per_cta, &a.group_bytes))) return st;
+  if ((st = pick_shape(ctx, walkers, n, fp64, nsteps, &a.G, &a.groups_per_cta, &a.group_bytes, &a.tile_budget)))
+    return st;
   a.nw = n;
   a.coords = coords;
   a.coff = reinterpret_cast<const long long *>(coff);

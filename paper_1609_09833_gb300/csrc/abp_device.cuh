@@ -1,14 +1,16 @@
 // abp_device.cuh -- device building blocks of one walker step, executed by a
 // "walker group" of G threads (one to eight warps) that owns the walker for
-// the whole step. Every reduction runs in a fixed order, so a walker's result
-// does not depend on which other walkers share the launch.
+// all steps of a launch. Every reduction runs in a fixed order, so a walker's
+// result does not depend on which other walkers share the launch, and the
+// optional shared-memory grid tile is an exact cache of the grid (same values,
+// same arithmetic), so it does not change results either.
 //
 // Steps (arXiv:1609.09833):
-//   a1 CVs + Jacobians          cv_com / cv_dihedral / cv_coord
-//   a2 well-tempered height     interp_corners<double> + w exp(-V / dT)
-//   a3 Gaussian stencil deposit build_tables + deposit_stencil
-//   a4 multilinear interpolation interp_corners<Real>
-//   a5 chain rule               scatter_forces
+//   a1 CVs + Jacobians           cv_com / cv_dihedral / cv_coord
+//   a2 well-tempered height      height_interp + w exp(-V / dT)
+//   a3 Gaussian stencil deposit  build_tables + deposit_stencil
+//   a4 multilinear interpolation interp_step
+//   a5 chain rule                scatter_forces
 #pragma once
 
 #include <math.h>
@@ -44,10 +46,13 @@ __device__ __forceinline__ typename Rec4<Real>::T make_rec(Real x, Real y, Real 
   return r;
 }
 
-template <typename Real>
-__device__ __forceinline__ typename Rec4<Real>::T ld_rec(const void *base, long long i) {
-  return reinterpret_cast<const typename Rec4<Real>::T *>(base)[i];
+// 16-byte asynchronous global -> shared copy (completes at cp_async_wait).
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
+  unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem_src) : "memory");
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // ---------------------------------------------------------------- groups
 
@@ -74,18 +79,30 @@ struct GroupFixed {
   WalkerDev wd;
   Real red[kMaxGroupWarps * 8];
   double redd[kMaxGroupWarps * 8];
-  double s[kMaxCv];           // CV values (FP32 arithmetic per term, FP64 sums)
+  Real sh[kMaxCv], sl[kMaxCv];  // CV value s = sh + sl (sl carries the low bits of long FP32 sums)
   Real dvds[kMaxCv];
-  Real com_u[kMaxCv][3];      // COM unit separation (J_A = -w u, J_B = +w u)
-  Real dih_g[kMaxCv][4][3];   // dihedral gradient per atom
-  double u[kMaxCv];           // fractional grid coordinate of s (deposit)
-  int ic[kMaxCv];
-  int ic_log[kMaxCv];         // floor(u + 1/2) before the out-of-range limit (deposit log)
+  Real com_u[kMaxCv][3];     // COM unit separation (J_A = -w u, J_B = +w u)
+  Real dih_g[kMaxCv][4][3];  // dihedral gradient per atom
+  // per-step axis state (one thread per axis)
+  int i0[kMaxCv], i1[kMaxCv];  // interpolation corners
+  Real f[kMaxCv];            // interpolation weight of i1
+  int da[kMaxCv];            // deposit: node below u (unwrapped)
+  Real df[kMaxCv];           // deposit: u - da, in [0, 1)
+  int dc[kMaxCv];            // deposit: centre offset, i_c = da + dc (dc = 1 iff df >= 1/2)
+  int ic_log[kMaxCv];        // i_c for the deposit log (wrapped; unclamped outside a range)
+  int clamped;               // interpolation clamp mask
   int flags;
   int bad;
-  double V;                   // V_b(s_t) after the step's deposit (a4)
-  double dV[kMaxCv];
-  Real hf;                    // hill height (rounded to Real)
+  int reload;                // the tile must be reloaded this step
+  int org[kMaxCv];           // tile origin node per axis
+  Real V;
+  Real dV[kMaxCv];
+  Real hf;                   // hill height (rounded to Real)
+  // atom lists of each CV (shared memory, or global in the plain form)
+  const int32_t *ia[kMaxCv];
+  const int32_t *ib[kMaxCv];
+  const Real *wa[kMaxCv];
+  const Real *wb[kMaxCv];
   Real tabG[kMaxCv][2 * kRMax + 1];
   Real tabD[kMaxCv][2 * kRMax + 1];
   int tabJ[kMaxCv][2 * kRMax + 1];
@@ -116,6 +133,20 @@ __device__ __forceinline__ void grp_sum(const Grp &g, Real (&v)[K], Real *red) {
   g.sync();
 }
 
+// Any thread of the group set `flag`?
+template <typename Real>
+__device__ __forceinline__ bool grp_any(const Grp &g, GroupFixed<Real> *fx, int flag) {
+  int w = __any_sync(0xffffffffu, flag);
+  if (g.G == 32) return w != 0;
+  if (g.t == 0) fx->bad = 0;
+  g.sync();
+  if (g.lane == 0 && w) fx->bad = 1;
+  g.sync();
+  int r = fx->bad;
+  g.sync();
+  return r != 0;
+}
+
 template <typename Real>
 __device__ __forceinline__ Real min_image(Real dx, double box, double inv_box) {
   return dx - (Real)box * floor(dx * (Real)inv_box + (Real)0.5);
@@ -132,6 +163,55 @@ __device__ __forceinline__ double rcp_fast<double>(double x) {
   return 1.0 / x;
 }
 
+// Error-free sum a + b = s + e (two-sum); exact in round-to-nearest.
+template <typename Real>
+__device__ __forceinline__ void two_sum(Real a, Real b, Real &s, Real &e);
+template <>
+__device__ __forceinline__ void two_sum<float>(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  float bp = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+}
+template <>
+__device__ __forceinline__ void two_sum<double>(double a, double b, double &s, double &e) {
+  s = __dadd_rn(a, b);
+  double bp = __dsub_rn(s, a);
+  e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bp)), __dsub_rn(b, bp));
+}
+
+// (ah, al) += (bh, bl) in hi + lo ("double-single") arithmetic, renormalized.
+// Commutative bit for bit, since two_sum's error term is exact.
+template <typename Real>
+__device__ __forceinline__ void ff_add(Real &ah, Real &al, Real bh, Real bl) {
+  Real s, e;
+  two_sum<Real>(ah, bh, s, e);
+  e = e + (al + bl);
+  ah = s + e;
+  al = e - (ah - s);
+}
+
+// Group sum of a hi + lo pair (fixed order, all threads get the total).
+template <typename Real>
+__device__ __forceinline__ void grp_sum_ff(const Grp &g, Real &h, Real &l, Real *red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    Real oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+    ff_add<Real>(h, l, oh, ol);
+  }
+  h = __shfl_sync(0xffffffffu, h, 0);
+  l = __shfl_sync(0xffffffffu, l, 0);
+  if (g.G == 32) return;
+  if (g.lane == 0) {
+    red[g.warp * 8] = h;
+    red[g.warp * 8 + 1] = l;
+  }
+  g.sync();
+  h = red[0];
+  l = red[1];
+  for (int w = 1; w < g.nwarps; ++w) ff_add<Real>(h, l, red[w * 8], red[w * 8 + 1]);
+  g.sync();
+}
+
 // ---------------------------------------------------------------- a1: CVs
 
 // Centre-of-mass distance s = |R_B - R_A| (minimum image if pbc). Each
@@ -141,19 +221,21 @@ __device__ __forceinline__ double rcp_fast<double>(double x) {
 template <typename Real>
 __device__ void cv_com(const Grp &g, GroupFixed<Real> *fx, int k, const typename Rec4<Real>::T *xs) {
   const CvDev &c = fx->wd.cv[k];
-  const auto ra = xs[__ldg(c.ia)];
-  const auto rb = xs[__ldg(c.ib)];
+  const int32_t *ia = fx->ia[k], *ib = fx->ib[k];
+  const Real *wa = fx->wa[k], *wb = fx->wb[k];
+  const auto ra = xs[ia[0]];
+  const auto rb = xs[ib[0]];
   Real v[6] = {0, 0, 0, 0, 0, 0};
   for (int i = g.t; i < c.na; i += g.G) {
-    Real w = sizeof(Real) == 4 ? (Real)c.wa[i] : (Real)c.wa64[i];
-    auto p = xs[__ldg(c.ia + i)];
+    Real w = wa[i];
+    auto p = xs[ia[i]];
     v[0] += w * (p.x - ra.x);
     v[1] += w * (p.y - ra.y);
     v[2] += w * (p.z - ra.z);
   }
   for (int i = g.t; i < c.nb; i += g.G) {
-    Real w = sizeof(Real) == 4 ? (Real)c.wb[i] : (Real)c.wb64[i];
-    auto p = xs[__ldg(c.ib + i)];
+    Real w = wb[i];
+    auto p = xs[ib[i]];
     v[3] += w * (p.x - rb.x);
     v[4] += w * (p.y - rb.y);
     v[5] += w * (p.z - rb.z);
@@ -163,10 +245,13 @@ __device__ void cv_com(const Grp &g, GroupFixed<Real> *fx, int k, const typename
     Real d[3] = {(rb.x - ra.x) + (v[3] - v[0]), (rb.y - ra.y) + (v[4] - v[1]), (rb.z - ra.z) + (v[5] - v[2])};
     if (c.pbc)
       for (int q = 0; q < 3; ++q) d[q] = min_image(d[q], c.box[q], c.inv_box[q]);
-    Real r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-    fx->s[k] = (double)r;
+    Real r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    Real r = sqrt(r2);
+    fx->sh[k] = r;
+    fx->sl[k] = 0;
     if (r > 0) {
-      for (int q = 0; q < 3; ++q) fx->com_u[k][q] = d[q] / r;
+      Real ir = rcp_fast<Real>(r);
+      for (int q = 0; q < 3; ++q) fx->com_u[k][q] = d[q] * ir;
     } else {
       for (int q = 0; q < 3; ++q) fx->com_u[k][q] = 0;
       fx->flags |= ABP_WFLAG_SINGULAR;
@@ -186,14 +271,16 @@ __device__ __forceinline__ Real dot3(const Real *a, const Real *b) {
 }
 
 // Dihedral of atoms 1-2-3-4: phi = atan2(|b2| b1.(b2 x b3), (b1 x b2).(b2 x b3)),
-// gradient in the Blondel-Karplus form. One thread.
+// gradient in the Blondel-Karplus form. One thread (the last thread of the
+// group, so that with several warps it overlaps the COM work of warp 0).
 template <typename Real>
 __device__ void cv_dihedral(const Grp &g, GroupFixed<Real> *fx, int k, const typename Rec4<Real>::T *xs) {
-  if (g.t != 0) return;
+  if (g.t != g.G - 1) return;
   const CvDev &c = fx->wd.cv[k];
+  const int32_t *ia = fx->ia[k];
   Real x[4][3];
   for (int a = 0; a < 4; ++a) {
-    auto p = xs[__ldg(c.ia + a)];
+    auto p = xs[ia[a]];
     x[a][0] = p.x;
     x[a][1] = p.y;
     x[a][2] = p.z;
@@ -211,8 +298,10 @@ __device__ void cv_dihedral(const Grp &g, GroupFixed<Real> *fx, int k, const typ
   }
   cross3(b1, b2, m);
   cross3(b2, b3, n);
-  Real lb2 = sqrt(dot3(b2, b2));
-  fx->s[k] = (double)atan2(lb2 * dot3(b1, n), dot3(m, n));
+  Real b2sq = dot3(b2, b2);
+  Real lb2 = sqrt(b2sq);
+  fx->sh[k] = atan2(lb2 * dot3(b1, n), dot3(m, n));
+  fx->sl[k] = 0;
   Real mm = dot3(m, m), nn = dot3(n, n);
   if (!(mm > 0) || !(nn > 0) || !(lb2 > 0)) {
     for (int a = 0; a < 4; ++a)
@@ -220,11 +309,12 @@ __device__ void cv_dihedral(const Grp &g, GroupFixed<Real> *fx, int k, const typ
     fx->flags |= ABP_WFLAG_SINGULAR;
     return;
   }
-  Real inv_b2sq = 1 / (lb2 * lb2);
+  Real inv_b2sq = rcp_fast<Real>(b2sq);
   Real p = dot3(b1, b2) * inv_b2sq, r = dot3(b3, b2) * inv_b2sq;
+  Real cm = -lb2 * rcp_fast<Real>(mm), cn = lb2 * rcp_fast<Real>(nn);
   for (int q = 0; q < 3; ++q) {
-    Real g1 = -lb2 / mm * m[q];
-    Real g4 = lb2 / nn * n[q];
+    Real g1 = cm * m[q];
+    Real g4 = cn * n[q];
     fx->dih_g[k][0][q] = g1;
     fx->dih_g[k][3][q] = g4;
     fx->dih_g[k][1][q] = -(1 + p) * g1 + r * g4;
@@ -245,6 +335,7 @@ __device__ void cv_coord(const Grp &g, GroupFixed<Real> *fx, int k, const typena
                          typename Rec4<Real>::T *jA, typename Rec4<Real>::T *jB, Real *lig) {
   using R4 = typename Rec4<Real>::T;
   const CvDev &c = fx->wd.cv[k];
+  const int32_t *ia = fx->ia[k], *ib = fx->ib[k];
   const Real k2 = (Real)c.inv_r0sq;
   const Real c6 = (Real)-6 * k2;
   const bool pbc = c.pbc != 0;
@@ -253,7 +344,7 @@ __device__ void cv_coord(const Grp &g, GroupFixed<Real> *fx, int k, const typena
   Real *mylig = lig + g.warp * c.na * 3;
   for (int q = g.lane; q < c.na * 3; q += 32) mylig[q] = 0;
   __syncwarp();
-  Real sacc = 0;  // this thread's partial sum (a few terms of size <= 1)
+  Real sacc = 0;  // this thread's partial sum (a few hundred terms of size <= 1)
   constexpr int JB = 4;
   for (int jb0 = 0; jb0 < c.nb; jb0 += g.G * JB) {
     Real xj[JB], yj[JB], zj[JB], gxj[JB], gyj[JB], gzj[JB], mj[JB];
@@ -261,7 +352,7 @@ __device__ void cv_coord(const Grp &g, GroupFixed<Real> *fx, int k, const typena
     for (int jj = 0; jj < JB; ++jj) {
       int j = jb0 + jj * g.G + g.t;
       bool ok = j < c.nb;
-      R4 p = xs[__ldg(c.ib + (ok ? j : 0))];
+      R4 p = xs[ib[ok ? j : 0]];
       xj[jj] = p.x;
       yj[jj] = p.y;
       zj[jj] = p.z;
@@ -275,7 +366,7 @@ __device__ void cv_coord(const Grp &g, GroupFixed<Real> *fx, int k, const typena
         gi[ii][0] = gi[ii][1] = gi[ii][2] = 0;
         int i = i0 + ii;
         bool oki = i < c.na;
-        R4 a = xs[__ldg(c.ia + (oki ? i : 0))];
+        R4 a = xs[ia[oki ? i : 0]];
 #pragma unroll
         for (int jj = 0; jj < JB; ++jj) {
           Real dx = a.x - xj[jj], dy = a.y - yj[jj], dz = a.z - zj[jj];
@@ -314,11 +405,15 @@ __device__ void cv_coord(const Grp &g, GroupFixed<Real> *fx, int k, const typena
       if (j < c.nb) jB[j] = make_rec<Real>(gxj[jj], gyj[jj], gzj[jj], (Real)0);
     }
   }
-  // the sum of FP32 pair terms is reduced in FP64: a CN of a few hundred
-  // needs more than FP32's 24 bits to place a hill two grid spacings wide
-  double v[1] = {(double)sacc};
-  grp_sum<1>(g, v, fx->redd);
-  if (g.t == 0) fx->s[k] = v[0];
+  // the per-thread partial sums are combined in hi + lo arithmetic: a CN of
+  // a few hundred needs more than FP32's 24 bits to place a hill two grid
+  // spacings wide
+  Real sh = sacc, sl = 0;
+  grp_sum_ff<Real>(g, sh, sl, fx->red);
+  if (g.t == 0) {
+    fx->sh[k] = sh;
+    fx->sl[k] = sl;
+  }
   g.sync();
   for (int i = g.t; i < c.na; i += g.G) {
     Real a0 = 0, a1 = 0, a2 = 0;
@@ -332,38 +427,247 @@ __device__ void cv_coord(const Grp &g, GroupFixed<Real> *fx, int k, const typena
   }
 }
 
-// ---------------------------------------------------------------- grid helpers
+// ---------------------------------------------------------------- grid axes
 
-// Fractional coordinate of s along axis k; periodic axes wrapped into [0, n).
-// (Any finite or non-finite s maps to a u whose stencil indices stay in
-// range: a periodic u is forced into [0, n); a non-periodic u far outside the
-// axis is limited so that its box holds no node.)
-__device__ __forceinline__ double axis_u(const GridDev &gd, int k, double s, int R) {
-  double u = (s - gd.lo[k]) * gd.invD[k];
-  double n = (double)gd.n[k];
-  if (gd.periodic[k]) {
-    u = u - n * floor(u / n);
-    if (u >= n) u -= n;
-    if (u < 0) u += n;
-    if (!(u >= 0.0 && u < n)) u = 0.0;
-  } else {
-    if (!(u >= -R - 2.0)) u = -R - 2.0;
-    if (!(u <= n + R + 1.0)) u = n + R + 1.0;
-  }
-  return u;
+// u = (s - lo) / D = s invD + u0 as hi + lo (FP32 grids: hi + lo floats,
+// exact to ~2^-44 relative; FP64 grids: one double).
+template <typename Real>
+__device__ __forceinline__ void axis_u(const GridDev &gd, int k, Real sh, Real sl, Real &uh, Real &ul);
+template <>
+__device__ __forceinline__ void axis_u<float>(const GridDev &gd, int k, float sh, float sl, float &uh, float &ul) {
+  const float ih = gd.invD_h[k], il = gd.invD_l[k];
+  float p = sh * ih;
+  float pe = fmaf(sh, ih, -p);  // exact error of the product
+  pe = fmaf(sh, il, fmaf(sl, ih, pe));
+  float t, te;
+  two_sum<float>(p, gd.u0_h[k], t, te);
+  te = te + (pe + gd.u0_l[k]);
+  uh = t + te;
+  ul = te - (uh - t);
+}
+template <>
+__device__ __forceinline__ void axis_u<double>(const GridDev &gd, int k, double sh, double sl, double &uh,
+                                               double &ul) {
+  uh = fma(sh + sl, gd.invD[k], gd.u0[k]);
+  ul = 0;
 }
 
-// Load node `node` of the grid as 1 + d values (value + compensation).
+// Split u = uh + ul into a node index a and a fraction f in [0, 1).
+template <typename Real>
+__device__ __forceinline__ void split_u(Real uh, Real ul, int &a, Real &f) {
+  Real fa = floor(uh);
+  a = (int)fa;
+  f = (uh - fa) + ul;  // uh - fa is exact
+  if (f < 0) {
+    a -= 1;
+    f += 1;
+  } else if (f >= 1) {
+    a += 1;
+    f -= 1;
+  }
+}
+
+// Per-step axis state, one thread per axis (k = g.t < d): interpolation
+// corners i0/i1 and weight f (a non-periodic axis clamps s into its range and
+// flags a zero gradient), and on deposit steps the stencil centre
+// i_c = floor(u + 1/2) = da + dc with the fraction df = u - da. Every s,
+// finite or not, maps to in-range indices (a non-periodic centre far outside
+// is limited to where its box holds no node).
+template <typename Real>
+__device__ __forceinline__ void axis_setup(GroupFixed<Real> *fx, int k, bool dep) {
+  const GridDev &gd = fx->wd.g;
+  const int n = gd.n[k];
+  const Real rn = (Real)n;
+  Real uh, ul;
+  axis_u<Real>(gd, k, fx->sh[k], fx->sl[k], uh, ul);
+  if (gd.periodic[k]) {
+    if (!(uh >= 0 && uh < rn)) {
+      Real q = floor(uh / rn);
+      if (!(q == q) || q > (Real)1e6 || q < (Real)-1e6) {
+        uh = 0;
+        ul = 0;
+      } else {
+        ff_add<Real>(uh, ul, -q * rn, (Real)0);
+      }
+    }
+    int a;
+    Real f;
+    split_u<Real>(uh, ul, a, f);
+    if (a >= n) a -= n;
+    if (a < 0) a += n;
+    if (a < 0 || a >= n) a = 0;
+    fx->i0[k] = a;
+    fx->i1[k] = (a + 1 == n) ? 0 : a + 1;
+    fx->f[k] = f;
+    if (dep) {
+      int c = f >= (Real)0.5 ? 1 : 0;
+      fx->da[k] = a;
+      fx->df[k] = f;
+      fx->dc[k] = c;
+      fx->ic_log[k] = (a + c == n) ? 0 : a + c;
+    }
+  } else {
+    if (dep) {
+      const int R = fx->wd.R[k];
+      Real dh = uh, dl = ul;
+      bool out = false;
+      if (!(dh >= (Real)(-R - 2))) {
+        dh = (Real)(-R - 2);
+        dl = 0;
+        out = true;
+      }
+      if (!(dh <= (Real)(n + R + 1))) {
+        dh = (Real)(n + R + 1);
+        dl = 0;
+        out = true;
+      }
+      int a;
+      Real f;
+      split_u<Real>(dh, dl, a, f);
+      int c = f >= (Real)0.5 ? 1 : 0;
+      fx->da[k] = a;
+      fx->df[k] = f;
+      fx->dc[k] = c;
+      if (out) {
+        Real raw = uh + (Real)0.5;
+        raw = raw > (Real)1e9 ? (Real)1e9 : (raw < (Real)-1e9 ? (Real)-1e9 : raw);
+        fx->ic_log[k] = (int)floor(raw == raw ? raw : (Real)0);
+      } else {
+        fx->ic_log[k] = a + c;
+      }
+    }
+    int a;
+    Real f;
+    bool cl = false;
+    if (!(uh >= 0)) {
+      a = 0;
+      f = 0;
+      cl = true;
+    } else if (uh > rn - 1 || (uh == rn - 1 && ul > 0)) {
+      a = n - 2;
+      f = 1;
+      cl = true;
+    } else {
+      split_u<Real>(uh, ul, a, f);
+      if (a > n - 2) {
+        a = n - 2;
+        f += 1;
+      }
+    }
+    if (cl) atomicOr(&fx->clamped, 1 << k);
+    fx->i0[k] = a;
+    fx->i1[k] = a + 1;
+    fx->f[k] = f;
+  }
+}
+
+// ---------------------------------------------------------------- the grid tile
+//
+// A box of T[0] x T[1] x T[2] nodes of the walker's grid, origin org[k],
+// held in shared memory with the grid's record layout. The walker's group is
+// the grid's only writer, so deposits update the tile and the grid together
+// and the tile stays an exact copy; nodes outside the box are read from and
+// written to the grid directly.
+
+// Tile-local index of node j along axis k, or -1 outside the box.
+__device__ __forceinline__ int tile_rel(const GridDev &gd, const GroupLayout &L, const int *org, int k, int j) {
+  int r = j - org[k];
+  if (gd.periodic[k]) {
+    if (r < 0) r += gd.n[k];
+    if (r >= gd.n[k]) r -= gd.n[k];
+  }
+  return (r >= 0 && r < L.T[k]) ? r : -1;
+}
+
+// Thread k: does the box cover what this step needs along axis k (the
+// interpolation cell, and the deposit box on deposit steps)? If not, move the
+// origin to centre the need and request a reload.
+template <typename Real>
+__device__ __forceinline__ void tile_check_axis(GroupFixed<Real> *fx, const GroupLayout &L, int k, bool dep) {
+  const GridDev &gd = fx->wd.g;
+  const int n = gd.n[k], T = L.T[k];
+  if (T >= n) return;  // the whole axis is resident (every node has a unique tile index)
+  int lo, hi;  // needed node range (unwrapped)
+  if (dep) {
+    const int R = fx->wd.R[k];
+    lo = fx->da[k] + fx->dc[k] - R;
+    hi = fx->da[k] + fx->dc[k] + R;
+    if (!gd.periodic[k]) {
+      lo = max(lo, 0);
+      hi = min(hi, n - 1);
+      if (lo > hi) lo = hi = fx->i0[k];  // box entirely outside: nothing to hold
+      lo = min(lo, fx->i0[k]);
+      hi = max(hi, fx->i0[k] + 1);
+    }
+  } else {
+    lo = fx->i0[k];
+    hi = fx->i0[k] + 1;
+  }
+  int span = hi - lo + 1;
+  int r = lo - fx->org[k];
+  if (gd.periodic[k]) {
+    r %= n;
+    if (r < 0) r += n;
+  }
+  if (r >= 0 && r + span <= T) return;
+  int o = lo - (T - span) / 2;
+  if (gd.periodic[k]) {
+    o %= n;
+    if (o < 0) o += n;
+  } else {
+    o = max(0, min(o, n - T));
+  }
+  fx->org[k] = o;
+  fx->reload = 1;
+}
+
+// All group threads: copy the box from the grid (cp.async, 16 B pieces),
+// one axis-0 row at a time (a row is contiguous in the grid unless it wraps
+// around a periodic axis 0, where it splits in two).
+template <typename Real>
+__device__ void tile_load(const Grp &g, GroupFixed<Real> *fx, const GroupLayout &L, unsigned char *tile) {
+  const GridDev &gd = fx->wd.g;
+  const int rb = gd.rec_bytes;
+  const int T0 = L.T[0], T1 = gd.d > 1 ? L.T[1] : 1, T2 = gd.d > 2 ? L.T[2] : 1;
+  const int n0 = gd.n[0];
+  const long long row_stride = (long long)n0 * rb, plane_stride = row_stride * (gd.d > 1 ? gd.n[1] : 1);
+  const int o0 = fx->org[0];
+  const int first = min(T0, n0 - o0);  // nodes before the wrap of axis 0
+  const int pieces_row = T0 * rb / 16, first_pieces = first * rb / 16;
+  const unsigned char *grid = reinterpret_cast<const unsigned char *>(gd.rec);
+  int j1 = fx->org[1], j2 = fx->org[2];
+  for (int r2 = 0; r2 < T2; ++r2) {
+    int jj1 = j1;
+    for (int r1 = 0; r1 < T1; ++r1) {
+      const unsigned char *row = grid + j2 * plane_stride + jj1 * row_stride;
+      unsigned char *dst = tile + ((size_t)r2 * T1 + r1) * T0 * rb;
+      for (int p = g.t; p < pieces_row; p += g.G) {
+        const unsigned char *src =
+            p < first_pieces ? row + (size_t)o0 * rb + p * 16 : row + (size_t)(p - first_pieces) * 16;
+        cp_async16(dst + p * 16, src);
+      }
+      if (++jj1 == gd.n[1]) jj1 = 0;
+    }
+    if (++j2 == gd.n[2]) j2 = 0;
+  }
+  cp_async_commit();
+  cp_async_wait_all();
+  g.sync();
+}
+
+// ---------------------------------------------------------------- node access
+
+// 1 + d values (value + compensation) of a node record at p.
 template <typename Acc>
-__device__ __forceinline__ void load_node(const GridDev &gd, long long node, Acc *v) {
+__device__ __forceinline__ void rec_values(const GridDev &gd, const unsigned char *p, Acc *v) {
   if (gd.prec == ABP_PREC_FP32_COMP) {
     if (gd.d == 1) {
-      float4 r = reinterpret_cast<const float4 *>(gd.rec)[node];
+      float4 r = *reinterpret_cast<const float4 *>(p);
       v[0] = (Acc)r.x + (Acc)r.z;
       v[1] = (Acc)r.y + (Acc)r.w;
     } else {
-      const float4 *p = reinterpret_cast<const float4 *>(gd.rec) + 2 * node;
-      float4 a = p[0], b = p[1];
+      const float4 *q = reinterpret_cast<const float4 *>(p);
+      float4 a = q[0], b = q[1];
       v[0] = (Acc)a.x + (Acc)b.x;
       v[1] = (Acc)a.y + (Acc)b.y;
       v[2] = (Acc)a.z + (Acc)b.z;
@@ -371,11 +675,11 @@ __device__ __forceinline__ void load_node(const GridDev &gd, long long node, Acc
     }
   } else {
     if (gd.d == 1) {
-      const double2 r = reinterpret_cast<const double2 *>(gd.rec)[node];
+      double2 r = *reinterpret_cast<const double2 *>(p);
       v[0] = (Acc)r.x;
       v[1] = (Acc)r.y;
     } else {
-      const D4 r = reinterpret_cast<const D4 *>(gd.rec)[node];
+      D4 r = *reinterpret_cast<const D4 *>(p);
       v[0] = (Acc)r.x;
       v[1] = (Acc)r.y;
       v[2] = (Acc)r.z;
@@ -384,99 +688,64 @@ __device__ __forceinline__ void load_node(const GridDev &gd, long long node, Acc
   }
 }
 
-// a4: multilinear interpolation of V and dV/dxi_k at s, by the first 2^d
-// lanes of warp 0 of the group (one corner per lane), combined with a fixed
-// xor-butterfly. Non-periodic axes clamp s to the range and report a zero
-// gradient along a clamped axis. Result valid in lane 0 of warp 0.
-template <typename Acc>
-__device__ __forceinline__ int interp_corners(const GridDev &gd, const double *s, int lane, Acc *out) {
-  int d = gd.d;
-  int i0[3] = {0, 0, 0}, i1[3] = {0, 0, 0}, clamped = 0;
-  Acc f[3] = {0, 0, 0};
-  for (int k = 0; k < d; ++k) {
-    double u = (s[k] - gd.lo[k]) * gd.invD[k];
-    int n = gd.n[k];
-    if (gd.periodic[k]) {
-      u = u - (double)n * floor(u / (double)n);
-      if (u >= (double)n) u -= (double)n;
-      if (u < 0) u += (double)n;
-      if (!(u >= 0.0 && u < (double)n)) u = 0.0;
-      int a = (int)floor(u);
-      if (a > n - 1) a = n - 1;
-      i0[k] = a;
-      i1[k] = (a + 1 == n) ? 0 : a + 1;
-      f[k] = (Acc)(u - (double)a);
+// Address of corner `lane` (bit k selects i1 on axis k) in the tile or grid.
+template <typename Real, bool TILE>
+__device__ __forceinline__ const unsigned char *corner_ptr(const GroupFixed<Real> *fx, const GroupLayout &L,
+                                                           const unsigned char *tile, int lane) {
+  const GridDev &gd = fx->wd.g;
+  long long node = 0, mul = 1;
+  for (int k = 0; k < gd.d; ++k) {
+    int j = ((lane >> k) & 1) ? fx->i1[k] : fx->i0[k];
+    if (TILE) {
+      int r = tile_rel(gd, L, fx->org, k, j);
+      node += mul * r;
+      mul *= L.T[k];
     } else {
-      if (!(u >= 0)) {
-        u = 0;
-        clamped |= 1 << k;
-      }
-      if (u > (double)(n - 1)) {
-        u = (double)(n - 1);
-        clamped |= 1 << k;
-      }
-      int a = (int)floor(u);
-      if (a > n - 2) a = n - 2;
-      i0[k] = a;
-      i1[k] = a + 1;
-      f[k] = (Acc)(u - (double)a);
-    }
-  }
-  Acc acc[4] = {0, 0, 0, 0};
-  if (lane < (1 << d)) {
-    Acc wgt = 1;
-    long long node = 0, mul = 1;
-    for (int k = 0; k < d; ++k) {
-      int hi = (lane >> k) & 1;
-      wgt *= hi ? f[k] : (Acc)1 - f[k];
-      node += mul * (hi ? i1[k] : i0[k]);
+      node += mul * j;
       mul *= gd.n[k];
     }
-    Acc v[4];
-    load_node<Acc>(gd, node, v);
-    for (int q = 0; q <= d; ++q) acc[q] = wgt * v[q];
   }
-  for (int q = 0; q < 4; ++q)
-    for (int o = 1; o < 8; o <<= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
-  out[0] = acc[0];
-  for (int k = 0; k < d; ++k) out[1 + k] = (clamped >> k) & 1 ? (Acc)0 : acc[1 + k];
-  return clamped ? ABP_WFLAG_OOR : 0;
+  return (TILE ? tile : reinterpret_cast<const unsigned char *>(gd.rec)) + node * gd.rec_bytes;
 }
 
-// a3 (part 1): per-axis factor tables of the stencil box around s:
-// node index j (or -1 outside a non-periodic axis), G_k = exp(-d^2 / 2 sigma^2)
-// and -d / sigma^2, d = (j_unwrapped - u) D the node-to-centre distance.
+// a2: V_b(s_t) from the grid before the deposit, in FP64, by warp 0's first
+// 2^d lanes; returns the value in lane 0.
+template <typename Real, bool TILE>
+__device__ __forceinline__ double height_interp(const GroupFixed<Real> *fx, const GroupLayout &L,
+                                                const unsigned char *tile, int lane) {
+  const GridDev &gd = fx->wd.g;
+  double acc = 0;
+  if (lane < (1 << gd.d)) {
+    double w = 1;
+    for (int k = 0; k < gd.d; ++k) {
+      double f = (double)fx->f[k];
+      w *= ((lane >> k) & 1) ? f : 1.0 - f;
+    }
+    double v[4];
+    rec_values<double>(gd, corner_ptr<Real, TILE>(fx, L, tile, lane), v);
+    acc = w * v[0];
+  }
+  for (int o = 1; o < 8; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  return acc;
+}
+
+// a3 (part 1): per-axis factor tables of the stencil box around s: node index
+// j = i_c - R + o (or -1 outside a non-periodic axis), G_k = exp(-d^2 / 2 sigma^2)
+// and -d / sigma^2, d = (j - u) D the node-to-centre distance, formed as
+// ((dc - R + o) - df) D from the small exact parts of u.
 template <typename Real>
 __device__ void build_tables(const Grp &g, GroupFixed<Real> *fx) {
   const WalkerDev &wd = fx->wd;
   const GridDev &gd = wd.g;
-  if (g.t < gd.d) {
-    int k = g.t;
-    double u = axis_u(gd, k, fx->s[k], fx->wd.R[k]);
-    int ic = (int)floor(u + 0.5);
-    if (!gd.periodic[k]) {
-      double raw = (fx->s[k] - gd.lo[k]) * gd.invD[k] + 0.5;
-      raw = raw > 1e9 ? 1e9 : (raw < -1e9 ? -1e9 : raw);
-      fx->ic_log[k] = (int)floor(raw == raw ? raw : 0.0);
-    }
-    if (gd.periodic[k] && ic >= gd.n[k]) {
-      // u in [n - 1/2, n): the nearest node is node 0, one period up
-      ic -= gd.n[k];
-      u -= gd.n[k];
-    }
-    fx->u[k] = u;
-    fx->ic[k] = ic;
-    if (gd.periodic[k]) fx->ic_log[k] = ic;
-  }
-  g.sync();
   for (int k = 0; k < gd.d; ++k) {
-    int R = wd.R[k], span = 2 * R + 1, n = gd.n[k];
-    double u = fx->u[k];
-    int ic = fx->ic[k];
-    Real i2 = (Real)wd.inv2s2[k], is2 = (Real)wd.invs2[k];
+    const int R = wd.R[k], span = 2 * R + 1, n = gd.n[k];
+    const int a = fx->da[k], c = fx->dc[k];
+    const Real f = fx->df[k], D = (Real)gd.D[k];
+    const Real i2 = (Real)wd.inv2s2[k], is2 = (Real)wd.invs2[k];
     for (int o = g.t; o < span; o += g.G) {
-      int j = ic - R + o;
-      Real dist = (Real)(((double)j - u) * gd.D[k]);
+      int rel = c - R + o;
+      int j = a + rel;
+      Real dist = ((Real)rel - f) * D;
       int jj = j;
       if (gd.periodic[k]) {
         jj = j % n;
@@ -499,75 +768,185 @@ __device__ __forceinline__ void two_sum_add(float &s, float &c, float x) {
   c = __fadd_rn(c, e);
 }
 
+// Apply h G (and its derivative terms) to one node record held in two
+// 16-byte halves a, b (b unused for 16-byte records).
+template <typename Real>
+__device__ __forceinline__ void rmw_regs(int d, float4 &a, float4 &b, Real G, Real d0, Real d1, Real d2);
+template <>
+__device__ __forceinline__ void rmw_regs<float>(int d, float4 &a, float4 &b, float G, float d0, float d1, float d2) {
+  if (d == 1) {
+    two_sum_add(a.x, a.z, G);
+    two_sum_add(a.y, a.w, __fmul_rn(G, d0));
+  } else {
+    two_sum_add(a.x, b.x, G);
+    two_sum_add(a.y, b.y, __fmul_rn(G, d0));
+    two_sum_add(a.z, b.z, __fmul_rn(G, d1));
+    if (d > 2) two_sum_add(a.w, b.w, __fmul_rn(G, d2));
+  }
+}
+template <>
+__device__ __forceinline__ void rmw_regs<double>(int d, float4 &a, float4 &b, double G, double d0, double d1,
+                                                 double d2) {
+  union U {
+    float4 f;
+    double2 v;
+  };
+  U ua, ub;
+  ua.f = a;
+  ub.f = b;
+  ua.v.x += G;
+  ua.v.y += G * d0;
+  if (d > 1) ub.v.x += G * d1;
+  if (d > 2) ub.v.y += G * d2;
+  a = ua.f;
+  b = ub.f;
+}
+
+template <typename Real>
+__device__ __forceinline__ void rmw_node(const GridDev &gd, unsigned char *p, Real G, Real d0, Real d1, Real d2) {
+  float4 *q = reinterpret_cast<float4 *>(p);
+  float4 a = q[0], b = gd.rec_bytes == 32 ? q[1] : make_float4(0, 0, 0, 0);
+  rmw_regs<Real>(gd.d, a, b, G, d0, d1, d2);
+  q[0] = a;
+  if (gd.rec_bytes == 32) q[1] = b;
+}
+
 // a3 (part 2): add h G and h G (-d_k / sigma_k^2) at every in-range node of
 // the box. FP32_COMP grids accumulate with two-sum compensation; FP64 grids
-// add directly. Each walker's grid has a single writer (its group).
-template <typename Real>
-__device__ void deposit_stencil(const Grp &g, GroupFixed<Real> *fx) {
+// add directly. With a tile, nodes inside it are updated in shared memory and
+// the result stored to the grid; other nodes are updated in the grid.
+template <typename Real, bool TILE>
+__device__ void deposit_stencil(const Grp &g, GroupFixed<Real> *fx, const GroupLayout &L, unsigned char *tile) {
   const WalkerDev &wd = fx->wd;
   const GridDev &gd = wd.g;
-  const int d = gd.d;
+  const int d = gd.d, rb = gd.rec_bytes;
   const int s0 = 2 * wd.R[0] + 1;
   const int s1 = d > 1 ? 2 * wd.R[1] + 1 : 1;
   const int s2 = d > 2 ? 2 * wd.R[2] + 1 : 1;
   const int total = s0 * s1 * s2;
   const Real h = fx->hf;
   const long long n0 = gd.n[0], n01 = (long long)gd.n[0] * (d > 1 ? gd.n[1] : 1);
-  for (int idx = g.t; idx < total; idx += g.G) {
-    int o0 = idx % s0;
-    int r = idx / s0;
-    int o1 = r % s1;
-    int o2 = r / s1;
-    int j0 = fx->tabJ[0][o0];
-    int j1 = d > 1 ? fx->tabJ[1][o1] : 0;
-    int j2 = d > 2 ? fx->tabJ[2][o2] : 0;
-    if ((j0 | j1 | j2) < 0) continue;
-    Real G = h * fx->tabG[0][o0];
-    if (d > 1) G = G * fx->tabG[1][o1];
-    if (d > 2) G = G * fx->tabG[2][o2];
-    long long node = j0 + n0 * j1 + n01 * j2;
-    if constexpr (sizeof(Real) == 4) {
-      if (d == 1) {
-        float4 *p = reinterpret_cast<float4 *>(gd.rec) + node;
-        float4 v = *p;
-        two_sum_add(v.x, v.z, G);
-        two_sum_add(v.y, v.w, __fmul_rn(G, fx->tabD[0][o0]));
-        *p = v;
-      } else {
-        float4 *p = reinterpret_cast<float4 *>(gd.rec) + 2 * node;
-        float4 a = p[0], b = p[1];
-        two_sum_add(a.x, b.x, G);
-        two_sum_add(a.y, b.y, __fmul_rn(G, fx->tabD[0][o0]));
-        two_sum_add(a.z, b.z, __fmul_rn(G, fx->tabD[1][o1]));
-        if (d > 2) two_sum_add(a.w, b.w, __fmul_rn(G, fx->tabD[2][o2]));
-        p[0] = a;
-        p[1] = b;
+  unsigned char *grid = reinterpret_cast<unsigned char *>(gd.rec);
+  // thread t visits box nodes t, t + G, ... (axis 0 fastest); the box index
+  // (o0, o1, o2) advances incrementally instead of by division
+  int o0 = g.t, o1 = 0, o2 = 0;
+  while (o0 >= s0) {
+    o0 -= s0;
+    if (++o1 == s1) {
+      o1 = 0;
+      ++o2;
+    }
+  }
+  const int step0 = g.G % s0, step1 = g.G / s0;
+  auto advance = [&]() {
+    o0 += step0;
+    o1 += step1;
+    if (o0 >= s0) {
+      o0 -= s0;
+      ++o1;
+    }
+    while (o1 >= s1) {
+      o1 -= s1;
+      ++o2;
+    }
+  };
+  // UNR nodes per round: their records are loaded before any is updated, so
+  // the grid reads of a round overlap
+  constexpr int UNR = 4;
+  for (int base = g.t; base < total; base += UNR * g.G) {
+    unsigned char *ptr[UNR];
+    bool intile[UNR];
+    Real Gv[UNR], d0v[UNR], d1v[UNR], d2v[UNR];
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      ptr[u] = nullptr;
+      intile[u] = false;
+      Gv[u] = d0v[u] = d1v[u] = d2v[u] = 0;
+      if (u > 0) advance();
+      if (base + u * g.G >= total) continue;
+      int j0 = fx->tabJ[0][o0];
+      int j1 = d > 1 ? fx->tabJ[1][o1] : 0;
+      int j2 = d > 2 ? fx->tabJ[2][o2] : 0;
+      if ((j0 | j1 | j2) < 0) continue;
+      Real G = h * fx->tabG[0][o0];
+      if (d > 1) G = G * fx->tabG[1][o1];
+      if (d > 2) G = G * fx->tabG[2][o2];
+      Gv[u] = G;
+      d0v[u] = fx->tabD[0][o0];
+      d1v[u] = d > 1 ? fx->tabD[1][o1] : (Real)0;
+      d2v[u] = d > 2 ? fx->tabD[2][o2] : (Real)0;
+      ptr[u] = grid + (j0 + n0 * j1 + n01 * j2) * rb;
+      if (TILE) {
+        int t0 = tile_rel(gd, L, fx->org, 0, j0);
+        int t1 = d > 1 ? tile_rel(gd, L, fx->org, 1, j1) : 0;
+        int t2 = d > 2 ? tile_rel(gd, L, fx->org, 2, j2) : 0;
+        if ((t0 | t1 | t2) >= 0) {
+          unsigned char *tp = tile + (t0 + L.T[0] * (t1 + (d > 1 ? L.T[1] : 1) * t2)) * rb;
+          rmw_node<Real>(gd, tp, G, d0v[u], d1v[u], d2v[u]);
+          const float4 *src = reinterpret_cast<const float4 *>(tp);
+          float4 *dst = reinterpret_cast<float4 *>(ptr[u]);
+          dst[0] = src[0];
+          if (rb == 32) dst[1] = src[1];
+          intile[u] = true;
+        }
       }
-    } else {
-      if (d == 1) {
-        double2 *p = reinterpret_cast<double2 *>(gd.rec) + node;
-        double2 v = *p;
-        v.x += G;
-        v.y += G * fx->tabD[0][o0];
-        *p = v;
-      } else {
-        D4 *p = reinterpret_cast<D4 *>(gd.rec) + node;
-        D4 v = *p;
-        v.x += G;
-        v.y += G * fx->tabD[0][o0];
-        v.z += G * fx->tabD[1][o1];
-        if (d > 2) v.w += G * fx->tabD[2][o2];
-        *p = v;
+    }
+    advance();  // to this thread's first node of the next round
+    // grid nodes outside the tile: load all, then update all
+    float4 ra[UNR], rbv[UNR];
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      if (ptr[u] && !intile[u]) {
+        const float4 *q = reinterpret_cast<const float4 *>(ptr[u]);
+        ra[u] = q[0];
+        rbv[u] = rb == 32 ? q[1] : make_float4(0, 0, 0, 0);
       }
+    }
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      if (!ptr[u] || intile[u]) continue;
+      rmw_regs<Real>(d, ra[u], rbv[u], Gv[u], d0v[u], d1v[u], d2v[u]);
+      float4 *q = reinterpret_cast<float4 *>(ptr[u]);
+      q[0] = ra[u];
+      if (rb == 32) q[1] = rbv[u];
     }
   }
 }
 
-// ---------------------------------------------------------------- a5
+// ---------------------------------------------------------------- a4 + a5
 
-// F_i = - sum_k dV/ds_k ds_k/dx_i into the force accumulators fs (zeroed by
-// the caller). Lists are unique, and each list is a separate phase, so every
-// accumulator is updated in a fixed order.
+// a4: V and dV/ds_k at s after the deposit, by warp 0's first 2^d lanes,
+// combined with a fixed xor-butterfly; a clamped axis gets a zero gradient.
+template <typename Real, bool TILE>
+__device__ void interp_step(const Grp &g, GroupFixed<Real> *fx, const GroupLayout &L, const unsigned char *tile) {
+  const GridDev &gd = fx->wd.g;
+  if (g.warp == 0) {
+    Real acc[4] = {0, 0, 0, 0};
+    if (g.lane < (1 << gd.d)) {
+      Real w = 1;
+      for (int k = 0; k < gd.d; ++k) w *= ((g.lane >> k) & 1) ? fx->f[k] : (Real)1 - fx->f[k];
+      Real v[4];
+      rec_values<Real>(gd, corner_ptr<Real, TILE>(fx, L, tile, g.lane), v);
+      for (int q = 0; q <= gd.d; ++q) acc[q] = w * v[q];
+    }
+    for (int q = 0; q < 4; ++q)
+      for (int o = 1; o < 8; o <<= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+    if (g.lane == 0) {
+      fx->V = acc[0];
+      for (int k = 0; k < gd.d; ++k) {
+        Real dv = ((fx->clamped >> k) & 1) ? (Real)0 : acc[1 + k];
+        fx->dvds[k] = dv;
+        fx->dV[k] = dv;
+      }
+      if (fx->clamped) fx->flags |= ABP_WFLAG_OOR;
+    }
+  }
+  g.sync();
+}
+
+// a5: F_i = - sum_k dV/ds_k ds_k/dx_i into the force accumulators fs (zeroed
+// by the caller). Lists are unique, and each list is a separate phase, so
+// every accumulator is updated in a fixed order.
 template <typename Real>
 __device__ void scatter_forces(const Grp &g, GroupFixed<Real> *fx, typename Rec4<Real>::T *fs,
                                unsigned char *cnmem) {
@@ -578,20 +957,22 @@ __device__ void scatter_forces(const Grp &g, GroupFixed<Real> *fx, typename Rec4
   unsigned char *cur = cnmem;
   for (int k = 0; k < d; ++k) {
     const CvDev &c = wd.cv[k];
+    const int32_t *ia = fx->ia[k], *ib = fx->ib[k];
     Real dv = fx->dvds[k];
     if (c.type == ABP_CV_COM_DIST) {
+      const Real *wa = fx->wa[k], *wb = fx->wb[k];
       Real ux = fx->com_u[k][0] * dv, uy = fx->com_u[k][1] * dv, uz = fx->com_u[k][2] * dv;
       for (int i = g.t; i < c.na; i += g.G) {
-        Real w = sizeof(Real) == 4 ? (Real)c.wa[i] : (Real)c.wa64[i];
-        R4 &f = fs[__ldg(c.ia + i)];
+        Real w = wa[i];
+        R4 &f = fs[ia[i]];
         f.x += w * ux;
         f.y += w * uy;
         f.z += w * uz;
       }
       g.sync();
       for (int i = g.t; i < c.nb; i += g.G) {
-        Real w = sizeof(Real) == 4 ? (Real)c.wb[i] : (Real)c.wb64[i];
-        R4 &f = fs[__ldg(c.ib + i)];
+        Real w = wb[i];
+        R4 &f = fs[ib[i]];
         f.x -= w * ux;
         f.y -= w * uy;
         f.z -= w * uz;
@@ -599,7 +980,7 @@ __device__ void scatter_forces(const Grp &g, GroupFixed<Real> *fx, typename Rec4
       g.sync();
     } else if (c.type == ABP_CV_DIHEDRAL) {
       if (g.t < 4) {
-        R4 &f = fs[__ldg(c.ia + g.t)];
+        R4 &f = fs[ia[g.t]];
         f.x -= dv * fx->dih_g[k][g.t][0];
         f.y -= dv * fx->dih_g[k][g.t][1];
         f.z -= dv * fx->dih_g[k][g.t][2];
@@ -609,7 +990,7 @@ __device__ void scatter_forces(const Grp &g, GroupFixed<Real> *fx, typename Rec4
       const R4 *jA = reinterpret_cast<const R4 *>(cur);
       const R4 *jB = jA + c.na;
       for (int i = g.t; i < c.na; i += g.G) {
-        R4 &f = fs[__ldg(c.ia + i)];
+        R4 &f = fs[ia[i]];
         R4 j = jA[i];
         f.x -= dv * j.x;
         f.y -= dv * j.y;
@@ -617,15 +998,14 @@ __device__ void scatter_forces(const Grp &g, GroupFixed<Real> *fx, typename Rec4
       }
       g.sync();
       for (int i = g.t; i < c.nb; i += g.G) {
-        R4 &f = fs[__ldg(c.ib + i)];
+        R4 &f = fs[ib[i]];
         R4 j = jB[i];
         f.x -= dv * j.x;
         f.y -= dv * j.y;
         f.z -= dv * j.z;
       }
       g.sync();
-      int lig = (g.nwarps * c.na * 3 * (int)sizeof(Real) + 31) & ~31;
-      cur += (c.na + c.nb) * rsz + lig;
+      cur += (c.na + c.nb) * rsz + align32(g.nwarps * c.na * 3 * (int)sizeof(Real));
     }
   }
 }

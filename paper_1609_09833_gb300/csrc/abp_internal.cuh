@@ -35,6 +35,10 @@ struct GridDev {
   double D[3];       // node spacing
   double invD[3];
   double L[3];       // axis length (periodic wrap)
+  double u0[3];      // -lo / D: u = s * invD + u0
+  double inv_n[3];   // 1 / n
+  float invD_h[3], invD_l[3];  // invD and u0 as hi + lo floats (FP32 grids)
+  float u0_h[3], u0_l[3];
   int prec;          // ABP_PREC_*
   int rec_bytes;     // bytes per node record
   long long nodes;
@@ -87,20 +91,74 @@ struct DevCounters {
   int pad[31];
 };
 
-// Bytes of dynamic shared memory one walker group needs beyond its fixed
-// part, for a walker with these CVs (computed identically on host and
-// device). rsz = bytes of one 4-component record (16 for float, 32 double).
-__host__ __device__ inline int group_dyn_bytes(int natoms, const CvDev *cv, int ncv, int nwarps, int rsz) {
-  int b = 2 * natoms * rsz;  // coordinates + force accumulators
-  int real = rsz / 4;
-  for (int k = 0; k < ncv; ++k) {
-    if (cv[k].type == ABP_CV_COORD) {
-      b += (cv[k].na + cv[k].nb) * rsz;                       // dCN/dx per list entry
-      int lig = nwarps * cv[k].na * 3 * real;                 // per-warp ligand partials
-      b += (lig + 31) & ~31;
+__host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
+__host__ __device__ inline int align32(int x) { return (x + 31) & ~31; }
+
+// Shared-memory layout of one walker group (computed identically on host and
+// device). Offsets are bytes from the start of the group's dynamic part.
+//   xs0, xs1  coordinates of two steps (the next step's arrive by cp.async)
+//   fs        force accumulators
+//   lists     per-CV atom index lists (+ COM weights)
+//   cn        per COORD CV: dCN/dx per list entry and per-warp partials
+//   tile      optional copy of a box of the walker's grid (node records)
+struct GroupLayout {
+  int xs0, xs1, fs, lists, cn, tile, total;
+  int T[3];        // tile nodes per axis (all 0 = no tile)
+  int tile_nodes;
+};
+
+// Tile box: every axis spans min(n, 2R + 1 + 2m) nodes for the largest margin
+// m <= 24 that fits the byte budget; no tile if even m = 1 does not fit.
+__host__ __device__ inline void tile_dims(const GridDev &g, const int *R, int budget, int *T) {
+  T[0] = T[1] = T[2] = 0;
+  if (budget <= 0) return;
+  for (int m = 24; m >= 1; --m) {
+    long long nodes = 1;
+    int t[3] = {1, 1, 1};
+    for (int k = 0; k < g.d; ++k) {
+      int want = 2 * R[k] + 1 + 2 * m;
+      t[k] = want < g.n[k] ? want : g.n[k];
+      nodes *= t[k];
+    }
+    if (nodes * g.rec_bytes <= budget) {
+      for (int k = 0; k < g.d; ++k) T[k] = t[k];
+      return;
     }
   }
-  return b;
+}
+
+__host__ __device__ inline GroupLayout group_layout(int natoms, const CvDev *cv, const GridDev &g, const int *R,
+                                                    int nwarps, int rsz, int tile_budget) {
+  GroupLayout L;
+  const int real = rsz / 4;
+  int off = 0;
+  L.xs0 = off;
+  off += natoms * rsz;
+  L.xs1 = off;
+  off += natoms * rsz;
+  L.fs = off;
+  off += natoms * rsz;
+  L.lists = off;
+  for (int k = 0; k < g.d; ++k) {
+    off += align16((cv[k].na + cv[k].nb) * 4);
+    if (cv[k].type == ABP_CV_COM_DIST) off += align16((cv[k].na + cv[k].nb) * real);
+  }
+  off = align32(off);
+  L.cn = off;
+  for (int k = 0; k < g.d; ++k)
+    if (cv[k].type == ABP_CV_COORD) off += (cv[k].na + cv[k].nb) * rsz + align32(nwarps * cv[k].na * 3 * real);
+  off = align32(off);
+  L.tile = off;
+  int budget = tile_budget - off;
+  tile_dims(g, R, budget, L.T);
+  L.tile_nodes = 0;
+  if (L.T[0] > 0) {
+    L.tile_nodes = 1;
+    for (int k = 0; k < g.d; ++k) L.tile_nodes *= L.T[k];
+    off += L.tile_nodes * g.rec_bytes;
+  }
+  L.total = align32(off);
+  return L;
 }
 
 }  // namespace abp

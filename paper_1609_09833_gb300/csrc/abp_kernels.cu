@@ -1,6 +1,9 @@
 // abp_kernels.cu -- the kernels of the force call and their launchers:
-//   k_run      fused batched form: one walker group per walker, every step
-//              a1..a5 for nsteps consecutive MD steps in one launch;
+//   k_run      fused batched form: one walker group per walker, steps a1..a5
+//              for nsteps consecutive MD steps in one launch; the next step's
+//              coordinates stream into shared memory (cp.async) while the
+//              current step runs, and an optional shared-memory tile of the
+//              walker's grid serves the interpolation and the deposit;
 //   k_plain_*  plain form: CV, deposit and interpolation/force as separate
 //              single-walker launches (the comparison point);
 //   k_deliver  copies each walker's force buffer to the caller (abp_forces).
@@ -26,17 +29,54 @@ __device__ __forceinline__ void copy_desc(const Grp &g, WalkerDev *dst, const Wa
 }
 
 template <typename Real>
+__device__ __forceinline__ GroupLayout layout_of(const GroupFixed<Real> *fx, int nwarps, int tile_budget) {
+  return group_layout(fx->wd.natoms, fx->wd.cv, fx->wd.g, fx->wd.R, nwarps, (int)sizeof(typename Rec4<Real>::T),
+                      tile_budget);
+}
+
+// Copy each CV's atom lists (and COM weights as Real) into shared memory and
+// point fx->ia/ib/wa/wb at them. Caller syncs.
+template <typename Real>
+__device__ void setup_lists(const Grp &g, GroupFixed<Real> *fx, unsigned char *mem) {
+  const WalkerDev &wd = fx->wd;
+  unsigned char *cur = mem;
+  for (int k = 0; k < wd.g.d; ++k) {
+    const CvDev &c = wd.cv[k];
+    int32_t *ia = reinterpret_cast<int32_t *>(cur);
+    int32_t *ib = ia + c.na;
+    for (int i = g.t; i < c.na; i += g.G) ia[i] = c.ia[i];
+    for (int i = g.t; i < c.nb; i += g.G) ib[i] = c.ib[i];
+    cur += align16((c.na + c.nb) * 4);
+    Real *wa = nullptr, *wb = nullptr;
+    if (c.type == ABP_CV_COM_DIST) {
+      wa = reinterpret_cast<Real *>(cur);
+      wb = wa + c.na;
+      for (int i = g.t; i < c.na; i += g.G) wa[i] = sizeof(Real) == 4 ? (Real)c.wa[i] : (Real)c.wa64[i];
+      for (int i = g.t; i < c.nb; i += g.G) wb[i] = sizeof(Real) == 4 ? (Real)c.wb[i] : (Real)c.wb64[i];
+      cur += align16((c.na + c.nb) * (int)sizeof(Real));
+    }
+    if (g.t == 0) {
+      fx->ia[k] = ia;
+      fx->ib[k] = ib;
+      fx->wa[k] = wa;
+      fx->wb[k] = wb;
+    }
+  }
+}
+
+template <typename Real>
 __device__ __forceinline__ unsigned char *cn_slot(unsigned char *cnmem, const WalkerDev &wd, int k, int nwarps) {
   int rsz = (int)sizeof(typename Rec4<Real>::T);
   unsigned char *cur = cnmem;
   for (int q = 0; q < k; ++q) {
     const CvDev &c = wd.cv[q];
-    if (c.type == ABP_CV_COORD) cur += (c.na + c.nb) * rsz + ((nwarps * c.na * 3 * (int)sizeof(Real) + 31) & ~31);
+    if (c.type == ABP_CV_COORD) cur += (c.na + c.nb) * rsz + align32(nwarps * c.na * 3 * (int)sizeof(Real));
   }
   return cur;
 }
 
-// a1 for every CV of the walker (coordinates already in xs).
+// a1 for every CV of the walker (coordinates in xs); ends with a group sync.
+// CVs write disjoint state, so no sync is needed between them.
 template <typename Real>
 __device__ void eval_cvs(const Grp &g, GroupFixed<Real> *fx, const typename Rec4<Real>::T *xs, unsigned char *cnmem) {
   using R4 = typename Rec4<Real>::T;
@@ -52,23 +92,25 @@ __device__ void eval_cvs(const Grp &g, GroupFixed<Real> *fx, const typename Rec4
       R4 *jA = reinterpret_cast<R4 *>(slot);
       R4 *jB = jA + c.na;
       Real *lig = reinterpret_cast<Real *>(jB + c.nb);
+      g.sync();
       cv_coord<Real>(g, fx, k, xs, jA, jB, lig);
     }
-    g.sync();
   }
+  g.sync();
 }
 
-// a2 + a3: height from the grid before the deposit, then the stencil.
-template <typename Real>
-__device__ void deposit_step(const Grp &g, GroupFixed<Real> *fx, long long step, const DepositLog &log) {
+// a2 + a3: tables, height from the grid before the deposit, the stencil.
+template <typename Real, bool TILE>
+__device__ void deposit_step(const Grp &g, GroupFixed<Real> *fx, const GroupLayout &L, unsigned char *tile,
+                             long long step, const DepositLog &log) {
   const WalkerDev &wd = fx->wd;
   build_tables<Real>(g, fx);
   if (g.warp == 0) {
-    double out[4];
-    interp_corners<double>(wd.g, fx->s, g.lane, out);
+    double V0 = height_interp<Real, TILE>(fx, L, tile, g.lane);
     if (g.lane == 0) {
-      double h = wd.w * exp(-out[0] * wd.inv_dT);
+      double h = wd.w * exp(-V0 * wd.inv_dT);
       fx->hf = (Real)h;
+      fx->flags |= ABP_WFLAG_DEPOSIT;
       if (log.rec) {
         unsigned long long slot = atomicAdd(log.count, 1ull);
         if (slot < log.cap) {
@@ -77,7 +119,7 @@ __device__ void deposit_step(const Grp &g, GroupFixed<Real> *fx, long long step,
           r.walker_id = wd.id;
           for (int k = 0; k < 3; ++k) {
             r.ic[k] = k < wd.g.d ? fx->ic_log[k] : 0;
-            r.s[k] = k < wd.g.d ? fx->s[k] : 0.0;
+            r.s[k] = k < wd.g.d ? (double)fx->sh[k] + (double)fx->sl[k] : 0.0;
           }
           r.height = h;
           log.rec[slot] = r;
@@ -86,39 +128,19 @@ __device__ void deposit_step(const Grp &g, GroupFixed<Real> *fx, long long step,
     }
   }
   g.sync();
-  deposit_stencil<Real>(g, fx);
-  g.sync();
-}
-
-// a4: V and dV/ds at s after the deposit (warp 0), broadcast via fx.
-template <typename Real>
-__device__ void interp_step(const Grp &g, GroupFixed<Real> *fx) {
-  const WalkerDev &wd = fx->wd;
-  if (g.warp == 0) {
-    Real out[4];
-    int fl = interp_corners<Real>(wd.g, fx->s, g.lane, out);
-    if (g.lane == 0) {
-      fx->V = (double)out[0];
-      for (int k = 0; k < wd.g.d; ++k) {
-        fx->dvds[k] = out[1 + k];
-        fx->dV[k] = (double)out[1 + k];
-      }
-      fx->flags |= fl;
-    }
-  }
+  deposit_stencil<Real, TILE>(g, fx, L, tile);
   g.sync();
 }
 
 template <typename Real>
-__device__ void write_state(const Grp &g, GroupFixed<Real> *fx, long long step) {
-  if (g.t != 0) return;
+__device__ void write_state(GroupFixed<Real> *fx, long long step) {
   const WalkerDev &wd = fx->wd;
   WalkerState st;
   for (int k = 0; k < 3; ++k) {
-    st.s[k] = k < wd.g.d ? fx->s[k] : 0.0;
-    st.dV[k] = k < wd.g.d ? fx->dV[k] : 0.0;
+    st.s[k] = k < wd.g.d ? (double)fx->sh[k] + (double)fx->sl[k] : 0.0;
+    st.dV[k] = k < wd.g.d ? (double)fx->dV[k] : 0.0;
   }
-  st.V = fx->V;
+  st.V = (double)fx->V;
   st.flags = fx->flags;
   st.pad = 0;
   st.step = step;
@@ -130,73 +152,99 @@ __device__ __forceinline__ bool finite_rec(const typename Rec4<Real>::T &p) {
   return isfinite(p.x) && isfinite(p.y) && isfinite(p.z);
 }
 
-// nsteps MD steps of one walker (steps a1..a5 each), by one group.
 template <typename Real>
-__device__ void walker_steps(const Grp &g, GroupFixed<Real> *fx, unsigned char *dyn, const RunArgs &a, int widx) {
+__device__ __forceinline__ void store_force(typename Rec4<Real>::T *fo, const typename Rec4<Real>::T &f, int mode) {
+  if (mode == ABP_FORCES_ACCUMULATE) {
+    typename Rec4<Real>::T o = *fo;
+    o.x += f.x;
+    o.y += f.y;
+    o.z += f.z;
+    *fo = o;
+  } else {
+    *fo = make_rec<Real>(f.x, f.y, f.z, 0);
+  }
+}
+
+// nsteps MD steps of one walker (steps a1..a5 each), by one group.
+template <typename Real, bool TILE>
+__device__ void walker_steps(const Grp &g, GroupFixed<Real> *fx, unsigned char *dyn, const GroupLayout &L,
+                             const RunArgs &a, int widx) {
   using R4 = typename Rec4<Real>::T;
   const WalkerDev &wd = fx->wd;
-  const int natoms = wd.natoms;
-  R4 *xs = reinterpret_cast<R4 *>(dyn);
-  R4 *fs = xs + natoms;
-  unsigned char *cnmem = reinterpret_cast<unsigned char *>(fs + natoms);
+  const int natoms = wd.natoms, d = wd.g.d;
+  R4 *xb[2] = {reinterpret_cast<R4 *>(dyn + L.xs0), reinterpret_cast<R4 *>(dyn + L.xs1)};
+  R4 *fs = reinterpret_cast<R4 *>(dyn + L.fs);
+  unsigned char *cnmem = dyn + L.cn;
+  unsigned char *tile = dyn + L.tile;
   const R4 *cin = reinterpret_cast<const R4 *>(a.coords);
   R4 *fout = a.forces ? reinterpret_cast<R4 *>(a.forces) : reinterpret_cast<R4 *>(wd.fbuf);
   const long long coff = a.coff[widx];
   const long long foff = a.forces ? a.foff[widx] : 0;
   const int mode = a.forces ? a.mode : ABP_FORCES_OVERWRITE;
+  const int pieces = natoms * (int)(sizeof(R4) / 16);
+  auto prefetch = [&](int t, R4 *dst) {
+    const unsigned char *src = reinterpret_cast<const unsigned char *>(cin + coff + (long long)t * a.cstride);
+    for (int p = g.t; p < pieces; p += g.G) cp_async16(reinterpret_cast<unsigned char *>(dst) + p * 16, src + p * 16);
+    cp_async_commit();
+  };
+  long long rem = a.step0 % wd.stride;
+  long long next_dep = rem == 0 ? 0 : wd.stride - rem;  // step index (t) of the next deposit
+  if (TILE && g.t == 0) {
+    fx->reload = 1;
+    for (int k = 0; k < kMaxCv; ++k) fx->org[k] = 0;
+  }
+  prefetch(0, xb[0]);
   for (int t = 0; t < a.nsteps; ++t) {
     const long long step = a.step0 + t;
-    const R4 *xin = cin + coff + (long long)t * a.cstride;
+    R4 *xs = xb[t & 1];
+    cp_async_wait_all();
+    g.sync();
+    const bool dep = (t == next_dep);
+    if (dep) next_dep += wd.stride;
     R4 *fo = fout + foff + (a.forces ? (long long)t * a.fstride : 0);
     int bad = 0;
     for (int i = g.t; i < natoms; i += g.G) {
-      R4 p = xin[i];
-      xs[i] = p;
+      bad |= finite_rec<Real>(xs[i]) ? 0 : 1;
       fs[i] = make_rec<Real>(0, 0, 0, 0);
-      bad |= finite_rec<Real>(p) ? 0 : 1;
     }
-    if (g.t == 0) fx->flags = 0;
-    Real bv[1] = {(Real)bad};
-    grp_sum<1>(g, bv, fx->red);
-    g.sync();
-    if (bv[0] != 0) {
+    if (g.t == 0) {
+      fx->flags = 0;
+      fx->clamped = 0;
+    }
+    if (grp_any<Real>(g, fx, bad)) {
       // non-finite coordinates: no deposit, zero bias force, state kept
+      if (t + 1 < a.nsteps) prefetch(t + 1, xb[(t + 1) & 1]);
       if (mode == ABP_FORCES_OVERWRITE)
         for (int i = g.t; i < natoms; i += g.G) fo[i] = make_rec<Real>(0, 0, 0, 0);
       if (g.t == 0) {
         wd.state->flags = ABP_WFLAG_NONFINITE;
         atomicAdd(&a.ctr->nonfinite, 1);
       }
-      g.sync();
       continue;
     }
-    eval_cvs<Real>(g, fx, xs, cnmem);
-    const bool dep = (step % wd.stride) == 0;
-    if (dep) {
-      deposit_step<Real>(g, fx, step, a.log);
-      if (g.t == 0) fx->flags |= ABP_WFLAG_DEPOSIT;
-    }
-    interp_step<Real>(g, fx);
-    scatter_forces<Real>(g, fx, fs, cnmem);
-    for (int i = g.t; i < natoms; i += g.G) {
-      R4 f = fs[i];
-      if (mode == ABP_FORCES_ACCUMULATE) {
-        R4 o = fo[i];
-        o.x += f.x;
-        o.y += f.y;
-        o.z += f.z;
-        fo[i] = o;
-      } else {
-        fo[i] = make_rec<Real>(f.x, f.y, f.z, 0);
-      }
-    }
-    write_state<Real>(g, fx, step);
     g.sync();
+    eval_cvs<Real>(g, fx, xs, cnmem);
+    // the next step's coordinates stream in while this step finishes
+    if (t + 1 < a.nsteps) prefetch(t + 1, xb[(t + 1) & 1]);
+    if (g.t < d) {
+      axis_setup<Real>(fx, g.t, dep);
+      if (TILE) tile_check_axis<Real>(fx, L, g.t, dep);
+    }
+    g.sync();
+    if (TILE && fx->reload) {
+      tile_load<Real>(g, fx, L, tile);
+      if (g.t == 0) fx->reload = 0;
+    }
+    if (dep) deposit_step<Real, TILE>(g, fx, L, tile, step, a.log);
+    interp_step<Real, TILE>(g, fx, L, tile);
+    scatter_forces<Real>(g, fx, fs, cnmem);
+    for (int i = g.t; i < natoms; i += g.G) store_force<Real>(fo + i, fs[i], mode);
+    if (t == a.nsteps - 1 && g.t == 0) write_state<Real>(fx, step);
   }
 }
 
-template <typename Real>
-__global__ void __launch_bounds__(256) k_run(RunArgs a) {
+template <typename Real, bool TILE>
+__global__ void __launch_bounds__(256, 1) k_run(RunArgs a) {
   extern __shared__ __align__(32) unsigned char smem[];
   const int gid = threadIdx.x / a.G;
   const int slot = blockIdx.x * a.groups_per_cta + gid;
@@ -210,10 +258,17 @@ __global__ void __launch_bounds__(256) k_run(RunArgs a) {
   g.nwarps = a.G >> 5;
   unsigned char *base = smem + (size_t)gid * a.group_bytes;
   GroupFixed<Real> *fx = reinterpret_cast<GroupFixed<Real> *>(base);
+  unsigned char *dyn = base + fixed_bytes<Real>();
   const TableEntry te = a.table[slot];
   copy_desc<Real>(g, &fx->wd, te.wd);
   g.sync();
-  walker_steps<Real>(g, fx, base + fixed_bytes<Real>(), a, te.idx);
+  const GroupLayout L = layout_of<Real>(fx, g.nwarps, TILE ? a.tile_budget : 0);
+  setup_lists<Real>(g, fx, dyn + L.lists);
+  g.sync();
+  if (TILE && L.tile_nodes > 0)
+    walker_steps<Real, true>(g, fx, dyn, L, a, te.idx);
+  else
+    walker_steps<Real, false>(g, fx, dyn, L, a, te.idx);
 }
 
 cudaError_t launch_run(const RunArgs &a, int fp64, cudaStream_t st) {
@@ -223,15 +278,24 @@ cudaError_t launch_run(const RunArgs &a, int fp64, cudaStream_t st) {
   if (a.nw == 0) return cudaSuccess;
   cudaError_t e;
   if (fp64) {
-    e = cudaFuncSetAttribute(k_run<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_run<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_run<double><<<blocks, threads, smem, st>>>(a);
+    k_run<double, false><<<blocks, threads, smem, st>>>(a);
+  } else if (a.tile_budget > 0) {
+    e = cudaFuncSetAttribute(k_run<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_run<float, true><<<blocks, threads, smem, st>>>(a);
   } else {
-    e = cudaFuncSetAttribute(k_run<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_run<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_run<float><<<blocks, threads, smem, st>>>(a);
+    k_run<float, false><<<blocks, threads, smem, st>>>(a);
   }
   return cudaGetLastError();
+}
+
+int run_group_bytes(const WalkerDev &hd, int fp64, int G, int tile_budget) {
+  GroupLayout L = group_layout(hd.natoms, hd.cv, hd.g, hd.R, G / 32, fp64 ? 32 : 16, tile_budget);
+  return align32(group_fixed_bytes(fp64) + L.total);
 }
 
 // ---------------------------------------------------------------- plain form
@@ -241,7 +305,7 @@ cudaError_t launch_run(const RunArgs &a, int fp64, cudaStream_t st) {
 
 template <typename Real>
 struct PlainScratch {
-  double s[kMaxCv];
+  Real sh[kMaxCv], sl[kMaxCv];
   Real com_u[kMaxCv][3];
   Real dih_g[kMaxCv][4][3];
   int flags;
@@ -273,6 +337,20 @@ __device__ __forceinline__ Grp cta_group() {
   return g;
 }
 
+template <typename Real>
+__device__ GroupLayout plain_prologue(const Grp &g, GroupFixed<Real> *fx, const WalkerDev *wdp, unsigned char *dyn) {
+  copy_desc<Real>(g, &fx->wd, wdp);
+  g.sync();
+  GroupLayout L = layout_of<Real>(fx, g.nwarps, 0);
+  setup_lists<Real>(g, fx, dyn + L.lists);
+  if (g.t == 0) {
+    fx->flags = 0;
+    fx->clamped = 0;
+  }
+  g.sync();
+  return L;
+}
+
 // a1 for one walker; results to the walker's scratch.
 template <typename Real>
 __global__ void __launch_bounds__(256) k_plain_cv(const WalkerDev *wdp, const void *coords, const long long *coff,
@@ -281,11 +359,11 @@ __global__ void __launch_bounds__(256) k_plain_cv(const WalkerDev *wdp, const vo
   extern __shared__ __align__(32) unsigned char smem[];
   Grp g = cta_group<Real>();
   GroupFixed<Real> *fx = reinterpret_cast<GroupFixed<Real> *>(smem);
-  copy_desc<Real>(g, &fx->wd, wdp);
-  g.sync();
+  unsigned char *dyn = smem + fixed_bytes<Real>();
+  const GroupLayout L = plain_prologue<Real>(g, fx, wdp, dyn);
   const WalkerDev &wd = fx->wd;
-  R4 *xs = reinterpret_cast<R4 *>(smem + fixed_bytes<Real>());
-  unsigned char *cnmem = reinterpret_cast<unsigned char *>(xs + 2 * wd.natoms);
+  R4 *xs = reinterpret_cast<R4 *>(dyn + L.xs0);
+  unsigned char *cnmem = dyn + L.cn;
   const R4 *xin = reinterpret_cast<const R4 *>(coords) + coff[widx];
   int bad = 0;
   for (int i = g.t; i < wd.natoms; i += g.G) {
@@ -293,27 +371,25 @@ __global__ void __launch_bounds__(256) k_plain_cv(const WalkerDev *wdp, const vo
     xs[i] = p;
     bad |= finite_rec<Real>(p) ? 0 : 1;
   }
-  if (g.t == 0) fx->flags = 0;
-  Real bv[1] = {(Real)bad};
-  grp_sum<1>(g, bv, fx->red);
-  g.sync();
   PlainScratch<Real> *ps = reinterpret_cast<PlainScratch<Real> *>(wd.jscratch);
-  if (bv[0] != 0) {
+  if (grp_any<Real>(g, fx, bad)) {
     if (g.t == 0) {
       ps->bad = 1;
       ps->flags = ABP_WFLAG_NONFINITE;
     }
     return;
   }
+  g.sync();
   eval_cvs<Real>(g, fx, xs, cnmem);
   if (g.t == 0) {
     ps->bad = 0;
     ps->flags = fx->flags;
     for (int k = 0; k < kMaxCv; ++k) {
-      ps->s[k] = fx->s[k];
+      ps->sh[k] = fx->sh[k];
+      ps->sl[k] = fx->sl[k];
       for (int q = 0; q < 3; ++q) ps->com_u[k][q] = fx->com_u[k][q];
-      for (int a = 0; a < 4; ++a)
-        for (int q = 0; q < 3; ++q) ps->dih_g[k][a][q] = fx->dih_g[k][a][q];
+      for (int b = 0; b < 4; ++b)
+        for (int q = 0; q < 3; ++q) ps->dih_g[k][b][q] = fx->dih_g[k][b][q];
     }
   }
   R4 *jout = reinterpret_cast<R4 *>(reinterpret_cast<unsigned char *>(wd.jscratch) + plain_head_bytes<Real>());
@@ -332,13 +408,18 @@ __global__ void __launch_bounds__(256) k_plain_deposit(const WalkerDev *wdp, lon
   extern __shared__ __align__(32) unsigned char smem[];
   Grp g = cta_group<Real>();
   GroupFixed<Real> *fx = reinterpret_cast<GroupFixed<Real> *>(smem);
-  copy_desc<Real>(g, &fx->wd, wdp);
-  g.sync();
+  unsigned char *dyn = smem + fixed_bytes<Real>();
+  const GroupLayout L = plain_prologue<Real>(g, fx, wdp, dyn);
   const PlainScratch<Real> *ps = reinterpret_cast<const PlainScratch<Real> *>(fx->wd.jscratch);
   if (ps->bad) return;
-  if (g.t < kMaxCv) fx->s[g.t] = ps->s[g.t];
+  if (g.t < kMaxCv) {
+    fx->sh[g.t] = ps->sh[g.t];
+    fx->sl[g.t] = ps->sl[g.t];
+  }
   g.sync();
-  deposit_step<Real>(g, fx, step, log);
+  if (g.t < fx->wd.g.d) axis_setup<Real>(fx, g.t, true);
+  g.sync();
+  deposit_step<Real, false>(g, fx, L, nullptr, step, log);
 }
 
 // a4 + a5 for one walker.
@@ -349,11 +430,11 @@ __global__ void __launch_bounds__(256) k_plain_force(const WalkerDev *wdp, void 
   extern __shared__ __align__(32) unsigned char smem[];
   Grp g = cta_group<Real>();
   GroupFixed<Real> *fx = reinterpret_cast<GroupFixed<Real> *>(smem);
-  copy_desc<Real>(g, &fx->wd, wdp);
-  g.sync();
+  unsigned char *dyn = smem + fixed_bytes<Real>();
+  const GroupLayout L = plain_prologue<Real>(g, fx, wdp, dyn);
   const WalkerDev &wd = fx->wd;
-  R4 *fs = reinterpret_cast<R4 *>(smem + fixed_bytes<Real>()) + wd.natoms;
-  unsigned char *cnmem = reinterpret_cast<unsigned char *>(fs + wd.natoms);
+  R4 *fs = reinterpret_cast<R4 *>(dyn + L.fs);
+  unsigned char *cnmem = dyn + L.cn;
   const PlainScratch<Real> *ps = reinterpret_cast<const PlainScratch<Real> *>(wd.jscratch);
   R4 *fo = reinterpret_cast<R4 *>(forces) + foff[widx];
   if (ps->bad) {
@@ -368,10 +449,11 @@ __global__ void __launch_bounds__(256) k_plain_force(const WalkerDev *wdp, void 
   if (g.t == 0) {
     fx->flags = ps->flags | ((step % wd.stride) == 0 ? ABP_WFLAG_DEPOSIT : 0);
     for (int k = 0; k < kMaxCv; ++k) {
-      fx->s[k] = ps->s[k];
+      fx->sh[k] = ps->sh[k];
+      fx->sl[k] = ps->sl[k];
       for (int q = 0; q < 3; ++q) fx->com_u[k][q] = ps->com_u[k][q];
-      for (int a = 0; a < 4; ++a)
-        for (int q = 0; q < 3; ++q) fx->dih_g[k][a][q] = ps->dih_g[k][a][q];
+      for (int b = 0; b < 4; ++b)
+        for (int q = 0; q < 3; ++q) fx->dih_g[k][b][q] = ps->dih_g[k][b][q];
     }
   }
   const R4 *jin =
@@ -385,21 +467,12 @@ __global__ void __launch_bounds__(256) k_plain_force(const WalkerDev *wdp, void 
   }
   for (int i = g.t; i < wd.natoms; i += g.G) fs[i] = make_rec<Real>(0, 0, 0, 0);
   g.sync();
-  interp_step<Real>(g, fx);
+  if (g.t < wd.g.d) axis_setup<Real>(fx, g.t, false);
+  g.sync();
+  interp_step<Real, false>(g, fx, L, nullptr);
   scatter_forces<Real>(g, fx, fs, cnmem);
-  for (int i = g.t; i < wd.natoms; i += g.G) {
-    R4 f = fs[i];
-    if (mode == ABP_FORCES_ACCUMULATE) {
-      R4 o = fo[i];
-      o.x += f.x;
-      o.y += f.y;
-      o.z += f.z;
-      fo[i] = o;
-    } else {
-      fo[i] = make_rec<Real>(f.x, f.y, f.z, 0);
-    }
-  }
-  write_state<Real>(g, fx, step);
+  for (int i = g.t; i < wd.natoms; i += g.G) store_force<Real>(fo + i, fs[i], mode);
+  if (g.t == 0) write_state<Real>(fx, step);
 }
 
 template <typename Real>
@@ -412,8 +485,9 @@ static cudaError_t plain_one(const PlainArgs &a, int w, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   k_plain_cv<Real><<<1, T, smem, st>>>(wd, a.coords, a.coff, w);
   if (a.deposit[w]) {
-    size_t sm2 = (size_t)fixed_bytes<Real>();
-    k_plain_deposit<Real><<<1, 256, sm2, st>>>(wd, a.step, a.log);
+    e = cudaFuncSetAttribute(k_plain_deposit<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_plain_deposit<Real><<<1, T, smem, st>>>(wd, a.step, a.log);
   }
   e = cudaFuncSetAttribute(k_plain_force<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -440,18 +514,7 @@ __global__ void __launch_bounds__(256) k_deliver(const TableEntry *table, int nw
   const int natoms = wd->natoms;
   const R4 *src = reinterpret_cast<const R4 *>(wd->fbuf);
   R4 *dst = reinterpret_cast<R4 *>(forces) + foff[te.idx];
-  for (int i = threadIdx.x; i < natoms; i += blockDim.x) {
-    R4 f = src[i];
-    if (mode == ABP_FORCES_ACCUMULATE) {
-      R4 o = dst[i];
-      o.x += f.x;
-      o.y += f.y;
-      o.z += f.z;
-      dst[i] = o;
-    } else {
-      dst[i] = make_rec<Real>(f.x, f.y, f.z, 0);
-    }
-  }
+  for (int i = threadIdx.x; i < natoms; i += blockDim.x) store_force<Real>(dst + i, src[i], mode);
 }
 
 cudaError_t launch_deliver(const TableEntry *table, int nw, void *forces, const long long *foff, int mode, int fp64,

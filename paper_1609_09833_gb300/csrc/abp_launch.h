@@ -31,6 +31,7 @@ struct RunArgs {
   int mode;
   long long step0;
   int nsteps;
+  int tile_budget;     // >0: dynamic shared bytes per group, the rest of which holds a grid tile
   DepositLog log;
   DevCounters *ctr;
 };
@@ -53,6 +54,7 @@ struct PlainArgs {
 
 int group_fixed_bytes(int fp64);
 int plain_scratch_bytes(int fp64, const CvDev *cv, int ncv);
+int run_group_bytes(const WalkerDev &hd, int fp64, int G, int tile_budget);
 cudaError_t launch_run(const RunArgs &a, int fp64, cudaStream_t st);
 cudaError_t launch_plain(const PlainArgs &a, int fp64, cudaStream_t st);
 cudaError_t launch_deliver(const TableEntry *table, int nw, void *forces, const long long *foff, int mode, int fp64,

@@ -184,6 +184,35 @@ def test_chunked_calls_and_step_forces_are_bitwise_equal(abp, ctx):
         assert np.array_equal(ctx.bias(x), ctx.bias(y))
 
 
+def test_grid_tile_is_bitwise_exact(abp, ctx):
+    """The opt-in shared-memory grid tile (ABP_TUNE_TILE = 1) gives the same
+    bits as the untiled path: sweeps that cross the periodic seam and leave
+    the tile (forcing reloads), and 1D / 2D / 3D CN walkers."""
+    specs = synth.mb64_specs(nw=6, stride=4)
+    frames = synth.SweepFrames(6, seed=18, period=(60, 90), dihedral_period=(40, 70)).frames(0, 240)
+    w0 = ctx.make_walkers(specs)
+    F0 = gpu_replay(abp, ctx, w0, frames, 0, chunks=4)
+    abp.abp_ctx_tune(ctx.handle, abp.ABP_TUNE_TILE, 1)
+    w1 = ctx.make_walkers(specs)
+    F1 = gpu_replay(abp, ctx, w1, frames, 0, chunks=4)
+    abp.abp_ctx_tune(ctx.handle, abp.ABP_TUNE_TILE, -1)
+    assert np.array_equal(F0, F1)
+    for a, b in zip(w0, w1):
+        assert np.array_equal(ctx.bias(a), ctx.bias(b))
+    uspecs = synth.uneven1000_specs(seed=5, nw=6, stride=6, sizes_2d=(48,), n1d=200, n3d=20)
+    tm = synth.uneven1000_templates(5, nw=6)
+    uframes = synth.JitterFrames(tm, seed=6, jitter=0.05).frames(0, 48)
+    u0 = ctx.make_walkers(uspecs)
+    G0 = gpu_replay(abp, ctx, u0, uframes, 0, chunks=2)
+    abp.abp_ctx_tune(ctx.handle, abp.ABP_TUNE_TILE, 1)
+    u1 = ctx.make_walkers(uspecs)
+    G1 = gpu_replay(abp, ctx, u1, uframes, 0, chunks=2)
+    abp.abp_ctx_tune(ctx.handle, abp.ABP_TUNE_TILE, -1)
+    assert np.array_equal(G0, G1)
+    for a, b in zip(u0, u1):
+        assert np.array_equal(ctx.bias(a), ctx.bias(b))
+
+
 def test_plain_form_matches_batched_and_oracle(abp, ctx):
     specs = synth.mb64_specs(nw=3, stride=4)
     frames = synth.SweepFrames(3, seed=9, period=(100, 200)).frames(0, 40)
