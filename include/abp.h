@@ -241,6 +241,47 @@ abp_status abp_deposit_log_readout(abp_ctx *ctx, abp_deposit_rec *dst, size_t ca
                                    size_t *n_total);
 abp_status abp_deposit_log_clear(abp_ctx *ctx);
 
+/* ---- allocation-free step -------------------------------------------------- */
+
+/* abp_step_static: one MD step (a1..a5) of one walker, allocating nothing on
+ * the device. The paper has no counterpart; it exists for callers that
+ * cannot call cudaMalloc (a host routine running while a CUDA graph is being
+ * captured, a plugin confined to another program's memory pool, a bias call
+ * made where the device allocator must not be touched). It runs the kernels of
+ * abp_step_plain and gives the same results, but keeps everything beyond the
+ * caller's buffers (the walker description, its atom lists, the Jacobian
+ * passed between the kernels, a counter) in one static device array of
+ * ABP_STATIC_SCRATCH_BYTES that every GPU loading the library holds until the
+ * process exits. No cudaMalloc, cudaFree or other allocating call is made.
+ *
+ *   device, cuda_stream   the GPU and the cudaStream_t to run on (the caller's
+ *                         current device is restored on return)
+ *   grid_desc             the grid (as for abp_create_grid)
+ *   grid_records_dev      caller-owned grid storage: nodes records of 16 bytes
+ *                         (ncv = 1) or 32 bytes (ncv > 1), node order and
+ *                         record layout of the library's grids (FP32_COMP:
+ *                         float {V, dV0, cV, cdV0} or float {V, dV0, dV1, dV2},
+ *                         {cV, cdV0, cdV1, cdV2}, c = compensation; FP64:
+ *                         double {V, dV0} or {V, dV0, dV1, dV2}); zero it
+ *                         before the first step (V_b = 0); updated in place
+ *   walker_desc           the walker (as for abp_walker_create; host arrays)
+ *   coords_dev, forces_dev  the walker's atoms and its force records
+ *   mode, step            as for abp_step_plain
+ *
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture begins.
+ * Every call shares the array and leaves the last call's contents in it; the
+ * call rewrites what the kernels read before they run, so calls must not
+ * overlap on the GPU: two calls in flight at once (other streams, other host
+ * threads) race on the array. The call is asynchronous on cuda_stream; it
+ * reports no non-finite coordinates (forces are zeroed, nothing is
+ * deposited). A walker whose description, lists and Jacobian need more than
+ * ABP_STATIC_SCRATCH_BYTES is rejected with ABP_ERR_INVALID_ARG. */
+#define ABP_STATIC_SCRATCH_BYTES (1u << 20)
+abp_status abp_step_static(int device, void *cuda_stream, const abp_grid_desc *grid_desc, void *grid_records_dev,
+                           const abp_walker_desc *walker_desc, const void *coords_dev, int coords_dtype,
+                           void *forces_dev, int mode, int64_t step);
+
 /* Waits for the context stream; returns ABP_ERR_NONFINITE if any walker
  * stepped since the last sync saw non-finite coordinates. */
 abp_status abp_sync(abp_ctx *ctx);

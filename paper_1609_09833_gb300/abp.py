@@ -85,6 +85,8 @@ _SIGS = {
                                 C.POINTER(C.c_size_t)],
     "abp_deposit_log_clear": [_vp],
     "abp_sync": [_vp],
+    "abp_step_static": [C.c_int, _vp, C.POINTER(GridDesc), _vp, C.POINTER(WalkerDesc), _vp, C.c_int, _vp, C.c_int,
+                        C.c_int64],
     "abp_last_error": [],
     "abp_version": [],
 }
@@ -265,6 +267,12 @@ def abp_deposit_log_clear(ctx):
 
 def abp_sync(ctx):
     _check(load().abp_sync(ctx))
+
+
+def abp_step_static(device, stream, grid_desc: GridDesc, grid_records, walker_desc: WalkerDesc, coords,
+                    coords_dtype, forces, mode, step):
+    _check(load().abp_step_static(int(device), stream, C.byref(grid_desc), _ptr(grid_records), C.byref(walker_desc),
+                                  _ptr(coords), int(coords_dtype), _ptr(forces), int(mode), int(step)))
 
 
 def abp_last_error() -> str:

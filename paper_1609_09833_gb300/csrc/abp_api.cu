@@ -50,6 +50,10 @@ struct TableCache {
 
 }  // namespace
 
+namespace abp {
+abp_status record_error(abp_status code, const char *msg) { return fail(code, "%s", msg); }
+}  // namespace abp
+
 struct abp_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;

@@ -57,6 +57,8 @@ int plain_scratch_bytes(int fp64, const CvDev *cv, int ncv);
 int run_group_bytes(const WalkerDev &hd, int fp64, int G, int tile_budget);
 cudaError_t launch_run(const RunArgs &a, int fp64, cudaStream_t st);
 cudaError_t launch_plain(const PlainArgs &a, int fp64, cudaStream_t st);
+// Records `msg` as the calling thread's abp_last_error() and returns code.
+abp_status record_error(abp_status code, const char *msg);
 cudaError_t launch_deliver(const TableEntry *table, int nw, void *forces, const long long *foff, int mode, int fp64,
                            cudaStream_t st);
 
