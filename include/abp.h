@@ -99,6 +99,9 @@ typedef struct {
   double lo[3];
   double hi[3];
   int precision; /* ABP_PREC_* */
+  int shared;    /* nonzero: several walkers deposit here in the same step; an
+                    FP64 accumulator shadow receives every hill (atomics) and the
+                    FP32 fields are refreshed from it (FP32_COMP grids only) */
 } abp_grid_desc;
 
 /* One CV over the walker's own block of natoms atoms. Index arrays are

@@ -38,7 +38,7 @@ class AbpError(RuntimeError):
 
 class GridDesc(C.Structure):
     _fields_ = [("ncv", C.c_int), ("n", C.c_int * 3), ("periodic", C.c_int * 3), ("lo", C.c_double * 3),
-                ("hi", C.c_double * 3), ("precision", C.c_int)]
+                ("hi", C.c_double * 3), ("precision", C.c_int), ("shared", C.c_int)]
 
 
 class CvDesc(C.Structure):
@@ -286,7 +286,7 @@ def abp_version() -> str:
 # ---------------------------------------------------------------- spec marshalling
 
 
-def grid_desc(spec_grid: dict, precision: int = ABP_PREC_FP32_COMP) -> GridDesc:
+def grid_desc(spec_grid: dict, precision: int = ABP_PREC_FP32_COMP, shared: bool = False) -> GridDesc:
     d = GridDesc()
     n = spec_grid["n"]
     d.ncv = len(n)
@@ -296,6 +296,7 @@ def grid_desc(spec_grid: dict, precision: int = ABP_PREC_FP32_COMP) -> GridDesc:
         d.lo[k] = float(spec_grid["lo"][k])
         d.hi[k] = float(spec_grid["hi"][k])
     d.precision = int(precision)
+    d.shared = int(bool(shared))
     return d
 
 
@@ -361,8 +362,8 @@ class Context:
     def set_stream(self, stream):
         abp_ctx_set_stream(self.handle, stream)
 
-    def make_grid(self, spec_grid: dict, precision: int = ABP_PREC_FP32_COMP) -> int:
-        g = abp_create_grid(self.handle, grid_desc(spec_grid, precision))
+    def make_grid(self, spec_grid: dict, precision: int = ABP_PREC_FP32_COMP, shared: bool = False) -> int:
+        g = abp_create_grid(self.handle, grid_desc(spec_grid, precision, shared))
         self.grids.append(g)
         return g
 
@@ -374,7 +375,7 @@ class Context:
             if key is not None and key in shared:
                 g = shared[key]
             else:
-                g = self.make_grid(sp["grid"], precision)
+                g = self.make_grid(sp["grid"], precision, shared=key is not None)
                 if key is not None:
                     shared[key] = g
             desc, keep = walker_desc(sp)

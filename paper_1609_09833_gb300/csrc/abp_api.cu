@@ -66,6 +66,9 @@ struct abp_ctx {
   int next_id = 0;
   int sms = 0;  // multiprocessors of the device
   int tune_G = 0, tune_gpc = 0, tune_tile = -1;  // tile -1: library default (off; opt in with 1)
+  std::vector<BigItem> big_key;                   // phased-form item lists of the last call
+  BigItem *big_dev = nullptr;
+  size_t big_cap = 0;
   std::mutex mu;
 };
 
@@ -74,6 +77,7 @@ struct abp_grid {
   GridDev g{};
   abp_grid_desc desc{};
   size_t bytes = 0;
+  size_t shadow_bytes = 0;
 };
 
 struct abp_walker {
@@ -83,6 +87,7 @@ struct abp_walker {
   WalkerDev *dd = nullptr;
   std::vector<std::pair<void *, size_t>> allocs;
   bool has_cn = false;
+  bool big = false;    // runs in the phased form (shared grid, or too large for a walker group)
   long long cost = 0;  // rough work estimate used to order batched launches
 };
 
@@ -309,6 +314,7 @@ void abp_ctx_destroy(abp_ctx *ctx) {
   cudaStreamSynchronize(ctx->stream);
   for (auto &t : ctx->tables)
     if (t.dev) cudaFree(t.dev);
+  if (ctx->big_dev) cudaFree(ctx->big_dev);
   if (ctx->log.rec) cudaFree(ctx->log.rec);
   if (ctx->log.count) cudaFree(ctx->log.count);
   if (ctx->ctr) cudaFree(ctx->ctr);
@@ -323,6 +329,8 @@ abp_status abp_create_grid(abp_ctx *ctx, const abp_grid_desc *d, abp_grid **out)
   if (d->ncv < 1 || d->ncv > 3) return fail(ABP_ERR_INVALID_ARG, "ncv must be 1..3 (got %d)", d->ncv);
   if (d->precision != ABP_PREC_FP32_COMP && d->precision != ABP_PREC_FP64)
     return fail(ABP_ERR_INVALID_ARG, "unknown precision %d", d->precision);
+  if (d->shared && d->precision != ABP_PREC_FP32_COMP)
+    return fail(ABP_ERR_UNSUPPORTED, "shared grids are FP32_COMP grids (their accumulator is FP64)");
   long long nodes = 1;
   for (int k = 0; k < d->ncv; ++k) {
     if (d->n[k] < 2) return fail(ABP_ERR_INVALID_ARG, "axis %d needs >= 2 grid points", k);
@@ -364,10 +372,25 @@ abp_status abp_create_grid(abp_ctx *ctx, const abp_grid_desc *d, abp_grid **out)
     delete g;
     return st;
   }
+  gd.shared = d->shared ? 1 : 0;
+  gd.shadow = nullptr;
+  if (gd.shared) {
+    g->shadow_bytes = (size_t)nodes * 4 * sizeof(double);
+    void *p = nullptr;
+    st = dev_alloc(ctx, g->shadow_bytes, &p);
+    if (st) {
+      dev_free(ctx, gd.rec, g->bytes);
+      delete g;
+      return st;
+    }
+    gd.shadow = static_cast<double *>(p);
+  }
   cudaError_t e = cudaMemsetAsync(gd.rec, 0, g->bytes, ctx->stream);
+  if (e == cudaSuccess && gd.shadow) e = cudaMemsetAsync(gd.shadow, 0, g->shadow_bytes, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) {
     dev_free(ctx, gd.rec, g->bytes);
+    if (gd.shadow) dev_free(ctx, gd.shadow, g->shadow_bytes);
     delete g;
     return fail(ABP_ERR_CUDA, "grid clear: %s", cudaGetErrorString(e));
   }
@@ -381,6 +404,7 @@ void abp_grid_destroy(abp_grid *g) {
   set_device(g->ctx);
   cudaStreamSynchronize(g->ctx->stream);
   dev_free(g->ctx, g->g.rec, g->bytes);
+  if (g->g.shadow) dev_free(g->ctx, g->g.shadow, g->shadow_bytes);
   delete g;
 }
 
@@ -389,6 +413,7 @@ abp_status abp_grid_clear(abp_ctx *ctx, abp_grid *g) {
   abp_status st = set_device(ctx);
   if (st) return st;
   CUDA_TRY(cudaMemsetAsync(g->g.rec, 0, g->bytes, ctx->stream));
+  if (g->g.shadow) CUDA_TRY(cudaMemsetAsync(g->g.shadow, 0, g->shadow_bytes, ctx->stream));
   return ABP_OK;
 }
 
@@ -550,11 +575,21 @@ abp_status abp_walker_create(abp_ctx *ctx, abp_grid *grid, const abp_walker_desc
     if (d->cv[k].type == ABP_CV_COORD) w->has_cn = true;
   }
   int rsz = fp64 ? 32 : 16;
+  // the phased form serves walkers on a shared grid and walkers too large
+  // for one shared-memory walker group (FP32, at most one CN)
+  w->big = grid->desc.shared || run_group_bytes(hd, fp64, 32, 0) > 227 * 1024;
+  if (w->big && (fp64 || big_cn_count(hd) > 1)) {
+    walker_free(w);
+    delete w;
+    return fail(ABP_ERR_UNSUPPORTED,
+                "walkers on a shared grid or with too many atoms for one SM need FP32 grids and at most one CN");
+  }
+  size_t js_bytes = std::max((size_t)plain_scratch_bytes(fp64, hd.cv, ncv), w->big ? big_scratch_bytes(hd) : 0);
   void *p;
   if ((st = walker_alloc(w, (size_t)rsz * d->natoms, &p)) == ABP_OK) {
     hd.fbuf = p;
     CUDA_TRY(cudaMemset(p, 0, (size_t)rsz * d->natoms));
-    if ((st = walker_alloc(w, plain_scratch_bytes(fp64, hd.cv, ncv), &p)) == ABP_OK) {
+    if ((st = walker_alloc(w, js_bytes, &p)) == ABP_OK) {
       hd.jscratch = p;
       if ((st = walker_alloc(w, sizeof(WalkerState), &p)) == ABP_OK) {
         hd.state = static_cast<WalkerState *>(p);
@@ -562,10 +597,8 @@ abp_status abp_walker_create(abp_ctx *ctx, abp_grid *grid, const abp_walker_desc
       }
     }
   }
-  if (st == ABP_OK) {
-    int need = run_group_bytes(hd, fp64, 32, 0);
-    if (need > 227 * 1024) st = fail(ABP_ERR_UNSUPPORTED, "walker of %d atoms needs %d bytes of shared memory", d->natoms, need);
-  }
+  if (st == ABP_OK && w->big && big_cn_smem(hd) > 200 * 1024)
+    st = fail(ABP_ERR_UNSUPPORTED, "a coordination number with more than ~2000 A atoms is not built");
   if (st == ABP_OK) {
     hd.id = ctx->next_id++;
     if ((st = walker_alloc(w, sizeof(WalkerDev), &p)) == ABP_OK) {
@@ -599,15 +632,102 @@ int32_t abp_walker_id(const abp_walker *w) { return w ? w->hd.id : -1; }
 
 // ---------------------------------------------------------------- the force call
 
+// Device table for a sub-list of the caller's walkers (entries keep the
+// caller's index, which selects coordinate and force offsets).
+static abp_status sub_table(abp_ctx *ctx, const std::vector<abp_walker *> &ws, const std::vector<int> &idx,
+                            const TableEntry **out) {
+  std::vector<TableEntry> key(ws.size());
+  for (size_t i = 0; i < ws.size(); ++i) key[i] = TableEntry{ws[i]->dd, idx[i], 0};
+  std::vector<long long> cost(ws.size());
+  std::vector<size_t> order(ws.size());
+  for (size_t i = 0; i < ws.size(); ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return ws[a]->cost > ws[b]->cost; });
+  std::vector<TableEntry> sorted(ws.size());
+  for (size_t i = 0; i < ws.size(); ++i) sorted[i] = key[order[i]];
+  ++ctx->use_clock;
+  TableCache *victim = &ctx->tables[0];
+  for (auto &t : ctx->tables) {
+    if (t.dev && t.key.size() == sorted.size() &&
+        std::memcmp(t.key.data(), sorted.data(), sorted.size() * sizeof(TableEntry)) == 0) {
+      t.last_use = ctx->use_clock;
+      *out = t.dev;
+      return ABP_OK;
+    }
+    if (t.last_use < victim->last_use) victim = &t;
+  }
+  size_t need = std::max<size_t>(1, sorted.size()) * sizeof(TableEntry);
+  if (victim->cap < need) {
+    if (victim->dev) cudaFree(victim->dev);
+    victim->dev = nullptr;
+    victim->cap = 0;
+    CUDA_TRY(cudaMalloc(&victim->dev, need));
+    victim->cap = need;
+  }
+  CUDA_TRY(cudaMemcpyAsync(victim->dev, sorted.data(), sorted.size() * sizeof(TableEntry), cudaMemcpyHostToDevice,
+                           ctx->stream));
+  victim->key = std::move(sorted);
+  victim->last_use = ctx->use_clock;
+  *out = victim->dev;
+  return ABP_OK;
+}
+
+// Items of the phased form: one per walker, then one per CN chunk.
+static abp_status big_items(abp_ctx *ctx, const std::vector<abp_walker *> &ws, const std::vector<int> &idx,
+                            BigArgs *a) {
+  std::vector<BigItem> key;
+  int max_stencil = 0, any_shared = 0;
+  size_t cn_smem = 0;
+  for (size_t i = 0; i < ws.size(); ++i) {
+    key.push_back(BigItem{ws[i]->dd, idx[i], 0});
+    const WalkerDev &hd = ws[i]->hd;
+    int box = 1;
+    for (int k = 0; k < hd.g.d; ++k) box *= 2 * hd.R[k] + 1;
+    max_stencil = std::max(max_stencil, box);
+    any_shared |= hd.g.shared;
+    cn_smem = std::max(cn_smem, big_cn_smem(hd));
+  }
+  int ncn = 0;
+  for (size_t i = 0; i < ws.size(); ++i) {
+    int nc = big_chunks(ws[i]->hd);
+    for (int c = 0; c < nc; ++c) key.push_back(BigItem{ws[i]->dd, idx[i], c});
+    ncn += nc;
+  }
+  if (key.size() != ctx->big_key.size() ||
+      std::memcmp(key.data(), ctx->big_key.data(), key.size() * sizeof(BigItem)) != 0) {
+    size_t need = key.size() * sizeof(BigItem);
+    if (ctx->big_cap < need) {
+      if (ctx->big_dev) cudaFree(ctx->big_dev);
+      ctx->big_dev = nullptr;
+      ctx->big_cap = 0;
+      CUDA_TRY(cudaMalloc(&ctx->big_dev, need));
+      ctx->big_cap = need;
+    }
+    CUDA_TRY(cudaMemcpyAsync(ctx->big_dev, key.data(), need, cudaMemcpyHostToDevice, ctx->stream));
+    ctx->big_key = key;
+  }
+  a->walkers = ctx->big_dev;
+  a->nw = (int)ws.size();
+  a->cn_items = ctx->big_dev + ws.size();
+  a->ncn_items = ncn;
+  a->cn_smem = cn_smem;
+  a->max_stencil = max_stencil;
+  a->any_shared = any_shared;
+  return ABP_OK;
+}
+
 static abp_status run_common(abp_ctx *ctx, abp_walker *const *walkers, int n, const void *coords, int cdt,
                              const int64_t *coff, int64_t cstride, void *forces, const int64_t *foff,
-                             int64_t fstride, int mode, int64_t step0, int nsteps, bool allow_shared_check) {
+                             int64_t fstride, int mode, int64_t step0, int nsteps) {
   int fp64;
   bool shared;
   abp_status st = check_list(ctx, walkers, n, &fp64, &shared);
   if (st) return st;
-  if (shared && allow_shared_check)
-    return fail(ABP_ERR_UNSUPPORTED, "walkers that share a grid cannot run in the fused form");
+  if (shared) {
+    std::set<const abp_grid *> seen;
+    for (int i = 0; i < n; ++i)
+      if (!seen.insert(walkers[i]->grid).second && !walkers[i]->grid->desc.shared)
+        return fail(ABP_ERR_INVALID_ARG, "walkers that deposit into one grid need a grid created with shared = 1");
+  }
   if (n == 0 || nsteps == 0) return ABP_OK;
   if (nsteps < 0) return fail(ABP_ERR_INVALID_ARG, "nsteps must be >= 0");
   if (step0 < 0) return fail(ABP_ERR_INVALID_ARG, "step must be >= 0");
@@ -621,24 +741,56 @@ static abp_status run_common(abp_ctx *ctx, abp_walker *const *walkers, int n, co
     return fail(ABP_ERR_INVALID_ARG, "FP64 coordinate and force buffers must be 32-byte aligned");
   st = set_device(ctx);
   if (st) return st;
-  RunArgs a{};
-  if ((st = get_table(ctx, walkers, n, true, &a.table))) return st;
-  if ((st = pick_shape(ctx, walkers, n, fp64, nsteps, &a.G, &a.groups_per_cta, &a.group_bytes, &a.tile_budget)))
-    return st;
-  a.nw = n;
-  a.coords = coords;
-  a.coff = reinterpret_cast<const long long *>(coff);
-  a.cstride = cstride;
-  a.forces = forces;
-  a.foff = reinterpret_cast<const long long *>(foff);
-  a.fstride = fstride;
-  a.mode = mode;
-  a.step0 = step0;
-  a.nsteps = nsteps;
-  a.log = ctx->log;
-  a.ctr = ctx->ctr;
-  cudaError_t e = launch_run(a, fp64, ctx->stream);
-  if (e != cudaSuccess) return fail(ABP_ERR_CUDA, "fused launch: %s", cudaGetErrorString(e));
+  std::vector<abp_walker *> fw, bw;
+  std::vector<int> fi, bi;
+  for (int i = 0; i < n; ++i) {
+    if (walkers[i]->big) {
+      bw.push_back(walkers[i]);
+      bi.push_back(i);
+    } else {
+      fw.push_back(walkers[i]);
+      fi.push_back(i);
+    }
+  }
+  if (!fw.empty()) {
+    RunArgs a{};
+    if ((st = sub_table(ctx, fw, fi, &a.table))) return st;
+    if ((st = pick_shape(ctx, fw.data(), (int)fw.size(), fp64, nsteps, &a.G, &a.groups_per_cta, &a.group_bytes,
+                         &a.tile_budget)))
+      return st;
+    a.nw = (int)fw.size();
+    a.coords = coords;
+    a.coff = reinterpret_cast<const long long *>(coff);
+    a.cstride = cstride;
+    a.forces = forces;
+    a.foff = reinterpret_cast<const long long *>(foff);
+    a.fstride = fstride;
+    a.mode = mode;
+    a.step0 = step0;
+    a.nsteps = nsteps;
+    a.log = ctx->log;
+    a.ctr = ctx->ctr;
+    cudaError_t e = launch_run(a, fp64, ctx->stream);
+    if (e != cudaSuccess) return fail(ABP_ERR_CUDA, "fused launch: %s", cudaGetErrorString(e));
+  }
+  if (!bw.empty()) {
+    BigArgs b{};
+    if ((st = big_items(ctx, bw, bi, &b))) return st;
+    b.coords = coords;
+    b.coff = reinterpret_cast<const long long *>(coff);
+    b.forces = forces;
+    b.foff = reinterpret_cast<const long long *>(foff);
+    b.mode = mode;
+    b.log = ctx->log;
+    b.ctr = ctx->ctr;
+    for (int t = 0; t < nsteps; ++t) {
+      b.step = step0 + t;
+      b.step_off = (long long)t * cstride;
+      b.force_step_off = (long long)t * fstride;
+      cudaError_t e = launch_big_step(b, ctx->stream);
+      if (e != cudaSuccess) return fail(ABP_ERR_CUDA, "phased launch: %s", cudaGetErrorString(e));
+    }
+  }
   return ABP_OK;
 }
 
@@ -649,14 +801,14 @@ abp_status abp_run(abp_ctx *ctx, abp_walker *const *walkers, int n, const void *
   if (n > 0 && nsteps > 0 && (!forces_dev || !force_offsets_dev))
     return fail(ABP_ERR_INVALID_ARG, "forces or force offsets are NULL");
   return run_common(ctx, walkers, n, coords_dev, coords_dtype, coord_offsets_dev, coord_step_stride, forces_dev,
-                    force_offsets_dev, force_step_stride, mode, step0, nsteps, true);
+                    force_offsets_dev, force_step_stride, mode, step0, nsteps);
 }
 
 abp_status abp_step(abp_ctx *ctx, abp_walker *const *walkers, int n, const void *coords_dev, int coords_dtype,
                     const int64_t *coord_offsets_dev, int64_t step) {
   if (!ctx) return fail(ABP_ERR_INVALID_ARG, "ctx is NULL");
   return run_common(ctx, walkers, n, coords_dev, coords_dtype, coord_offsets_dev, 0, nullptr, nullptr, 0,
-                    ABP_FORCES_OVERWRITE, step, 1, true);
+                    ABP_FORCES_OVERWRITE, step, 1);
 }
 
 abp_status abp_forces(abp_ctx *ctx, abp_walker *const *walkers, int n, void *forces_dev, int forces_dtype,
@@ -688,6 +840,9 @@ abp_status abp_step_plain(abp_ctx *ctx, abp_walker *const *walkers, int n, const
   abp_status st = check_list(ctx, walkers, n, &fp64, &shared);
   if (st) return st;
   if (shared) return fail(ABP_ERR_UNSUPPORTED, "the plain form takes walkers with their own grids");
+  for (int i = 0; i < n; ++i)
+    if (walkers[i]->big)
+      return fail(ABP_ERR_UNSUPPORTED, "walker %d runs only in the batched form (shared grid or too many atoms)", i);
   if (n == 0) return ABP_OK;
   if (step < 0) return fail(ABP_ERR_INVALID_ARG, "step must be >= 0");
   if (!coords_dev || !coord_offsets_dev || !forces_dev || !force_offsets_dev)
@@ -801,6 +956,17 @@ abp_status abp_bias_upload(abp_ctx *ctx, abp_grid *g, const void *src, int src_i
   }
   CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   CUDA_TRY(cudaMemcpy(gd.rec, raw.data(), g->bytes, cudaMemcpyHostToDevice));
+  if (gd.shadow) {
+    // a shared grid's accumulator takes the exact values
+    std::vector<double> sh((size_t)gd.nodes * 4, 0.0);
+    for (long long i = 0; i < gd.nodes; ++i)
+      for (int q = 0; q < nf; ++q) {
+        size_t j = (size_t)i * nf + q;
+        sh[(size_t)i * 4 + q] = dtype == ABP_F64 ? reinterpret_cast<const double *>(in.data())[j]
+                                                 : (double)reinterpret_cast<const float *>(in.data())[j];
+      }
+    CUDA_TRY(cudaMemcpy(gd.shadow, sh.data(), sh.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
   return ABP_OK;
 }
 

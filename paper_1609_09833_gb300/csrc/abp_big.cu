@@ -1,0 +1,674 @@
+// abp_big.cu -- the phased form of the force call, for walkers that share a
+// grid (multiple-walker runs) or that are too large for one shared-memory
+// walker group. One MD step is five launches over all such walkers:
+//
+//   k_big_cn       a1, coordination numbers: the A x B pair sum split over
+//                  CTAs by chunks of B (kBigChunk entries); each CTA writes
+//                  dCN/dx of its B entries and its partial CN and A gradients
+//   k_big_cvs      a1 (other CVs, partial sums combined in chunk order) and
+//                  a2: every walker's hill height from the grid as it was
+//                  before any deposit of the step (Jacobi order)
+//   k_big_deposit  a3: the hills; shared grids add them to the FP64 shadow
+//                  with atomics (order-independent up to FP64 rounding), own
+//                  grids with the two-sum update of the fused form
+//   k_big_refresh  shared grids: FP32 fields = FP64 shadow split into
+//                  value + compensation (about 48 bits kept)
+//   k_big_force    a4 + a5: interpolation after all deposits, chain rule
+//
+// FP32_COMP grids only. The paper's bias routine is the serial counterpart
+// (one CPU rank), SI "Minimization of Interprocess Communications".
+#include <cuda_runtime.h>
+
+#include "abp_device.cuh"
+#include "abp_launch.h"
+
+namespace abp {
+
+namespace {
+
+constexpr int kBigThreads = 256;
+constexpr int kBigJB = 4;
+constexpr int kBigChunk = kBigThreads * kBigJB;
+constexpr int kStencilPerBlock = 2048;
+
+__host__ __device__ constexpr int fixed_bytes_f() { return (int)((sizeof(GroupFixed<float>) + 31) & ~(size_t)31); }
+
+__host__ __device__ inline size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+// Per-walker scratch of the phased form (in the walker's jscratch):
+//   BigHead | jA[na] | jB[nb] | part_s[nchunk][2] | part_g[nchunk][na][3]
+// for the walker's (single) COORD CV; jA/jB hold dCN/dx per list entry.
+struct BigHead {
+  float sh[kMaxCv], sl[kMaxCv];
+  float com_u[kMaxCv][3];
+  float dih_g[kMaxCv][4][3];
+  int da[kMaxCv], dc[kMaxCv], ic_log[kMaxCv];
+  float df[kMaxCv];
+  float hf;
+  int dep, bad, flags;
+  double h;
+};
+
+__host__ __device__ inline int big_cn_index(const WalkerDev &wd) {
+  for (int k = 0; k < wd.g.d; ++k)
+    if (wd.cv[k].type == ABP_CV_COORD) return k;
+  return -1;
+}
+
+__host__ __device__ inline int big_nchunks(const WalkerDev &wd) {
+  int k = big_cn_index(wd);
+  return k < 0 ? 0 : (wd.cv[k].nb + kBigChunk - 1) / kBigChunk;
+}
+
+struct BigLayout {
+  size_t head, jA, jB, part_s, part_g, total;
+};
+
+__host__ __device__ inline BigLayout big_layout(const WalkerDev &wd) {
+  BigLayout L;
+  int k = big_cn_index(wd);
+  int na = k < 0 ? 0 : wd.cv[k].na, nb = k < 0 ? 0 : wd.cv[k].nb;
+  int nc = big_nchunks(wd);
+  L.head = 0;
+  L.jA = up256(sizeof(BigHead));
+  L.jB = L.jA + (size_t)na * 16;
+  L.part_s = up256(L.jB + (size_t)nb * 16);
+  L.part_g = up256(L.part_s + (size_t)nc * 8);
+  L.total = up256(L.part_g + (size_t)nc * na * 12);
+  return L;
+}
+
+size_t big_scratch_bytes(const WalkerDev &hd) { return big_layout(hd).total; }
+int big_cn_count(const WalkerDev &hd) {
+  int n = 0;
+  for (int k = 0; k < hd.g.d; ++k) n += hd.cv[k].type == ABP_CV_COORD;
+  return n;
+}
+int big_chunks(const WalkerDev &hd) { return big_nchunks(hd); }
+
+// ---------------------------------------------------------------- k_big_cn
+
+// One CTA: the A x (one chunk of B) pairs of one walker's CN.
+__global__ void __launch_bounds__(kBigThreads) k_big_cn(const BigItem *items, const void *coords,
+                                                        const long long *coff, long long step_off) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const BigItem it = items[blockIdx.x];
+  const WalkerDev *wd = it.wd;
+  const int k = big_cn_index(*wd);
+  const CvDev &c = wd->cv[k];
+  const int na = c.na, nb = c.nb;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarps = kBigThreads / 32;
+  const float4 *x = reinterpret_cast<const float4 *>(coords) + coff[it.widx] + step_off;
+  float4 *As = reinterpret_cast<float4 *>(smem);
+  float *lig = reinterpret_cast<float *>(As + na);  // [nwarps][na][3]
+  for (int i = t; i < na; i += kBigThreads) As[i] = x[c.ia[i]];
+  for (int q = t; q < nwarps * na * 3; q += kBigThreads) lig[q] = 0.f;
+  __syncthreads();
+  const float k2 = (float)c.inv_r0sq, c6 = -6.f * k2;
+  const bool pbc = c.pbc != 0;
+  const float bx = (float)c.box[0], by = (float)c.box[1], bz = (float)c.box[2];
+  const float ibx = (float)c.inv_box[0], iby = (float)c.inv_box[1], ibz = (float)c.inv_box[2];
+  const int j0 = it.chunk * kBigChunk;
+  float xj[kBigJB], yj[kBigJB], zj[kBigJB], gxj[kBigJB], gyj[kBigJB], gzj[kBigJB], mj[kBigJB];
+#pragma unroll
+  for (int jj = 0; jj < kBigJB; ++jj) {
+    int j = j0 + jj * kBigThreads + t;
+    bool ok = j < nb;
+    float4 p = x[c.ib[ok ? j : 0]];
+    xj[jj] = p.x;
+    yj[jj] = p.y;
+    zj[jj] = p.z;
+    mj[jj] = ok ? 1.f : 0.f;
+    gxj[jj] = gyj[jj] = gzj[jj] = 0.f;
+  }
+  float sacc = 0.f, scomp = 0.f;  // compensated (two-sum per term)
+  float *mylig = lig + warp * na * 3;
+  for (int i0 = 0; i0 < na; i0 += 4) {
+    float gi[4][3];
+#pragma unroll
+    for (int ii = 0; ii < 4; ++ii) {
+      gi[ii][0] = gi[ii][1] = gi[ii][2] = 0.f;
+      int i = i0 + ii;
+      bool oki = i < na;
+      float4 a = As[oki ? i : 0];
+#pragma unroll
+      for (int jj = 0; jj < kBigJB; ++jj) {
+        float dx = a.x - xj[jj], dy = a.y - yj[jj], dz = a.z - zj[jj];
+        if (pbc) {
+          dx = min_image(dx, bx, ibx);
+          dy = min_image(dy, by, iby);
+          dz = min_image(dz, bz, ibz);
+        }
+        float q = (dx * dx + dy * dy + dz * dz) * k2;
+        float q2 = q * q;
+        float sw = __fdividef(1.f, 1.f + q2 * q);
+        float m = oki ? mj[jj] : 0.f;
+        float term = m * sw, tsum, terr;
+        two_sum<float>(sacc, term, tsum, terr);
+        sacc = tsum;
+        scomp += terr;
+        float gf = c6 * m * q2 * sw * sw;
+        gi[ii][0] += gf * dx;
+        gi[ii][1] += gf * dy;
+        gi[ii][2] += gf * dz;
+        gxj[jj] -= gf * dx;
+        gyj[jj] -= gf * dy;
+        gzj[jj] -= gf * dz;
+      }
+    }
+#pragma unroll
+    for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        float v = gi[ii][q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0 && i0 + ii < na) mylig[(i0 + ii) * 3 + q] += v;
+      }
+  }
+  unsigned char *js = reinterpret_cast<unsigned char *>(wd->jscratch);
+  const BigLayout L = big_layout(*wd);
+  float4 *jB = reinterpret_cast<float4 *>(js + L.jB);
+#pragma unroll
+  for (int jj = 0; jj < kBigJB; ++jj) {
+    int j = j0 + jj * kBigThreads + t;
+    if (j < nb) jB[j] = make_float4(gxj[jj], gyj[jj], gzj[jj], 0.f);
+  }
+  // this chunk's CN as hi + lo: warps in order, lanes by butterfly
+  float sh, sl;
+  two_sum<float>(sacc, scomp, sh, sl);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    float oh = __shfl_xor_sync(0xffffffffu, sh, o), ol = __shfl_xor_sync(0xffffffffu, sl, o);
+    ff_add<float>(sh, sl, oh, ol);
+  }
+  // (every lane now holds the same pair: the pairwise add is commutative)
+  __shared__ float wsum[kBigThreads / 32][2];
+  if (lane == 0) {
+    wsum[warp][0] = sh;
+    wsum[warp][1] = sl;
+  }
+  __syncthreads();
+  float *part_s = reinterpret_cast<float *>(js + L.part_s) + 2 * it.chunk;
+  if (t == 0) {
+    float h = wsum[0][0], l = wsum[0][1];
+    for (int w = 1; w < nwarps; ++w) ff_add<float>(h, l, wsum[w][0], wsum[w][1]);
+    part_s[0] = h;
+    part_s[1] = l;
+  }
+  float *part_g = reinterpret_cast<float *>(js + L.part_g) + (size_t)it.chunk * na * 3;
+  for (int q = t; q < na * 3; q += kBigThreads) {
+    float acc = 0.f;
+    for (int w = 0; w < nwarps; ++w) acc += lig[w * na * 3 + q];
+    part_g[q] = acc;
+  }
+}
+
+// ---------------------------------------------------------------- k_big_cvs
+
+__device__ __forceinline__ Grp big_group() {
+  Grp g;
+  g.G = blockDim.x;
+  g.gid = 0;
+  g.t = threadIdx.x;
+  g.lane = threadIdx.x & 31;
+  g.warp = threadIdx.x >> 5;
+  g.nwarps = blockDim.x >> 5;
+  return g;
+}
+
+__device__ void big_load_desc(const Grp &g, GroupFixed<float> *fx, const WalkerDev *wdp) {
+  const int *s = reinterpret_cast<const int *>(wdp);
+  int *d = reinterpret_cast<int *>(&fx->wd);
+  for (int i = g.t; i < (int)(sizeof(WalkerDev) / 4); i += g.G) d[i] = s[i];
+  g.sync();
+  if (g.t < kMaxCv) {
+    const CvDev &c = fx->wd.cv[g.t];
+    fx->ia[g.t] = c.ia;
+    fx->ib[g.t] = c.ib;
+    fx->wa[g.t] = c.wa;
+    fx->wb[g.t] = c.wb;
+  }
+  if (g.t == 0) {
+    fx->flags = 0;
+    fx->clamped = 0;
+  }
+  g.sync();
+}
+
+// Centre-of-mass distance with compensated arithmetic: each weighted offset
+// w (x - r_G) is split exactly into hi + lo (fma), summed as hi + lo pairs,
+// and |d| is taken in hi + lo. Groups spread over a large box (as a group of
+// environment atoms is) otherwise lose the ~1e-8 relative accuracy a hill a
+// few grid spacings wide needs.
+__device__ void cv_com_ff(const Grp &g, GroupFixed<float> *fx, int k, const float4 *xs) {
+  const CvDev &c = fx->wd.cv[k];
+  const float4 ra = xs[c.ia[0]], rb = xs[c.ib[0]];
+  float h[6] = {0, 0, 0, 0, 0, 0}, l[6] = {0, 0, 0, 0, 0, 0};
+  auto acc = [&](int q, float w, float dx) {
+    float p = w * dx;
+    float e = fmaf(w, dx, -p);
+    ff_add<float>(h[q], l[q], p, e);
+  };
+  for (int i = g.t; i < c.na; i += g.G) {
+    float w = c.wa[i];
+    float4 p = xs[c.ia[i]];
+    acc(0, w, p.x - ra.x);
+    acc(1, w, p.y - ra.y);
+    acc(2, w, p.z - ra.z);
+  }
+  for (int i = g.t; i < c.nb; i += g.G) {
+    float w = c.wb[i];
+    float4 p = xs[c.ib[i]];
+    acc(3, w, p.x - rb.x);
+    acc(4, w, p.y - rb.y);
+    acc(5, w, p.z - rb.z);
+  }
+  for (int q = 0; q < 6; ++q) grp_sum_ff<float>(g, h[q], l[q], fx->red);
+  if (g.t != 0) return;
+  float dh[3], dl[3];
+  const float ra3[3] = {ra.x, ra.y, ra.z}, rb3[3] = {rb.x, rb.y, rb.z};
+  for (int q = 0; q < 3; ++q) {
+    float rdh, rdl;  // r_B - r_A exactly, as hi + lo
+    two_sum<float>(rb3[q], -ra3[q], rdh, rdl);
+    float s, e;
+    two_sum<float>(rdh, h[3 + q], s, e);
+    e += l[3 + q] + rdl;
+    float s2, e2;
+    two_sum<float>(s, -h[q], s2, e2);
+    e2 += e - l[q];
+    dh[q] = s2 + e2;
+    dl[q] = e2 - (dh[q] - s2);
+    if (c.pbc) {
+      float shift = (float)c.box[q] * floor(dh[q] * (float)c.inv_box[q] + 0.5f);
+      float t, te;
+      two_sum<float>(dh[q], -shift, t, te);
+      dh[q] = t;
+      dl[q] += te;
+    }
+  }
+  // r^2 = sum (dh + dl)^2 in hi + lo, then r = sqrt with one Newton correction
+  float r2h = 0, r2l = 0;
+  for (int q = 0; q < 3; ++q) {
+    float p = dh[q] * dh[q];
+    float e = fmaf(dh[q], dh[q], -p) + 2.f * dh[q] * dl[q];
+    ff_add<float>(r2h, r2l, p, e);
+  }
+  float rh = sqrtf(r2h);
+  float rl = rh > 0 ? (fmaf(-rh, rh, r2h) + r2l) / (2.f * rh) : 0.f;
+  fx->sh[k] = rh;
+  fx->sl[k] = rl;
+  if (rh > 0) {
+    float ir = 1.f / rh;
+    for (int q = 0; q < 3; ++q) fx->com_u[k][q] = dh[q] * ir;
+  } else {
+    for (int q = 0; q < 3; ++q) fx->com_u[k][q] = 0;
+    fx->flags |= ABP_WFLAG_SINGULAR;
+  }
+}
+
+// One CTA per walker: CVs, axis state, height; hill record to the head.
+__global__ void __launch_bounds__(kBigThreads) k_big_cvs(const BigItem *walkers, const void *coords,
+                                                         const long long *coff, long long step_off, long long step,
+                                                         DepositLog log, DevCounters *ctr) {
+  extern __shared__ __align__(32) unsigned char smem[];
+  Grp g = big_group();
+  GroupFixed<float> *fx = reinterpret_cast<GroupFixed<float> *>(smem);
+  const BigItem it = walkers[blockIdx.x];
+  big_load_desc(g, fx, it.wd);
+  const WalkerDev &wd = fx->wd;
+  const float4 *x = reinterpret_cast<const float4 *>(coords) + coff[it.widx] + step_off;
+  unsigned char *js = reinterpret_cast<unsigned char *>(wd.jscratch);
+  BigHead *head = reinterpret_cast<BigHead *>(js);
+  int bad = 0;
+  for (int i = g.t; i < wd.natoms; i += g.G) {
+    float4 p = x[i];
+    bad |= (isfinite(p.x) && isfinite(p.y) && isfinite(p.z)) ? 0 : 1;
+  }
+  if (grp_any<float>(g, fx, bad)) {
+    if (g.t == 0) {
+      head->bad = 1;
+      head->dep = 0;
+      head->flags = ABP_WFLAG_NONFINITE;
+      atomicAdd(&ctr->nonfinite, 1);
+    }
+    return;
+  }
+  const BigLayout L = big_layout(wd);
+  const int kc = big_cn_index(wd);
+  for (int k = 0; k < wd.g.d; ++k) {
+    const CvDev &c = wd.cv[k];
+    if (c.type == ABP_CV_COM_DIST) {
+      cv_com_ff(g, fx, k, x);
+    } else if (c.type == ABP_CV_DIHEDRAL) {
+      cv_dihedral<float>(g, fx, k, x);
+    }
+  }
+  if (kc >= 0) {
+    const CvDev &c = wd.cv[kc];
+    const int nc = big_nchunks(wd);
+    const float *part_s = reinterpret_cast<const float *>(js + L.part_s);
+    const float *part_g = reinterpret_cast<const float *>(js + L.part_g);
+    if (g.t == 0) {
+      float h = part_s[0], l = part_s[1];
+      for (int q = 1; q < nc; ++q) ff_add<float>(h, l, part_s[2 * q], part_s[2 * q + 1]);
+      fx->sh[kc] = h;
+      fx->sl[kc] = l;
+    }
+    float4 *jA = reinterpret_cast<float4 *>(js + L.jA);
+    for (int i = g.t; i < c.na; i += g.G) {
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+      for (int q = 0; q < nc; ++q) {
+        const float *p = part_g + ((size_t)q * c.na + i) * 3;
+        a0 += p[0];
+        a1 += p[1];
+        a2 += p[2];
+      }
+      jA[i] = make_float4(a0, a1, a2, 0.f);
+    }
+  }
+  g.sync();
+  const bool dep = (step % wd.stride) == 0;
+  if (g.t < wd.g.d) axis_setup<float>(fx, g.t, dep);
+  g.sync();
+  if (dep && g.warp == 0) {
+    // V_b(s_t) before this step's deposits: the FP64 shadow of a shared
+    // grid, the value + compensation records of an own grid
+    const GridDev &gd = wd.g;
+    double acc = 0;
+    if (g.lane < (1 << gd.d)) {
+      double w = 1;
+      long long node = 0, mul = 1;
+      for (int k = 0; k < gd.d; ++k) {
+        int hi = (g.lane >> k) & 1;
+        double f = (double)fx->f[k];
+        w *= hi ? f : 1.0 - f;
+        node += mul * (hi ? fx->i1[k] : fx->i0[k]);
+        mul *= gd.n[k];
+      }
+      double v;
+      if (gd.shared) {
+        v = gd.shadow[node * 4];
+      } else {
+        double vv[4];
+        rec_values<double>(gd, reinterpret_cast<const unsigned char *>(gd.rec) + node * gd.rec_bytes, vv);
+        v = vv[0];
+      }
+      acc = w * v;
+    }
+    for (int o = 1; o < 8; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (g.lane == 0) {
+      double h = wd.w * exp(-acc * wd.inv_dT);
+      head->h = h;
+      head->hf = (float)h;
+      if (log.rec) {
+        unsigned long long slot = atomicAdd(log.count, 1ull);
+        if (slot < log.cap) {
+          abp_deposit_rec r;
+          r.step = step;
+          r.walker_id = wd.id;
+          for (int k = 0; k < 3; ++k) {
+            r.ic[k] = k < gd.d ? fx->ic_log[k] : 0;
+            r.s[k] = k < gd.d ? (double)fx->sh[k] + (double)fx->sl[k] : 0.0;
+          }
+          r.height = h;
+          log.rec[slot] = r;
+        }
+      }
+    }
+  }
+  if (g.t == 0) {
+    head->bad = 0;
+    head->dep = dep ? 1 : 0;
+    head->flags = fx->flags | (dep ? ABP_WFLAG_DEPOSIT : 0);
+    for (int k = 0; k < kMaxCv; ++k) {
+      head->sh[k] = fx->sh[k];
+      head->sl[k] = fx->sl[k];
+      head->da[k] = fx->da[k];
+      head->dc[k] = fx->dc[k];
+      head->df[k] = fx->df[k];
+      head->ic_log[k] = fx->ic_log[k];
+      for (int q = 0; q < 3; ++q) head->com_u[k][q] = fx->com_u[k][q];
+      for (int a = 0; a < 4; ++a)
+        for (int q = 0; q < 3; ++q) head->dih_g[k][a][q] = fx->dih_g[k][a][q];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- deposit + refresh
+
+// Stencil tables from the hill record (all CTAs of a walker build the same).
+__device__ bool big_tables(const Grp &g, GroupFixed<float> *fx, const BigItem &it) {
+  big_load_desc(g, fx, it.wd);
+  const BigHead *head = reinterpret_cast<const BigHead *>(fx->wd.jscratch);
+  if (!head->dep || head->bad) return false;
+  if (g.t < kMaxCv) {
+    fx->da[g.t] = head->da[g.t];
+    fx->dc[g.t] = head->dc[g.t];
+    fx->df[g.t] = head->df[g.t];
+  }
+  if (g.t == 0) fx->hf = head->hf;
+  g.sync();
+  build_tables<float>(g, fx);
+  g.sync();
+  return true;
+}
+
+__global__ void __launch_bounds__(kBigThreads) k_big_deposit(const BigItem *walkers) {
+  extern __shared__ __align__(32) unsigned char smem[];
+  Grp g = big_group();
+  GroupFixed<float> *fx = reinterpret_cast<GroupFixed<float> *>(smem);
+  if (!big_tables(g, fx, walkers[blockIdx.x])) return;
+  const WalkerDev &wd = fx->wd;
+  const GridDev &gd = wd.g;
+  const int d = gd.d;
+  const int s0 = 2 * wd.R[0] + 1, s1 = d > 1 ? 2 * wd.R[1] + 1 : 1, s2 = d > 2 ? 2 * wd.R[2] + 1 : 1;
+  const int total = s0 * s1 * s2;
+  const int first = blockIdx.y * kStencilPerBlock, last = min(total, first + kStencilPerBlock);
+  const long long n0 = gd.n[0], n01 = n0 * (d > 1 ? gd.n[1] : 1);
+  const float h = fx->hf;
+  for (int idx = first + g.t; idx < last; idx += g.G) {
+    int o0 = idx % s0, r = idx / s0, o1 = r % s1, o2 = r / s1;
+    int j0 = fx->tabJ[0][o0];
+    int j1 = d > 1 ? fx->tabJ[1][o1] : 0;
+    int j2 = d > 2 ? fx->tabJ[2][o2] : 0;
+    if ((j0 | j1 | j2) < 0) continue;
+    float G = h * fx->tabG[0][o0];
+    if (d > 1) G = G * fx->tabG[1][o1];
+    if (d > 2) G = G * fx->tabG[2][o2];
+    float d0 = fx->tabD[0][o0], d1 = d > 1 ? fx->tabD[1][o1] : 0.f, d2 = d > 2 ? fx->tabD[2][o2] : 0.f;
+    long long node = j0 + n0 * j1 + n01 * j2;
+    if (gd.shared) {
+      double *p = gd.shadow + node * 4;
+      atomicAdd(p, (double)G);
+      atomicAdd(p + 1, (double)__fmul_rn(G, d0));
+      if (d > 1) atomicAdd(p + 2, (double)__fmul_rn(G, d1));
+      if (d > 2) atomicAdd(p + 3, (double)__fmul_rn(G, d2));
+    } else {
+      rmw_node<float>(gd, reinterpret_cast<unsigned char *>(gd.rec) + node * gd.rec_bytes, G, d0, d1, d2);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBigThreads) k_big_refresh(const BigItem *walkers) {
+  extern __shared__ __align__(32) unsigned char smem[];
+  Grp g = big_group();
+  GroupFixed<float> *fx = reinterpret_cast<GroupFixed<float> *>(smem);
+  if (!big_tables(g, fx, walkers[blockIdx.x])) return;
+  const WalkerDev &wd = fx->wd;
+  const GridDev &gd = wd.g;
+  if (!gd.shared) return;
+  const int d = gd.d;
+  const int s0 = 2 * wd.R[0] + 1, s1 = d > 1 ? 2 * wd.R[1] + 1 : 1, s2 = d > 2 ? 2 * wd.R[2] + 1 : 1;
+  const int total = s0 * s1 * s2;
+  const int first = blockIdx.y * kStencilPerBlock, last = min(total, first + kStencilPerBlock);
+  const long long n0 = gd.n[0], n01 = n0 * (d > 1 ? gd.n[1] : 1);
+  for (int idx = first + g.t; idx < last; idx += g.G) {
+    int o0 = idx % s0, r = idx / s0, o1 = r % s1, o2 = r / s1;
+    int j0 = fx->tabJ[0][o0];
+    int j1 = d > 1 ? fx->tabJ[1][o1] : 0;
+    int j2 = d > 2 ? fx->tabJ[2][o2] : 0;
+    if ((j0 | j1 | j2) < 0) continue;
+    long long node = j0 + n0 * j1 + n01 * j2;
+    const double *p = gd.shadow + node * 4;
+    float hi[4], lo[4];
+    for (int q = 0; q < 4; ++q) {
+      double v = q <= d ? p[q] : 0.0;
+      hi[q] = (float)v;
+      lo[q] = (float)(v - (double)hi[q]);
+    }
+    if (d == 1) {
+      *reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(gd.rec) + node * 16) =
+          make_float4(hi[0], hi[1], lo[0], lo[1]);
+    } else {
+      float4 *q = reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(gd.rec) + node * 32);
+      q[0] = make_float4(hi[0], hi[1], hi[2], hi[3]);
+      q[1] = make_float4(lo[0], lo[1], lo[2], lo[3]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- k_big_force
+
+__global__ void __launch_bounds__(kBigThreads) k_big_force(const BigItem *walkers, void *forces,
+                                                           const long long *foff, long long force_step_off, int mode,
+                                                           long long step) {
+  extern __shared__ __align__(32) unsigned char smem[];
+  Grp g = big_group();
+  GroupFixed<float> *fx = reinterpret_cast<GroupFixed<float> *>(smem);
+  const BigItem it = walkers[blockIdx.x];
+  big_load_desc(g, fx, it.wd);
+  const WalkerDev &wd = fx->wd;
+  unsigned char *js = reinterpret_cast<unsigned char *>(wd.jscratch);
+  const BigHead *head = reinterpret_cast<const BigHead *>(js);
+  float4 *fb = reinterpret_cast<float4 *>(wd.fbuf);
+  float4 *fo = forces ? reinterpret_cast<float4 *>(forces) + foff[it.widx] + force_step_off : fb;
+  const int fmode = forces ? mode : ABP_FORCES_OVERWRITE;
+  if (head->bad) {
+    if (fmode == ABP_FORCES_OVERWRITE)
+      for (int i = g.t; i < wd.natoms; i += g.G) fo[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (g.t == 0) wd.state->flags = ABP_WFLAG_NONFINITE;
+    return;
+  }
+  if (g.t < kMaxCv) {
+    fx->sh[g.t] = head->sh[g.t];
+    fx->sl[g.t] = head->sl[g.t];
+    for (int q = 0; q < 3; ++q) fx->com_u[g.t][q] = head->com_u[g.t][q];
+    for (int a = 0; a < 4; ++a)
+      for (int q = 0; q < 3; ++q) fx->dih_g[g.t][a][q] = head->dih_g[g.t][a][q];
+  }
+  if (g.t == 0) fx->flags = head->flags;
+  g.sync();
+  if (g.t < wd.g.d) axis_setup<float>(fx, g.t, false);
+  g.sync();
+  GroupLayout Ldummy{};
+  interp_step<float, false>(g, fx, Ldummy, nullptr);
+  // a5 into the walker's force buffer, one list per phase (fixed order)
+  for (int i = g.t; i < wd.natoms; i += g.G) fb[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  g.sync();
+  const BigLayout L = big_layout(wd);
+  for (int k = 0; k < wd.g.d; ++k) {
+    const CvDev &c = wd.cv[k];
+    const float dv = fx->dvds[k];
+    if (c.type == ABP_CV_COM_DIST) {
+      const float ux = fx->com_u[k][0] * dv, uy = fx->com_u[k][1] * dv, uz = fx->com_u[k][2] * dv;
+      for (int i = g.t; i < c.na; i += g.G) {
+        float w = c.wa[i];
+        float4 &f = fb[c.ia[i]];
+        f.x += w * ux;
+        f.y += w * uy;
+        f.z += w * uz;
+      }
+      g.sync();
+      for (int i = g.t; i < c.nb; i += g.G) {
+        float w = c.wb[i];
+        float4 &f = fb[c.ib[i]];
+        f.x -= w * ux;
+        f.y -= w * uy;
+        f.z -= w * uz;
+      }
+      g.sync();
+    } else if (c.type == ABP_CV_DIHEDRAL) {
+      if (g.t < 4) {
+        float4 &f = fb[c.ia[g.t]];
+        f.x -= dv * fx->dih_g[k][g.t][0];
+        f.y -= dv * fx->dih_g[k][g.t][1];
+        f.z -= dv * fx->dih_g[k][g.t][2];
+      }
+      g.sync();
+    } else {
+      const float4 *jA = reinterpret_cast<const float4 *>(js + L.jA);
+      const float4 *jB = reinterpret_cast<const float4 *>(js + L.jB);
+      for (int i = g.t; i < c.na; i += g.G) {
+        float4 j = jA[i];
+        float4 &f = fb[c.ia[i]];
+        f.x -= dv * j.x;
+        f.y -= dv * j.y;
+        f.z -= dv * j.z;
+      }
+      g.sync();
+      for (int i = g.t; i < c.nb; i += g.G) {
+        float4 j = jB[i];
+        float4 &f = fb[c.ib[i]];
+        f.x -= dv * j.x;
+        f.y -= dv * j.y;
+        f.z -= dv * j.z;
+      }
+      g.sync();
+    }
+  }
+  if (fo != fb) {
+    for (int i = g.t; i < wd.natoms; i += g.G) {
+      float4 f = fb[i];
+      if (fmode == ABP_FORCES_ACCUMULATE) {
+        float4 o = fo[i];
+        o.x += f.x;
+        o.y += f.y;
+        o.z += f.z;
+        fo[i] = o;
+      } else {
+        fo[i] = make_float4(f.x, f.y, f.z, 0.f);
+      }
+    }
+  }
+  if (g.t == 0) {
+    WalkerState st;
+    for (int k = 0; k < 3; ++k) {
+      st.s[k] = k < wd.g.d ? (double)fx->sh[k] + (double)fx->sl[k] : 0.0;
+      st.dV[k] = k < wd.g.d ? (double)fx->dV[k] : 0.0;
+    }
+    st.V = (double)fx->V;
+    st.flags = fx->flags;
+    st.pad = 0;
+    st.step = step;
+    *wd.state = st;
+  }
+}
+
+// ---------------------------------------------------------------- launcher
+
+cudaError_t launch_big_step(const BigArgs &a, cudaStream_t st) {
+  const size_t fixed = (size_t)fixed_bytes_f();
+  cudaError_t e;
+  if (a.ncn_items > 0) {
+    e = cudaFuncSetAttribute(k_big_cn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.cn_smem);
+    if (e != cudaSuccess) return e;
+    k_big_cn<<<a.ncn_items, kBigThreads, a.cn_smem, st>>>(a.cn_items, a.coords, a.coff, a.step_off);
+  }
+  k_big_cvs<<<a.nw, kBigThreads, fixed, st>>>(a.walkers, a.coords, a.coff, a.step_off, a.step, a.log, a.ctr);
+  dim3 grid(a.nw, (a.max_stencil + kStencilPerBlock - 1) / kStencilPerBlock);
+  k_big_deposit<<<grid, kBigThreads, fixed, st>>>(a.walkers);
+  if (a.any_shared) k_big_refresh<<<grid, kBigThreads, fixed, st>>>(a.walkers);
+  k_big_force<<<a.nw, kBigThreads, fixed, st>>>(a.walkers, a.forces, a.foff, a.force_step_off, a.mode, a.step);
+  return cudaGetLastError();
+}
+
+size_t big_cn_smem(const WalkerDev &hd) {
+  int k = big_cn_index(hd);
+  if (k < 0) return 0;
+  return (size_t)hd.cv[k].na * 16 + (size_t)(kBigThreads / 32) * hd.cv[k].na * 12;
+}
+
+}  // namespace abp

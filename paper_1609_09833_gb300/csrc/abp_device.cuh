@@ -344,7 +344,10 @@ __device__ void cv_coord(const Grp &g, GroupFixed<Real> *fx, int k, const typena
   Real *mylig = lig + g.warp * c.na * 3;
   for (int q = g.lane; q < c.na * 3; q += 32) mylig[q] = 0;
   __syncwarp();
-  Real sacc = 0;  // this thread's partial sum (a few hundred terms of size <= 1)
+  // this thread's partial sum, compensated (two-sum per term): a CN of
+  // thousands must be exact to ~1e-8 relative to place a hill two grid
+  // spacings wide, below FP32's resolution
+  Real sacc = 0, scomp = 0;
   constexpr int JB = 4;
   for (int jb0 = 0; jb0 < c.nb; jb0 += g.G * JB) {
     Real xj[JB], yj[JB], zj[JB], gxj[JB], gyj[JB], gzj[JB], mj[JB];
@@ -379,7 +382,10 @@ __device__ void cv_coord(const Grp &g, GroupFixed<Real> *fx, int k, const typena
           Real q2 = q * q;
           Real sw = rcp_fast<Real>((Real)1 + q2 * q);
           Real m = oki ? mj[jj] : (Real)0;
-          sacc += m * sw;
+          Real term = m * sw, tsum, terr;
+          two_sum<Real>(sacc, term, tsum, terr);
+          sacc = tsum;
+          scomp += terr;
           Real gf = c6 * m * q2 * sw * sw;
           gi[ii][0] += gf * dx;
           gi[ii][1] += gf * dy;
@@ -408,7 +414,8 @@ __device__ void cv_coord(const Grp &g, GroupFixed<Real> *fx, int k, const typena
   // the per-thread partial sums are combined in hi + lo arithmetic: a CN of
   // a few hundred needs more than FP32's 24 bits to place a hill two grid
   // spacings wide
-  Real sh = sacc, sl = 0;
+  Real sh, sl;
+  two_sum<Real>(sacc, scomp, sh, sl);
   grp_sum_ff<Real>(g, sh, sl, fx->red);
   if (g.t == 0) {
     fx->sh[k] = sh;

@@ -43,6 +43,8 @@ struct GridDev {
   int rec_bytes;     // bytes per node record
   long long nodes;
   void *rec;         // node records (see GridLayout below)
+  int shared;        // several walkers deposit per step (see shadow)
+  double *shadow;    // shared grids: FP64 accumulator, 4 doubles per node {V, dV0, dV1, dV2}
 };
 
 // Node record layouts:

@@ -52,6 +52,40 @@ struct PlainArgs {
   DevCounters *ctr;
 };
 
+// One work item of the phased form: a walker (and, for the pair kernel, one
+// chunk of its coordination-number B list).
+struct BigItem {
+  const WalkerDev *wd;
+  int widx;
+  int chunk;
+};
+
+struct BigArgs {
+  const BigItem *cn_items;
+  int ncn_items;
+  size_t cn_smem;
+  const BigItem *walkers;
+  int nw;
+  const void *coords;
+  const long long *coff;
+  long long step_off;        // records: step t of a multi-step call
+  void *forces;              // NULL: the walkers' own force buffers (abp_step)
+  const long long *foff;
+  long long force_step_off;
+  int mode;
+  long long step;
+  int max_stencil;           // largest stencil box (nodes) among the walkers
+  int any_shared;
+  DepositLog log;
+  DevCounters *ctr;
+};
+
+size_t big_scratch_bytes(const WalkerDev &hd);
+int big_cn_count(const WalkerDev &hd);
+int big_chunks(const WalkerDev &hd);
+size_t big_cn_smem(const WalkerDev &hd);
+cudaError_t launch_big_step(const BigArgs &a, cudaStream_t st);
+
 int group_fixed_bytes(int fp64);
 int plain_scratch_bytes(int fp64, const CvDev *cv, int ncv);
 int run_group_bytes(const WalkerDev &hd, int fp64, int G, int tile_budget);

@@ -308,13 +308,14 @@ def serve_templates(seed: int, specs):
 
 
 def shared256_specs(nw: int = 32, n: int = 256, n_lig: int = 200, n_env: int = 10_000, box: float = 6.0,
-                    stride: int = 10, w: float = 0.2, gamma: float = 20.0, kT: float = 2.5):
+                    stride: int = 10, w: float = 0.2, gamma: float = 20.0, kT: float = 2.5,
+                    cn_range=CN_RANGE_SHARED):
     nat = n_lig + n_env
     lig = np.arange(0, n_lig)
     env = np.arange(n_lig, nat)
     bx = (box, box, box)
     # the minimum-image COM distance in a cubic box of edge L is at most L*sqrt(3)/2
-    g = grid((0.0, -math.pi, CN_RANGE_SHARED[0]), (box * math.sqrt(3.0) / 2.0, math.pi, CN_RANGE_SHARED[1]),
+    g = grid((0.0, -math.pi, cn_range[0]), (box * math.sqrt(3.0) / 2.0, math.pi, cn_range[1]),
              (n, n, n), (False, True, False))
     cvs = [{"type": "com_dist", "a": lig, "b": env[:16], "pbc": True, "box": bx},
            {"type": "dihedral", "a": np.arange(0, 4), "pbc": True, "box": bx},
