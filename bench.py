@@ -55,14 +55,15 @@ BYTES_PER_WALKER_STEP = NATOMS * 16 * 2 + 4 * NODE_BYTES + (STENCIL_NODES * NODE
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--md-steps", type=int, default=100, help="MD steps per benchmark step (one launch)")
+    ap.add_argument("--md-steps", type=int, default=1000, help="MD steps per benchmark step (one launch)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--tile", default="auto", choices=["auto", "on", "off"])
     ap.add_argument("--group-threads", type=int, default=0)
+    ap.add_argument("--no-extra", action="store_true", help="skip the other workloads")
     return ap.parse_args()
 
 
@@ -75,49 +76,110 @@ def load_peaks():
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """SM clock and clock-event reasons sampled every few ms during the timed
+    region (NVML through ctypes; nvidia-smi as a fallback)."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # NVML clock-event reason bits
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown"}
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, period_s: float = 0.005):
         self.index = index
-        self.p = None
+        self.period = period_s
+        self.samples = []
+        self.max_mhz = None
+        self._stop = None
+        self._thread = None
+        self._nvml = None
+        self._smi = None
+
+    def _open_nvml(self):
+        import ctypes
+
+        for name in ("libnvidia-ml.so.1", "libnvidia-ml.so"):
+            try:
+                lib = ctypes.CDLL(name)
+                break
+            except OSError:
+                lib = None
+        if lib is None or lib.nvmlInit_v2() != 0:
+            return None
+        h = ctypes.c_void_p()
+        if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.index), ctypes.byref(h)) != 0:
+            return None
+        mx = ctypes.c_uint()
+        if lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0:
+            self.max_mhz = float(mx.value)
+        getr = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        return lib, h, getr
+
+    def _loop(self):
+        import ctypes
+
+        lib, h, getr = self._nvml
+        clk, rs = ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self._stop.is_set():
+            if lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) == 0 and getr(h, ctypes.byref(rs)) == 0:
+                self.samples.append((float(clk.value), int(rs.value)))
+            self._stop.wait(self.period)
 
     def __enter__(self):
+        import threading
+
         try:
-            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
-                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._nvml = self._open_nvml()
         except Exception:
-            self.p = None
+            self._nvml = None
+        if self._nvml is not None:
+            self._stop = threading.Event()
+            self._thread = threading.Thread(target=self._loop, daemon=True)
+            self._thread.start()
+        else:
+            try:
+                q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+                     "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                     "clocks_event_reasons.sw_power_cap")
+                self._smi = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                              "--format=csv,noheader,nounits", "-lms", "20"],
+                                             stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            except Exception:
+                self._smi = None
         return self
 
     def __exit__(self, *a):
-        self.rows = []
-        if self.p is None:
-            return
-        self.p.terminate()
-        try:
-            out, _ = self.p.communicate(timeout=5)
-        except Exception:
-            self.p.kill()
-            out, _ = self.p.communicate()
-        for line in out.strip().splitlines():
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) >= 9:
-                self.rows.append(parts)
+        if self._thread is not None:
+            self._stop.set()
+            self._thread.join(timeout=2)
+        if self._smi is not None:
+            self._smi.terminate()
+            try:
+                out, _ = self._smi.communicate(timeout=5)
+            except Exception:
+                self._smi.kill()
+                out, _ = self._smi.communicate()
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for line in out.strip().splitlines():
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 6 and p[0].replace(".", "").isdigit():
+                    self.max_mhz = float(p[1]) if p[1].replace(".", "").isdigit() else self.max_mhz
+                    bits = sum(1 << i for i in range(4) if p[2 + i].lower() == "active")
+                    self.samples.append((float(p[0]), -bits - 1))  # negative: smi-encoded reasons
+            self._smi_names = names
 
     def summary(self):
-        if not getattr(self, "rows", None):
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
-        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows)}
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["no samples"], "samples": 0}
+        sm = [c for c, _ in self.samples]
+        reasons = set()
+        for _, r in self.samples:
+            if r >= 0:
+                reasons |= {n for b, n in self.REASONS.items() if r & b}
+            else:
+                bits = -r - 1
+                reasons |= {n for i, n in enumerate(self._smi_names) if bits >> i & 1}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": self.max_mhz, "reasons": sorted(reasons),
+                "samples": len(self.samples), "source": "nvml" if self._nvml is not None else "nvidia-smi"}
 
 
 def dist_env():
@@ -197,6 +259,152 @@ def cpu_baseline(seconds: float):
     return {"value": NW * T / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"MD steps {pilot}..{pilot + T - 1} of the same 64-walker workload ({NW * T} bias steps, "
                       f"{dt:.1f} s), FP64 C oracle, OpenMP over walkers"}
+
+
+# ---------------------------------------------------------------- the other workloads
+
+CN_FLOPS = 30          # flops per CN pair, no minimum image (see the design notes)
+CN_FLOPS_PBC = 39      # with the minimum image
+
+
+def fp32_peak_tflops(sm_mhz):
+    """FP32 FMA peak: 152 SMs x 128 lanes x 2 flops x SM clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def _time_loop(torch, fn, reps):
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def bench_double_well(abp, synth, torch, dev):
+    """One FP64 walker, COM distance of two 8-atom groups, 512-node grid."""
+    ctx = abp.Context(dev)
+    try:
+        spec = synth.double_well_com_spec()
+        w = ctx.make_walkers([spec], precision=abp.ABP_PREC_FP64)
+        T = 2000
+        x0 = synth.double_well_com_coords(5)
+        frames = x0[None] + np.cumsum(synth.rng(6).normal(scale=0.03, size=(T, 16, 3)), axis=0)
+        rec = abp.to_records(frames, torch.float64).cuda()
+        offs = torch.zeros(1, dtype=torch.int64, device="cuda")
+        F = torch.zeros_like(rec)
+        st = {"md": 0}
+
+        def run():
+            abp.abp_run(ctx.handle, w, rec, abp.ABP_F64, offs, 16, F, offs, 16, abp.ABP_FORCES_OVERWRITE, st["md"], T)
+            st["md"] += T
+
+        ms = _time_loop(torch, run, 5)
+        return {"workload": "1 walker, FP64 end to end, COM distance 2x8 atoms, 512-node grid, stride 100",
+                "value": T / (ms / 1e3), "unit": "bias steps/s", "us_per_step": 1e3 * ms / T,
+                "md_steps_per_launch": T, "dtype": "f64", "bound": "latency (one walker)"}
+    finally:
+        torch.cuda.synchronize()
+        ctx.close()
+
+
+def bench_uneven(abp, synth, torch, dev, sm_mhz):
+    """1000 walkers: 40 % 1D / 50 % 2D / 10 % 3D grids, CN 40 x 400 each."""
+    from paper_1609_09833_gb300 import autotune
+
+    ctx = abp.Context(dev)
+    try:
+        nw, C = 1000, 25
+        specs = synth.uneven1000_specs(seed=31, nw=nw)
+        tm = synth.uneven1000_templates(31, nw=nw)
+        rec = abp.to_records(synth.JitterFrames(tm, seed=32).frames(0, C)).cuda()
+        A = rec.shape[1]
+        offs = torch.tensor(synth.offsets_of(specs), dtype=torch.int64, device="cuda")
+        tuned = autotune.tune(ctx, specs, rec, offs, C)
+        walkers = ctx.make_walkers(specs)
+        F = torch.zeros_like(rec)
+        st = {"md": 0}
+
+        def run():
+            abp.abp_run(ctx.handle, walkers, rec, abp.ABP_F32, offs, A, F, offs, A, abp.ABP_FORCES_OVERWRITE,
+                        st["md"], C)
+            st["md"] += C
+
+        ms = _time_loop(torch, run, 6)
+        flops = nw * C * 40 * 400 * CN_FLOPS
+        achieved = flops / (ms / 1e3) / 1e12
+        peak = fp32_peak_tflops(sm_mhz)
+        return {"workload": "1000 walkers (40% 1D 1024, 50% 2D 128^2/256^2/512^2, 10% 3D 64^3), CN 40x400, "
+                            "jitter frames, one launch per 25 MD steps",
+                "value": nw * C / (ms / 1e3), "unit": "bias steps/s", "ms_per_launch": ms,
+                "tuned": tuned["best"],
+                "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                             "frac": achieved / peak, "kernel": "k_run<float> (CN pairs)",
+                             "peak_source": f"derived: 152 SM x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz"}}
+    finally:
+        torch.cuda.synchronize()
+        ctx.close()
+
+
+def bench_shared(abp, synth, torch, dev, sm_mhz):
+    """32 walkers on one shared 256^3 grid, 200 x 10,000-atom CN each."""
+    ctx = abp.Context(dev)
+    try:
+        nw, C = 32, 10
+        specs = synth.shared256_specs(nw=nw)
+        tm = synth.shared256_templates(41, nw=nw)
+        rec = abp.to_records(synth.JitterFrames(tm, seed=42).frames(0, C)).cuda()
+        A = rec.shape[1]
+        offs = torch.tensor(synth.offsets_of(specs), dtype=torch.int64, device="cuda")
+        walkers = ctx.make_walkers(specs)
+        F = torch.zeros_like(rec)
+        abp.abp_deposit_log_enable(ctx.handle, 1 << 16)
+        # direct calls (also uploads the walker tables before capture)
+        st = {"md": 0}
+
+        def run():
+            abp.abp_run(ctx.handle, walkers, rec, abp.ABP_F32, offs, A, F, offs, A, abp.ABP_FORCES_OVERWRITE,
+                        st["md"], C)
+            st["md"] += C
+
+        ms_direct = _time_loop(torch, run, 3)
+        # CUDA-graph replay of the same call (5 launches per MD step captured)
+        s = torch.cuda.Stream()
+        ctx.set_stream(s.cuda_stream)
+        g = torch.cuda.CUDAGraph()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=s):
+            abp.abp_run(ctx.handle, walkers, rec, abp.ABP_F32, offs, A, F, offs, A, abp.ABP_FORCES_OVERWRITE,
+                        10 ** 6, C)
+        ctx.set_stream(torch.cuda.current_stream().cuda_stream)
+        ms_graph = _time_loop(torch, g.replay, 5)
+        log = abp.abp_deposit_log_readout(ctx.handle, 1 << 16)
+        flops = nw * C * 200 * 10_000 * CN_FLOPS_PBC
+        achieved = flops / (ms_graph / 1e3) / 1e12
+        peak = fp32_peak_tflops(sm_mhz)
+        # overlap of the hills of one deposit step (atomic contention)
+        overlap = None
+        if len(log["step"]):
+            st0 = log["step"][0]
+            ic = log["ic"][log["step"] == st0]
+            R = 8
+            pairs = sum(1 for a in range(len(ic)) for b in range(a + 1, len(ic))
+                        if np.all(np.abs(ic[a] - ic[b]) <= 2 * R))
+            overlap = {"hills_per_deposit_step": int(len(ic)), "overlapping_box_pairs": int(pairs)}
+        return {"workload": "32 walkers, one shared 256^3 grid (FP64 shadow), 200 ligand + 10,000 environment "
+                            "atoms, 6 nm periodic box, stride 10; 10 MD steps per call, CUDA-graph replay",
+                "value": nw * C / (ms_graph / 1e3), "unit": "bias steps/s", "ms_per_md_step": ms_graph / C,
+                "value_direct_calls": nw * C / (ms_direct / 1e3), "gpu_launches_per_md_step": 5,
+                "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                             "frac": achieved / peak, "kernel": "whole step (CN pair kernel dominant)",
+                             "peak_source": f"derived: 152 SM x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz"},
+                "deposit_contention": overlap}
+    finally:
+        torch.cuda.synchronize()
+        ctx.close()
 
 
 # ---------------------------------------------------------------- our arm
@@ -330,6 +538,17 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds)
     clocks = clk.summary()
+    extra = None
+    if rank == 0 and world == 1 and not args.no_extra:
+        sm = clocks["sm_mhz"] or 2070.0
+        extra = {}
+        for name, fn in (("double_well_fp64", lambda: bench_double_well(abp, synth, torch, dev)),
+                         ("uneven1000", lambda: bench_uneven(abp, synth, torch, dev, sm)),
+                         ("shared256", lambda: bench_shared(abp, synth, torch, dev, sm))):
+            try:
+                extra[name] = fn()
+            except Exception as e:  # report, do not hide the headline
+                extra[name] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -349,6 +568,7 @@ def main():
                       "form": "3 launches per walker per MD step from a host loop"},
             "latency_us": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "what": "one MD step of all 64 walkers, one call, CUDA events"},
+            "other_workloads": extra,
         }
         print(json.dumps(line), flush=True)
     torch.cuda.synchronize()

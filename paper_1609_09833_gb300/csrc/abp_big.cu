@@ -123,7 +123,9 @@ __global__ void __launch_bounds__(kBigThreads) k_big_cn(const BigItem *items, co
     mj[jj] = ok ? 1.f : 0.f;
     gxj[jj] = gyj[jj] = gzj[jj] = 0.f;
   }
-  float sacc = 0.f, scomp = 0.f;  // compensated (two-sum per term)
+  float sacc[kBigJB], scomp[kBigJB];  // compensated (two-sum per term), one chain per B entry
+#pragma unroll
+  for (int jj = 0; jj < kBigJB; ++jj) sacc[jj] = scomp[jj] = 0.f;
   float *mylig = lig + warp * na * 3;
   for (int i0 = 0; i0 < na; i0 += 4) {
     float gi[4][3];
@@ -146,9 +148,9 @@ __global__ void __launch_bounds__(kBigThreads) k_big_cn(const BigItem *items, co
         float sw = __fdividef(1.f, 1.f + q2 * q);
         float m = oki ? mj[jj] : 0.f;
         float term = m * sw, tsum, terr;
-        two_sum<float>(sacc, term, tsum, terr);
-        sacc = tsum;
-        scomp += terr;
+        two_sum<float>(sacc[jj], term, tsum, terr);
+        sacc[jj] = tsum;
+        scomp[jj] += terr;
         float gf = c6 * m * q2 * sw * sw;
         gi[ii][0] += gf * dx;
         gi[ii][1] += gf * dy;
@@ -178,7 +180,9 @@ __global__ void __launch_bounds__(kBigThreads) k_big_cn(const BigItem *items, co
   }
   // this chunk's CN as hi + lo: warps in order, lanes by butterfly
   float sh, sl;
-  two_sum<float>(sacc, scomp, sh, sl);
+  two_sum<float>(sacc[0], scomp[0], sh, sl);
+#pragma unroll
+  for (int jj = 1; jj < kBigJB; ++jj) ff_add<float>(sh, sl, sacc[jj], scomp[jj]);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     float oh = __shfl_xor_sync(0xffffffffu, sh, o), ol = __shfl_xor_sync(0xffffffffu, sl, o);

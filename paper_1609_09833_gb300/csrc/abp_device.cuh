@@ -344,11 +344,14 @@ __device__ void cv_coord(const Grp &g, GroupFixed<Real> *fx, int k, const typena
   Real *mylig = lig + g.warp * c.na * 3;
   for (int q = g.lane; q < c.na * 3; q += 32) mylig[q] = 0;
   __syncwarp();
-  // this thread's partial sum, compensated (two-sum per term): a CN of
+  // this thread's partial sums, compensated (two-sum per term): a CN of
   // thousands must be exact to ~1e-8 relative to place a hill two grid
-  // spacings wide, below FP32's resolution
-  Real sacc = 0, scomp = 0;
+  // spacings wide, below FP32's resolution. One accumulator per owned B
+  // entry keeps the two-sum chains independent.
   constexpr int JB = 4;
+  Real sacc[JB], scomp[JB];
+#pragma unroll
+  for (int jj = 0; jj < JB; ++jj) sacc[jj] = scomp[jj] = 0;
   for (int jb0 = 0; jb0 < c.nb; jb0 += g.G * JB) {
     Real xj[JB], yj[JB], zj[JB], gxj[JB], gyj[JB], gzj[JB], mj[JB];
 #pragma unroll
@@ -383,9 +386,9 @@ __device__ void cv_coord(const Grp &g, GroupFixed<Real> *fx, int k, const typena
           Real sw = rcp_fast<Real>((Real)1 + q2 * q);
           Real m = oki ? mj[jj] : (Real)0;
           Real term = m * sw, tsum, terr;
-          two_sum<Real>(sacc, term, tsum, terr);
-          sacc = tsum;
-          scomp += terr;
+          two_sum<Real>(sacc[jj], term, tsum, terr);
+          sacc[jj] = tsum;
+          scomp[jj] += terr;
           Real gf = c6 * m * q2 * sw * sw;
           gi[ii][0] += gf * dx;
           gi[ii][1] += gf * dy;
@@ -415,7 +418,9 @@ __device__ void cv_coord(const Grp &g, GroupFixed<Real> *fx, int k, const typena
   // a few hundred needs more than FP32's 24 bits to place a hill two grid
   // spacings wide
   Real sh, sl;
-  two_sum<Real>(sacc, scomp, sh, sl);
+  two_sum<Real>(sacc[0], scomp[0], sh, sl);
+#pragma unroll
+  for (int jj = 1; jj < JB; ++jj) ff_add<Real>(sh, sl, sacc[jj], scomp[jj]);
   grp_sum_ff<Real>(g, sh, sl, fx->red);
   if (g.t == 0) {
     fx->sh[k] = sh;
