@@ -407,6 +407,111 @@ def bench_shared(abp, synth, torch, dev, sm_mhz):
         ctx.close()
 
 
+def bench_serve(abp, synth, torch, dev, seconds=2.0, rate=20_000.0):
+    """4096 simulations (2D grids 64^2..1024^2, 8..256 atoms, stride 20..500):
+    Poisson step requests at `rate`/s for `seconds` (latency), then a deep
+    backlog (saturation throughput)."""
+    import threading
+
+    ctx = abp.Context(dev, budget=120 << 30)
+    srv = None
+    try:
+        nsim = 4096
+        specs = synth.serve_specs(seed=61, nsim=nsim)
+        tmpl = synth.serve_templates(61, specs)
+        srv = abp.abp_server_create(ctx.handle, max_batch=4096, max_atoms=256, nstreams=2)
+        sims, keep = [], []
+        for sp in specs:
+            desc, k = abp.walker_desc(sp)
+            keep.append(k)
+            sims.append(abp.abp_server_admit(srv, abp.grid_desc(sp["grid"]), desc))
+        hbm = abp.abp_ctx_bytes(ctx.handle)[0]
+        r = synth.rng(62)
+        nf = 4
+        frames = []
+        for t in tmpl:
+            x = np.zeros((nf, t.shape[0], 4), dtype=np.float32)
+            x[..., :3] = t[None] + r.normal(scale=0.02, size=(nf,) + t.shape)
+            frames.append(x)
+        forces = [np.zeros_like(f[0]) for f in frames]
+        step = np.zeros(nsim, dtype=np.int64)
+        results = []
+        done = threading.Event()
+
+        def poller():
+            while not done.is_set():
+                results.extend(abp.abp_server_poll(srv, 8192, wait_ms=20))
+            results.extend(abp.abp_server_poll(srv, 1 << 20))
+
+        # warm-up: one request per simulation
+        th = threading.Thread(target=poller)
+        th.start()
+        for i in range(nsim):
+            abp.abp_server_submit(srv, sims[i], int(step[i]), frames[i][0], forces[i], i)
+            step[i] += 1
+        while len(results) < nsim:
+            time.sleep(0.01)
+        results.clear()
+        # Poisson arrivals
+        n_req = int(rate * seconds)
+        gaps = r.exponential(1.0 / rate, size=n_req)
+        who = r.integers(0, nsim, size=n_req)
+        t0 = time.perf_counter()
+        t_next = t0
+        for k in range(n_req):
+            t_next += gaps[k]
+            while time.perf_counter() < t_next:
+                pass
+            i = int(who[k])
+            abp.abp_server_submit(srv, sims[i], int(step[i]), frames[i][step[i] % nf], forces[i], i)
+            step[i] += 1
+        t_sub = time.perf_counter() - t0
+        while len(results) < n_req and time.perf_counter() - t0 < seconds + 30:
+            time.sleep(0.005)
+        t_all = time.perf_counter() - t0
+        lat = np.array([x.t_done - x.t_submit for x in results]) * 1e6
+        batches = np.array([x.batch for x in results])
+        poisson = {"offered_rate": rate, "requests": n_req, "completed": len(results),
+                   "achieved_rate": len(results) / t_all, "submit_rate": n_req / t_sub,
+                   "p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
+                   "mean_batch": float(batches.mean())}
+        results.clear()
+        # saturation: a backlog of `depth` requests per simulation, queued in one call
+        depth = 8
+        order = [i for d in range(depth) for i in range(nsim)]
+        sim_ids = np.array([sims[i] for i in order], dtype=np.int64)
+        steps_arr = np.empty(len(order), dtype=np.int64)
+        chunks = []
+        for k, i in enumerate(order):
+            steps_arr[k] = step[i]
+            chunks.append(frames[i][step[i] % nf])
+            step[i] += 1
+        packed = np.ascontiguousarray(np.concatenate(chunks, axis=0))
+        out = np.zeros_like(packed)
+        t0 = time.perf_counter()
+        abp.abp_server_submit_many(srv, sim_ids, steps_arr, packed, out)
+        t_sub = time.perf_counter() - t0
+        while len(results) < nsim * depth and time.perf_counter() - t0 < 120:
+            time.sleep(0.005)
+        t_all = time.perf_counter() - t0
+        lat = np.array([x.t_done - x.t_submit for x in results]) * 1e6
+        sat = {"requests": nsim * depth, "completed": len(results), "throughput": len(results) / t_all,
+               "submit_seconds": t_sub, "mean_batch": float(np.mean([x.batch for x in results]))}
+        done.set()
+        th.join()
+        st = abp.abp_server_stats(srv)
+        return {"workload": "4096 simulations, 2D grids 64^2..1024^2 FP32+comp, 8..256 atoms, stride 20..500; "
+                            "Poisson step requests (host coords in, host forces out)",
+                "value": sat["throughput"], "unit": "bias steps/s (served, saturated)",
+                "admitted": len(sims), "hbm_bytes": hbm, "poisson": poisson, "saturation": sat,
+                "launches": st["launches"]}
+    finally:
+        if srv is not None:
+            abp.abp_server_destroy(srv)
+        torch.cuda.synchronize()
+        ctx.close()
+
+
 # ---------------------------------------------------------------- our arm
 
 
@@ -544,7 +649,8 @@ def main():
         extra = {}
         for name, fn in (("double_well_fp64", lambda: bench_double_well(abp, synth, torch, dev)),
                          ("uneven1000", lambda: bench_uneven(abp, synth, torch, dev, sm)),
-                         ("shared256", lambda: bench_shared(abp, synth, torch, dev, sm))):
+                         ("shared256", lambda: bench_shared(abp, synth, torch, dev, sm)),
+                         ("serve4096", lambda: bench_serve(abp, synth, torch, dev))):
             try:
                 extra[name] = fn()
             except Exception as e:  # report, do not hide the headline

@@ -244,6 +244,69 @@ abp_status abp_deposit_log_readout(abp_ctx *ctx, abp_deposit_rec *dst, size_t ca
                                    size_t *n_total);
 abp_status abp_deposit_log_clear(abp_ctx *ctx);
 
+/* ---- serving: continuous batching of step requests ------------------------ */
+
+/* A request loop over many concurrent simulations (one walker each): every
+ * simulation's grid and state stay on the device; callers submit one MD step
+ * at a time (host coordinates in, host forces out) from any thread; a worker
+ * thread packs the requests that are ready into the next launch of the fused
+ * kernel on one of nstreams streams while earlier launches are still in
+ * flight (continuous batching), and hands each finished request back through
+ * abp_server_poll. A simulation has at most one step in flight: its later
+ * requests wait, in order, for the earlier ones (each step depends on the
+ * grid after the previous one). A walker's result is the same alone and in
+ * any mix of requests. The server owns the context's stream while it runs. */
+typedef struct abp_server abp_server;
+
+typedef struct {
+  int max_batch;   /* requests per launch (0 = 4096) */
+  int max_atoms;   /* largest walker block accepted (0 = 1024 atoms) */
+  int nstreams;    /* launches in flight at once (0 = 2) */
+} abp_server_desc;
+
+typedef struct {
+  int64_t sim;        /* simulation id */
+  int64_t step;       /* MD step of the request */
+  uint64_t tag;       /* the caller's tag */
+  double t_submit;    /* host steady-clock seconds at submit */
+  double t_done;      /* host steady-clock seconds when the forces were in forces_host */
+  int32_t status;     /* ABP_OK, or an error code (then forces_host is untouched) */
+  int32_t batch;      /* requests in the launch that served it */
+} abp_result;
+
+abp_status abp_server_create(abp_ctx *ctx, const abp_server_desc *desc, abp_server **out);
+/* Stops the worker after the requests in flight finish; unfinished queued
+ * requests are dropped. Frees every admitted simulation. */
+void abp_server_destroy(abp_server *srv);
+/* Admits a simulation: creates its grid and walker against the context's
+ * HBM budget; returns ABP_ERR_ADMISSION (nothing allocated) when they do not
+ * fit, so the caller can retry after abp_server_release frees memory.
+ * Simulations sharing a grid are not served (walkers on own grids only). */
+abp_status abp_server_admit(abp_server *srv, const abp_grid_desc *grid, const abp_walker_desc *walker,
+                            int64_t *sim);
+/* Releases a simulation once its requests have finished (waits for them). */
+abp_status abp_server_release(abp_server *srv, int64_t sim);
+/* Queues MD step `step` of simulation `sim`: coords_host (natoms float
+ * records x, y, z, pad) is copied before the call returns; the bias forces
+ * are written (overwrite) to forces_host (natoms float records, caller-owned,
+ * valid until the request is polled). */
+abp_status abp_server_submit(abp_server *srv, int64_t sim, int64_t step, const float *coords_host,
+                             float *forces_host, uint64_t tag);
+/* n requests in one call: request k is (sims[k], steps[k], tags[k]); its
+ * coordinates follow those of request k-1 in coords_host (natoms records of
+ * its simulation each) and its forces land at the same offset of
+ * forces_host. All are queued together (under one lock), in order. */
+abp_status abp_server_submit_many(abp_server *srv, int n, const int64_t *sims, const int64_t *steps,
+                                  const float *coords_host, float *forces_host, const uint64_t *tags);
+/* Up to cap finished requests, oldest first; waits up to wait_ms for the
+ * first one when none is ready (0 = do not wait). */
+abp_status abp_server_poll(abp_server *srv, abp_result *out, int cap, int *n_out, int wait_ms);
+/* Counters: requests submitted, finished, launches, and requests queued now. */
+abp_status abp_server_stats(abp_server *srv, int64_t *submitted, int64_t *finished, int64_t *launches,
+                            int64_t *queued);
+/* Host steady-clock seconds (the clock of abp_result). */
+double abp_server_now(void);
+
 /* ---- allocation-free step -------------------------------------------------- */
 
 /* abp_step_static: one MD step (a1..a5) of one walker, allocating nothing on

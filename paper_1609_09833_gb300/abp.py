@@ -58,6 +58,15 @@ class DepositRec(C.Structure):
                 ("height", C.c_double)]
 
 
+class ServerDesc(C.Structure):
+    _fields_ = [("max_batch", C.c_int), ("max_atoms", C.c_int), ("nstreams", C.c_int)]
+
+
+class Result(C.Structure):
+    _fields_ = [("sim", C.c_int64), ("step", C.c_int64), ("tag", C.c_uint64), ("t_submit", C.c_double),
+                ("t_done", C.c_double), ("status", C.c_int32), ("batch", C.c_int32)]
+
+
 _vp, _i64p = C.c_void_p, C.POINTER(C.c_int64)
 _SIGS = {
     "abp_ctx_create": [C.POINTER(_vp), C.c_int, _vp, C.c_size_t],
@@ -87,10 +96,19 @@ _SIGS = {
     "abp_sync": [_vp],
     "abp_step_static": [C.c_int, _vp, C.POINTER(GridDesc), _vp, C.POINTER(WalkerDesc), _vp, C.c_int, _vp, C.c_int,
                         C.c_int64],
+    "abp_server_create": [_vp, C.POINTER(ServerDesc), C.POINTER(_vp)],
+    "abp_server_destroy": [_vp],
+    "abp_server_admit": [_vp, C.POINTER(GridDesc), C.POINTER(WalkerDesc), C.POINTER(C.c_int64)],
+    "abp_server_release": [_vp, C.c_int64],
+    "abp_server_submit": [_vp, C.c_int64, C.c_int64, _vp, _vp, C.c_uint64],
+    "abp_server_submit_many": [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp],
+    "abp_server_poll": [_vp, C.POINTER(Result), C.c_int, C.POINTER(C.c_int), C.c_int],
+    "abp_server_stats": [_vp, _i64p, _i64p, _i64p, _i64p],
+    "abp_server_now": [],
     "abp_last_error": [],
     "abp_version": [],
 }
-_VOID = {"abp_ctx_destroy", "abp_grid_destroy", "abp_walker_destroy"}
+_VOID = {"abp_ctx_destroy", "abp_grid_destroy", "abp_walker_destroy", "abp_server_destroy"}
 _STR = {"abp_last_error", "abp_version"}
 
 _lib_handle = None
@@ -113,6 +131,7 @@ def load():
             f.argtypes = args
             f.restype = None if name in _VOID else (C.c_char_p if name in _STR else C.c_int)
         L.abp_walker_id.restype = C.c_int32
+        L.abp_server_now.restype = C.c_double
         _lib_handle = L
     return _lib_handle
 
@@ -273,6 +292,56 @@ def abp_step_static(device, stream, grid_desc: GridDesc, grid_records, walker_de
                     coords_dtype, forces, mode, step):
     _check(load().abp_step_static(int(device), stream, C.byref(grid_desc), _ptr(grid_records), C.byref(walker_desc),
                                   _ptr(coords), int(coords_dtype), _ptr(forces), int(mode), int(step)))
+
+
+def abp_server_create(ctx, max_batch=0, max_atoms=0, nstreams=0):
+    d = ServerDesc(int(max_batch), int(max_atoms), int(nstreams))
+    h = _vp()
+    _check(load().abp_server_create(ctx, C.byref(d), C.byref(h)))
+    return h.value
+
+
+def abp_server_destroy(srv):
+    load().abp_server_destroy(srv)
+
+
+def abp_server_admit(srv, grid: GridDesc, walker: WalkerDesc) -> int:
+    sim = C.c_int64()
+    _check(load().abp_server_admit(srv, C.byref(grid), C.byref(walker), C.byref(sim)))
+    return sim.value
+
+
+def abp_server_release(srv, sim: int):
+    _check(load().abp_server_release(srv, int(sim)))
+
+
+def abp_server_submit(srv, sim: int, step: int, coords_host, forces_host, tag: int = 0):
+    _check(load().abp_server_submit(srv, int(sim), int(step), _ptr(coords_host), _ptr(forces_host), int(tag)))
+
+
+def abp_server_submit_many(srv, sims, steps, coords_host, forces_host, tags=None):
+    sims = np.ascontiguousarray(sims, dtype=np.int64)
+    steps = np.ascontiguousarray(steps, dtype=np.int64)
+    tg = None if tags is None else np.ascontiguousarray(tags, dtype=np.uint64)
+    _check(load().abp_server_submit_many(srv, len(sims), _ptr(sims), _ptr(steps), _ptr(coords_host),
+                                         _ptr(forces_host), _ptr(tg)))
+
+
+def abp_server_poll(srv, cap: int = 4096, wait_ms: int = 0):
+    buf = (Result * max(1, cap))()
+    n = C.c_int()
+    _check(load().abp_server_poll(srv, buf, int(cap), C.byref(n), int(wait_ms)))
+    return [buf[i] for i in range(n.value)]
+
+
+def abp_server_stats(srv):
+    v = [C.c_int64() for _ in range(4)]
+    _check(load().abp_server_stats(srv, *[C.byref(x) for x in v]))
+    return {"submitted": v[0].value, "finished": v[1].value, "launches": v[2].value, "queued": v[3].value}
+
+
+def abp_server_now() -> float:
+    return float(load().abp_server_now())
 
 
 def abp_last_error() -> str:

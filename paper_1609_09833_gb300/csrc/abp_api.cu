@@ -1042,3 +1042,443 @@ abp_status abp_sync(abp_ctx *ctx) {
 }
 
 }  // extern "C"
+
+// ===================================================================== serving
+//
+// abp_server: continuous batching of single-step requests from many
+// simulations. A worker thread owns nstreams "slots" (stream, event, pinned
+// and device buffers for coordinates, forces, offsets, per-walker steps and
+// the walker table). It fills a free slot with the front request of every
+// ready simulation (FIFO, up to max_batch), launches the fused kernel for one
+// step on the slot's stream and moves on; finished slots are harvested by
+// event query, their forces copied to the callers' buffers, and the
+// simulations made ready again if they have queued requests.
+
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <thread>
+#include <unordered_map>
+
+namespace {
+
+double steady_now() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct SrvRequest {
+  int64_t sim = 0, step = 0;
+  uint64_t tag = 0;
+  float *forces_host = nullptr;
+  double t_submit = 0;
+  std::vector<float> coords;
+};
+
+struct SrvSim {
+  abp_grid *grid = nullptr;
+  abp_walker *walker = nullptr;
+  int natoms = 0;
+  std::deque<SrvRequest> pending;
+  bool busy = false;
+};
+
+struct SrvSlot {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  float *h_in = nullptr, *h_out = nullptr;
+  long long *h_off = nullptr, *h_step = nullptr;
+  TableEntry *h_table = nullptr;
+  float *d_in = nullptr, *d_out = nullptr;
+  long long *d_off = nullptr, *d_step = nullptr;
+  TableEntry *d_table = nullptr;
+  std::vector<SrvRequest> reqs;
+  bool busy = false;
+  int status = ABP_OK;
+};
+
+}  // namespace
+
+struct abp_server {
+  abp_ctx *ctx = nullptr;
+  int max_batch = 4096, max_atoms = 1024, nstreams = 2;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::unordered_map<int64_t, SrvSim> sims;
+  int64_t next_sim = 0;
+  std::deque<int64_t> ready;
+  std::deque<abp_result> results;
+  std::vector<SrvSlot> slots;
+  std::thread worker;
+  bool stop = false;
+  int64_t submitted = 0, finished = 0, launches = 0, queued = 0;
+};
+
+namespace {
+
+void srv_free_slots(abp_server *s) {
+  for (auto &sl : s->slots) {
+    if (sl.stream) cudaStreamSynchronize(sl.stream);
+    cudaFreeHost(sl.h_in);
+    cudaFreeHost(sl.h_out);
+    cudaFreeHost(sl.h_off);
+    cudaFreeHost(sl.h_step);
+    cudaFreeHost(sl.h_table);
+    cudaFree(sl.d_in);
+    cudaFree(sl.d_out);
+    cudaFree(sl.d_off);
+    cudaFree(sl.d_step);
+    cudaFree(sl.d_table);
+    if (sl.done) cudaEventDestroy(sl.done);
+    if (sl.stream) cudaStreamDestroy(sl.stream);
+  }
+  s->slots.clear();
+}
+
+// Launch the requests now in the slot (called without the server lock).
+int srv_launch(abp_server *s, SrvSlot &sl) {
+  const int n = (int)sl.reqs.size();
+  std::vector<abp_walker *> ws(n);
+  long long off = 0;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (int i = 0; i < n; ++i) ws[i] = s->sims[sl.reqs[i].sim].walker;
+  }
+  for (int i = 0; i < n; ++i) {
+    const SrvRequest &r = sl.reqs[i];
+    sl.h_off[i] = off;
+    sl.h_step[i] = r.step;
+    sl.h_table[i] = TableEntry{ws[i]->dd, i, 0};
+    std::memcpy(sl.h_in + off * 4, r.coords.data(), r.coords.size() * sizeof(float));
+    off += ws[i]->hd.natoms;
+  }
+  RunArgs a{};
+  int st = pick_shape(s->ctx, ws.data(), n, 0, 1, &a.G, &a.groups_per_cta, &a.group_bytes, &a.tile_budget);
+  if (st) return st;
+  cudaStream_t stream = sl.stream;
+  if (cudaMemcpyAsync(sl.d_in, sl.h_in, (size_t)off * 16, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+      cudaMemcpyAsync(sl.d_off, sl.h_off, (size_t)n * 8, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+      cudaMemcpyAsync(sl.d_step, sl.h_step, (size_t)n * 8, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+      cudaMemcpyAsync(sl.d_table, sl.h_table, (size_t)n * sizeof(TableEntry), cudaMemcpyHostToDevice, stream) !=
+          cudaSuccess)
+    return ABP_ERR_CUDA;
+  a.table = sl.d_table;
+  a.nw = n;
+  a.coords = sl.d_in;
+  a.coff = sl.d_off;
+  a.cstride = 0;
+  a.forces = sl.d_out;
+  a.foff = sl.d_off;
+  a.fstride = 0;
+  a.mode = ABP_FORCES_OVERWRITE;
+  a.step0 = 0;
+  a.wstep = sl.d_step;
+  a.nsteps = 1;
+  a.log = s->ctx->log;
+  a.ctr = s->ctx->ctr;
+  if (launch_run(a, 0, stream) != cudaSuccess) return ABP_ERR_CUDA;
+  if (cudaMemcpyAsync(sl.h_out, sl.d_out, (size_t)off * 16, cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+    return ABP_ERR_CUDA;
+  if (cudaEventRecord(sl.done, stream) != cudaSuccess) return ABP_ERR_CUDA;
+  return ABP_OK;
+}
+
+// Deliver a finished slot's requests (called without the server lock).
+void srv_complete(abp_server *s, SrvSlot &sl) {
+  const int n = (int)sl.reqs.size();
+  const double t = steady_now();
+  std::vector<abp_result> res(n);
+  for (int i = 0; i < n; ++i) {
+    SrvRequest &r = sl.reqs[i];
+    if (sl.status == ABP_OK)
+      std::memcpy(r.forces_host, sl.h_out + sl.h_off[i] * 4, r.coords.size() * sizeof(float));
+    res[i] = abp_result{r.sim, r.step, r.tag, r.t_submit, t, sl.status, n};
+  }
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (int i = 0; i < n; ++i) {
+      s->results.push_back(res[i]);
+      auto it = s->sims.find(sl.reqs[i].sim);
+      if (it != s->sims.end()) {
+        it->second.busy = false;
+        if (!it->second.pending.empty()) s->ready.push_back(sl.reqs[i].sim);
+      }
+    }
+    s->finished += n;
+    sl.reqs.clear();
+    sl.busy = false;
+  }
+  s->cv_done.notify_all();
+}
+
+void srv_worker(abp_server *s) {
+  cudaSetDevice(s->ctx->device);
+  for (;;) {
+    // harvest
+    bool any_busy = false;
+    for (auto &sl : s->slots) {
+      if (!sl.busy) continue;
+      cudaError_t q = cudaEventQuery(sl.done);
+      if (q == cudaSuccess || (q != cudaErrorNotReady && (sl.status = ABP_ERR_CUDA, true))) {
+        if (q != cudaSuccess) cudaGetLastError();
+        srv_complete(s, sl);
+      } else {
+        any_busy = true;
+      }
+    }
+    // launch
+    SrvSlot *free_slot = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      if (s->stop && !any_busy) break;
+      for (auto &sl : s->slots)
+        if (!sl.busy) {
+          free_slot = &sl;
+          break;
+        }
+      if (free_slot && !s->ready.empty() && !s->stop) {
+        int atoms = 0;
+        while (!s->ready.empty() && (int)free_slot->reqs.size() < s->max_batch) {
+          int64_t id = s->ready.front();
+          auto it = s->sims.find(id);
+          if (it == s->sims.end() || it->second.busy || it->second.pending.empty()) {
+            s->ready.pop_front();
+            continue;
+          }
+          if (atoms + it->second.natoms > s->max_batch * s->max_atoms) break;
+          s->ready.pop_front();
+          it->second.busy = true;
+          atoms += it->second.natoms;
+          free_slot->reqs.push_back(std::move(it->second.pending.front()));
+          it->second.pending.pop_front();
+          --s->queued;
+        }
+        free_slot->busy = !free_slot->reqs.empty();
+      } else {
+        free_slot = nullptr;
+        if (!any_busy) {
+          s->cv_work.wait_for(lk, std::chrono::milliseconds(2));
+          continue;
+        }
+      }
+    }
+    if (free_slot && free_slot->busy) {
+      free_slot->status = srv_launch(s, *free_slot);
+      if (free_slot->status != ABP_OK) {
+        cudaGetLastError();
+        srv_complete(s, *free_slot);
+      } else {
+        std::lock_guard<std::mutex> lk(s->mu);
+        ++s->launches;
+      }
+      continue;
+    }
+    if (any_busy) std::this_thread::sleep_for(std::chrono::microseconds(5));
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+double abp_server_now(void) { return steady_now(); }
+
+abp_status abp_server_create(abp_ctx *ctx, const abp_server_desc *desc, abp_server **out) {
+  if (!ctx || !out) return fail(ABP_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  abp_server *s = new (std::nothrow) abp_server();
+  if (!s) return fail(ABP_ERR_OOM, "host allocation failed");
+  s->ctx = ctx;
+  if (desc) {
+    if (desc->max_batch < 0 || desc->max_atoms < 0 || desc->nstreams < 0 || desc->nstreams > 8) {
+      delete s;
+      return fail(ABP_ERR_INVALID_ARG, "bad server descriptor");
+    }
+    if (desc->max_batch) s->max_batch = desc->max_batch;
+    if (desc->max_atoms) s->max_atoms = desc->max_atoms;
+    if (desc->nstreams) s->nstreams = desc->nstreams;
+  }
+  abp_status st = set_device(ctx);
+  if (st) {
+    delete s;
+    return st;
+  }
+  const size_t rec = (size_t)s->max_batch * s->max_atoms * 16;
+  s->slots.resize(s->nstreams);
+  cudaError_t e = cudaSuccess;
+  for (auto &sl : s->slots) {
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaHostAlloc(&sl.h_in, rec, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc(&sl.h_out, rec, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc(&sl.h_off, (size_t)s->max_batch * 8, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc(&sl.h_step, (size_t)s->max_batch * 8, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc(&sl.h_table, (size_t)s->max_batch * sizeof(TableEntry), cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaMalloc(&sl.d_in, rec);
+    if (e == cudaSuccess) e = cudaMalloc(&sl.d_out, rec);
+    if (e == cudaSuccess) e = cudaMalloc(&sl.d_off, (size_t)s->max_batch * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&sl.d_step, (size_t)s->max_batch * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&sl.d_table, (size_t)s->max_batch * sizeof(TableEntry));
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    srv_free_slots(s);
+    delete s;
+    return fail(ABP_ERR_OOM, "server buffers: %s", cudaGetErrorString(e));
+  }
+  s->worker = std::thread(srv_worker, s);
+  *out = s;
+  return ABP_OK;
+}
+
+void abp_server_destroy(abp_server *s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv_work.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  set_device(s->ctx);
+  srv_free_slots(s);
+  for (auto &kv : s->sims) {
+    abp_walker_destroy(kv.second.walker);
+    abp_grid_destroy(kv.second.grid);
+  }
+  delete s;
+}
+
+abp_status abp_server_admit(abp_server *s, const abp_grid_desc *g, const abp_walker_desc *w, int64_t *sim) {
+  if (!s || !g || !w || !sim) return fail(ABP_ERR_INVALID_ARG, "NULL argument");
+  if (g->shared) return fail(ABP_ERR_UNSUPPORTED, "the server takes walkers on their own grids");
+  if (g->precision != ABP_PREC_FP32_COMP) return fail(ABP_ERR_UNSUPPORTED, "the server serves FP32_COMP grids");
+  if (w->natoms > s->max_atoms) return fail(ABP_ERR_INVALID_ARG, "walker has more atoms than max_atoms");
+  abp_grid *grid = nullptr;
+  abp_status st = abp_create_grid(s->ctx, g, &grid);
+  if (st) return st;
+  abp_walker *walker = nullptr;
+  st = abp_walker_create(s->ctx, grid, w, &walker);
+  if (st) {
+    std::string msg = g_err;
+    abp_grid_destroy(grid);
+    return fail(st, "%s", msg.c_str());
+  }
+  if (walker->big) {
+    abp_walker_destroy(walker);
+    abp_grid_destroy(grid);
+    return fail(ABP_ERR_UNSUPPORTED, "the server serves walkers that fit one walker group");
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  int64_t id = s->next_sim++;
+  SrvSim &sm = s->sims[id];
+  sm.grid = grid;
+  sm.walker = walker;
+  sm.natoms = w->natoms;
+  *sim = id;
+  return ABP_OK;
+}
+
+abp_status abp_server_release(abp_server *s, int64_t sim) {
+  if (!s) return fail(ABP_ERR_INVALID_ARG, "NULL argument");
+  SrvSim sm;
+  {
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->sims.find(sim);
+    if (it == s->sims.end()) return fail(ABP_ERR_INVALID_ARG, "unknown simulation %lld", (long long)sim);
+    if (!s->cv_done.wait_for(lk, std::chrono::seconds(60), [&] {
+          auto jt = s->sims.find(sim);
+          return jt == s->sims.end() || (!jt->second.busy && jt->second.pending.empty());
+        }))
+      return fail(ABP_ERR_TIMEOUT, "simulation %lld still has requests after 60 s", (long long)sim);
+    it = s->sims.find(sim);
+    sm = std::move(it->second);
+    s->sims.erase(it);
+  }
+  abp_walker_destroy(sm.walker);
+  abp_grid_destroy(sm.grid);
+  return ABP_OK;
+}
+
+abp_status abp_server_submit(abp_server *s, int64_t sim, int64_t step, const float *coords_host, float *forces_host,
+                             uint64_t tag) {
+  if (!s || !coords_host || !forces_host) return fail(ABP_ERR_INVALID_ARG, "NULL argument");
+  if (step < 0) return fail(ABP_ERR_INVALID_ARG, "step must be >= 0");
+  SrvRequest r;
+  r.sim = sim;
+  r.step = step;
+  r.tag = tag;
+  r.forces_host = forces_host;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->sims.find(sim);
+    if (it == s->sims.end()) return fail(ABP_ERR_INVALID_ARG, "unknown simulation %lld", (long long)sim);
+    r.coords.assign(coords_host, coords_host + (size_t)it->second.natoms * 4);
+    r.t_submit = steady_now();
+    bool was_idle = !it->second.busy && it->second.pending.empty();
+    it->second.pending.push_back(std::move(r));
+    if (was_idle) s->ready.push_back(sim);
+    ++s->submitted;
+    ++s->queued;
+  }
+  s->cv_work.notify_one();
+  return ABP_OK;
+}
+
+abp_status abp_server_submit_many(abp_server *s, int n, const int64_t *sims, const int64_t *steps,
+                                  const float *coords_host, float *forces_host, const uint64_t *tags) {
+  if (!s || n < 0 || (n > 0 && (!sims || !steps || !coords_host || !forces_host)))
+    return fail(ABP_ERR_INVALID_ARG, "NULL argument");
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    size_t off = 0;
+    for (int k = 0; k < n; ++k) {
+      auto it = s->sims.find(sims[k]);
+      if (it == s->sims.end()) return fail(ABP_ERR_INVALID_ARG, "unknown simulation %lld", (long long)sims[k]);
+      if (steps[k] < 0) return fail(ABP_ERR_INVALID_ARG, "step must be >= 0");
+    }
+    const double t = steady_now();
+    for (int k = 0; k < n; ++k) {
+      SrvSim &sm = s->sims[sims[k]];
+      SrvRequest r;
+      r.sim = sims[k];
+      r.step = steps[k];
+      r.tag = tags ? tags[k] : 0;
+      r.forces_host = forces_host + off * 4;
+      r.coords.assign(coords_host + off * 4, coords_host + (off + sm.natoms) * 4);
+      r.t_submit = t;
+      off += sm.natoms;
+      bool was_idle = !sm.busy && sm.pending.empty();
+      sm.pending.push_back(std::move(r));
+      if (was_idle) s->ready.push_back(sims[k]);
+    }
+    s->submitted += n;
+    s->queued += n;
+  }
+  s->cv_work.notify_one();
+  return ABP_OK;
+}
+
+abp_status abp_server_poll(abp_server *s, abp_result *out, int cap, int *n_out, int wait_ms) {
+  if (!s || !n_out || (cap > 0 && !out)) return fail(ABP_ERR_INVALID_ARG, "NULL argument");
+  std::unique_lock<std::mutex> lk(s->mu);
+  if (s->results.empty() && wait_ms > 0)
+    s->cv_done.wait_for(lk, std::chrono::milliseconds(wait_ms), [&] { return !s->results.empty(); });
+  int n = 0;
+  while (n < cap && !s->results.empty()) {
+    out[n++] = s->results.front();
+    s->results.pop_front();
+  }
+  *n_out = n;
+  return ABP_OK;
+}
+
+abp_status abp_server_stats(abp_server *s, int64_t *submitted, int64_t *finished, int64_t *launches, int64_t *queued) {
+  if (!s) return fail(ABP_ERR_INVALID_ARG, "NULL argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (submitted) *submitted = s->submitted;
+  if (finished) *finished = s->finished;
+  if (launches) *launches = s->launches;
+  if (queued) *queued = s->queued;
+  return ABP_OK;
+}
+
+}  // extern "C"

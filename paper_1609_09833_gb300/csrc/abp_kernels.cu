@@ -182,12 +182,13 @@ __device__ void walker_steps(const Grp &g, GroupFixed<Real> *fx, unsigned char *
   const long long foff = a.forces ? a.foff[widx] : 0;
   const int mode = a.forces ? a.mode : ABP_FORCES_OVERWRITE;
   const int pieces = natoms * (int)(sizeof(R4) / 16);
+  const long long step0 = a.wstep ? a.wstep[widx] : a.step0;
   auto prefetch = [&](int t, R4 *dst) {
     const unsigned char *src = reinterpret_cast<const unsigned char *>(cin + coff + (long long)t * a.cstride);
     for (int p = g.t; p < pieces; p += g.G) cp_async16(reinterpret_cast<unsigned char *>(dst) + p * 16, src + p * 16);
     cp_async_commit();
   };
-  long long rem = a.step0 % wd.stride;
+  long long rem = step0 % wd.stride;
   long long next_dep = rem == 0 ? 0 : wd.stride - rem;  // step index (t) of the next deposit
   if (TILE && g.t == 0) {
     fx->reload = 1;
@@ -195,7 +196,7 @@ __device__ void walker_steps(const Grp &g, GroupFixed<Real> *fx, unsigned char *
   }
   prefetch(0, xb[0]);
   for (int t = 0; t < a.nsteps; ++t) {
-    const long long step = a.step0 + t;
+    const long long step = step0 + t;
     R4 *xs = xb[t & 1];
     cp_async_wait_all();
     g.sync();

@@ -30,6 +30,7 @@ struct RunArgs {
   long long fstride;
   int mode;
   long long step0;
+  const long long *wstep;  // optional: per-walker first step (indexed like coff), overrides step0
   int nsteps;
   int tile_budget;     // >0: dynamic shared bytes per group, the rest of which holds a grid tile
   DepositLog log;

@@ -1,0 +1,122 @@
+"""The serving loop (abp_server_*): continuous batching of single-step
+requests from many simulations. Each simulation's result is the same alone
+and in any mix (bit for bit: a walker's reductions have a fixed order) and
+matches the FP64 oracle; requests of one simulation complete in order;
+admission follows the context's HBM budget and resumes as memory frees."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1609_09833_gb300 import synth
+from tests import parity as P
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def abp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1609_09833_gb300 import abp as A
+    from paper_1609_09833_gb300 import build
+
+    build.build()
+    A.load()
+    return A
+
+
+def _frames(tmpl, seed, T):
+    r = synth.rng(seed)
+    return np.stack([tmpl + r.normal(scale=0.02, size=tmpl.shape) for _ in range(T)]).astype(np.float32)
+
+
+def _records(x):
+    rec = np.zeros(x.shape[:-1] + (4,), dtype=np.float32)
+    rec[..., :3] = x
+    return np.ascontiguousarray(rec)
+
+
+def _serve(abp, srv, sims, coords, steps, order):
+    """Submit requests in `order` ((sim index, step) pairs) and wait for all."""
+    out = {}
+    for i, t in order:
+        f = np.zeros_like(coords[i][t])
+        out[(i, t)] = f
+        abp.abp_server_submit(srv, sims[i], steps[t], coords[i][t], f, tag=i * 1000 + t)
+    got, deadline = [], time.time() + 60
+    while len(got) < len(order) and time.time() < deadline:
+        got += abp.abp_server_poll(srv, 4096, wait_ms=50)
+    assert len(got) == len(order)
+    assert all(r.status == 0 for r in got)
+    return out, got
+
+
+def test_results_alone_and_in_the_mix(abp):
+    ctx = abp.Context(0)
+    srv = abp.abp_server_create(ctx.handle, max_batch=256, max_atoms=256, nstreams=2)
+    try:
+        specs = synth.serve_specs(seed=3, nsim=40, side=(64, 160), stride=(2, 5))
+        tmpl = synth.serve_templates(3, specs)
+        T = 12
+        coords = [_records(_frames(t, 100 + i, T)) for i, t in enumerate(tmpl)]
+        steps = list(range(T))
+        keep = []
+
+        def admit(sp):
+            desc, k = abp.walker_desc(sp)
+            keep.append(k)
+            return abp.abp_server_admit(srv, abp.grid_desc(sp["grid"]), desc)
+
+        # simulation 0 alone (its twin is admitted separately for the mix)
+        alone = [admit(specs[0])]
+        out_alone, _ = _serve(abp, srv, alone, coords[:1], steps, [(0, t) for t in range(T)])
+        mix = [admit(sp) for sp in specs]
+        order = [(i, t) for t in range(T) for i in np.random.default_rng(7).permutation(len(specs))]
+        out_mix, got = _serve(abp, srv, mix, coords, steps, order)
+        for t in range(T):
+            assert np.array_equal(out_alone[(0, t)], out_mix[(0, t)])
+        # the mix really was batched, and each simulation's steps came back in order
+        assert max(r.batch for r in got) > 1
+        for i in range(len(specs)):
+            seq = [r.step for r in got if r.sim == mix[i]]
+            assert seq == sorted(seq)
+        # against the oracle, for a few simulations
+        for i in (0, 7, 21):
+            wo = oracle.Walker(specs[i])
+            ref = oracle.run([wo], coords[i][:, :, :3].astype(np.float64), [0], 0, T)
+            Fg = np.stack([out_mix[(i, t)][:, :3] for t in range(T)]).astype(np.float64)
+            assert P.force_err(Fg, ref["F"]) < P.TOL_F
+        st = abp.abp_server_stats(srv)
+        assert st["finished"] == st["submitted"] == T * (len(specs) + 1)
+        assert st["launches"] < st["finished"]
+    finally:
+        abp.abp_server_destroy(srv)
+        ctx.close()
+
+
+def test_admission_by_hbm_budget(abp):
+    ctx = abp.Context(0, budget=40 << 20)
+    srv = abp.abp_server_create(ctx.handle, max_batch=64, max_atoms=64, nstreams=2)
+    try:
+        spec = synth.serve_specs(seed=5, nsim=1, side=(512, 512), atoms=(16, 16))[0]  # 512^2 x 32 B = 8 MB grid
+        desc, keep = abp.walker_desc(spec)
+        sims = []
+        with pytest.raises(abp.AbpError) as e:
+            for _ in range(10):
+                sims.append(abp.abp_server_admit(srv, abp.grid_desc(spec["grid"]), desc))
+        assert e.value.code == abp.ABP_ERR_ADMISSION
+        assert 2 <= len(sims) < 10
+        x = _records(_frames(synth.serve_templates(5, [spec])[0], 1, 1))[0]
+        f = np.zeros_like(x)
+        abp.abp_server_submit(srv, sims[0], 0, x, f)
+        abp.abp_server_release(srv, sims[0])  # waits for its request, then frees its memory
+        sims.append(abp.abp_server_admit(srv, abp.grid_desc(spec["grid"]), desc))
+        got = abp.abp_server_poll(srv, 16, wait_ms=1000)
+        assert len(got) == 1 and got[0].status == 0
+        assert np.any(f != 0)
+    finally:
+        abp.abp_server_destroy(srv)
+        ctx.close()
