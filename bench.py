@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--tile", default="auto", choices=["auto", "on", "off"])
     ap.add_argument("--group-threads", type=int, default=0)
     ap.add_argument("--no-extra", action="store_true", help="skip the other workloads")
+    ap.add_argument("--only", default=None, choices=["double_well", "uneven", "shared", "serve"],
+                    help="run just one of the other workloads (for profiling) and print its record")
     return ap.parse_args()
 
 
@@ -515,6 +517,30 @@ def bench_serve(abp, synth, torch, dev, seconds=2.0, rate=20_000.0):
 # ---------------------------------------------------------------- our arm
 
 
+def kernel_source_hash():
+    import hashlib
+
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1609_09833_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def captured_traffic(kernel_key, units_per_launch):
+    """DRAM bytes per launch from the committed ncu capture, scaled to this
+    launch's units, or None when the kernel sources changed since."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)[kernel_key]
+    except (OSError, ValueError, KeyError):
+        return None
+    if rec.get("source_hash") != kernel_source_hash():
+        return None
+    return rec["dram_bytes"] / rec["units"] * units_per_launch
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -522,6 +548,16 @@ def main():
     import torch
 
     from paper_1609_09833_gb300 import abp, build, synth
+
+    if args.only:
+        torch.cuda.set_device(0)
+        build.build()
+        fn = {"double_well": lambda: bench_double_well(abp, synth, torch, 0),
+              "uneven": lambda: bench_uneven(abp, synth, torch, 0, 2070.0),
+              "shared": lambda: bench_shared(abp, synth, torch, 0, 2070.0),
+              "serve": lambda: bench_serve(abp, synth, torch, 0)}[args.only]
+        print(json.dumps({"only": args.only, **fn()}), flush=True)
+        return 0
 
     world, rank, local = dist_env()
     if world > 1:
@@ -635,8 +671,9 @@ def main():
 
     peaks, src = load_peaks()
     achieved = BYTES_PER_WALKER_STEP * NW * C / (kernel_ms / 1e3) / 1e9
+    traffic = captured_traffic("k_run_mb64", NW * C)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                 "kernel": "k_run<float>", "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs, copy)"
                 if src == "measured" else "fallback 6.8 TB/s"}
     cpu = None
