@@ -574,12 +574,17 @@ def main():
     abp.abp_ctx_tune(ctx.handle, abp.ABP_TUNE_TILE, {"auto": -1, "on": 1, "off": 0}[args.tile])
     abp.abp_ctx_tune(ctx.handle, abp.ABP_TUNE_GROUP_THREADS, args.group_threads)
     specs, fr = workload(SEED + 7919 * rank)
-    walkers = ctx.make_walkers(specs)
     C = args.md_steps
     nframes = max(FRAMES // C, 1) * C
     frames = abp.to_records(fr.frames(0, nframes)).cuda()  # [nframes, 64*36, 4]
     A = frames.shape[1]
     offs = torch.tensor(synth.offsets_of(specs), dtype=torch.int64, device="cuda")
+    tuned = None
+    if args.tile == "auto" and args.group_threads == 0:
+        from paper_1609_09833_gb300 import autotune
+
+        tuned = autotune.tune(ctx, specs, frames[:C], offs, C)["best"]
+    walkers = ctx.make_walkers(specs)
     F = torch.zeros(C, A, 4, device="cuda")
     OVER = abp.ABP_FORCES_OVERWRITE
     state = {"md": 0}
@@ -701,7 +706,7 @@ def main():
                                    "open-loop frames", "md_steps_per_step": C, "walkers_per_gpu": NW,
                        "atoms_per_walker": NATOMS, "grid": "256x256x3 fields", "deposit_stride": 50,
                        "l2": "inputs larger than L2: 4000 resident frames (147 MB) cycled",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}", "launch_shape": tuned},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -162,10 +162,14 @@ abp_status abp_ctx_bytes(const abp_ctx *ctx, size_t *used, size_t *budget);
  *   ABP_TUNE_TILE            1 = give groups a shared-memory tile of their
  *                            grid when it fits (launches of >= 8 steps),
  *                            0 or -1 = never (the default)
+ *   ABP_TUNE_LEAN            1 = FP32 launches without a tile use the
+ *                            kernel compiled for 128 registers per thread
+ *                            (two 256-thread CTAs per SM), 0 = the default
  * Invalid values return ABP_ERR_INVALID_ARG and leave the knob unchanged. */
 #define ABP_TUNE_GROUP_THREADS 1
 #define ABP_TUNE_GROUPS_PER_CTA 2
 #define ABP_TUNE_TILE 3
+#define ABP_TUNE_LEAN 4
 abp_status abp_ctx_tune(abp_ctx *ctx, int knob, int value);
 void abp_ctx_destroy(abp_ctx *ctx);
 

@@ -181,7 +181,7 @@ def abp_ctx_bytes(ctx):
     return u.value, b.value
 
 
-ABP_TUNE_GROUP_THREADS, ABP_TUNE_GROUPS_PER_CTA, ABP_TUNE_TILE = 1, 2, 3
+ABP_TUNE_GROUP_THREADS, ABP_TUNE_GROUPS_PER_CTA, ABP_TUNE_TILE, ABP_TUNE_LEAN = 1, 2, 3, 4
 
 
 def abp_ctx_tune(ctx, knob: int, value: int):

@@ -37,9 +37,10 @@ def candidates(specs):
     out = []
     for G in ((64, 128, 256) if cn else (32, 64)):
         for gpc in ((1, 2) if G >= 128 else (1, 2, 4)):
-            out.append({"group_threads": G, "groups_per_cta": gpc, "tile": 0})
+            for lean in (0, 1):
+                out.append({"group_threads": G, "groups_per_cta": gpc, "tile": 0, "lean": lean})
     if not cn:
-        out.append({"group_threads": 32, "groups_per_cta": 1, "tile": 1})
+        out.append({"group_threads": 32, "groups_per_cta": 1, "tile": 1, "lean": 0})
     return out
 
 
@@ -47,6 +48,7 @@ def _apply(ctx, c):
     abp.abp_ctx_tune(ctx.handle, abp.ABP_TUNE_GROUP_THREADS, c["group_threads"])
     abp.abp_ctx_tune(ctx.handle, abp.ABP_TUNE_GROUPS_PER_CTA, c["groups_per_cta"])
     abp.abp_ctx_tune(ctx.handle, abp.ABP_TUNE_TILE, c["tile"])
+    abp.abp_ctx_tune(ctx.handle, abp.ABP_TUNE_LEAN, c.get("lean", 0))
 
 
 def tune(ctx, specs, frames, offsets, nsteps: int, reps: int = 3, cache_path: str | None = DEFAULT_CACHE,
@@ -102,7 +104,7 @@ def tune(ctx, specs, frames, offsets, nsteps: int, reps: int = 3, cache_path: st
             abp.abp_grid_destroy(g)
         del ctx.grids[ngrids:]
     best = min(timings, key=lambda r: r["ms"])
-    best = {k: best[k] for k in ("group_threads", "groups_per_cta", "tile")}
+    best = {k: best[k] for k in ("group_threads", "groups_per_cta", "tile", "lean")}
     _apply(ctx, best)
     if cache_path:
         cache[key] = {"best": best, "timings": timings}

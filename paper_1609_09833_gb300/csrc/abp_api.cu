@@ -66,6 +66,7 @@ struct abp_ctx {
   int next_id = 0;
   int sms = 0;  // multiprocessors of the device
   int tune_G = 0, tune_gpc = 0, tune_tile = -1;  // tile -1: library default (off; opt in with 1)
+  int tune_lean = 0;
   std::vector<BigItem> big_key;                   // phased-form item lists of the last call
   BigItem *big_dev = nullptr;
   size_t big_cap = 0;
@@ -296,6 +297,10 @@ abp_status abp_ctx_tune(abp_ctx *ctx, int knob, int value) {
     case ABP_TUNE_TILE:
       if (value < -1 || value > 1) return fail(ABP_ERR_INVALID_ARG, "tile knob must be -1, 0 or 1");
       ctx->tune_tile = value;
+      return ABP_OK;
+    case ABP_TUNE_LEAN:
+      if (value < 0 || value > 1) return fail(ABP_ERR_INVALID_ARG, "lean knob must be 0 or 1");
+      ctx->tune_lean = value;
       return ABP_OK;
   }
   return fail(ABP_ERR_INVALID_ARG, "unknown knob %d", knob);
@@ -759,6 +764,7 @@ static abp_status run_common(abp_ctx *ctx, abp_walker *const *walkers, int n, co
                          &a.tile_budget)))
       return st;
     a.nw = (int)fw.size();
+    a.lean = ctx->tune_lean && !fp64;
     a.coords = coords;
     a.coff = reinterpret_cast<const long long *>(coff);
     a.cstride = cstride;

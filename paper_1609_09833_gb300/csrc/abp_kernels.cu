@@ -245,7 +245,7 @@ __device__ void walker_steps(const Grp &g, GroupFixed<Real> *fx, unsigned char *
 }
 
 template <typename Real, bool TILE>
-__global__ void __launch_bounds__(256, 1) k_run(RunArgs a) {
+__device__ __forceinline__ void run_body(const RunArgs &a) {
   extern __shared__ __align__(32) unsigned char smem[];
   const int gid = threadIdx.x / a.G;
   const int slot = blockIdx.x * a.groups_per_cta + gid;
@@ -272,6 +272,16 @@ __global__ void __launch_bounds__(256, 1) k_run(RunArgs a) {
     walker_steps<Real, false>(g, fx, dyn, L, a, te.idx);
 }
 
+template <typename Real, bool TILE>
+__global__ void __launch_bounds__(256, 1) k_run(RunArgs a) {
+  run_body<Real, TILE>(a);
+}
+
+// The same kernel compiled for two resident 256-thread CTAs per SM (at most
+// 128 registers per thread): more warps to hide latency for batches whose
+// walkers are busy in long CN pair loops. Chosen by ABP_TUNE_LEAN.
+__global__ void __launch_bounds__(256, 2) k_run_lean(RunArgs a) { run_body<float, false>(a); }
+
 cudaError_t launch_run(const RunArgs &a, int fp64, cudaStream_t st) {
   const int threads = a.G * a.groups_per_cta;
   const int blocks = (a.nw + a.groups_per_cta - 1) / a.groups_per_cta;
@@ -282,6 +292,10 @@ cudaError_t launch_run(const RunArgs &a, int fp64, cudaStream_t st) {
     e = cudaFuncSetAttribute(k_run<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_run<double, false><<<blocks, threads, smem, st>>>(a);
+  } else if (a.lean && a.tile_budget == 0) {
+    e = cudaFuncSetAttribute(k_run_lean, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_run_lean<<<blocks, threads, smem, st>>>(a);
   } else if (a.tile_budget > 0) {
     e = cudaFuncSetAttribute(k_run<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -33,6 +33,7 @@ struct RunArgs {
   const long long *wstep;  // optional: per-walker first step (indexed like coff), overrides step0
   int nsteps;
   int tile_budget;     // >0: dynamic shared bytes per group, the rest of which holds a grid tile
+  int lean;            // use the 128-register instantiation (FP32, no tile)
   DepositLog log;
   DevCounters *ctr;
 };

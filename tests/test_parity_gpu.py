@@ -213,6 +213,26 @@ def test_grid_tile_is_bitwise_exact(abp, ctx):
         assert np.array_equal(ctx.bias(a), ctx.bias(b))
 
 
+def test_lean_instantiation_matches(abp, ctx):
+    """The 128-register instantiation (ABP_TUNE_LEAN) computes the same steps:
+    CN walkers of the uneven mix, group width fixed."""
+    specs = synth.uneven1000_specs(seed=8, nw=8, stride=5, sizes_2d=(48,), n1d=200, n3d=20)
+    tm = synth.uneven1000_templates(8, nw=8)
+    frames = synth.JitterFrames(tm, seed=9).frames(0, 20)
+    abp.abp_ctx_tune(ctx.handle, abp.ABP_TUNE_GROUP_THREADS, 64)
+    w0 = ctx.make_walkers(specs)
+    F0 = gpu_replay(abp, ctx, w0, frames, 0)
+    abp.abp_ctx_tune(ctx.handle, abp.ABP_TUNE_LEAN, 1)
+    w1 = ctx.make_walkers(specs)
+    F1 = gpu_replay(abp, ctx, w1, frames, 0)
+    abp.abp_ctx_tune(ctx.handle, abp.ABP_TUNE_LEAN, 0)
+    abp.abp_ctx_tune(ctx.handle, abp.ABP_TUNE_GROUP_THREADS, 0)
+    assert P.force_err(F1, F0) < 1e-6
+    for a, b in zip(w0, w1):
+        assert np.all(P.rel_field_err(ctx.bias(b), ctx.bias(a)) < 1e-7)
+    print("lean bitwise equal:", np.array_equal(F0, F1))
+
+
 def test_plain_form_matches_batched_and_oracle(abp, ctx):
     specs = synth.mb64_specs(nw=3, stride=4)
     frames = synth.SweepFrames(3, seed=9, period=(100, 200)).frames(0, 40)
