@@ -248,6 +248,43 @@ abp_status abp_deposit_log_readout(abp_ctx *ctx, abp_deposit_rec *dst, size_t ca
                                    size_t *n_total);
 abp_status abp_deposit_log_clear(abp_ctx *ctx);
 
+/* ---- shared grids across GPUs: hill exchange -------------------------------- */
+
+/* Walkers of one multiple-walker run may live on several GPUs, each GPU
+ * holding a replica of the shared grid. A step then runs in three calls:
+ * abp_shared_hills (CVs and heights, from this replica, no deposit), an
+ * exchange of the hill records among the GPUs (by the caller, e.g. an
+ * all-gather), abp_grid_apply_hills with every record of the step in
+ * (rank, walker) order on every replica, and abp_shared_forces. Replicas that
+ * start equal and apply the same records stay bit-identical. The paper's
+ * counterpart is the master rank that gathers CV atoms and returns forces
+ * (SI "Minimization of Interprocess Communications"); here only the few bytes
+ * of each hill move. */
+typedef struct {
+  double s[3];        /* hill centre s_t */
+  double height;      /* h */
+  int64_t step;
+  int32_t walker_id;
+  int32_t pad;
+} abp_hill;
+
+/* Steps a1 + a2 of MD step `step` for walkers on one shared grid (created
+ * with shared = 1): writes to host memory, in list order, the hills the
+ * walkers deposit this step (none if step % stride != 0), without depositing
+ * them; *n_out receives the count. Syncs. */
+abp_status abp_shared_hills(abp_ctx *ctx, abp_walker *const *walkers, int n, const void *coords_dev, int coords_dtype,
+                            const int64_t *coord_offsets_dev, int64_t step, abp_hill *hills_out, size_t cap,
+                            size_t *n_out);
+/* Deposits n hill records (host memory) into the shared grid of `shape_walker`,
+ * whose sigma and cutoff every record uses, exactly as if they were applied one
+ * after another in list order: records whose stencil boxes cannot overlap go
+ * in one launch, overlapping ones in list order, without atomics. */
+abp_status abp_grid_apply_hills(abp_ctx *ctx, const abp_walker *shape_walker, const abp_hill *hills, size_t n);
+/* Steps a4 + a5 after the step's hills are applied: forces for the walkers of
+ * the last abp_shared_hills call, written as abp_run writes them. */
+abp_status abp_shared_forces(abp_ctx *ctx, abp_walker *const *walkers, int n, void *forces_dev, int forces_dtype,
+                             const int64_t *force_offsets_dev, int mode, int64_t step);
+
 /* ---- serving: continuous batching of step requests ------------------------ */
 
 /* A request loop over many concurrent simulations (one walker each): every

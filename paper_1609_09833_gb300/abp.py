@@ -58,6 +58,12 @@ class DepositRec(C.Structure):
                 ("height", C.c_double)]
 
 
+# abp_hill: one hill record of a shared-grid exchange (48 bytes)
+HILL_DTYPE = np.dtype([("s", "<f8", (3,)), ("height", "<f8"), ("step", "<i8"), ("walker_id", "<i4"),
+                       ("pad", "<i4")])
+assert HILL_DTYPE.itemsize == 48
+
+
 class ServerDesc(C.Structure):
     _fields_ = [("max_batch", C.c_int), ("max_atoms", C.c_int), ("nstreams", C.c_int)]
 
@@ -85,6 +91,10 @@ _SIGS = {
     "abp_run": [_vp, C.POINTER(_vp), C.c_int, _vp, C.c_int, _vp, C.c_int64, _vp, _vp, C.c_int64, C.c_int,
                 C.c_int64, C.c_int],
     "abp_step_plain": [_vp, C.POINTER(_vp), C.c_int, _vp, C.c_int, _vp, _vp, _vp, C.c_int, C.c_int64],
+    "abp_shared_hills": [_vp, C.POINTER(_vp), C.c_int, _vp, C.c_int, _vp, C.c_int64, _vp, C.c_size_t,
+                         C.POINTER(C.c_size_t)],
+    "abp_grid_apply_hills": [_vp, _vp, _vp, C.c_size_t],
+    "abp_shared_forces": [_vp, C.POINTER(_vp), C.c_int, _vp, C.c_int, _vp, C.c_int, C.c_int64],
     "abp_bias_readout": [_vp, _vp, _vp, C.c_int, C.c_int],
     "abp_bias_upload": [_vp, _vp, _vp, C.c_int, C.c_int],
     "abp_walker_readout": [_vp, _vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
@@ -240,6 +250,26 @@ def abp_run(ctx, walkers, coords, coords_dtype, coord_offsets, coord_step_stride
 def abp_step_plain(ctx, walkers, coords, coords_dtype, coord_offsets, forces, force_offsets, mode, step):
     _check(load().abp_step_plain(ctx, _walkers(walkers), len(walkers), _ptr(coords), coords_dtype,
                                  _ptr(coord_offsets), _ptr(forces), _ptr(force_offsets), int(mode), int(step)))
+
+
+def abp_shared_hills(ctx, walkers, coords, coords_dtype, coord_offsets, step: int) -> np.ndarray:
+    """Hill records (HILL_DTYPE) of this step's depositing walkers, in list order."""
+    out = np.zeros(max(1, len(walkers)), dtype=HILL_DTYPE)
+    n = C.c_size_t()
+    _check(load().abp_shared_hills(ctx, _walkers(walkers), len(walkers), _ptr(coords), coords_dtype,
+                                   _ptr(coord_offsets), int(step), out.ctypes.data, out.shape[0], C.byref(n)))
+    return out[:n.value].copy()
+
+
+def abp_grid_apply_hills(ctx, shape_walker, hills: np.ndarray):
+    h = np.ascontiguousarray(hills, dtype=HILL_DTYPE)
+    w = shape_walker.handle if hasattr(shape_walker, "handle") else shape_walker
+    _check(load().abp_grid_apply_hills(ctx, w, h.ctypes.data if h.shape[0] else None, h.shape[0]))
+
+
+def abp_shared_forces(ctx, walkers, forces, forces_dtype, force_offsets, mode, step: int):
+    _check(load().abp_shared_forces(ctx, _walkers(walkers), len(walkers), _ptr(forces), forces_dtype,
+                                    _ptr(force_offsets), int(mode), int(step)))
 
 
 def abp_bias_readout(ctx, grid, dst, dst_is_device: bool, dtype: int):

@@ -70,6 +70,8 @@ struct abp_ctx {
   std::vector<BigItem> big_key;                   // phased-form item lists of the last call
   BigItem *big_dev = nullptr;
   size_t big_cap = 0;
+  HillDev *hill_dev = nullptr;  // hill records of the last abp_grid_apply_hills
+  size_t hill_cap = 0;
   std::mutex mu;
 };
 
@@ -320,6 +322,7 @@ void abp_ctx_destroy(abp_ctx *ctx) {
   for (auto &t : ctx->tables)
     if (t.dev) cudaFree(t.dev);
   if (ctx->big_dev) cudaFree(ctx->big_dev);
+  if (ctx->hill_dev) cudaFree(ctx->hill_dev);
   if (ctx->log.rec) cudaFree(ctx->log.rec);
   if (ctx->log.count) cudaFree(ctx->log.count);
   if (ctx->ctr) cudaFree(ctx->ctr);
@@ -880,6 +883,196 @@ abp_status abp_step_plain(abp_ctx *ctx, abp_walker *const *walkers, int n, const
   a.ctr = ctx->ctr;
   cudaError_t e = launch_plain(a, fp64, ctx->stream);
   if (e != cudaSuccess) return fail(ABP_ERR_CUDA, "plain launch: %s", cudaGetErrorString(e));
+  return ABP_OK;
+}
+
+// ---------------------------------------------------------------- hill exchange
+
+namespace {
+
+// Walkers of an exchange call: all in the phased form on shared grids.
+abp_status exchange_list(abp_ctx *ctx, abp_walker *const *walkers, int n) {
+  int fp64;
+  bool shared;
+  abp_status st = check_list(ctx, walkers, n, &fp64, &shared);
+  if (st) return st;
+  for (int i = 0; i < n; ++i)
+    if (!walkers[i]->grid->desc.shared)
+      return fail(ABP_ERR_INVALID_ARG, "walker %d: hill exchange needs a grid created with shared = 1", i);
+  return ABP_OK;
+}
+
+// Grid-index position of a hill centre on axis k, as the deposit places it
+// (non-periodic centres clamped like the deposit's guard).
+double hill_axis(const abp_walker *w, int k, double s) {
+  const GridDev &g = w->hd.g;
+  const int n = g.n[k], R = w->hd.R[k];
+  double x = (s - g.lo[k]) * g.invD[k];
+  if (g.periodic[k]) return x - std::floor(x / n) * n;
+  return std::min(std::max(x, (double)(-R - 2)), (double)(n + R + 1));
+}
+
+// Whether the stencil boxes of two hills may share a node. A box spans
+// centre +- R nodes and a centre lies within 1/2 node (plus float-float
+// rounding) of the position u, so positions more than 2R + 2 apart on some
+// axis give disjoint boxes.
+bool boxes_may_overlap(const abp_walker *w, const double *ua, const double *ub) {
+  const GridDev &g = w->hd.g;
+  for (int k = 0; k < g.d; ++k) {
+    const double reach = 2.0 * w->hd.R[k] + 2.0;
+    double dist = std::fabs(ua[k] - ub[k]);
+    if (g.periodic[k]) {
+      const int n = g.n[k];
+      if (2 * w->hd.R[k] + 3 >= n) continue;  // a box that spans the axis meets every other
+      dist = std::min(dist, n - dist);
+    }
+    if (dist > reach) return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+abp_status abp_shared_hills(abp_ctx *ctx, abp_walker *const *walkers, int n, const void *coords_dev, int coords_dtype,
+                            const int64_t *coord_offsets_dev, int64_t step, abp_hill *hills_out, size_t cap,
+                            size_t *n_out) {
+  if (!ctx) return fail(ABP_ERR_INVALID_ARG, "ctx is NULL");
+  if (n_out) *n_out = 0;
+  abp_status st = exchange_list(ctx, walkers, n);
+  if (st) return st;
+  if (n == 0) return ABP_OK;
+  if (step < 0) return fail(ABP_ERR_INVALID_ARG, "step must be >= 0");
+  if (!coords_dev || !coord_offsets_dev || !n_out) return fail(ABP_ERR_INVALID_ARG, "NULL argument");
+  if (coords_dtype != ABP_F32) return fail(ABP_ERR_INVALID_ARG, "coordinate dtype must be ABP_F32");
+  if (reinterpret_cast<uintptr_t>(coords_dev) & 15)
+    return fail(ABP_ERR_INVALID_ARG, "coordinate buffer must be 16-byte aligned");
+  if ((st = set_device(ctx))) return st;
+  std::vector<abp_walker *> ws(walkers, walkers + n);
+  std::vector<int> idx(n);
+  for (int i = 0; i < n; ++i) idx[i] = i;
+  BigArgs b{};
+  if ((st = big_items(ctx, ws, idx, &b))) return st;
+  b.coords = coords_dev;
+  b.coff = reinterpret_cast<const long long *>(coord_offsets_dev);
+  b.mode = ABP_FORCES_OVERWRITE;
+  b.log = ctx->log;
+  b.ctr = ctx->ctr;
+  b.step = step;
+  b.phases = 1 | 2;
+  cudaError_t e = launch_big_step(b, ctx->stream);
+  if (e != cudaSuccess) return fail(ABP_ERR_CUDA, "hill phase: %s", cudaGetErrorString(e));
+  std::vector<const WalkerDev *> hd(n);
+  for (int i = 0; i < n; ++i) hd[i] = &walkers[i]->hd;
+  std::vector<double> s3h(4 * (size_t)n);
+  std::vector<int> dep(n);
+  e = read_hill_heads(hd.data(), n, s3h.data(), dep.data(), ctx->stream);
+  if (e != cudaSuccess) return fail(ABP_ERR_CUDA, "hill readout: %s", cudaGetErrorString(e));
+  size_t m = 0;
+  for (int i = 0; i < n; ++i) {
+    if (!dep[i]) continue;
+    if (m < cap && hills_out) {
+      abp_hill &h = hills_out[m];
+      for (int k = 0; k < 3; ++k) h.s[k] = k < walkers[i]->hd.g.d ? s3h[4 * i + k] : 0.0;
+      h.height = s3h[4 * i + 3];
+      h.step = step;
+      h.walker_id = walkers[i]->hd.id;
+      h.pad = 0;
+    }
+    ++m;
+  }
+  *n_out = m;
+  if (m > cap || (m > 0 && !hills_out))
+    return fail(ABP_ERR_INVALID_ARG, "%zu hills but room for %zu", m, hills_out ? cap : (size_t)0);
+  return ABP_OK;
+}
+
+abp_status abp_grid_apply_hills(abp_ctx *ctx, const abp_walker *shape, const abp_hill *hills, size_t n) {
+  if (!ctx || !shape) return fail(ABP_ERR_INVALID_ARG, "NULL argument");
+  if (shape->ctx != ctx) return fail(ABP_ERR_INVALID_ARG, "walker belongs to another context");
+  if (!shape->grid->desc.shared) return fail(ABP_ERR_INVALID_ARG, "hill records apply to grids created with shared = 1");
+  if (n == 0) return ABP_OK;
+  if (!hills) return fail(ABP_ERR_INVALID_ARG, "hills is NULL");
+  if (n > (1u << 24)) return fail(ABP_ERR_INVALID_ARG, "too many hill records");
+  const int d = shape->hd.g.d;
+  std::vector<double> u(3 * n, 0.0);
+  for (size_t j = 0; j < n; ++j) {
+    if (!std::isfinite(hills[j].height) || hills[j].height < 0)
+      return fail(ABP_ERR_INVALID_ARG, "hill %zu: height must be finite and >= 0", j);
+    for (int k = 0; k < d; ++k) {
+      if (!std::isfinite(hills[j].s[k])) return fail(ABP_ERR_INVALID_ARG, "hill %zu: centre is not finite", j);
+      u[3 * j + k] = hill_axis(shape, k, hills[j].s[k]);
+    }
+  }
+  // wave of record j: one past the last wave holding an earlier record whose
+  // box may meet j's, so every node receives its hills in list order
+  std::vector<int> wave(n, 0);
+  int nwaves = 0;
+  for (size_t j = 0; j < n; ++j) {
+    int w = 0;
+    for (size_t i = 0; i < j; ++i)
+      if (wave[i] >= w && boxes_may_overlap(shape, &u[3 * i], &u[3 * j])) w = wave[i] + 1;
+    wave[j] = w;
+    nwaves = std::max(nwaves, w + 1);
+  }
+  std::vector<HillDev> recs;
+  std::vector<int> start(nwaves + 1, 0);
+  recs.reserve(n);
+  for (int w = 0; w < nwaves; ++w) {
+    start[w] = (int)recs.size();
+    for (size_t j = 0; j < n; ++j)
+      if (wave[j] == w) {
+        HillDev h;
+        for (int k = 0; k < 3; ++k) h.s[k] = k < d ? hills[j].s[k] : 0.0;
+        h.h = hills[j].height;
+        recs.push_back(h);
+      }
+  }
+  start[nwaves] = (int)recs.size();
+  abp_status st = set_device(ctx);
+  if (st) return st;
+  const size_t need = recs.size() * sizeof(HillDev);
+  if (ctx->hill_cap < need) {
+    if (ctx->hill_dev) cudaFree(ctx->hill_dev);
+    ctx->hill_dev = nullptr;
+    ctx->hill_cap = 0;
+    CUDA_TRY(cudaMalloc(&ctx->hill_dev, need));
+    ctx->hill_cap = need;
+  }
+  CUDA_TRY(cudaMemcpyAsync(ctx->hill_dev, recs.data(), need, cudaMemcpyHostToDevice, ctx->stream));
+  int box = 1;
+  for (int k = 0; k < d; ++k) box *= 2 * shape->hd.R[k] + 1;
+  cudaError_t e = cudaSuccess;
+  for (int w = 0; w < nwaves && e == cudaSuccess; ++w)
+    e = launch_apply_hills(shape->dd, ctx->hill_dev + start[w], start[w + 1] - start[w], box, false, ctx->stream);
+  if (e == cudaSuccess) e = launch_apply_hills(shape->dd, ctx->hill_dev, (int)recs.size(), box, true, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);  // the host records may go once this returns
+  if (e != cudaSuccess) return fail(ABP_ERR_CUDA, "hill apply: %s", cudaGetErrorString(e));
+  return ABP_OK;
+}
+
+abp_status abp_shared_forces(abp_ctx *ctx, abp_walker *const *walkers, int n, void *forces_dev, int forces_dtype,
+                             const int64_t *force_offsets_dev, int mode, int64_t step) {
+  if (!ctx) return fail(ABP_ERR_INVALID_ARG, "ctx is NULL");
+  abp_status st = exchange_list(ctx, walkers, n);
+  if (st) return st;
+  if (n == 0) return ABP_OK;
+  if (!forces_dev || !force_offsets_dev) return fail(ABP_ERR_INVALID_ARG, "forces or offsets are NULL");
+  if (forces_dtype != ABP_F32) return fail(ABP_ERR_INVALID_ARG, "force dtype must be ABP_F32");
+  if (reinterpret_cast<uintptr_t>(forces_dev) & 15) return fail(ABP_ERR_INVALID_ARG, "force buffer must be 16-byte aligned");
+  if (mode != ABP_FORCES_ACCUMULATE && mode != ABP_FORCES_OVERWRITE) return fail(ABP_ERR_INVALID_ARG, "bad mode");
+  if ((st = set_device(ctx))) return st;
+  std::vector<abp_walker *> ws(walkers, walkers + n);
+  std::vector<int> idx(n);
+  for (int i = 0; i < n; ++i) idx[i] = i;
+  BigArgs b{};
+  if ((st = big_items(ctx, ws, idx, &b))) return st;
+  b.forces = forces_dev;
+  b.foff = reinterpret_cast<const long long *>(force_offsets_dev);
+  b.mode = mode;
+  b.step = step;
+  b.phases = 16;
+  cudaError_t e = launch_big_step(b, ctx->stream);
+  if (e != cudaSuccess) return fail(ABP_ERR_CUDA, "force phase: %s", cudaGetErrorString(e));
   return ABP_OK;
 }
 

@@ -655,18 +655,113 @@ __global__ void __launch_bounds__(kBigThreads) k_big_force(const BigItem *walker
 
 cudaError_t launch_big_step(const BigArgs &a, cudaStream_t st) {
   const size_t fixed = (size_t)fixed_bytes_f();
+  const int ph = a.phases ? a.phases : 31;
   cudaError_t e;
-  if (a.ncn_items > 0) {
+  if ((ph & 1) && a.ncn_items > 0) {
     e = cudaFuncSetAttribute(k_big_cn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.cn_smem);
     if (e != cudaSuccess) return e;
     k_big_cn<<<a.ncn_items, kBigThreads, a.cn_smem, st>>>(a.cn_items, a.coords, a.coff, a.step_off);
   }
-  k_big_cvs<<<a.nw, kBigThreads, fixed, st>>>(a.walkers, a.coords, a.coff, a.step_off, a.step, a.log, a.ctr);
+  if (ph & 2)
+    k_big_cvs<<<a.nw, kBigThreads, fixed, st>>>(a.walkers, a.coords, a.coff, a.step_off, a.step, a.log, a.ctr);
   dim3 grid(a.nw, (a.max_stencil + kStencilPerBlock - 1) / kStencilPerBlock);
-  k_big_deposit<<<grid, kBigThreads, fixed, st>>>(a.walkers);
-  if (a.any_shared) k_big_refresh<<<grid, kBigThreads, fixed, st>>>(a.walkers);
-  k_big_force<<<a.nw, kBigThreads, fixed, st>>>(a.walkers, a.forces, a.foff, a.force_step_off, a.mode, a.step);
+  if (ph & 4) k_big_deposit<<<grid, kBigThreads, fixed, st>>>(a.walkers);
+  if ((ph & 8) && a.any_shared) k_big_refresh<<<grid, kBigThreads, fixed, st>>>(a.walkers);
+  if (ph & 16)
+    k_big_force<<<a.nw, kBigThreads, fixed, st>>>(a.walkers, a.forces, a.foff, a.force_step_off, a.mode, a.step);
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- hill records
+
+// One CTA per (record, block of stencil nodes): the record's axis state from
+// its centre, its tables, and a plain FP64 read-modify-write of the shadow
+// (records of one launch have disjoint boxes), or the FP32 refresh.
+__global__ void __launch_bounds__(kBigThreads) k_apply_hills(const WalkerDev *shape, const HillDev *recs, int refresh) {
+  extern __shared__ __align__(32) unsigned char smem[];
+  Grp g = big_group();
+  GroupFixed<float> *fx = reinterpret_cast<GroupFixed<float> *>(smem);
+  const int *src = reinterpret_cast<const int *>(shape);
+  int *dst = reinterpret_cast<int *>(&fx->wd);
+  for (int i = g.t; i < (int)(sizeof(WalkerDev) / 4); i += g.G) dst[i] = src[i];
+  const HillDev r = recs[blockIdx.x];
+  if (g.t == 0) {
+    fx->clamped = 0;
+    fx->flags = 0;
+  }
+  g.sync();
+  const GridDev &gd = fx->wd.g;
+  if (g.t < kMaxCv) {
+    float h = (float)r.s[g.t];
+    fx->sh[g.t] = h;
+    fx->sl[g.t] = (float)(r.s[g.t] - (double)h);
+  }
+  g.sync();
+  if (g.t < gd.d) axis_setup<float>(fx, g.t, true);
+  g.sync();
+  build_tables<float>(g, fx);
+  g.sync();
+  const WalkerDev &wd = fx->wd;
+  const int d = gd.d;
+  const int s0 = 2 * wd.R[0] + 1, s1 = d > 1 ? 2 * wd.R[1] + 1 : 1, s2 = d > 2 ? 2 * wd.R[2] + 1 : 1;
+  const int total = s0 * s1 * s2;
+  const int first = blockIdx.y * kStencilPerBlock, last = min(total, first + kStencilPerBlock);
+  const long long n0 = gd.n[0], n01 = n0 * (d > 1 ? gd.n[1] : 1);
+  const float hf = (float)r.h;
+  for (int idx = first + g.t; idx < last; idx += g.G) {
+    int o0 = idx % s0, rr = idx / s0, o1 = rr % s1, o2 = rr / s1;
+    int j0 = fx->tabJ[0][o0];
+    int j1 = d > 1 ? fx->tabJ[1][o1] : 0;
+    int j2 = d > 2 ? fx->tabJ[2][o2] : 0;
+    if ((j0 | j1 | j2) < 0) continue;
+    long long node = j0 + n0 * j1 + n01 * j2;
+    double *p = gd.shadow + node * 4;
+    if (!refresh) {
+      float G = hf * fx->tabG[0][o0];
+      if (d > 1) G = G * fx->tabG[1][o1];
+      if (d > 2) G = G * fx->tabG[2][o2];
+      p[0] += (double)G;
+      p[1] += (double)__fmul_rn(G, fx->tabD[0][o0]);
+      if (d > 1) p[2] += (double)__fmul_rn(G, fx->tabD[1][o1]);
+      if (d > 2) p[3] += (double)__fmul_rn(G, fx->tabD[2][o2]);
+    } else {
+      float hi[4], lo[4];
+      for (int q = 0; q < 4; ++q) {
+        double v = q <= d ? p[q] : 0.0;
+        hi[q] = (float)v;
+        lo[q] = (float)(v - (double)hi[q]);
+      }
+      unsigned char *rec = reinterpret_cast<unsigned char *>(gd.rec) + node * gd.rec_bytes;
+      if (d == 1) {
+        *reinterpret_cast<float4 *>(rec) = make_float4(hi[0], hi[1], lo[0], lo[1]);
+      } else {
+        float4 *q = reinterpret_cast<float4 *>(rec);
+        q[0] = make_float4(hi[0], hi[1], hi[2], hi[3]);
+        q[1] = make_float4(lo[0], lo[1], lo[2], lo[3]);
+      }
+    }
+  }
+}
+
+cudaError_t launch_apply_hills(const WalkerDev *shape, const HillDev *recs, int n, int max_stencil, bool refresh,
+                               cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  dim3 grid(n, (max_stencil + kStencilPerBlock - 1) / kStencilPerBlock);
+  k_apply_hills<<<grid, kBigThreads, fixed_bytes_f(), st>>>(shape, recs, refresh ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t read_hill_heads(const WalkerDev *const *wd_host, int n, double *s3h, int *dep, cudaStream_t st) {
+  // wd_host[i] is a host copy of walker i's descriptor (for its jscratch)
+  cudaError_t e = cudaStreamSynchronize(st);
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    BigHead head;
+    e = cudaMemcpy(&head, wd_host[i]->jscratch, sizeof head, cudaMemcpyDeviceToHost);
+    for (int k = 0; k < 3; ++k) s3h[4 * i + k] = (double)head.sh[k] + (double)head.sl[k];
+    s3h[4 * i + 3] = head.h;
+    dep[i] = head.dep && !head.bad;
+  }
+  return e;
 }
 
 size_t big_cn_smem(const WalkerDev &hd) {

@@ -78,6 +78,7 @@ struct BigArgs {
   long long step;
   int max_stencil;           // largest stencil box (nodes) among the walkers
   int any_shared;
+  int phases;                // bits: 1 pairs, 2 CVs + heights, 4 deposit, 8 refresh, 16 forces (0 = all)
   DepositLog log;
   DevCounters *ctr;
 };
@@ -87,6 +88,15 @@ int big_cn_count(const WalkerDev &hd);
 int big_chunks(const WalkerDev &hd);
 size_t big_cn_smem(const WalkerDev &hd);
 cudaError_t launch_big_step(const BigArgs &a, cudaStream_t st);
+// Hill records handed to a grid: one per record, in waves of disjoint boxes.
+struct HillDev {
+  double s[3];
+  double h;
+};
+cudaError_t launch_apply_hills(const WalkerDev *shape, const HillDev *recs, int n, int max_stencil, bool refresh,
+                               cudaStream_t st);
+// Read back each walker's hill record of the last CVs + heights phase.
+cudaError_t read_hill_heads(const WalkerDev *const *wd_host, int n, double *s3h, int *dep, cudaStream_t st);
 
 int group_fixed_bytes(int fp64);
 int plain_scratch_bytes(int fp64, const CvDev *cv, int ncv);
