@@ -35,7 +35,7 @@ def signature(specs, nsteps: int) -> str:
 def candidates(specs):
     cn = any(c["type"] == "coord" for s in specs for c in s["cvs"])
     out = []
-    for G in ((64, 128, 256) if cn else (32, 64)):
+    for G in ((64, 128, 256) if cn else (32, 64, 128, 256)):
         for gpc in ((1, 2) if G >= 128 else (1, 2, 4)):
             for lean in (0, 1):
                 out.append({"group_threads": G, "groups_per_cta": gpc, "tile": 0, "lean": lean})

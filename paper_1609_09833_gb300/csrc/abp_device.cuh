@@ -51,6 +51,19 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
   unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem_src) : "memory");
 }
+// The same with an L2 eviction-priority policy (see l2_evict_first).
+__device__ __forceinline__ void cp_async16_hint(void *smem_dst, const void *gmem_src, unsigned long long policy) {
+  unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem_src), "l"(policy)
+               : "memory");
+}
+// L2 policy for data read once (streamed coordinates): evicted first, so the
+// grids that are read and written again keep their lines.
+__device__ __forceinline__ unsigned long long l2_evict_first() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
@@ -93,11 +106,13 @@ struct GroupFixed {
   int clamped;               // interpolation clamp mask
   int flags;
   int bad;
+  unsigned winbad[2];        // windowed form: non-finite steps of a window, by window parity
   int reload;                // the tile must be reloaded this step
   int org[kMaxCv];           // tile origin node per axis
   Real V;
   Real dV[kMaxCv];
   Real hf;                   // hill height (rounded to Real)
+  double hV;                 // windowed form: V_b(s_t) before the deposit at hand
   // atom lists of each CV (shared memory, or global in the plain form)
   const int32_t *ia[kMaxCv];
   const int32_t *ib[kMaxCv];
@@ -274,10 +289,8 @@ __device__ __forceinline__ Real dot3(const Real *a, const Real *b) {
 // gradient in the Blondel-Karplus form. One thread (the last thread of the
 // group, so that with several warps it overlaps the COM work of warp 0).
 template <typename Real>
-__device__ void cv_dihedral(const Grp &g, GroupFixed<Real> *fx, int k, const typename Rec4<Real>::T *xs) {
-  if (g.t != g.G - 1) return;
-  const CvDev &c = fx->wd.cv[k];
-  const int32_t *ia = fx->ia[k];
+__device__ __forceinline__ int dihedral_eval(const CvDev &c, const int32_t *ia, const typename Rec4<Real>::T *xs,
+                                             Real &phi, Real (*grad)[3]) {
   Real x[4][3];
   for (int a = 0; a < 4; ++a) {
     auto p = xs[ia[a]];
@@ -300,14 +313,12 @@ __device__ void cv_dihedral(const Grp &g, GroupFixed<Real> *fx, int k, const typ
   cross3(b2, b3, n);
   Real b2sq = dot3(b2, b2);
   Real lb2 = sqrt(b2sq);
-  fx->sh[k] = atan2(lb2 * dot3(b1, n), dot3(m, n));
-  fx->sl[k] = 0;
+  phi = atan2(lb2 * dot3(b1, n), dot3(m, n));
   Real mm = dot3(m, m), nn = dot3(n, n);
   if (!(mm > 0) || !(nn > 0) || !(lb2 > 0)) {
     for (int a = 0; a < 4; ++a)
-      for (int q = 0; q < 3; ++q) fx->dih_g[k][a][q] = 0;
-    fx->flags |= ABP_WFLAG_SINGULAR;
-    return;
+      for (int q = 0; q < 3; ++q) grad[a][q] = 0;
+    return ABP_WFLAG_SINGULAR;
   }
   Real inv_b2sq = rcp_fast<Real>(b2sq);
   Real p = dot3(b1, b2) * inv_b2sq, r = dot3(b3, b2) * inv_b2sq;
@@ -315,11 +326,22 @@ __device__ void cv_dihedral(const Grp &g, GroupFixed<Real> *fx, int k, const typ
   for (int q = 0; q < 3; ++q) {
     Real g1 = cm * m[q];
     Real g4 = cn * n[q];
-    fx->dih_g[k][0][q] = g1;
-    fx->dih_g[k][3][q] = g4;
-    fx->dih_g[k][1][q] = -(1 + p) * g1 + r * g4;
-    fx->dih_g[k][2][q] = -(1 + r) * g4 + p * g1;
+    grad[0][q] = g1;
+    grad[3][q] = g4;
+    grad[1][q] = -(1 + p) * g1 + r * g4;
+    grad[2][q] = -(1 + r) * g4 + p * g1;
   }
+  return 0;
+}
+
+template <typename Real>
+__device__ void cv_dihedral(const Grp &g, GroupFixed<Real> *fx, int k, const typename Rec4<Real>::T *xs) {
+  if (g.t != g.G - 1) return;
+  Real phi;
+  int fl = dihedral_eval<Real>(fx->wd.cv[k], fx->ia[k], xs, phi, fx->dih_g[k]);
+  fx->sh[k] = phi;
+  fx->sl[k] = 0;
+  if (fl) fx->flags |= fl;
 }
 
 // Coordination number s = sum_{i in A, j in B} 1 / (1 + (r_ij / r0)^6)
@@ -479,19 +501,31 @@ __device__ __forceinline__ void split_u(Real uh, Real ul, int &a, Real &f) {
   }
 }
 
-// Per-step axis state, one thread per axis (k = g.t < d): interpolation
-// corners i0/i1 and weight f (a non-periodic axis clamps s into its range and
-// flags a zero gradient), and on deposit steps the stencil centre
-// i_c = floor(u + 1/2) = da + dc with the fraction df = u - da. Every s,
-// finite or not, maps to in-range indices (a non-periodic centre far outside
-// is limited to where its box holds no node).
+// Per-step axis state of axis k at s = sh + sl: interpolation corners i0/i1
+// and weight f (a non-periodic axis clamps s into its range and reports it in
+// `clamped`, which zeroes that gradient), and on deposit steps the stencil
+// centre i_c = floor(u + 1/2) = da + dc with the fraction df = u - da. Every
+// s, finite or not, maps to in-range indices (a non-periodic centre far
+// outside is limited to where its box holds no node).
 template <typename Real>
-__device__ __forceinline__ void axis_setup(GroupFixed<Real> *fx, int k, bool dep) {
-  const GridDev &gd = fx->wd.g;
+struct AxisSt {
+  int i0, i1;
+  Real f;
+  int da, dc, ic_log;
+  Real df;
+  int clamped;
+};
+
+template <typename Real>
+__device__ __forceinline__ AxisSt<Real> axis_eval(const GridDev &gd, int R, int k, Real sh, Real sl, bool dep) {
+  AxisSt<Real> r;
+  r.da = r.dc = r.ic_log = 0;
+  r.df = 0;
+  r.clamped = 0;
   const int n = gd.n[k];
   const Real rn = (Real)n;
   Real uh, ul;
-  axis_u<Real>(gd, k, fx->sh[k], fx->sl[k], uh, ul);
+  axis_u<Real>(gd, k, sh, sl, uh, ul);
   if (gd.periodic[k]) {
     if (!(uh >= 0 && uh < rn)) {
       Real q = floor(uh / rn);
@@ -508,19 +542,18 @@ __device__ __forceinline__ void axis_setup(GroupFixed<Real> *fx, int k, bool dep
     if (a >= n) a -= n;
     if (a < 0) a += n;
     if (a < 0 || a >= n) a = 0;
-    fx->i0[k] = a;
-    fx->i1[k] = (a + 1 == n) ? 0 : a + 1;
-    fx->f[k] = f;
+    r.i0 = a;
+    r.i1 = (a + 1 == n) ? 0 : a + 1;
+    r.f = f;
     if (dep) {
       int c = f >= (Real)0.5 ? 1 : 0;
-      fx->da[k] = a;
-      fx->df[k] = f;
-      fx->dc[k] = c;
-      fx->ic_log[k] = (a + c == n) ? 0 : a + c;
+      r.da = a;
+      r.df = f;
+      r.dc = c;
+      r.ic_log = (a + c == n) ? 0 : a + c;
     }
   } else {
     if (dep) {
-      const int R = fx->wd.R[k];
       Real dh = uh, dl = ul;
       bool out = false;
       if (!(dh >= (Real)(-R - 2))) {
@@ -537,28 +570,27 @@ __device__ __forceinline__ void axis_setup(GroupFixed<Real> *fx, int k, bool dep
       Real f;
       split_u<Real>(dh, dl, a, f);
       int c = f >= (Real)0.5 ? 1 : 0;
-      fx->da[k] = a;
-      fx->df[k] = f;
-      fx->dc[k] = c;
+      r.da = a;
+      r.df = f;
+      r.dc = c;
       if (out) {
         Real raw = uh + (Real)0.5;
         raw = raw > (Real)1e9 ? (Real)1e9 : (raw < (Real)-1e9 ? (Real)-1e9 : raw);
-        fx->ic_log[k] = (int)floor(raw == raw ? raw : (Real)0);
+        r.ic_log = (int)floor(raw == raw ? raw : (Real)0);
       } else {
-        fx->ic_log[k] = a + c;
+        r.ic_log = a + c;
       }
     }
     int a;
     Real f;
-    bool cl = false;
     if (!(uh >= 0)) {
       a = 0;
       f = 0;
-      cl = true;
+      r.clamped = 1;
     } else if (uh > rn - 1 || (uh == rn - 1 && ul > 0)) {
       a = n - 2;
       f = 1;
-      cl = true;
+      r.clamped = 1;
     } else {
       split_u<Real>(uh, ul, a, f);
       if (a > n - 2) {
@@ -566,11 +598,27 @@ __device__ __forceinline__ void axis_setup(GroupFixed<Real> *fx, int k, bool dep
         f += 1;
       }
     }
-    if (cl) atomicOr(&fx->clamped, 1 << k);
-    fx->i0[k] = a;
-    fx->i1[k] = a + 1;
-    fx->f[k] = f;
+    r.i0 = a;
+    r.i1 = a + 1;
+    r.f = f;
   }
+  return r;
+}
+
+// The group's axis state, one thread per axis (k = g.t < d).
+template <typename Real>
+__device__ __forceinline__ void axis_setup(GroupFixed<Real> *fx, int k, bool dep) {
+  AxisSt<Real> r = axis_eval<Real>(fx->wd.g, fx->wd.R[k], k, fx->sh[k], fx->sl[k], dep);
+  fx->i0[k] = r.i0;
+  fx->i1[k] = r.i1;
+  fx->f[k] = r.f;
+  if (dep) {
+    fx->da[k] = r.da;
+    fx->df[k] = r.df;
+    fx->dc[k] = r.dc;
+    fx->ic_log[k] = r.ic_log;
+  }
+  if (r.clamped) atomicOr(&fx->clamped, 1 << k);
 }
 
 // ---------------------------------------------------------------- the grid tile
@@ -827,7 +875,7 @@ __device__ __forceinline__ void rmw_node(const GridDev &gd, unsigned char *p, Re
 // the box. FP32_COMP grids accumulate with two-sum compensation; FP64 grids
 // add directly. With a tile, nodes inside it are updated in shared memory and
 // the result stored to the grid; other nodes are updated in the grid.
-template <typename Real, bool TILE>
+template <typename Real, bool TILE, int UNR = 4>
 __device__ void deposit_stencil(const Grp &g, GroupFixed<Real> *fx, const GroupLayout &L, unsigned char *tile) {
   const WalkerDev &wd = fx->wd;
   const GridDev &gd = wd.g;
@@ -864,7 +912,6 @@ __device__ void deposit_stencil(const Grp &g, GroupFixed<Real> *fx, const GroupL
   };
   // UNR nodes per round: their records are loaded before any is updated, so
   // the grid reads of a round overlap
-  constexpr int UNR = 4;
   for (int base = g.t; base < total; base += UNR * g.G) {
     unsigned char *ptr[UNR];
     bool intile[UNR];

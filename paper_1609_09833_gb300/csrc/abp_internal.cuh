@@ -96,16 +96,66 @@ struct DevCounters {
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
 __host__ __device__ inline int align32(int x) { return (x + 31) & ~31; }
 
+// One MD step of a window of the windowed form (shared memory): the step's
+// CVs, Jacobian factors, axis state and interpolated bias.
+template <typename Real>
+struct StepRec {
+  Real s[kMaxCv];         // CV values
+  Real jac[kMaxCv][12];   // COM distance: unit separation (3); dihedral: gradient (4 x 3)
+  Real f[kMaxCv];         // interpolation weight of i1
+  Real df[kMaxCv];        // deposit: u - da
+  Real V;                 // V_b(s) after the step's deposits
+  Real dv[kMaxCv];        // dV_b/ds_k (0 on a clamped axis)
+  int i0[kMaxCv], i1[kMaxCv];
+  int da[kMaxCv], dc[kMaxCv], ic_log[kMaxCv];
+  int cfl[kMaxCv];        // per CV: ABP_WFLAG_SINGULAR, and bit 16 if the axis is clamped
+  int clamped;            // interpolation clamp mask
+  int flags;              // ABP_WFLAG_*
+};
+
+// One term of an atom's a5 in the windowed form: f += w v, v the 3-vector at
+// jac[0][0] + off of the step's record (a CV's Jacobian factor, scaled by
+// dV_b/ds_k once the step is interpolated).
+template <typename Real>
+struct AtomTerm {
+  Real w;
+  int off;
+};
+
+constexpr int kWinMax = 32;             // MD steps per window of the windowed form
+constexpr int kAtomTerms = 2 * kMaxCv;  // per atom: up to 2 list entries per CV
+constexpr int kWinBytes = 64 * 1024;    // its coordinate double buffer, at most
+
+// Steps per window for a walker in the windowed form (0: not eligible). The
+// form takes walkers whose CVs are all COM distances or dihedrals (one thread
+// evaluates a step's CVs); the window's coordinates are double buffered in
+// rows of natoms | 1 records (an odd row stride keeps the threads of a warp,
+// one row each, on distinct banks).
+__host__ __device__ inline int window_steps(int natoms, const CvDev *cv, int d, int rsz) {
+  for (int k = 0; k < d; ++k)
+    if (cv[k].type != ABP_CV_COM_DIST && cv[k].type != ABP_CV_DIHEDRAL) return 0;
+  const long long row = (long long)(natoms | 1) * rsz;
+  for (int W = kWinMax; W >= 4; W >>= 1)
+    if (2 * W * row <= kWinBytes) return W;
+  return 0;
+}
+
 // Shared-memory layout of one walker group (computed identically on host and
 // device). Offsets are bytes from the start of the group's dynamic part.
-//   xs0, xs1  coordinates of two steps (the next step's arrive by cp.async)
-//   fs        force accumulators
+//   xs0, xs1  coordinates of two steps (the next step's arrive by cp.async);
+//             in the windowed form, of two windows of `win` steps, rows of
+//             `xstride` records (the current window's rows then hold its
+//             force accumulators)
+//   fs        force accumulators (per-step form)
+//   steps     the window's StepRec array (windowed form)
+//   atoms     per atom, its a5 terms: counts, then AtomTerm[natoms][kAtomTerms] (windowed form)
 //   lists     per-CV atom index lists (+ COM weights)
 //   cn        per COORD CV: dCN/dx per list entry and per-warp partials
 //   tile      optional copy of a box of the walker's grid (node records)
 struct GroupLayout {
-  int xs0, xs1, fs, lists, cn, tile, total;
-  int T[3];        // tile nodes per axis (all 0 = no tile)
+  int xs0, xs1, fs, steps, atoms, lists, cn, tile, total;
+  int win, xstride;  // windowed form: steps per window (0 = per-step form), row stride in records
+  int T[3];          // tile nodes per axis (all 0 = no tile)
   int tile_nodes;
 };
 
@@ -129,17 +179,37 @@ __host__ __device__ inline void tile_dims(const GridDev &g, const int *R, int bu
   }
 }
 
+// window: the fused batched form, which runs eligible walkers windowed (and
+// gives them no grid tile).
 __host__ __device__ inline GroupLayout group_layout(int natoms, const CvDev *cv, const GridDev &g, const int *R,
-                                                    int nwarps, int rsz, int tile_budget) {
+                                                    int nwarps, int rsz, int tile_budget, bool window = false) {
   GroupLayout L;
   const int real = rsz / 4;
   int off = 0;
-  L.xs0 = off;
-  off += natoms * rsz;
-  L.xs1 = off;
-  off += natoms * rsz;
-  L.fs = off;
-  off += natoms * rsz;
+  L.win = window ? window_steps(natoms, cv, g.d, rsz) : 0;
+  if (L.win) tile_budget = 0;
+  L.xstride = natoms | 1;
+  if (L.win) {
+    const int rows = L.win * L.xstride * rsz;
+    L.xs0 = off;
+    off += rows;
+    L.xs1 = off;
+    off += rows;
+    L.fs = L.xs0;
+    L.steps = off;
+    off += L.win * (rsz == 16 ? (int)sizeof(StepRec<float>) : (int)sizeof(StepRec<double>));
+    off = align16(off);
+    L.atoms = off;
+    off += align16(natoms * 4) + natoms * kAtomTerms * (rsz == 16 ? 8 : 16);
+  } else {
+    L.xs0 = off;
+    off += natoms * rsz;
+    L.xs1 = off;
+    off += natoms * rsz;
+    L.fs = off;
+    off += natoms * rsz;
+    L.steps = L.atoms = off;
+  }
   L.lists = off;
   for (int k = 0; k < g.d; ++k) {
     off += align16((cv[k].na + cv[k].nb) * 4);
@@ -151,6 +221,12 @@ __host__ __device__ inline GroupLayout group_layout(int natoms, const CvDev *cv,
     if (cv[k].type == ABP_CV_COORD) off += (cv[k].na + cv[k].nb) * rsz + align32(nwarps * cv[k].na * 3 * real);
   off = align32(off);
   L.tile = off;
+  if (L.win) {
+    for (int k = 0; k < 3; ++k) L.T[k] = 0;
+    L.tile_nodes = 0;
+    L.total = align32(off);
+    return L;
+  }
   int budget = tile_budget - off;
   tile_dims(g, R, budget, L.T);
   L.tile_nodes = 0;

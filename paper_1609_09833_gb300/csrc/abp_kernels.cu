@@ -29,9 +29,10 @@ __device__ __forceinline__ void copy_desc(const Grp &g, WalkerDev *dst, const Wa
 }
 
 template <typename Real>
-__device__ __forceinline__ GroupLayout layout_of(const GroupFixed<Real> *fx, int nwarps, int tile_budget) {
+__device__ __forceinline__ GroupLayout layout_of(const GroupFixed<Real> *fx, int nwarps, int tile_budget,
+                                                 bool window) {
   return group_layout(fx->wd.natoms, fx->wd.cv, fx->wd.g, fx->wd.R, nwarps, (int)sizeof(typename Rec4<Real>::T),
-                      tile_budget);
+                      tile_budget, window);
 }
 
 // Copy each CV's atom lists (and COM weights as Real) into shared memory and
@@ -100,7 +101,7 @@ __device__ void eval_cvs(const Grp &g, GroupFixed<Real> *fx, const typename Rec4
 }
 
 // a2 + a3: tables, height from the grid before the deposit, the stencil.
-template <typename Real, bool TILE>
+template <typename Real, bool TILE, int UNR = 4>
 __device__ void deposit_step(const Grp &g, GroupFixed<Real> *fx, const GroupLayout &L, unsigned char *tile,
                              long long step, const DepositLog &log) {
   const WalkerDev &wd = fx->wd;
@@ -128,7 +129,7 @@ __device__ void deposit_step(const Grp &g, GroupFixed<Real> *fx, const GroupLayo
     }
   }
   g.sync();
-  deposit_stencil<Real, TILE>(g, fx, L, tile);
+  deposit_stencil<Real, TILE, UNR>(g, fx, L, tile);
   g.sync();
 }
 
@@ -244,7 +245,468 @@ __device__ void walker_steps(const Grp &g, GroupFixed<Real> *fx, unsigned char *
   }
 }
 
-template <typename Real, bool TILE>
+// ---------------------------------------------------------------- windowed form
+//
+// Walkers whose CVs are all COM distances and dihedrals run their nsteps MD
+// steps in windows of L.win steps. The coordinates of a whole window arrive
+// by cp.async while the previous window runs; within a window:
+//   A  the non-finite check of every (step, atom), then one thread per step:
+//      a1 (CVs and their Jacobian factors) and the axis state into the step's
+//      StepRec, and a4 at once for the steps before the window's first
+//      deposit (the grid cannot change before it); the thread of a deposit
+//      step starts an L2 prefetch of its stencil box;
+//   B  the window's deposits in step order, each by the whole group (a2 + a3
+//      as in the per-step form), each followed by a4 of the steps up to the
+//      next one, one thread per step;
+//   C  a5 for every (step, atom) pair from the atom's list entries, summed
+//      in registers in CV order and stored.
+// Every step reads the grid with exactly the deposits of the steps before it
+// and its own: the per-step order of the method, with the step-independent
+// work of a window done side by side. A step's arithmetic does not depend on
+// the window it falls in, so chunked calls give the same bits.
+
+// (j, i) = divmod(t, n), advanced by G each time without a division.
+struct Iter2 {
+  int j, i, q, r, n;
+  __device__ __forceinline__ Iter2(int t, int G, int n_) : n(n_) {
+    j = t / n;
+    i = t - j * n;
+    q = G / n;
+    r = G - q * n;
+  }
+  __device__ __forceinline__ void next() {
+    i += r;
+    j += q;
+    if (i >= n) {
+      i -= n;
+      ++j;
+    }
+  }
+};
+
+// COM distance of one step by one thread: each group's weighted offsets from
+// its first atom summed in list order, then s = |R_B - R_A| and u = d / s.
+template <typename Real>
+__device__ __forceinline__ int com_thread(const CvDev &c, const int32_t *ia, const int32_t *ib, const Real *wa,
+                                          const Real *wb, const typename Rec4<Real>::T *x, Real &s, Real *u) {
+  const auto ra = x[ia[0]];
+  const auto rb = x[ib[0]];
+  Real a0 = 0, a1 = 0, a2 = 0, b0 = 0, b1 = 0, b2 = 0;
+#pragma unroll 4
+  for (int i = 0; i < c.na; ++i) {
+    Real w = wa[i];
+    auto p = x[ia[i]];
+    a0 += w * (p.x - ra.x);
+    a1 += w * (p.y - ra.y);
+    a2 += w * (p.z - ra.z);
+  }
+#pragma unroll 4
+  for (int i = 0; i < c.nb; ++i) {
+    Real w = wb[i];
+    auto p = x[ib[i]];
+    b0 += w * (p.x - rb.x);
+    b1 += w * (p.y - rb.y);
+    b2 += w * (p.z - rb.z);
+  }
+  Real d[3] = {(rb.x - ra.x) + (b0 - a0), (rb.y - ra.y) + (b1 - a1), (rb.z - ra.z) + (b2 - a2)};
+  if (c.pbc)
+    for (int q = 0; q < 3; ++q) d[q] = min_image(d[q], c.box[q], c.inv_box[q]);
+  Real r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  s = r;
+  if (r > 0) {
+    Real ir = rcp_fast<Real>(r);
+    for (int q = 0; q < 3; ++q) u[q] = d[q] * ir;
+    return 0;
+  }
+  for (int q = 0; q < 3; ++q) u[q] = 0;
+  return ABP_WFLAG_SINGULAR;
+}
+
+// a4 of one step: the 2^d corners' records loaded together, then combined in
+// corner order.
+template <typename Real>
+__device__ __forceinline__ void interp_one(const WalkerDev &wd, StepRec<Real> &st) {
+  const GridDev &gd = wd.g;
+  const int d = gd.d, nc = 1 << d;
+  const unsigned char *rec = reinterpret_cast<const unsigned char *>(gd.rec);
+  Real f[3] = {0, 0, 0};
+  int i0[3] = {0, 0, 0}, i1[3] = {0, 0, 0};
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    if (k < d) {
+      f[k] = st.f[k];
+      i0[k] = st.i0[k];
+      i1[k] = st.i1[k];
+    }
+  Real v[8][4];
+  Real w[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    w[c] = 0;
+    v[c][0] = v[c][1] = v[c][2] = v[c][3] = 0;
+    if (c < nc) {
+      Real wc = 1;
+      long long node = 0, mul = 1;
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        if (k < d) {
+          const bool hi = (c >> k) & 1;
+          wc *= hi ? f[k] : (Real)1 - f[k];
+          node += mul * (hi ? i1[k] : i0[k]);
+          mul *= gd.n[k];
+        }
+      w[c] = wc;
+      rec_values<Real>(gd, rec + node * gd.rec_bytes, v[c]);
+    }
+  }
+  Real acc[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int c = 0; c < 8; ++c)
+    if (c < nc) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] += w[c] * v[c][q];
+    }
+  st.V = acc[0];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    if (k < d) {
+      const Real dv = ((st.clamped >> k) & 1) ? (Real)0 : acc[1 + k];
+      st.dv[k] = dv;
+      // the Jacobian factor, scaled for a5
+      const int nj = wd.cv[k].type == ABP_CV_COM_DIST ? 3 : 12;
+      for (int q = 0; q < nj; ++q) st.jac[k][q] *= dv;
+    }
+}
+
+// Phase A task: CV k of one step (row x of the window), its Jacobian
+// factors and axis state.
+template <typename Real>
+__device__ __forceinline__ void window_cv(const GroupFixed<Real> *fx, const typename Rec4<Real>::T *x, int k,
+                                          bool dep, StepRec<Real> &st) {
+  const WalkerDev &wd = fx->wd;
+  const CvDev &c = wd.cv[k];
+  Real sk;
+  int fl;
+  if (c.type == ABP_CV_COM_DIST)
+    fl = com_thread<Real>(c, fx->ia[k], fx->ib[k], fx->wa[k], fx->wb[k], x, sk, st.jac[k]);
+  else
+    fl = dihedral_eval<Real>(c, fx->ia[k], x, sk, reinterpret_cast<Real(*)[3]>(st.jac[k]));
+  st.s[k] = sk;
+  AxisSt<Real> ax = axis_eval<Real>(wd.g, wd.R[k], k, sk, (Real)0, dep);
+  st.i0[k] = ax.i0;
+  st.i1[k] = ax.i1;
+  st.f[k] = ax.f;
+  st.da[k] = ax.da;
+  st.dc[k] = ax.dc;
+  st.df[k] = ax.df;
+  st.ic_log[k] = ax.ic_log;
+  st.cfl[k] = fl | (ax.clamped << 16);
+}
+
+// a2 of a window deposit, by one thread: V_b(s_t) from the grid before the
+// deposit in FP64 (the 2^d corners' value fields, combined pairwise in corner
+// order), the height h = w exp(-V / dT), and the deposit log record.
+template <typename Real>
+__device__ void window_height(GroupFixed<Real> *fx, const StepRec<Real> &st, long long step, const DepositLog &log) {
+  const WalkerDev &wd = fx->wd;
+  const GridDev &gd = wd.g;
+  const int d = gd.d, nc = 1 << d;
+  const unsigned char *rec = reinterpret_cast<const unsigned char *>(gd.rec);
+  double t[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    t[c] = 0;
+    if (c < nc) {
+      double w = 1;
+      long long node = 0, mul = 1;
+      for (int k = 0; k < d; ++k) {
+        const bool hi = (c >> k) & 1;
+        const double f = (double)st.f[k];
+        w *= hi ? f : 1.0 - f;
+        node += mul * (hi ? st.i1[k] : st.i0[k]);
+        mul *= gd.n[k];
+      }
+      double v[4];
+      rec_values<double>(gd, rec + node * gd.rec_bytes, v);
+      t[c] = w * v[0];
+    }
+  }
+  const double V0 = ((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7]));
+  const double h = wd.w * exp(-V0 * wd.inv_dT);
+  fx->hV = V0;
+  fx->hf = (Real)h;
+  if (log.rec) {
+    unsigned long long slot = atomicAdd(log.count, 1ull);
+    if (slot < log.cap) {
+      abp_deposit_rec r;
+      r.step = step;
+      r.walker_id = wd.id;
+      for (int k = 0; k < 3; ++k) {
+        r.ic[k] = k < d ? st.ic_log[k] : 0;
+        r.s[k] = k < d ? (double)st.s[k] : 0.0;
+      }
+      r.height = h;
+      log.rec[slot] = r;
+    }
+  }
+}
+
+// The deposit's axis state into the group's fixed state (threads k < d), for
+// build_tables and the stencil.
+template <typename Real>
+__device__ __forceinline__ void window_dep_axis(const Grp &g, GroupFixed<Real> *fx, const StepRec<Real> &st) {
+  if (g.t < fx->wd.g.d) {
+    const int k = g.t;
+    fx->da[k] = st.da[k];
+    fx->dc[k] = st.dc[k];
+    fx->df[k] = st.df[k];
+  }
+}
+
+// The step's flags and clamp mask from its CV tasks.
+template <typename Real>
+__device__ __forceinline__ void step_flags(int d, bool dep, StepRec<Real> &st) {
+  int flags = dep ? ABP_WFLAG_DEPOSIT : 0, clamped = 0;
+  for (int k = 0; k < d; ++k) {
+    flags |= st.cfl[k] & 0xffff;
+    clamped |= ((st.cfl[k] >> 16) & 1) << k;
+  }
+  if (clamped) flags |= ABP_WFLAG_OOR;
+  st.clamped = clamped;
+  st.flags = flags;
+}
+
+// Per atom, its a5 terms in the order they are added (CV by CV, list A
+// before list B): COM distance list A w_i, list B -w_i (both on the unit
+// separation); dihedral atom a: -1 on its gradient row.
+template <typename Real>
+__device__ void build_atom_terms(const Grp &g, const GroupFixed<Real> *fx, int *cnt, AtomTerm<Real> *terms) {
+  const WalkerDev &wd = fx->wd;
+  for (int a = g.t; a < wd.natoms; a += g.G) cnt[a] = 0;
+  g.sync();
+  if (g.t == 0) {
+    for (int k = 0; k < wd.g.d; ++k) {
+      const CvDev &c = wd.cv[k];
+      const bool com = c.type == ABP_CV_COM_DIST;
+      for (int l = 0; l < (com ? 2 : 1); ++l) {
+        const int n = l ? c.nb : (com ? c.na : 4);
+        const int32_t *list = l ? fx->ib[k] : fx->ia[k];
+        for (int i = 0; i < n; ++i) {
+          const int at = list[i];
+          AtomTerm<Real> t;
+          t.w = com ? (l ? -fx->wb[k][i] : fx->wa[k][i]) : (Real)-1;
+          t.off = k * 12 + (com ? 0 : 3 * i);
+          terms[at * kAtomTerms + cnt[at]] = t;
+          cnt[at] += 1;
+        }
+      }
+    }
+  }
+  g.sync();
+}
+
+// a5 of atom a at one interpolated step, summed in the atom's term order.
+template <typename Real>
+__device__ __forceinline__ typename Rec4<Real>::T atom_force(const int *cnt, const AtomTerm<Real> *terms, int a,
+                                                             const StepRec<Real> &st) {
+  const AtomTerm<Real> *t = terms + a * kAtomTerms;
+  const int ne = cnt[a];
+  const Real *J = &st.jac[0][0];
+  Real f0 = 0, f1 = 0, f2 = 0;
+  for (int q = 0; q < ne; ++q) {
+    const Real w = t[q].w;
+    const Real *v = J + t[q].off;
+    f0 += w * v[0];
+    f1 += w * v[1];
+    f2 += w * v[2];
+  }
+  return make_rec<Real>(f0, f1, f2, 0);
+}
+
+// Force store of the windowed form: written once and not read again here,
+// so it streams past L2 (evict-first).
+template <typename Real>
+__device__ __forceinline__ void store_force_stream(typename Rec4<Real>::T *fo, const typename Rec4<Real>::T &f,
+                                                   int mode);
+template <>
+__device__ __forceinline__ void store_force_stream<float>(float4 *fo, const float4 &f, int mode) {
+  if (mode == ABP_FORCES_ACCUMULATE) {
+    float4 o = __ldcs(fo);
+    __stcs(fo, make_float4(o.x + f.x, o.y + f.y, o.z + f.z, o.w));
+  } else {
+    __stcs(fo, make_float4(f.x, f.y, f.z, 0.f));
+  }
+}
+template <>
+__device__ __forceinline__ void store_force_stream<double>(D4 *fo, const D4 &f, int mode) {
+  double2 *p = reinterpret_cast<double2 *>(fo);
+  if (mode == ABP_FORCES_ACCUMULATE) {
+    double2 a = __ldcs(p), b = __ldcs(p + 1);
+    __stcs(p, make_double2(a.x + f.x, a.y + f.y));
+    __stcs(p + 1, make_double2(b.x + f.z, b.y));
+  } else {
+    __stcs(p, make_double2(f.x, f.y));
+    __stcs(p + 1, make_double2(f.z, 0.0));
+  }
+}
+
+template <typename Real, int UNR>
+__device__ void walker_window(const Grp &g, GroupFixed<Real> *fx, unsigned char *dyn, const GroupLayout &L,
+                              const RunArgs &a, int widx) {
+  using R4 = typename Rec4<Real>::T;
+  const WalkerDev &wd = fx->wd;
+  const int natoms = wd.natoms, d = wd.g.d, W = L.win, xst = L.xstride;
+  R4 *xb[2] = {reinterpret_cast<R4 *>(dyn + L.xs0), reinterpret_cast<R4 *>(dyn + L.xs1)};
+  StepRec<Real> *steps = reinterpret_cast<StepRec<Real> *>(dyn + L.steps);
+  int *cnt = reinterpret_cast<int *>(dyn + L.atoms);
+  AtomTerm<Real> *terms = reinterpret_cast<AtomTerm<Real> *>(dyn + L.atoms + align16(natoms * 4));
+  const R4 *cin = reinterpret_cast<const R4 *>(a.coords);
+  R4 *fout = a.forces ? reinterpret_cast<R4 *>(a.forces) : reinterpret_cast<R4 *>(wd.fbuf);
+  const long long coff = a.coff[widx];
+  const long long foff = a.forces ? a.foff[widx] : 0;
+  const int mode = a.forces ? a.mode : ABP_FORCES_OVERWRITE;
+  const int pieces = natoms * (int)(sizeof(R4) / 16);
+  const long long step0 = a.wstep ? a.wstep[widx] : a.step0;
+  const long long last = (long long)a.nsteps - 1;
+  const int nwin = (a.nsteps + W - 1) / W;
+  // forces of several steps to one address must be added in step order
+  const bool serial_out = a.forces && a.fstride == 0;
+  const unsigned long long stream = l2_evict_first();
+  auto prefetch = [&](int w, R4 *dst) {
+    const int t0 = w * W, nt = min(W, a.nsteps - t0);
+    for (Iter2 it(g.t, g.G, pieces); it.j < nt; it.next()) {
+      const unsigned char *src =
+          reinterpret_cast<const unsigned char *>(cin + coff + (long long)(t0 + it.j) * a.cstride) + it.i * 16;
+      cp_async16_hint(reinterpret_cast<unsigned char *>(dst + it.j * xst) + it.i * 16, src, stream);
+    }
+    cp_async_commit();
+  };
+  if (g.t == 0) fx->winbad[0] = fx->winbad[1] = 0;
+  build_atom_terms<Real>(g, fx, cnt, terms);
+  // offset (in steps from step0) of the next deposit step
+  const long long rem = step0 % wd.stride;
+  long long next_dep = rem == 0 ? 0 : wd.stride - rem;
+  prefetch(0, xb[0]);
+  for (int w = 0; w < nwin; ++w) {
+    const int t0 = w * W, nt = min(W, a.nsteps - t0);
+    const R4 *xs = xb[w & 1];
+    cp_async_wait_all();
+    g.sync();
+    if (w + 1 < nwin) prefetch(w + 1, xb[(w + 1) & 1]);
+    if (g.t == 0) fx->winbad[(w + 1) & 1] = 0;  // last read in window w - 1
+    // deposit steps of this window (bit j: step t0 + j)
+    unsigned dmask = 0;
+    for (; next_dep < (long long)t0 + nt; next_dep += wd.stride) dmask |= 1u << (int)(next_dep - t0);
+    // A: non-finite check of every (step, atom): a mask per thread, OR-ed
+    // over the warp, one shared-memory OR per warp
+    {
+      unsigned mine = 0;
+      Iter2 it(g.t, g.G, natoms);
+      while (it.j < nt) {
+        R4 p[4];
+        int jj[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          jj[u] = it.j;
+          if (it.j < nt) {
+            p[u] = xs[it.j * xst + it.i];
+            it.next();
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (jj[u] < nt && !finite_rec<Real>(p[u])) mine |= 1u << jj[u];
+      }
+      mine = __reduce_or_sync(0xffffffffu, mine);
+      if (g.lane == 0 && mine) atomicOr(&fx->winbad[w & 1], mine);
+    }
+    g.sync();
+    const unsigned bad = fx->winbad[w & 1];
+    if (g.t == 0 && bad) atomicAdd(&a.ctr->nonfinite, __popc(bad));
+    const unsigned gdep = dmask & ~bad;  // a step with non-finite coordinates deposits nothing
+    const int first = gdep ? __ffs(gdep) - 1 : nt;
+    // A: a1 and the axis state, one thread per (CV, step)
+    for (Iter2 it(g.t, g.G, nt); it.j < d; it.next())
+      if (!((bad >> it.i) & 1)) window_cv<Real>(fx, xs + it.i * xst, it.j, (dmask >> it.i) & 1, steps[it.i]);
+    g.sync();
+    // the first deposit's tables and height are formed while the steps
+    // before it interpolate (the grid is the same for both)
+    if (gdep) window_dep_axis<Real>(g, fx, steps[first]);
+    g.sync();
+    for (int j = g.t; j < nt; j += g.G)
+      if (!((bad >> j) & 1)) {
+        step_flags<Real>(d, (dmask >> j) & 1, steps[j]);
+        if (j < first) interp_one<Real>(wd, steps[j]);
+      }
+    if (gdep) {
+      build_tables<Real>(g, fx);
+      if (g.t == g.G - 1) window_height<Real>(fx, steps[first], step0 + t0 + first, a.log);
+    }
+    g.sync();
+    // B: deposits in step order, each followed by a4 of the steps up to the next
+    int seg = first;
+    for (unsigned m = gdep; m; m &= m - 1) {
+      const int j = __ffs(m) - 1;
+      if (j != first) {
+        for (int q = seg + g.t; q < j; q += g.G)
+          if (!((bad >> q) & 1)) interp_one<Real>(wd, steps[q]);
+        window_dep_axis<Real>(g, fx, steps[j]);
+        g.sync();
+        build_tables<Real>(g, fx);
+        if (g.t == g.G - 1) window_height<Real>(fx, steps[j], step0 + t0 + j, a.log);
+        g.sync();
+      }
+      deposit_stencil<Real, false, UNR>(g, fx, L, nullptr);
+      g.sync();
+      seg = j;
+    }
+    for (int q = seg + g.t; q < nt; q += g.G)
+      if (!((bad >> q) & 1)) interp_one<Real>(wd, steps[q]);
+    g.sync();
+    // C: a5 per (step, atom), stored as it is formed
+    if (!serial_out) {
+      for (Iter2 it(g.t, g.G, natoms); it.j < nt; it.next()) {
+        const long long t = (long long)t0 + it.j;
+        if (!a.forces && t != last) continue;  // the walker's own buffer keeps the last step
+        R4 *fo = fout + foff + (a.forces ? t * a.fstride : 0) + it.i;
+        if ((bad >> it.j) & 1) {
+          if (mode == ABP_FORCES_OVERWRITE) *fo = make_rec<Real>(0, 0, 0, 0);
+        } else {
+          store_force_stream<Real>(fo, atom_force<Real>(cnt, terms, it.i, steps[it.j]), mode);
+        }
+      }
+    } else {
+      for (int i = g.t; i < natoms; i += g.G)
+        for (int j = 0; j < nt; ++j) {
+          R4 *fo = fout + foff + i;
+          if ((bad >> j) & 1) {
+            if (mode == ABP_FORCES_OVERWRITE) *fo = make_rec<Real>(0, 0, 0, 0);
+          } else {
+            store_force<Real>(fo, atom_force<Real>(cnt, terms, i, steps[j]), mode);
+          }
+        }
+    }
+    if (w + 1 == nwin && g.t == 0) {
+      const StepRec<Real> &st = steps[nt - 1];
+      if ((bad >> (nt - 1)) & 1) {
+        wd.state->flags = ABP_WFLAG_NONFINITE;
+      } else {
+        WalkerState ws;
+        for (int k = 0; k < 3; ++k) {
+          ws.s[k] = k < d ? (double)st.s[k] : 0.0;
+          ws.dV[k] = k < d ? (double)st.dv[k] : 0.0;
+        }
+        ws.V = (double)st.V;
+        ws.flags = st.flags;
+        ws.pad = 0;
+        ws.step = step0 + last;
+        *wd.state = ws;
+      }
+    }
+  }
+}
+
+template <typename Real, bool TILE, int UNR>
 __device__ __forceinline__ void run_body(const RunArgs &a) {
   extern __shared__ __align__(32) unsigned char smem[];
   const int gid = threadIdx.x / a.G;
@@ -263,10 +725,12 @@ __device__ __forceinline__ void run_body(const RunArgs &a) {
   const TableEntry te = a.table[slot];
   copy_desc<Real>(g, &fx->wd, te.wd);
   g.sync();
-  const GroupLayout L = layout_of<Real>(fx, g.nwarps, TILE ? a.tile_budget : 0);
+  const GroupLayout L = layout_of<Real>(fx, g.nwarps, TILE ? a.tile_budget : 0, true);
   setup_lists<Real>(g, fx, dyn + L.lists);
   g.sync();
-  if (TILE && L.tile_nodes > 0)
+  if (L.win > 0)
+    walker_window<Real, UNR>(g, fx, dyn, L, a, te.idx);
+  else if (TILE && L.tile_nodes > 0)
     walker_steps<Real, true>(g, fx, dyn, L, a, te.idx);
   else
     walker_steps<Real, false>(g, fx, dyn, L, a, te.idx);
@@ -274,13 +738,13 @@ __device__ __forceinline__ void run_body(const RunArgs &a) {
 
 template <typename Real, bool TILE>
 __global__ void __launch_bounds__(256, 1) k_run(RunArgs a) {
-  run_body<Real, TILE>(a);
+  run_body<Real, TILE, 8>(a);
 }
 
 // The same kernel compiled for two resident 256-thread CTAs per SM (at most
 // 128 registers per thread): more warps to hide latency for batches whose
 // walkers are busy in long CN pair loops. Chosen by ABP_TUNE_LEAN.
-__global__ void __launch_bounds__(256, 2) k_run_lean(RunArgs a) { run_body<float, false>(a); }
+__global__ void __launch_bounds__(256, 2) k_run_lean(RunArgs a) { run_body<float, false, 4>(a); }
 
 cudaError_t launch_run(const RunArgs &a, int fp64, cudaStream_t st) {
   const int threads = a.G * a.groups_per_cta;
@@ -309,7 +773,7 @@ cudaError_t launch_run(const RunArgs &a, int fp64, cudaStream_t st) {
 }
 
 int run_group_bytes(const WalkerDev &hd, int fp64, int G, int tile_budget) {
-  GroupLayout L = group_layout(hd.natoms, hd.cv, hd.g, hd.R, G / 32, fp64 ? 32 : 16, tile_budget);
+  GroupLayout L = group_layout(hd.natoms, hd.cv, hd.g, hd.R, G / 32, fp64 ? 32 : 16, tile_budget, true);
   return align32(group_fixed_bytes(fp64) + L.total);
 }
 
@@ -356,7 +820,7 @@ template <typename Real>
 __device__ GroupLayout plain_prologue(const Grp &g, GroupFixed<Real> *fx, const WalkerDev *wdp, unsigned char *dyn) {
   copy_desc<Real>(g, &fx->wd, wdp);
   g.sync();
-  GroupLayout L = layout_of<Real>(fx, g.nwarps, 0);
+  GroupLayout L = layout_of<Real>(fx, g.nwarps, 0, false);
   setup_lists<Real>(g, fx, dyn + L.lists);
   if (g.t == 0) {
     fx->flags = 0;

@@ -187,7 +187,9 @@ def test_chunked_calls_and_step_forces_are_bitwise_equal(abp, ctx):
 def test_grid_tile_is_bitwise_exact(abp, ctx):
     """The opt-in shared-memory grid tile (ABP_TUNE_TILE = 1) gives the same
     bits as the untiled path: sweeps that cross the periodic seam and leave
-    the tile (forcing reloads), and 1D / 2D / 3D CN walkers."""
+    the tile (forcing reloads), and 1D / 2D / 3D CN walkers. (COM-distance
+    and dihedral walkers run in the windowed form, which takes no tile: for
+    them the setting must change nothing.)"""
     specs = synth.mb64_specs(nw=6, stride=4)
     frames = synth.SweepFrames(6, seed=18, period=(60, 90), dihedral_period=(40, 70)).frames(0, 240)
     w0 = ctx.make_walkers(specs)
