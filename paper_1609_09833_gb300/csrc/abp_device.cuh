@@ -106,7 +106,7 @@ struct GroupFixed {
   int clamped;               // interpolation clamp mask
   int flags;
   int bad;
-  unsigned winbad[2];        // windowed form: non-finite steps of a window, by window parity
+  unsigned winbad[3];        // windowed form: non-finite steps of the windows in flight (window % 3)
   int reload;                // the tile must be reloaded this step
   int org[kMaxCv];           // tile origin node per axis
   Real V;

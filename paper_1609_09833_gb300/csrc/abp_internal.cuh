@@ -147,7 +147,7 @@ __host__ __device__ inline int window_steps(int natoms, const CvDev *cv, int d, 
 //             `xstride` records (the current window's rows then hold its
 //             force accumulators)
 //   fs        force accumulators (per-step form)
-//   steps     the window's StepRec array (windowed form)
+//   steps     StepRec arrays of the three windows in flight (windowed form)
 //   atoms     per atom, its a5 terms: counts, then AtomTerm[natoms][kAtomTerms] (windowed form)
 //   lists     per-CV atom index lists (+ COM weights)
 //   cn        per COORD CV: dCN/dx per list entry and per-warp partials
@@ -197,7 +197,7 @@ __host__ __device__ inline GroupLayout group_layout(int natoms, const CvDev *cv,
     off += rows;
     L.fs = L.xs0;
     L.steps = off;
-    off += L.win * (rsz == 16 ? (int)sizeof(StepRec<float>) : (int)sizeof(StepRec<double>));
+    off += 3 * L.win * (rsz == 16 ? (int)sizeof(StepRec<float>) : (int)sizeof(StepRec<double>));
     off = align16(off);
     L.atoms = off;
     off += align16(natoms * 4) + natoms * kAtomTerms * (rsz == 16 ? 8 : 16);

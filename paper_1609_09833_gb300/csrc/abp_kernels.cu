@@ -550,56 +550,63 @@ __device__ __forceinline__ void store_force_stream<double>(D4 *fo, const D4 &f, 
   }
 }
 
-template <typename Real, int UNR>
-__device__ void walker_window(const Grp &g, GroupFixed<Real> *fx, unsigned char *dyn, const GroupLayout &L,
-                              const RunArgs &a, int widx) {
+// Deposit steps of a window (bit j: step t0 + j).
+__device__ __forceinline__ unsigned window_dmask(long long step0, int t0, int nt, long long stride) {
+  const long long rem = (step0 + t0) % stride;
+  unsigned m = 0;
+  for (long long j = rem == 0 ? 0 : stride - rem; j < nt; j += stride) m |= 1u << (int)j;
+  return m;
+}
+
+// Phases of one window, each run by a (sub)group `g` that ends synchronised.
+template <typename Real>
+struct WindowCtx {
   using R4 = typename Rec4<Real>::T;
-  const WalkerDev &wd = fx->wd;
-  const int natoms = wd.natoms, d = wd.g.d, W = L.win, xst = L.xstride;
-  R4 *xb[2] = {reinterpret_cast<R4 *>(dyn + L.xs0), reinterpret_cast<R4 *>(dyn + L.xs1)};
-  StepRec<Real> *steps = reinterpret_cast<StepRec<Real> *>(dyn + L.steps);
-  int *cnt = reinterpret_cast<int *>(dyn + L.atoms);
-  AtomTerm<Real> *terms = reinterpret_cast<AtomTerm<Real> *>(dyn + L.atoms + align16(natoms * 4));
-  const R4 *cin = reinterpret_cast<const R4 *>(a.coords);
-  R4 *fout = a.forces ? reinterpret_cast<R4 *>(a.forces) : reinterpret_cast<R4 *>(wd.fbuf);
-  const long long coff = a.coff[widx];
-  const long long foff = a.forces ? a.foff[widx] : 0;
-  const int mode = a.forces ? a.mode : ABP_FORCES_OVERWRITE;
-  const int pieces = natoms * (int)(sizeof(R4) / 16);
-  const long long step0 = a.wstep ? a.wstep[widx] : a.step0;
-  const long long last = (long long)a.nsteps - 1;
-  const int nwin = (a.nsteps + W - 1) / W;
-  // forces of several steps to one address must be added in step order
-  const bool serial_out = a.forces && a.fstride == 0;
-  const unsigned long long stream = l2_evict_first();
-  auto prefetch = [&](int w, R4 *dst) {
-    const int t0 = w * W, nt = min(W, a.nsteps - t0);
+  GroupFixed<Real> *fx;
+  GroupLayout L;          // copies, so the context stays in registers
+  const void *coords;
+  void *out;             // the caller's force records (NULL: the walker's own buffer)
+  long long cstride, fstride;
+  int nsteps, xst;
+  DevCounters *ctr;
+  DepositLog log;
+  R4 *xb[2];
+  StepRec<Real> *steps;  // 3 windows of W records
+  int *cnt;
+  AtomTerm<Real> *terms;
+  long long coff, foff, step0, last;
+  int W, nwin, mode;
+  bool serial_out;
+  unsigned long long stream;
+
+  __device__ __forceinline__ int nt_of(int w) const { return min(W, nsteps - w * W); }
+  __device__ __forceinline__ StepRec<Real> *steps_of(int w) const { return steps + (w % 3) * W; }
+
+  // coordinates of window w into its buffer (one cp.async commit group)
+  __device__ __forceinline__ void prefetch(const Grp &g, int w) const {
+    const int t0 = w * W, nt = nt_of(w);
+    const int pieces = fx->wd.natoms * (int)(sizeof(R4) / 16);
+    const R4 *cin = reinterpret_cast<const R4 *>(coords);
+    R4 *dst = xb[w & 1];
     for (Iter2 it(g.t, g.G, pieces); it.j < nt; it.next()) {
       const unsigned char *src =
-          reinterpret_cast<const unsigned char *>(cin + coff + (long long)(t0 + it.j) * a.cstride) + it.i * 16;
+          reinterpret_cast<const unsigned char *>(cin + coff + (long long)(t0 + it.j) * cstride) + it.i * 16;
       cp_async16_hint(reinterpret_cast<unsigned char *>(dst + it.j * xst) + it.i * 16, src, stream);
     }
     cp_async_commit();
-  };
-  if (g.t == 0) fx->winbad[0] = fx->winbad[1] = 0;
-  build_atom_terms<Real>(g, fx, cnt, terms);
-  // offset (in steps from step0) of the next deposit step
-  const long long rem = step0 % wd.stride;
-  long long next_dep = rem == 0 ? 0 : wd.stride - rem;
-  prefetch(0, xb[0]);
-  for (int w = 0; w < nwin; ++w) {
-    const int t0 = w * W, nt = min(W, a.nsteps - t0);
+  }
+
+  // A: non-finite check, then a1 and the axis state, one thread per (CV, step)
+  __device__ __forceinline__ void cvs(const Grp &g, int w) const {
+    const WalkerDev &wd = fx->wd;
+    const int nt = nt_of(w), natoms = wd.natoms, d = wd.g.d;
     const R4 *xs = xb[w & 1];
-    cp_async_wait_all();
+    StepRec<Real> *st = steps_of(w);
+    unsigned *badp = &fx->winbad[w % 3];
+    if (g.t == 0) *badp = 0;
     g.sync();
-    if (w + 1 < nwin) prefetch(w + 1, xb[(w + 1) & 1]);
-    if (g.t == 0) fx->winbad[(w + 1) & 1] = 0;  // last read in window w - 1
-    // deposit steps of this window (bit j: step t0 + j)
-    unsigned dmask = 0;
-    for (; next_dep < (long long)t0 + nt; next_dep += wd.stride) dmask |= 1u << (int)(next_dep - t0);
-    // A: non-finite check of every (step, atom): a mask per thread, OR-ed
-    // over the warp, one shared-memory OR per warp
     {
+      // a mask per thread, OR-ed over the warp, one shared-memory OR per warp
       unsigned mine = 0;
       Iter2 it(g.t, g.G, natoms);
       while (it.j < nt) {
@@ -618,42 +625,52 @@ __device__ void walker_window(const Grp &g, GroupFixed<Real> *fx, unsigned char 
           if (jj[u] < nt && !finite_rec<Real>(p[u])) mine |= 1u << jj[u];
       }
       mine = __reduce_or_sync(0xffffffffu, mine);
-      if (g.lane == 0 && mine) atomicOr(&fx->winbad[w & 1], mine);
+      if (g.lane == 0 && mine) atomicOr(badp, mine);
     }
     g.sync();
-    const unsigned bad = fx->winbad[w & 1];
-    if (g.t == 0 && bad) atomicAdd(&a.ctr->nonfinite, __popc(bad));
-    const unsigned gdep = dmask & ~bad;  // a step with non-finite coordinates deposits nothing
-    const int first = gdep ? __ffs(gdep) - 1 : nt;
-    // A: a1 and the axis state, one thread per (CV, step)
+    const unsigned bad = *badp;
+    if (g.t == 0 && bad) atomicAdd(&ctr->nonfinite, __popc(bad));
+    const unsigned dmask = window_dmask(step0, w * W, nt, wd.stride);
     for (Iter2 it(g.t, g.G, nt); it.j < d; it.next())
-      if (!((bad >> it.i) & 1)) window_cv<Real>(fx, xs + it.i * xst, it.j, (dmask >> it.i) & 1, steps[it.i]);
-    g.sync();
-    // the first deposit's tables and height are formed while the steps
-    // before it interpolate (the grid is the same for both)
-    if (gdep) window_dep_axis<Real>(g, fx, steps[first]);
+      if (!((bad >> it.i) & 1)) window_cv<Real>(fx, xs + it.i * xst, it.j, (dmask >> it.i) & 1, st[it.i]);
     g.sync();
     for (int j = g.t; j < nt; j += g.G)
-      if (!((bad >> j) & 1)) {
-        step_flags<Real>(d, (dmask >> j) & 1, steps[j]);
-        if (j < first) interp_one<Real>(wd, steps[j]);
-      }
+      if (!((bad >> j) & 1)) step_flags<Real>(d, (dmask >> j) & 1, st[j]);
+    g.sync();
+  }
+
+  // a2 .. a4 of window w on the grid: deposits in step order, each preceded
+  // by a4 of the steps before it; the first deposit's tables and height are
+  // formed while the steps before it interpolate (same grid for both)
+  template <int UNR>
+  __device__ __forceinline__ void chain(const Grp &g, int w) const {
+    const WalkerDev &wd = fx->wd;
+    const int nt = nt_of(w), t0 = w * W;
+    StepRec<Real> *st = steps_of(w);
+    const unsigned bad = fx->winbad[w % 3];
+    const unsigned gdep = window_dmask(step0, t0, nt, wd.stride) & ~bad;  // non-finite steps deposit nothing
+    const int first = gdep ? __ffs(gdep) - 1 : nt;
+    if (gdep) {
+      window_dep_axis<Real>(g, fx, st[first]);
+      g.sync();
+    }
+    for (int j = g.t; j < first; j += g.G)
+      if (!((bad >> j) & 1)) interp_one<Real>(wd, st[j]);
     if (gdep) {
       build_tables<Real>(g, fx);
-      if (g.t == g.G - 1) window_height<Real>(fx, steps[first], step0 + t0 + first, a.log);
+      if (g.t == g.G - 1) window_height<Real>(fx, st[first], step0 + t0 + first, log);
     }
     g.sync();
-    // B: deposits in step order, each followed by a4 of the steps up to the next
     int seg = first;
     for (unsigned m = gdep; m; m &= m - 1) {
       const int j = __ffs(m) - 1;
       if (j != first) {
         for (int q = seg + g.t; q < j; q += g.G)
-          if (!((bad >> q) & 1)) interp_one<Real>(wd, steps[q]);
-        window_dep_axis<Real>(g, fx, steps[j]);
+          if (!((bad >> q) & 1)) interp_one<Real>(wd, st[q]);
+        window_dep_axis<Real>(g, fx, st[j]);
         g.sync();
         build_tables<Real>(g, fx);
-        if (g.t == g.G - 1) window_height<Real>(fx, steps[j], step0 + t0 + j, a.log);
+        if (g.t == g.G - 1) window_height<Real>(fx, st[j], step0 + t0 + j, log);
         g.sync();
       }
       deposit_stencil<Real, false, UNR>(g, fx, L, nullptr);
@@ -661,48 +678,130 @@ __device__ void walker_window(const Grp &g, GroupFixed<Real> *fx, unsigned char 
       seg = j;
     }
     for (int q = seg + g.t; q < nt; q += g.G)
-      if (!((bad >> q) & 1)) interp_one<Real>(wd, steps[q]);
+      if (!((bad >> q) & 1)) interp_one<Real>(wd, st[q]);
     g.sync();
-    // C: a5 per (step, atom), stored as it is formed
+    if (w + 1 == nwin && g.t == 0) {
+      const StepRec<Real> &s = st[nt - 1];
+      if ((bad >> (nt - 1)) & 1) {
+        wd.state->flags = ABP_WFLAG_NONFINITE;
+      } else {
+        WalkerState ws;
+        for (int k = 0; k < 3; ++k) {
+          ws.s[k] = k < wd.g.d ? (double)s.s[k] : 0.0;
+          ws.dV[k] = k < wd.g.d ? (double)s.dv[k] : 0.0;
+        }
+        ws.V = (double)s.V;
+        ws.flags = s.flags;
+        ws.pad = 0;
+        ws.step = step0 + last;
+        *wd.state = ws;
+      }
+    }
+  }
+
+  // C: a5 per (step, atom), stored as it is formed
+  __device__ __forceinline__ void forces(const Grp &g, int w) const {
+    const int nt = nt_of(w), t0 = w * W, natoms = fx->wd.natoms;
+    const StepRec<Real> *st = steps_of(w);
+    const unsigned bad = fx->winbad[w % 3];
+    R4 *fout = out ? reinterpret_cast<R4 *>(out) : reinterpret_cast<R4 *>(fx->wd.fbuf);
     if (!serial_out) {
       for (Iter2 it(g.t, g.G, natoms); it.j < nt; it.next()) {
         const long long t = (long long)t0 + it.j;
-        if (!a.forces && t != last) continue;  // the walker's own buffer keeps the last step
-        R4 *fo = fout + foff + (a.forces ? t * a.fstride : 0) + it.i;
+        if (!out && t != last) continue;  // the walker's own buffer keeps the last step
+        R4 *fo = fout + foff + (out ? t * fstride : 0) + it.i;
         if ((bad >> it.j) & 1) {
           if (mode == ABP_FORCES_OVERWRITE) *fo = make_rec<Real>(0, 0, 0, 0);
         } else {
-          store_force_stream<Real>(fo, atom_force<Real>(cnt, terms, it.i, steps[it.j]), mode);
+          store_force_stream<Real>(fo, atom_force<Real>(cnt, terms, it.i, st[it.j]), mode);
         }
       }
     } else {
+      // forces of several steps to one address: added in step order
       for (int i = g.t; i < natoms; i += g.G)
         for (int j = 0; j < nt; ++j) {
           R4 *fo = fout + foff + i;
           if ((bad >> j) & 1) {
             if (mode == ABP_FORCES_OVERWRITE) *fo = make_rec<Real>(0, 0, 0, 0);
           } else {
-            store_force<Real>(fo, atom_force<Real>(cnt, terms, i, steps[j]), mode);
+            store_force<Real>(fo, atom_force<Real>(cnt, terms, i, st[j]), mode);
           }
         }
     }
-    if (w + 1 == nwin && g.t == 0) {
-      const StepRec<Real> &st = steps[nt - 1];
-      if ((bad >> (nt - 1)) & 1) {
-        wd.state->flags = ABP_WFLAG_NONFINITE;
-      } else {
-        WalkerState ws;
-        for (int k = 0; k < 3; ++k) {
-          ws.s[k] = k < d ? (double)st.s[k] : 0.0;
-          ws.dV[k] = k < d ? (double)st.dv[k] : 0.0;
-        }
-        ws.V = (double)st.V;
-        ws.flags = st.flags;
-        ws.pad = 0;
-        ws.step = step0 + last;
-        *wd.state = ws;
+  }
+};
+
+// The windowed form's driver. Iteration w runs A of window w + 1 and C of
+// window w - 1 (grid-independent) beside the grid chain of window w; the
+// three touch different StepRec arrays. A group of two or more warps splits
+// in halves on their own named barriers, the first half taking A and C (and
+// the coordinate copies), the second the chain; a one-warp group runs the
+// three in turn.
+template <typename Real, int UNR>
+__device__ void walker_window(const Grp &g, GroupFixed<Real> *fx, unsigned char *dyn, const GroupLayout &L,
+                              const RunArgs &a, int widx) {
+  using R4 = typename Rec4<Real>::T;
+  WindowCtx<Real> c;
+  c.fx = fx;
+  c.L = L;
+  c.coords = a.coords;
+  c.out = a.forces;
+  c.cstride = a.cstride;
+  c.fstride = a.fstride;
+  c.nsteps = a.nsteps;
+  c.xst = L.xstride;
+  c.ctr = a.ctr;
+  c.log = a.log;
+  c.xb[0] = reinterpret_cast<R4 *>(dyn + L.xs0);
+  c.xb[1] = reinterpret_cast<R4 *>(dyn + L.xs1);
+  c.steps = reinterpret_cast<StepRec<Real> *>(dyn + L.steps);
+  c.cnt = reinterpret_cast<int *>(dyn + L.atoms);
+  c.terms = reinterpret_cast<AtomTerm<Real> *>(dyn + L.atoms + align16(fx->wd.natoms * 4));
+  c.coff = a.coff[widx];
+  c.foff = a.forces ? a.foff[widx] : 0;
+  c.step0 = a.wstep ? a.wstep[widx] : a.step0;
+  c.last = (long long)a.nsteps - 1;
+  c.W = L.win;
+  c.nwin = (a.nsteps + L.win - 1) / L.win;
+  c.mode = a.forces ? a.mode : ABP_FORCES_OVERWRITE;
+  c.serial_out = a.forces && a.fstride == 0;
+  c.stream = l2_evict_first();
+  // the two halves (or the whole warp twice)
+  const bool split = g.G >= 64;
+  Grp gx = g, gy = g;
+  if (split) {
+    gx.G = gy.G = g.G / 2;
+    gx.nwarps = gy.nwarps = g.nwarps / 2;
+    gx.gid = a.groups_per_cta + 2 * g.gid;  // named barriers after the groups' own (gid + 1)
+    gy.gid = gx.gid + 1;
+    gy.t = g.t - gx.G;
+    gy.warp = g.warp - gx.nwarps;
+  }
+  const bool isx = !split || g.t < g.G / 2, isy = !split || !isx;
+  build_atom_terms<Real>(g, fx, c.cnt, c.terms);
+  if (isx) {
+    c.prefetch(gx, 0);
+    if (c.nwin > 1) c.prefetch(gx, 1);
+    if (c.nwin > 1)
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    else
+      cp_async_wait_all();
+    gx.sync();
+    c.cvs(gx, 0);
+  }
+  g.sync();
+  for (int w = 0; w <= c.nwin; ++w) {
+    if (isx) {
+      if (w + 1 < c.nwin) {
+        cp_async_wait_all();  // window w + 1's coordinates
+        gx.sync();
+        if (w + 2 < c.nwin) c.prefetch(gx, w + 2);  // into the buffer window w used
+        c.cvs(gx, w + 1);
       }
+      if (w >= 1) c.forces(gx, w - 1);
     }
+    if (isy && w < c.nwin) c.template chain<UNR>(gy, w);
+    g.sync();
   }
 }
 
