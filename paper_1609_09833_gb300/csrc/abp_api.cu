@@ -91,6 +91,7 @@ struct abp_walker {
   std::vector<std::pair<void *, size_t>> allocs;
   bool has_cn = false;
   bool big = false;    // runs in the phased form (shared grid, or too large for a walker group)
+  bool win = false;    // runs in the windowed form of the fused kernel (COM distance / dihedral CVs)
   long long cost = 0;  // rough work estimate used to order batched launches
 };
 
@@ -203,11 +204,27 @@ abp_status get_table(abp_ctx *ctx, abp_walker *const *walkers, int n, bool sort_
 // Launch shape for a batch: a group of G threads per walker, several
 // groups per CTA, as shared memory allows. Multi-step launches of FP32
 // walkers with few enough walkers per SM also give each group a shared-memory
-// tile of its grid (the rest of ~220 KB / walkers-per-SM).
-abp_status pick_shape(const abp_ctx *ctx, abp_walker *const *walkers, int n, int fp64, int nsteps, int *G, int *gpc,
-                      int *group_bytes, int *tile_budget) {
+// tile of its grid (the rest of ~220 KB / walkers-per-SM). A windowed batch
+// defaults to one 256-thread group per CTA: its two halves run the window
+// pipeline's two stages.
+abp_status pick_shape(const abp_ctx *ctx, abp_walker *const *walkers, int n, int fp64, int nsteps, bool window,
+                      int *G, int *gpc, int *group_bytes, int *tile_budget) {
   bool cn = false;
   for (int i = 0; i < n; ++i) cn = cn || walkers[i]->has_cn;
+  if (window) {
+    const int g = ctx->tune_G ? ctx->tune_G : 256;
+    int gb = 0;
+    for (int i = 0; i < n; ++i) gb = std::max(gb, run_group_bytes(walkers[i]->hd, fp64, g, 0, true));
+    const int smem_max = 227 * 1024;
+    if (gb > smem_max) return fail(ABP_ERR_UNSUPPORTED, "a walker needs %d bytes of shared memory (max %d)", gb, smem_max);
+    int per = ctx->tune_gpc ? ctx->tune_gpc : 1;
+    while (per > 1 && (per * gb > smem_max || per * g > 256)) --per;
+    *G = g;
+    *gpc = per;
+    *group_bytes = gb;
+    *tile_budget = 0;
+    return ABP_OK;
+  }
   int g = ctx->tune_G ? ctx->tune_G : (cn ? 128 : 32);
   const int smem_max = 227 * 1024;
   int fixed = group_fixed_bytes(fp64);
@@ -224,14 +241,14 @@ abp_status pick_shape(const abp_ctx *ctx, abp_walker *const *walkers, int n, int
   int gb = 0;
   bool any_tile = false;
   for (int i = 0; i < n; ++i) {
-    int b = run_group_bytes(walkers[i]->hd, fp64, g, tb);
+    int b = run_group_bytes(walkers[i]->hd, fp64, g, tb, false);
     gb = std::max(gb, b);
-    if (tb > 0 && b > run_group_bytes(walkers[i]->hd, fp64, g, 0)) any_tile = true;
+    if (tb > 0 && b > run_group_bytes(walkers[i]->hd, fp64, g, 0, false)) any_tile = true;
   }
   if (!any_tile) {
     tb = 0;
     gb = 0;
-    for (int i = 0; i < n; ++i) gb = std::max(gb, run_group_bytes(walkers[i]->hd, fp64, g, 0));
+    for (int i = 0; i < n; ++i) gb = std::max(gb, run_group_bytes(walkers[i]->hd, fp64, g, 0, false));
   }
   if (gb > smem_max) return fail(ABP_ERR_UNSUPPORTED, "a walker needs %d bytes of shared memory (max %d)", gb, smem_max);
   int per = 1;
@@ -585,7 +602,8 @@ abp_status abp_walker_create(abp_ctx *ctx, abp_grid *grid, const abp_walker_desc
   int rsz = fp64 ? 32 : 16;
   // the phased form serves walkers on a shared grid and walkers too large
   // for one shared-memory walker group (FP32, at most one CN)
-  w->big = grid->desc.shared || run_group_bytes(hd, fp64, 32, 0) > 227 * 1024;
+  w->big = grid->desc.shared || run_group_bytes(hd, fp64, 32, 0, false) > 227 * 1024;
+  w->win = !w->big && window_eligible(hd, fp64);
   if (w->big && (fp64 || big_cn_count(hd) > 1)) {
     walker_free(w);
     delete w;
@@ -749,25 +767,33 @@ static abp_status run_common(abp_ctx *ctx, abp_walker *const *walkers, int n, co
     return fail(ABP_ERR_INVALID_ARG, "FP64 coordinate and force buffers must be 32-byte aligned");
   st = set_device(ctx);
   if (st) return st;
-  std::vector<abp_walker *> fw, bw;
-  std::vector<int> fi, bi;
+  // three forms: windowed (k_win), per-step fused (k_run), phased (big)
+  std::vector<abp_walker *> ww, fw, bw;
+  std::vector<int> wi, fi, bi;
   for (int i = 0; i < n; ++i) {
     if (walkers[i]->big) {
       bw.push_back(walkers[i]);
       bi.push_back(i);
+    } else if (walkers[i]->win) {
+      ww.push_back(walkers[i]);
+      wi.push_back(i);
     } else {
       fw.push_back(walkers[i]);
       fi.push_back(i);
     }
   }
-  if (!fw.empty()) {
+  for (int form = 0; form < 2; ++form) {
+    std::vector<abp_walker *> &lw = form ? fw : ww;
+    std::vector<int> &li = form ? fi : wi;
+    if (lw.empty()) continue;
     RunArgs a{};
-    if ((st = sub_table(ctx, fw, fi, &a.table))) return st;
-    if ((st = pick_shape(ctx, fw.data(), (int)fw.size(), fp64, nsteps, &a.G, &a.groups_per_cta, &a.group_bytes,
-                         &a.tile_budget)))
+    if ((st = sub_table(ctx, lw, li, &a.table))) return st;
+    if ((st = pick_shape(ctx, lw.data(), (int)lw.size(), fp64, nsteps, form == 0, &a.G, &a.groups_per_cta,
+                         &a.group_bytes, &a.tile_budget)))
       return st;
-    a.nw = (int)fw.size();
-    a.lean = ctx->tune_lean && !fp64;
+    a.window = form == 0;
+    a.nw = (int)lw.size();
+    a.lean = ctx->tune_lean && !fp64 && form == 1;
     a.coords = coords;
     a.coff = reinterpret_cast<const long long *>(coff);
     a.cstride = cstride;
@@ -1351,7 +1377,7 @@ int srv_launch(abp_server *s, SrvSlot &sl) {
     off += ws[i]->hd.natoms;
   }
   RunArgs a{};
-  int st = pick_shape(s->ctx, ws.data(), n, 0, 1, &a.G, &a.groups_per_cta, &a.group_bytes, &a.tile_budget);
+  int st = pick_shape(s->ctx, ws.data(), n, 0, 1, false, &a.G, &a.groups_per_cta, &a.group_bytes, &a.tile_budget);
   if (st) return st;
   cudaStream_t stream = sl.stream;
   if (cudaMemcpyAsync(sl.d_in, sl.h_in, (size_t)off * 16, cudaMemcpyHostToDevice, stream) != cudaSuccess ||

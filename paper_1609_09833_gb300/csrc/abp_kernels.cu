@@ -805,7 +805,7 @@ __device__ void walker_window(const Grp &g, GroupFixed<Real> *fx, unsigned char 
   }
 }
 
-template <typename Real, bool TILE, int UNR>
+template <typename Real, bool TILE>
 __device__ __forceinline__ void run_body(const RunArgs &a) {
   extern __shared__ __align__(32) unsigned char smem[];
   const int gid = threadIdx.x / a.G;
@@ -824,12 +824,10 @@ __device__ __forceinline__ void run_body(const RunArgs &a) {
   const TableEntry te = a.table[slot];
   copy_desc<Real>(g, &fx->wd, te.wd);
   g.sync();
-  const GroupLayout L = layout_of<Real>(fx, g.nwarps, TILE ? a.tile_budget : 0, true);
+  const GroupLayout L = layout_of<Real>(fx, g.nwarps, TILE ? a.tile_budget : 0, false);
   setup_lists<Real>(g, fx, dyn + L.lists);
   g.sync();
-  if (L.win > 0)
-    walker_window<Real, UNR>(g, fx, dyn, L, a, te.idx);
-  else if (TILE && L.tile_nodes > 0)
+  if (TILE && L.tile_nodes > 0)
     walker_steps<Real, true>(g, fx, dyn, L, a, te.idx);
   else
     walker_steps<Real, false>(g, fx, dyn, L, a, te.idx);
@@ -837,13 +835,41 @@ __device__ __forceinline__ void run_body(const RunArgs &a) {
 
 template <typename Real, bool TILE>
 __global__ void __launch_bounds__(256, 1) k_run(RunArgs a) {
-  run_body<Real, TILE, 8>(a);
+  run_body<Real, TILE>(a);
 }
 
 // The same kernel compiled for two resident 256-thread CTAs per SM (at most
 // 128 registers per thread): more warps to hide latency for batches whose
 // walkers are busy in long CN pair loops. Chosen by ABP_TUNE_LEAN.
-__global__ void __launch_bounds__(256, 2) k_run_lean(RunArgs a) { run_body<float, false, 4>(a); }
+__global__ void __launch_bounds__(256, 2) k_run_lean(RunArgs a) { run_body<float, false>(a); }
+
+// The windowed form (walkers whose CVs are COM distances and dihedrals), in
+// its own kernel: its code alone fills the instruction cache.
+template <typename Real, int UNR>
+__global__ void __launch_bounds__(256, 1) k_win(RunArgs a) {
+  extern __shared__ __align__(32) unsigned char smem[];
+  const int gid = threadIdx.x / a.G;
+  const int slot = blockIdx.x * a.groups_per_cta + gid;
+  if (slot >= a.nw) return;
+  Grp g;
+  g.G = a.G;
+  g.gid = gid;
+  g.t = threadIdx.x - gid * a.G;
+  g.lane = threadIdx.x & 31;
+  g.warp = g.t >> 5;
+  g.nwarps = a.G >> 5;
+  unsigned char *base = smem + (size_t)gid * a.group_bytes;
+  GroupFixed<Real> *fx = reinterpret_cast<GroupFixed<Real> *>(base);
+  unsigned char *dyn = base + fixed_bytes<Real>();
+  const TableEntry te = a.table[slot];
+  copy_desc<Real>(g, &fx->wd, te.wd);
+  g.sync();
+  const GroupLayout L = layout_of<Real>(fx, g.nwarps, 0, true);
+  if (L.win == 0) return;  // the host sends only eligible walkers here
+  setup_lists<Real>(g, fx, dyn + L.lists);
+  g.sync();
+  walker_window<Real, UNR>(g, fx, dyn, L, a, te.idx);
+}
 
 cudaError_t launch_run(const RunArgs &a, int fp64, cudaStream_t st) {
   const int threads = a.G * a.groups_per_cta;
@@ -851,6 +877,18 @@ cudaError_t launch_run(const RunArgs &a, int fp64, cudaStream_t st) {
   const size_t smem = (size_t)a.group_bytes * a.groups_per_cta;
   if (a.nw == 0) return cudaSuccess;
   cudaError_t e;
+  if (a.window) {
+    if (fp64) {
+      e = cudaFuncSetAttribute(k_win<double, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      k_win<double, 8><<<blocks, threads, smem, st>>>(a);
+    } else {
+      e = cudaFuncSetAttribute(k_win<float, 13>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      k_win<float, 13><<<blocks, threads, smem, st>>>(a);
+    }
+    return cudaGetLastError();
+  }
   if (fp64) {
     e = cudaFuncSetAttribute(k_run<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -871,8 +909,12 @@ cudaError_t launch_run(const RunArgs &a, int fp64, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-int run_group_bytes(const WalkerDev &hd, int fp64, int G, int tile_budget) {
-  GroupLayout L = group_layout(hd.natoms, hd.cv, hd.g, hd.R, G / 32, fp64 ? 32 : 16, tile_budget, true);
+bool window_eligible(const WalkerDev &hd, int fp64) {
+  return window_steps(hd.natoms, hd.cv, hd.g.d, fp64 ? 32 : 16) > 0;
+}
+
+int run_group_bytes(const WalkerDev &hd, int fp64, int G, int tile_budget, bool window) {
+  GroupLayout L = group_layout(hd.natoms, hd.cv, hd.g, hd.R, G / 32, fp64 ? 32 : 16, tile_budget, window);
   return align32(group_fixed_bytes(fp64) + L.total);
 }
 

@@ -34,6 +34,7 @@ struct RunArgs {
   int nsteps;
   int tile_budget;     // >0: dynamic shared bytes per group, the rest of which holds a grid tile
   int lean;            // use the 128-register instantiation (FP32, no tile)
+  int window;          // every walker runs in the windowed form (k_win)
   DepositLog log;
   DevCounters *ctr;
 };
@@ -100,7 +101,8 @@ cudaError_t read_hill_heads(const WalkerDev *const *wd_host, int n, double *s3h,
 
 int group_fixed_bytes(int fp64);
 int plain_scratch_bytes(int fp64, const CvDev *cv, int ncv);
-int run_group_bytes(const WalkerDev &hd, int fp64, int G, int tile_budget);
+int run_group_bytes(const WalkerDev &hd, int fp64, int G, int tile_budget, bool window);
+bool window_eligible(const WalkerDev &hd, int fp64);
 cudaError_t launch_run(const RunArgs &a, int fp64, cudaStream_t st);
 cudaError_t launch_plain(const PlainArgs &a, int fp64, cudaStream_t st);
 // Records `msg` as the calling thread's abp_last_error() and returns code.
