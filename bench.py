@@ -676,10 +676,10 @@ def main():
 
     peaks, src = load_peaks()
     achieved = BYTES_PER_WALKER_STEP * NW * C / (kernel_ms / 1e3) / 1e9
-    traffic = captured_traffic("k_run_mb64", NW * C)
+    traffic = captured_traffic("k_win_mb64", NW * C)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                "kernel": "k_run<float>", "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs, copy)"
+                "kernel": "k_win<float> (windowed form)", "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs, copy)"
                 if src == "measured" else "fallback 6.8 TB/s"}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

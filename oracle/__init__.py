@@ -32,7 +32,8 @@ _LIB_PATH = os.path.join(_BUILD_DIR, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-CV_TYPES = {"com_dist": 0, "dihedral": 1, "coord": 2, "pos_x": 3}
+CV_TYPES = {"com_dist": 0, "dihedral": 1, "coord": 2, "pos_x": 3, "rmsd": 4}
+METHODS = {"wt": 0, "mabp": 1}
 FLAG_DEPOSIT, FLAG_OOR, FLAG_SINGULAR, FLAG_BADARG = 1, 2, 4, 8
 MAXCV = 3
 
@@ -51,6 +52,7 @@ class OrCv(C.Structure):
         ("mm", C.c_int),
         ("pbc", C.c_int),
         ("box", C.c_double * 3),
+        ("ref", C.POINTER(C.c_double)),
     ]
 
 
@@ -72,6 +74,11 @@ class OrHill(C.Structure):
         ("gamma", C.c_double),
         ("kT", C.c_double),
         ("stride", C.c_int64),
+        ("method", C.c_int),
+        ("a", C.c_double * 3),
+        ("p", C.c_int),
+        ("b", C.c_double),
+        ("c", C.c_double),
     ]
 
 
@@ -139,6 +146,12 @@ def lib():
             C.POINTER(OrWalker), dp, dp, C.c_int64, C.c_double, C.c_double, C.c_double, dp, dp,
         ]
         L.or_langevin_double_well.restype = C.c_int
+        L.or_compact.argtypes = [C.c_double, C.c_double, C.c_int, dp]
+        L.or_compact.restype = C.c_double
+        L.or_deposit_compact.argtypes = [C.POINTER(OrGrid), C.POINTER(OrHill), dp, dp, C.c_double, ip]
+        L.or_deposit_compact.restype = None
+        L.or_lookup_mabp.argtypes = [C.POINTER(OrGrid), C.POINTER(OrHill), dp, dp, dp, dp]
+        L.or_lookup_mabp.restype = C.c_int
         L.or_num_threads.argtypes = []
         L.or_num_threads.restype = C.c_int
         _lib = L
@@ -173,10 +186,18 @@ class Walker:
             s.g.lo[k] = float(g["lo"][k])
             s.g.hi[k] = float(g["hi"][k])
         s.hill.w = float(hl["w"])
-        for k in range(d):
-            s.hill.sigma[k] = float(hl["sigma"][k])
-        s.hill.cutoff = float(hl["cutoff"])
-        s.hill.gamma = float(hl["gamma"])
+        s.hill.method = METHODS[hl.get("method", "wt")]
+        if s.hill.method == METHODS["mabp"]:
+            for k in range(d):
+                s.hill.a[k] = float(hl["a"][k])
+            s.hill.p = int(hl["p"])
+            s.hill.b = float(hl["b"])
+            s.hill.c = float(hl["c"])
+        else:
+            for k in range(d):
+                s.hill.sigma[k] = float(hl["sigma"][k])
+            s.hill.cutoff = float(hl["cutoff"])
+            s.hill.gamma = float(hl["gamma"])
         s.hill.kT = float(hl["kT"])
         s.hill.stride = int(hl["stride"])
         cvs = spec["cvs"]
@@ -203,6 +224,10 @@ class Walker:
             box = cv.get("box", (0.0, 0.0, 0.0))
             for q in range(3):
                 c.box[q] = float(box[q])
+            if cv["type"] == "rmsd":
+                ref = np.ascontiguousarray(cv["ref"], dtype=np.float64).reshape(len(a), 3)
+                self._keep.append(ref)
+                c.ref = _dptr(ref)
         s.natoms = int(spec["natoms"])
         self.struct = s
         self.d = d
@@ -251,13 +276,34 @@ def height(walker: Walker, Vb: float) -> float:
 
 
 def deposit(walker: Walker, field: np.ndarray, s, h: float):
-    """Deposit one hill of height h at s into field (in place). Returns i_c."""
+    """Deposit one hill of height h at s into field (in place): a Gaussian
+    for a well-tempered walker, a compact hill at the nearest node (scaled by
+    h) for an mABP walker. Returns the centre node."""
     assert field.dtype == np.float64 and field.flags.c_contiguous
     s3 = np.zeros(3)
     s3[: walker.d] = s
     ic = np.zeros(3, dtype=np.int32)
-    lib().or_deposit_hill(C.byref(walker.struct.g), C.byref(walker.struct.hill), _dptr(field), _dptr(s3), float(h), _iptr(ic))
+    fn = lib().or_deposit_compact if walker.struct.hill.method == METHODS["mabp"] else lib().or_deposit_hill
+    fn(C.byref(walker.struct.g), C.byref(walker.struct.hill), _dptr(field), _dptr(s3), float(h), _iptr(ic))
     return ic[: walker.d].copy()
+
+
+def compact(u: float, a: float, p: int):
+    """The one-dimensional compact hill S_a^p(u) and dS/du."""
+    d = C.c_double()
+    v = lib().or_compact(float(u), float(a), int(p), C.byref(d))
+    return v, d.value
+
+
+def lookup_mabp(walker: Walker, field: np.ndarray, s):
+    """mABP bias V and dV/dxi at the nearest node to s. Returns (V, dV, flags)."""
+    s3 = np.zeros(3)
+    s3[: walker.d] = s
+    V = C.c_double()
+    dV = np.zeros(3)
+    fl = lib().or_lookup_mabp(C.byref(walker.struct.g), C.byref(walker.struct.hill), _dptr(field), _dptr(s3),
+                              C.byref(V), _dptr(dV))
+    return V.value, dV[: walker.d].copy(), fl
 
 
 # ---------------------------------------------------------------- replay

@@ -47,6 +47,22 @@
  *     that share one grid all read their heights before any deposit of the
  *     step and their forces after all of them (Jacobi order), deposits being
  *     applied in walker order.
+ *
+ * The mABP method with compact hills (SI "Streamlined bias potential
+ * updates") is the second method a walker may use (or_hill.method):
+ *   a3' at the nearest grid node xi* to s_t, the histograms h and h'_i get
+ *       the product hill S_a^p(xi* - xi) of Eq. (compacthill) and its
+ *       derivative along xi_i (Eq. (Cupdate)), on every node within a of
+ *       xi* per axis, scaled by w (w = 1 and stride 1 is the paper's update
+ *       at every timestep);
+ *   a4' V_b and dV_b/dxi_i from h and h' at xi* by Eq. (apfm) and
+ *       Eq. (btraj-grad) (a look-up, no interpolation), with beta^-1 = kT;
+ * with the conventions: xi* = the node floor(u + 1/2), limited to the grid on
+ * a non-periodic axis (where the gradient along a limited axis is zero); the
+ * stencil half-width is floor(a / D) nodes; the derivative field h'_i holds
+ * dh/dxi_i.
+ * The RMSD CV (SI "Definition of the RMSD") is offset by 0.01 so that it is
+ * never zero: s = (sum_i |x_i - x0_i|^2 / N + 0.01)^(1/2), no fit.
  */
 #include <math.h>
 #include <stdint.h>
@@ -58,7 +74,8 @@
 
 #define OR_MAXCV 3
 
-enum { OR_CV_COM_DIST = 0, OR_CV_DIHEDRAL = 1, OR_CV_COORD = 2, OR_CV_POS_X = 3 };
+enum { OR_CV_COM_DIST = 0, OR_CV_DIHEDRAL = 1, OR_CV_COORD = 2, OR_CV_POS_X = 3, OR_CV_RMSD = 4 };
+enum { OR_METHOD_WT_GAUSS = 0, OR_METHOD_MABP_COMPACT = 1 };
 
 enum {
   OR_FLAG_DEPOSIT = 1,   /* a hill was deposited on this step */
@@ -77,6 +94,7 @@ typedef struct {
   int nn, mm;           /* COORD exponents of (1 - (r/r0)^n) / (1 - (r/r0)^m) */
   int pbc;              /* minimum image on difference vectors */
   double box[3];        /* orthorhombic box edge lengths */
+  const double *ref;    /* RMSD: reference positions x0 of the atoms ia (na x 3) */
 } or_cv;
 
 typedef struct {
@@ -93,6 +111,10 @@ typedef struct {
   double gamma;         /* bias factor */
   double kT;            /* thermal energy */
   int64_t stride;       /* deposit every `stride` MD steps */
+  int method;           /* OR_METHOD_*; the fields below are mABP's */
+  double a[3];          /* compact hill half-width per CV */
+  int p;                /* compact hill shape exponent, >= 1 */
+  double b, c;          /* mABP parameters of Eq. (apfm) */
 } or_hill;
 
 typedef struct {
@@ -127,19 +149,23 @@ long or_grid_nodes(const or_grid *g) {
 }
 
 int or_stencil_halfwidth(const or_grid *g, const or_hill *hl, int k) {
+  if (hl->method == OR_METHOD_MABP_COMPACT) return (int)floor(hl->a[k] / grid_spacing(g, k));
   return (int)ceil(hl->cutoff * hl->sigma[k] / grid_spacing(g, k));
 }
 
 /* Returns 0 if the grid and hill are usable, nonzero otherwise. */
 int or_check(const or_grid *g, const or_hill *hl) {
   if (g->d < 1 || g->d > OR_MAXCV) return 1;
+  const int mabp = hl->method == OR_METHOD_MABP_COMPACT;
+  if (hl->method != OR_METHOD_WT_GAUSS && !mabp) return 6;
+  if (mabp && (hl->p < 1 || !(hl->b > 0 && hl->b < 1) || !(hl->c > 0))) return 7;
   for (int k = 0; k < g->d; ++k) {
     if (g->n[k] < 2 || !(g->hi[k] > g->lo[k])) return 2;
-    if (!(hl->sigma[k] > 0)) return 3;
+    if (mabp ? !(hl->a[k] > 0) : !(hl->sigma[k] > 0)) return 3;
     /* a periodic stencil must not wrap onto itself */
     if (g->periodic[k] && 2 * or_stencil_halfwidth(g, hl, k) + 1 > g->n[k]) return 4;
   }
-  if (!(hl->gamma > 1) || !(hl->kT > 0) || hl->stride < 1) return 5;
+  if ((!mabp && !(hl->gamma > 1)) || !(hl->kT > 0) || hl->stride < 1) return 5;
   return 0;
 }
 
@@ -294,6 +320,22 @@ static int cv_pos_x(const or_cv *c, const double *x, double *s, double *J) {
   return 0;
 }
 
+/* s = (sum_i |x_i - x0_i|^2 / N + 0.01)^(1/2) over the N atoms ia, no fit
+ * (SI "Definition of the RMSD"); ds/dx_i = (x_i - x0_i) / (N s). */
+static int cv_rmsd(const or_cv *c, const double *x, double *s, double *J) {
+  double acc = 0.0;
+  for (int i = 0; i < c->na; ++i)
+    for (int k = 0; k < 3; ++k) {
+      double dx = x[3 * c->ia[i] + k] - c->ref[3 * i + k];
+      acc += dx * dx;
+    }
+  double r = sqrt(acc / c->na + 0.01);
+  *s = r;
+  for (int i = 0; i < c->na; ++i)
+    for (int k = 0; k < 3; ++k) J[3 * c->ia[i] + k] += (x[3 * c->ia[i] + k] - c->ref[3 * i + k]) / (c->na * r);
+  return 0;
+}
+
 /* Evaluate one CV; J (natoms x 3) is overwritten with ds/dx. */
 int or_cv_eval(const or_cv *c, int natoms, const double *x, double *s, double *J) {
   memset(J, 0, sizeof(double) * 3 * (size_t)natoms);
@@ -302,6 +344,7 @@ int or_cv_eval(const or_cv *c, int natoms, const double *x, double *s, double *J
     case OR_CV_DIHEDRAL: return cv_dihedral(c, x, s, J);
     case OR_CV_COORD: return cv_coord(c, x, s, J);
     case OR_CV_POS_X: return cv_pos_x(c, x, s, J);
+    case OR_CV_RMSD: return cv_rmsd(c, x, s, J);
   }
   *s = 0;
   return OR_FLAG_BADARG;
@@ -416,6 +459,117 @@ void or_deposit_hill(const or_grid *g, const or_hill *hl, double *field, const d
 }
 
 /* ------------------------------------------------------------------ */
+/* mABP with compact hills                                              */
+/* ------------------------------------------------------------------ */
+
+/* The compact hill of Eq. (compacthill) along one CV, S = e^p e^(-p/(1-x^2))
+ * for |x| = |u/a| < 1 (written as e^(-p x^2/(1-x^2)), the same number), else
+ * 0; *dSdu receives dS/du. */
+double or_compact(double u, double a, int p, double *dSdu) {
+  double x = u / a;
+  if (!(fabs(x) < 1.0)) {
+    *dSdu = 0.0;
+    return 0.0;
+  }
+  double om = 1.0 - x * x;
+  double S = exp(-p * x * x / om);
+  *dSdu = -2.0 * p * x * S / (a * om * om);
+  return S;
+}
+
+/* Nearest grid node to s along every axis (limited to the grid on a
+ * non-periodic axis, recorded in limited[k]). */
+static void nearest_node(const or_grid *g, const double *s, int *ic, int *limited) {
+  for (int k = 0; k < g->d; ++k) {
+    double D = grid_spacing(g, k);
+    double u = (s[k] - g->lo[k]) / D;
+    limited[k] = 0;
+    if (g->periodic[k]) {
+      u = wrap_u(u, g->n[k]);
+      int i = (int)floor(u + 0.5);
+      ic[k] = i >= g->n[k] ? i - g->n[k] : i;
+    } else {
+      double i = floor(u + 0.5);
+      if (i < 0) { i = 0; limited[k] = 1; }
+      if (i > g->n[k] - 1) { i = g->n[k] - 1; limited[k] = 1; }
+      ic[k] = (int)i;
+    }
+  }
+}
+
+/* Eq. (Cupdate) at the nearest node xi* to s: h += w S(xi* - xi) and
+ * h'_i += w dS(xi* - xi)/dxi_i on every node within a of xi* (per axis),
+ * S the product of the one-dimensional compact hills. */
+void or_deposit_compact(const or_grid *g, const or_hill *hl, double *field, const double *s, double w,
+                        int *ic_out) {
+  int d = g->d, nf = 1 + d;
+  int ic[3] = {0, 0, 0}, R[3] = {0, 0, 0}, lim[3];
+  double D[3] = {1, 1, 1};
+  nearest_node(g, s, ic, lim);
+  for (int k = 0; k < d; ++k) {
+    D[k] = grid_spacing(g, k);
+    R[k] = or_stencil_halfwidth(g, hl, k);
+    ic_out[k] = ic[k];
+  }
+  for (int k = d; k < 3; ++k) ic_out[k] = 0;
+  int span[3] = {1, 1, 1};
+  for (int k = 0; k < d; ++k) span[k] = 2 * R[k] + 1;
+  for (int c2 = 0; c2 < span[2]; ++c2)
+    for (int c1 = 0; c1 < span[1]; ++c1)
+      for (int c0 = 0; c0 < span[0]; ++c0) {
+        int off[3] = {c0 - R[0], c1 - R[1], c2 - R[2]};
+        long node = 0, mul = 1;
+        double S[3] = {1, 1, 1}, dS[3] = {0, 0, 0};
+        int inside = 1;
+        for (int k = 0; k < d; ++k) {
+          int j = ic[k] + off[k];
+          if (g->periodic[k]) {
+            j %= g->n[k];
+            if (j < 0) j += g->n[k];
+          } else if (j < 0 || j >= g->n[k]) {
+            inside = 0;
+            break;
+          }
+          /* u = xi*_k - xi_k, the node's offset from the centre */
+          S[k] = or_compact(-off[k] * D[k], hl->a[k], hl->p, &dS[k]);
+          node += mul * j;
+          mul *= g->n[k];
+        }
+        if (!inside) continue;
+        double prod = S[0] * S[1] * S[2];
+        field[node * nf] += w * prod;
+        for (int k = 0; k < d; ++k) {
+          double other = 1.0;
+          for (int q = 0; q < d; ++q)
+            if (q != k) other *= S[q];
+          /* d S(xi* - xi) / d xi_k = - S'(u_k) * prod of the other axes */
+          field[node * nf + 1 + k] += w * (-dS[k]) * other;
+        }
+      }
+}
+
+/* Eq. (apfm) and Eq. (btraj-grad) at the nearest node to s:
+ *   V = kT b/(1-b) ln(c (1-b) h + 1),  dV/dxi_i = c b kT h'_i / (1 + c (1-b) h).
+ * Returns OR_FLAG_OOR if s left a non-periodic range (that gradient is 0). */
+int or_lookup_mabp(const or_grid *g, const or_hill *hl, const double *field, const double *s, double *V,
+                   double *dV) {
+  int d = g->d, nf = 1 + d, flag = 0;
+  int ic[3] = {0, 0, 0}, lim[3] = {0, 0, 0};
+  nearest_node(g, s, ic, lim);
+  long node = 0, mul = 1;
+  for (int k = 0; k < d; ++k) {
+    node += mul * ic[k];
+    mul *= g->n[k];
+    if (lim[k]) flag = OR_FLAG_OOR;
+  }
+  double h = field[node * nf];
+  double den = 1.0 + hl->c * (1.0 - hl->b) * h;
+  *V = hl->kT * hl->b / (1.0 - hl->b) * log(den);
+  for (int k = 0; k < d; ++k) dV[k] = lim[k] ? 0.0 : hl->c * hl->b * hl->kT * field[node * nf + 1 + k] / den;
+  return flag;
+}
+
+/* ------------------------------------------------------------------ */
 /* one MD step for a batch of walkers                                   */
 /* ------------------------------------------------------------------ */
 
@@ -446,10 +600,14 @@ int or_batch_step(int nw, const or_walker *wk, double *const *fields, const doub
   }
 
   /* a2: heights of this step's hills, all from the grids as they were
-   * before any deposit of this step */
+   * before any deposit of this step (mABP hills have height w) */
   double *h = (double *)calloc((size_t)nw, sizeof(double));
   for (int w = 0; w < nw; ++w) {
     if (step % wk[w].hill.stride != 0) continue;
+    if (wk[w].hill.method == OR_METHOD_MABP_COMPACT) {
+      h[w] = wk[w].hill.w;
+      continue;
+    }
     double Vb, g3[3];
     flags[w] |= or_interp(&wk[w].g, fields[w], &s[3 * w], &Vb, g3);
     h[w] = or_height(&wk[w].hill, Vb);
@@ -462,7 +620,10 @@ int or_batch_step(int nw, const or_walker *wk, double *const *fields, const doub
     dep[w].walker = w;
     dep[w].height = h[w];
     for (int k = 0; k < 3; ++k) dep[w].s[k] = s[3 * w + k];
-    or_deposit_hill(&wk[w].g, &wk[w].hill, fields[w], &s[3 * w], h[w], dep[w].ic);
+    if (wk[w].hill.method == OR_METHOD_MABP_COMPACT)
+      or_deposit_compact(&wk[w].g, &wk[w].hill, fields[w], &s[3 * w], h[w], dep[w].ic);
+    else
+      or_deposit_hill(&wk[w].g, &wk[w].hill, fields[w], &s[3 * w], h[w], dep[w].ic);
     flags[w] |= OR_FLAG_DEPOSIT;
   }
 
@@ -471,7 +632,10 @@ int or_batch_step(int nw, const or_walker *wk, double *const *fields, const doub
   for (int w = 0; w < nw; ++w) {
     int d = wk[w].g.d;
     double g3[3] = {0, 0, 0};
-    flags[w] |= or_interp(&wk[w].g, fields[w], &s[3 * w], &V[w], g3);
+    if (wk[w].hill.method == OR_METHOD_MABP_COMPACT)
+      flags[w] |= or_lookup_mabp(&wk[w].g, &wk[w].hill, fields[w], &s[3 * w], &V[w], g3);
+    else
+      flags[w] |= or_interp(&wk[w].g, fields[w], &s[3 * w], &V[w], g3);
     for (int k = 0; k < 3; ++k) dV[3 * w + k] = g3[k];
     double *Fw = F[w];
     for (int a = 0; a < 3 * wk[w].natoms; ++a) {
@@ -538,7 +702,7 @@ int or_run(int nw, const or_walker *wk, double *const *fields, const double *fra
 }
 
 /* ------------------------------------------------------------------ */
-/* closed-loop driver (used only to check well-tempered convergence)    */
+/* closed-loop driver (used only to check the converged bias)           */
 /* ------------------------------------------------------------------ */
 
 /* Overdamped Langevin for one walker under U(s) = kw (s^2 - 1)^2 on its

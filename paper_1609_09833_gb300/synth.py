@@ -94,6 +94,14 @@ def hill(w, sigma, stride, gamma, kT=2.5, cutoff=4.0):
             "kT": float(kT), "stride": int(stride)}
 
 
+def mabp_hill(a, p, b, c, kT=2.5, stride=1, w=1.0):
+    """Hill parameters of an mABP walker with compact S_a^p hills: half-width a
+    per CV, shape exponent p, bias parameters b, c; hills of height w every
+    `stride` steps."""
+    return {"method": "mabp", "a": list(map(float, a)), "p": int(p), "b": float(b), "c": float(c),
+            "kT": float(kT), "stride": int(stride), "w": float(w)}
+
+
 def bins(g: dict, k: int, nbins: float) -> float:
     """Width of `nbins` grid spacings along axis k (the node convention)."""
     n = g["n"][k]
