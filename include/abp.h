@@ -65,6 +65,15 @@ typedef int abp_status;
 #define ABP_CV_COM_DIST 0 /* |R_B - R_A|, R_G the mass-weighted centre of group G */
 #define ABP_CV_DIHEDRAL 1 /* IUPAC dihedral of idx_a[0..3], in [-pi, pi] */
 #define ABP_CV_COORD 2    /* sum over A x B of (1 - (r/r0)^n) / (1 - (r/r0)^m); n = 6, m = 12 */
+#define ABP_CV_RMSD 3     /* (sum_i |x_i - x0_i|^2 / n_a + 0.01)^(1/2) over idx_a, no fit (SI "Definition of the
+                             RMSD"); n_a <= 4; runs in the batched (windowed) form only */
+
+/* Biasing methods (abp_walker_desc.method). */
+#define ABP_METHOD_WT 0   /* well-tempered Gaussian hills, multilinear look-up (the default) */
+#define ABP_METHOD_MABP 1 /* mABP with compact S_a^p hills at the nearest node (SI "Streamlined bias
+                             potential updates"): the grid holds the histograms h and dh/dxi_k of
+                             Eqs. (histos)/(Cupdate); the force uses Eq. (btraj-grad) at the nearest
+                             node; not available to walkers on a shared grid */
 
 /* Grid precision. */
 #define ABP_PREC_FP32_COMP 0 /* FP32 fields with a two-sum compensation term per field */
@@ -117,18 +126,24 @@ typedef struct {
   int nn, mm;            /* COORD exponents; this build supports nn = 6, mm = 12 */
   int pbc;               /* minimum image on difference vectors (orthorhombic box) */
   double box[3];
+  const double *ref;     /* RMSD: reference positions of the atoms idx_a, 3 n_a values (host) */
 } abp_cv_desc;
 
-/* A walker: its atoms, one CV per grid axis and its well-tempered hills. */
+/* A walker: its atoms, one CV per grid axis and its hills. A zeroed tail
+ * (method = ABP_METHOD_WT) describes a well-tempered walker. */
 typedef struct {
   int natoms;
   abp_cv_desc cv[3];     /* cv[k] drives grid axis k; the grid's ncv are used */
-  double w;              /* initial hill height (kJ/mol) */
-  double sigma[3];       /* Gaussian width per CV */
-  double cutoff;         /* half-width R_k = ceil(cutoff sigma_k / D_k) of the stencil box, in sigma */
-  double gamma;          /* bias factor (> 1) */
-  double kT;             /* thermal energy (kJ/mol) */
+  double w;              /* WT: initial hill height (kJ/mol); mABP: the height of every hill (1 in the paper) */
+  double sigma[3];       /* WT: Gaussian width per CV */
+  double cutoff;         /* WT: half-width R_k = ceil(cutoff sigma_k / D_k) of the stencil box, in sigma */
+  double gamma;          /* WT: bias factor (> 1) */
+  double kT;             /* thermal energy (kJ/mol); beta^-1 of Eq. (apfm) */
   int64_t stride;        /* deposit when step % stride == 0 */
+  int method;            /* ABP_METHOD_* */
+  double a[3];           /* mABP: compact hill half-width per CV (CV units); stencil half-width floor(a_k / D_k) */
+  int p;                 /* mABP: compact hill shape exponent, >= 1 (Eq. (compacthill)) */
+  double b, c;           /* mABP: the parameters of Eq. (apfm), 0 < b < 1, c > 0 */
 } abp_walker_desc;
 
 /* One deposited hill (the deposit log). */

@@ -23,7 +23,8 @@ ERRORS = {-1: "INVALID_ARG", -2: "CUDA", -3: "OOM", -4: "ADMISSION", -5: "NONFIN
           -7: "UNSUPPORTED"}
 ABP_ERR_INVALID_ARG, ABP_ERR_CUDA, ABP_ERR_OOM, ABP_ERR_ADMISSION = -1, -2, -3, -4
 ABP_ERR_NONFINITE, ABP_ERR_TIMEOUT, ABP_ERR_UNSUPPORTED = -5, -6, -7
-CV_TYPES = {"com_dist": 0, "dihedral": 1, "coord": 2}
+CV_TYPES = {"com_dist": 0, "dihedral": 1, "coord": 2, "rmsd": 3}
+ABP_METHOD_WT, ABP_METHOD_MABP = 0, 1
 ABP_PREC_FP32_COMP, ABP_PREC_FP64 = 0, 1
 ABP_F32, ABP_F64 = 0, 1
 ABP_FORCES_ACCUMULATE, ABP_FORCES_OVERWRITE = 0, 1
@@ -45,12 +46,13 @@ class CvDesc(C.Structure):
     _fields_ = [("type", C.c_int), ("n_a", C.c_int), ("n_b", C.c_int), ("idx_a", C.POINTER(C.c_int32)),
                 ("idx_b", C.POINTER(C.c_int32)), ("mass_a", C.POINTER(C.c_double)),
                 ("mass_b", C.POINTER(C.c_double)), ("r0", C.c_double), ("nn", C.c_int), ("mm", C.c_int),
-                ("pbc", C.c_int), ("box", C.c_double * 3)]
+                ("pbc", C.c_int), ("box", C.c_double * 3), ("ref", C.POINTER(C.c_double))]
 
 
 class WalkerDesc(C.Structure):
     _fields_ = [("natoms", C.c_int), ("cv", CvDesc * 3), ("w", C.c_double), ("sigma", C.c_double * 3),
-                ("cutoff", C.c_double), ("gamma", C.c_double), ("kT", C.c_double), ("stride", C.c_int64)]
+                ("cutoff", C.c_double), ("gamma", C.c_double), ("kT", C.c_double), ("stride", C.c_int64),
+                ("method", C.c_int), ("a", C.c_double * 3), ("p", C.c_int), ("b", C.c_double), ("c", C.c_double)]
 
 
 class DepositRec(C.Structure):
@@ -426,14 +428,26 @@ def walker_desc(spec: dict):
         box = cv.get("box", (0.0, 0.0, 0.0))
         for q in range(3):
             c.box[q] = float(box[q])
+        if cv["type"] == "rmsd":
+            ref = np.ascontiguousarray(cv["ref"], dtype=np.float64).reshape(-1)
+            keep.append(ref)
+            c.ref = ref.ctypes.data_as(C.POINTER(C.c_double))
     hl = spec["hill"]
     d.w = float(hl["w"])
-    for k, s in enumerate(hl["sigma"]):
-        d.sigma[k] = float(s)
-    d.cutoff = float(hl["cutoff"])
-    d.gamma = float(hl["gamma"])
     d.kT = float(hl["kT"])
     d.stride = int(hl["stride"])
+    if hl.get("method", "wt") == "mabp":
+        d.method = ABP_METHOD_MABP
+        for k, a in enumerate(hl["a"]):
+            d.a[k] = float(a)
+        d.p = int(hl["p"])
+        d.b = float(hl["b"])
+        d.c = float(hl["c"])
+    else:
+        for k, s in enumerate(hl["sigma"]):
+            d.sigma[k] = float(s)
+        d.cutoff = float(hl["cutoff"])
+        d.gamma = float(hl["gamma"])
     return d, keep
 
 

@@ -92,6 +92,7 @@ struct abp_walker {
   bool has_cn = false;
   bool big = false;    // runs in the phased form (shared grid, or too large for a walker group)
   bool win = false;    // runs in the windowed form of the fused kernel (COM distance / dihedral CVs)
+  bool has_rmsd = false;
   long long cost = 0;  // rough work estimate used to order batched launches
 };
 
@@ -490,6 +491,13 @@ abp_status build_cv(abp_walker *w, const abp_cv_desc &c, int k, int natoms, CvDe
       if (c.n_a != 4) return fail(ABP_ERR_INVALID_ARG, "CV %d: a dihedral needs 4 atoms", k);
       cv.nb = 0;
       break;
+    case ABP_CV_RMSD:
+      if (c.n_a < 1 || c.n_a > 4) return fail(ABP_ERR_UNSUPPORTED, "CV %d: this build takes RMSDs of 1 to 4 atoms", k);
+      if (!c.ref) return fail(ABP_ERR_INVALID_ARG, "CV %d: an RMSD needs reference positions", k);
+      for (int i = 0; i < 3 * c.n_a; ++i)
+        if (!std::isfinite(c.ref[i])) return fail(ABP_ERR_INVALID_ARG, "CV %d: reference positions must be finite", k);
+      cv.nb = 0;
+      break;
     case ABP_CV_COORD:
       if (c.n_a < 1 || c.n_b < 1) return fail(ABP_ERR_INVALID_ARG, "CV %d: CN groups must be non-empty", k);
       if (c.nn != 6 || c.mm != 12)
@@ -513,6 +521,14 @@ abp_status build_cv(abp_walker *w, const abp_cv_desc &c, int k, int natoms, CvDe
   cv.ia = static_cast<const int32_t *>(p);
   if ((st = upload(w, cv.nb ? c.idx_b : nullptr, sizeof(int32_t) * cv.nb, &p))) return st;
   cv.ib = static_cast<const int32_t *>(p);
+  if (c.type == ABP_CV_RMSD) {
+    std::vector<float> rf(3 * cv.na);
+    for (int i = 0; i < 3 * cv.na; ++i) rf[i] = (float)c.ref[i];
+    if ((st = upload(w, rf.data(), sizeof(float) * rf.size(), &p))) return st;
+    cv.ref = static_cast<const float *>(p);
+    if ((st = upload(w, c.ref, sizeof(double) * 3 * cv.na, &p))) return st;
+    cv.ref64 = static_cast<const double *>(p);
+  }
   if (c.type == ABP_CV_COM_DIST) {
     // weights m_i / M_group, computed once in FP64
     for (int grp = 0; grp < 2; ++grp) {
@@ -548,9 +564,11 @@ abp_status abp_walker_create(abp_ctx *ctx, abp_grid *grid, const abp_walker_desc
   *out = nullptr;
   if (grid->ctx != ctx) return fail(ABP_ERR_INVALID_ARG, "grid belongs to another context");
   if (d->natoms < 1) return fail(ABP_ERR_INVALID_ARG, "natoms must be >= 1");
-  if (!(d->gamma > 1) || !(d->kT > 0) || d->stride < 1 || !(d->w >= 0) || !std::isfinite(d->w) ||
-      !std::isfinite(d->gamma) || !std::isfinite(d->kT) || !(d->cutoff > 0))
+  if (d->method == ABP_METHOD_WT &&
+      (!(d->gamma > 1) || !(d->kT > 0) || d->stride < 1 || !(d->w >= 0) || !std::isfinite(d->w) ||
+       !std::isfinite(d->gamma) || !std::isfinite(d->kT) || !(d->cutoff > 0)))
     return fail(ABP_ERR_INVALID_ARG, "need gamma > 1, kT > 0, w >= 0, cutoff > 0, stride >= 1");
+  if (d->stride < 1) return fail(ABP_ERR_INVALID_ARG, "stride must be >= 1");
   std::lock_guard<std::mutex> lk(ctx->mu);
   abp_status st = set_device(ctx);
   if (st) return st;
@@ -563,15 +581,32 @@ abp_status abp_walker_create(abp_ctx *ctx, abp_grid *grid, const abp_walker_desc
   hd.natoms = d->natoms;
   const int ncv = grid->desc.ncv;
   const int fp64 = grid->desc.precision == ABP_PREC_FP64;
+  const bool mabp = d->method == ABP_METHOD_MABP;
+  if (d->method != ABP_METHOD_WT && !mabp) {
+    delete w;
+    return fail(ABP_ERR_INVALID_ARG, "unknown method %d", d->method);
+  }
+  if (mabp && (d->p < 1 || !(d->b > 0 && d->b < 1) || !(d->c > 0) || !std::isfinite(d->c) || !(d->kT > 0) ||
+               !(d->w > 0) || !std::isfinite(d->w))) {
+    delete w;
+    return fail(ABP_ERR_INVALID_ARG, "mABP needs p >= 1, 0 < b < 1, c > 0, kT > 0 and w > 0");
+  }
+  if (mabp && grid->desc.shared) {
+    delete w;
+    return fail(ABP_ERR_UNSUPPORTED, "mABP walkers need their own grid");
+  }
+  hd.method = d->method;
   long long stencil = 1;
   for (int k = 0; k < ncv; ++k) {
-    double sig = d->sigma[k];
+    double sig = mabp ? d->a[k] : d->sigma[k];
     if (!(sig > 0) || !std::isfinite(sig)) {
       delete w;
-      return fail(ABP_ERR_INVALID_ARG, "sigma[%d] must be > 0", k);
+      return fail(ABP_ERR_INVALID_ARG, mabp ? "a[%d] must be > 0" : "sigma[%d] must be > 0", k);
     }
     double D = spacing(grid->desc, k);
-    double Rd = std::ceil(d->cutoff * sig / D);
+    // stencil half-width: the Gaussian's cutoff box, or the nodes within a of
+    // the compact hill's centre node
+    double Rd = mabp ? std::floor(sig / D) : std::ceil(d->cutoff * sig / D);
     if (Rd > kRMax) {
       delete w;
       return fail(ABP_ERR_UNSUPPORTED, "stencil half-width %g on axis %d exceeds %d nodes", Rd, k, kRMax);
@@ -585,11 +620,18 @@ abp_status abp_walker_create(abp_ctx *ctx, abp_grid *grid, const abp_walker_desc
     hd.sigma[k] = sig;
     hd.inv2s2[k] = 1.0 / (2.0 * sig * sig);
     hd.invs2[k] = 1.0 / (sig * sig);
+    hd.a[k] = mabp ? sig : 0.0;
     stencil *= 2 * hd.R[k] + 1;
   }
   hd.w = d->w;
-  hd.inv_dT = 1.0 / ((d->gamma - 1.0) * d->kT);
+  hd.inv_dT = mabp ? 0.0 : 1.0 / ((d->gamma - 1.0) * d->kT);
   hd.stride = d->stride;
+  if (mabp) {
+    hd.p = d->p;
+    hd.mabp_k = d->kT * d->b / (1.0 - d->b);
+    hd.mabp_g = d->c * d->b * d->kT;
+    hd.mabp_h = d->c * (1.0 - d->b);
+  }
   for (int k = 0; k < ncv; ++k) {
     st = build_cv(w, d->cv[k], k, d->natoms, &hd.cv[k]);
     if (st) {
@@ -598,12 +640,23 @@ abp_status abp_walker_create(abp_ctx *ctx, abp_grid *grid, const abp_walker_desc
       return st;
     }
     if (d->cv[k].type == ABP_CV_COORD) w->has_cn = true;
+    if (d->cv[k].type == ABP_CV_RMSD) w->has_rmsd = true;
   }
   int rsz = fp64 ? 32 : 16;
   // the phased form serves walkers on a shared grid and walkers too large
   // for one shared-memory walker group (FP32, at most one CN)
   w->big = grid->desc.shared || run_group_bytes(hd, fp64, 32, 0, false) > 227 * 1024;
   w->win = !w->big && window_eligible(hd, fp64);
+  if ((mabp || w->has_rmsd) && w->big) {
+    walker_free(w);
+    delete w;
+    return fail(ABP_ERR_UNSUPPORTED, "mABP and RMSD walkers run in the fused form: own grid, one SM's shared memory");
+  }
+  if (w->has_rmsd && !w->win) {
+    walker_free(w);
+    delete w;
+    return fail(ABP_ERR_UNSUPPORTED, "RMSD walkers run in the windowed form (COM distance, dihedral and RMSD CVs)");
+  }
   if (w->big && (fp64 || big_cn_count(hd) > 1)) {
     walker_free(w);
     delete w;
@@ -876,8 +929,9 @@ abp_status abp_step_plain(abp_ctx *ctx, abp_walker *const *walkers, int n, const
   if (st) return st;
   if (shared) return fail(ABP_ERR_UNSUPPORTED, "the plain form takes walkers with their own grids");
   for (int i = 0; i < n; ++i)
-    if (walkers[i]->big)
-      return fail(ABP_ERR_UNSUPPORTED, "walker %d runs only in the batched form (shared grid or too many atoms)", i);
+    if (walkers[i]->big || walkers[i]->has_rmsd)
+      return fail(ABP_ERR_UNSUPPORTED, "walker %d runs only in the batched form (shared grid, too many atoms or RMSD)",
+                  i);
   if (n == 0) return ABP_OK;
   if (step < 0) return fail(ABP_ERR_INVALID_ARG, "step must be >= 0");
   if (!coords_dev || !coord_offsets_dev || !forces_dev || !force_offsets_dev)
@@ -1587,10 +1641,10 @@ abp_status abp_server_admit(abp_server *s, const abp_grid_desc *g, const abp_wal
     abp_grid_destroy(grid);
     return fail(st, "%s", msg.c_str());
   }
-  if (walker->big) {
+  if (walker->big || walker->has_rmsd) {
     abp_walker_destroy(walker);
     abp_grid_destroy(grid);
-    return fail(ABP_ERR_UNSUPPORTED, "the server serves walkers that fit one walker group");
+    return fail(ABP_ERR_UNSUPPORTED, "the server serves walkers that fit one walker group (no RMSD CVs)");
   }
   std::lock_guard<std::mutex> lk(s->mu);
   int64_t id = s->next_sim++;

@@ -605,14 +605,51 @@ __device__ __forceinline__ AxisSt<Real> axis_eval(const GridDev &gd, int R, int 
   return r;
 }
 
+// mABP: the nearest node to s on axis k (from the deposit-step split of u),
+// the centre of both the hill and the look-up; wrapped on a periodic axis,
+// limited to the grid on a non-periodic one (a limited axis reports
+// `clamped` and gets a zero gradient). The hill is centred on the node, so
+// its offset within the node is 0.
+template <typename Real>
+__device__ __forceinline__ void mabp_node(const GridDev &gd, int k, AxisSt<Real> &r) {
+  const int n = gd.n[k];
+  int c = r.da + r.dc, lim = 0;
+  if (gd.periodic[k]) {
+    c %= n;
+    if (c < 0) c += n;
+  } else if (c < 0) {
+    c = 0;
+    lim = 1;
+  } else if (c > n - 1) {
+    c = n - 1;
+    lim = 1;
+  }
+  r.da = c;
+  r.dc = 0;
+  r.df = 0;
+  r.ic_log = c;
+  r.i0 = r.i1 = c;
+  r.f = 0;
+  r.clamped = lim;
+}
+
+// Axis state for the walker's method (mABP needs the nearest node every step).
+template <typename Real>
+__device__ __forceinline__ AxisSt<Real> axis_state(const WalkerDev &wd, int k, Real sh, Real sl, bool dep) {
+  const bool mabp = wd.method == ABP_METHOD_MABP;
+  AxisSt<Real> r = axis_eval<Real>(wd.g, wd.R[k], k, sh, sl, dep || mabp);
+  if (mabp) mabp_node<Real>(wd.g, k, r);
+  return r;
+}
+
 // The group's axis state, one thread per axis (k = g.t < d).
 template <typename Real>
 __device__ __forceinline__ void axis_setup(GroupFixed<Real> *fx, int k, bool dep) {
-  AxisSt<Real> r = axis_eval<Real>(fx->wd.g, fx->wd.R[k], k, fx->sh[k], fx->sl[k], dep);
+  AxisSt<Real> r = axis_state<Real>(fx->wd, k, fx->sh[k], fx->sl[k], dep);
   fx->i0[k] = r.i0;
   fx->i1[k] = r.i1;
   fx->f[k] = r.f;
-  if (dep) {
+  if (dep || fx->wd.method == ABP_METHOD_MABP) {
     fx->da[k] = r.da;
     fx->df[k] = r.df;
     fx->dc[k] = r.dc;
@@ -789,6 +826,24 @@ __device__ __forceinline__ double height_interp(const GroupFixed<Real> *fx, cons
   return acc;
 }
 
+// mABP's compact hill (Eq. (compacthill)) at the node-to-centre distance
+// `dist` along one CV, S = e^p e^(-p / (1 - x^2)) = e^(-p x^2 / (1 - x^2)),
+// x = dist / a (0 for |x| >= 1), and the factor that turns the deposit's S
+// into its derivative along the grid coordinate:
+// d S(xi* - xi) / d xi = S (-2 p dist / (a^2 (1 - x^2)^2)).
+template <typename Real>
+__device__ __forceinline__ void compact_factors(Real dist, Real a, int p, Real &S, Real &Dfac) {
+  const Real x = dist / a;
+  if (!(fabs(x) < (Real)1)) {
+    S = 0;
+    Dfac = 0;
+    return;
+  }
+  const Real om = (Real)1 - x * x;
+  S = exp(-(Real)p * x * x / om);
+  Dfac = (Real)-2 * (Real)p * dist / (a * a * om * om);
+}
+
 // a3 (part 1): per-axis factor tables of the stencil box around s: node index
 // j = i_c - R + o (or -1 outside a non-periodic axis), G_k = exp(-d^2 / 2 sigma^2)
 // and -d / sigma^2, d = (j - u) D the node-to-centre distance, formed as
@@ -797,11 +852,13 @@ template <typename Real>
 __device__ void build_tables(const Grp &g, GroupFixed<Real> *fx) {
   const WalkerDev &wd = fx->wd;
   const GridDev &gd = wd.g;
+  const bool mabp = wd.method == ABP_METHOD_MABP;
   for (int k = 0; k < gd.d; ++k) {
     const int R = wd.R[k], span = 2 * R + 1, n = gd.n[k];
     const int a = fx->da[k], c = fx->dc[k];
     const Real f = fx->df[k], D = (Real)gd.D[k];
     const Real i2 = (Real)wd.inv2s2[k], is2 = (Real)wd.invs2[k];
+    const Real ak = (Real)wd.a[k];
     for (int o = g.t; o < span; o += g.G) {
       int rel = c - R + o;
       int j = a + rel;
@@ -814,8 +871,12 @@ __device__ void build_tables(const Grp &g, GroupFixed<Real> *fx) {
         jj = -1;
       }
       fx->tabJ[k][o] = jj;
-      fx->tabG[k][o] = exp(-dist * dist * i2);
-      fx->tabD[k][o] = -dist * is2;
+      if (mabp) {
+        compact_factors<Real>(dist, ak, wd.p, fx->tabG[k][o], fx->tabD[k][o]);
+      } else {
+        fx->tabG[k][o] = exp(-dist * dist * i2);
+        fx->tabD[k][o] = -dist * is2;
+      }
     }
   }
 }
@@ -974,8 +1035,21 @@ __device__ void deposit_stencil(const Grp &g, GroupFixed<Real> *fx, const GroupL
 
 // ---------------------------------------------------------------- a4 + a5
 
+// mABP: the bias and its gradient from the histograms at the nearest node,
+// V = kT b/(1-b) ln(c (1-b) h + 1) (Eq. (apfm)) and
+// dV/dxi_k = c b kT h'_k / (1 + c (1-b) h) (Eq. (btraj-grad)).
+template <typename Real>
+__device__ __forceinline__ void mabp_bias(const WalkerDev &wd, const Real *acc, Real &V, Real *dv) {
+  const Real hh = acc[0], ch = (Real)wd.mabp_h * hh;
+  V = (Real)wd.mabp_k * log1p(ch);
+  const Real den = (Real)1 + ch;
+  for (int k = 0; k < wd.g.d; ++k) dv[k] = (Real)wd.mabp_g * acc[1 + k] / den;
+}
+
 // a4: V and dV/ds_k at s after the deposit, by warp 0's first 2^d lanes,
 // combined with a fixed xor-butterfly; a clamped axis gets a zero gradient.
+// (For mABP the corners all sit on the nearest node with weight 1 on the
+// first, which yields that node's histograms, turned into the bias.)
 template <typename Real, bool TILE>
 __device__ void interp_step(const Grp &g, GroupFixed<Real> *fx, const GroupLayout &L, const unsigned char *tile) {
   const GridDev &gd = fx->wd.g;
@@ -991,6 +1065,12 @@ __device__ void interp_step(const Grp &g, GroupFixed<Real> *fx, const GroupLayou
     for (int q = 0; q < 4; ++q)
       for (int o = 1; o < 8; o <<= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
     if (g.lane == 0) {
+      if (fx->wd.method == ABP_METHOD_MABP) {
+        Real V, dvm[3];
+        mabp_bias<Real>(fx->wd, acc, V, dvm);
+        acc[0] = V;
+        for (int k = 0; k < gd.d; ++k) acc[1 + k] = dvm[k];
+      }
       fx->V = acc[0];
       for (int k = 0; k < gd.d; ++k) {
         Real dv = ((fx->clamped >> k) & 1) ? (Real)0 : acc[1 + k];

@@ -22,6 +22,8 @@ struct CvDev {
   const float *wa, *wb;        // COM weights m_i / M_group (FP32 walkers)
   const double *wa64, *wb64;   // COM weights (FP64 walkers)
   double inv_r0sq;             // COORD: 1 / r0^2
+  const float *ref;            // RMSD: reference positions (3 per atom of ia), FP32 walkers
+  const double *ref64;         //       and FP64 walkers
   int pbc;
   double box[3];
   double inv_box[3];
@@ -75,6 +77,12 @@ struct WalkerDev {
   double w;
   double inv_dT;     // 1 / ((gamma - 1) kT)
   long long stride;
+  int method;        // ABP_METHOD_*
+  int p;             // mABP: compact hill exponent
+  double a[3];       // mABP: compact hill half-width per CV
+  double mabp_k;     // mABP: kT b / (1 - b)   (Eq. (apfm): V = mabp_k ln(mabp_h h + 1))
+  double mabp_g;     // mABP: c b kT           (Eq. (btraj-grad): dV = mabp_g h' / (1 + mabp_h h))
+  double mabp_h;     // mABP: c (1 - b)
   void *fbuf;        // library-owned force records (abp_step -> abp_forces)
   void *jscratch;    // library-owned Jacobian scratch (plain form)
   WalkerState *state;
@@ -101,7 +109,7 @@ __host__ __device__ inline int align32(int x) { return (x + 31) & ~31; }
 template <typename Real>
 struct StepRec {
   Real s[kMaxCv];         // CV values
-  Real jac[kMaxCv][12];   // COM distance: unit separation (3); dihedral: gradient (4 x 3)
+  Real jac[kMaxCv][12];   // COM distance: unit separation (3); dihedral, RMSD: gradient (4 x 3)
   Real f[kMaxCv];         // interpolation weight of i1
   Real df[kMaxCv];        // deposit: u - da
   Real V;                 // V_b(s) after the step's deposits
@@ -127,13 +135,16 @@ constexpr int kAtomTerms = 2 * kMaxCv;  // per atom: up to 2 list entries per CV
 constexpr int kWinBytes = 64 * 1024;    // its coordinate double buffer, at most
 
 // Steps per window for a walker in the windowed form (0: not eligible). The
-// form takes walkers whose CVs are all COM distances or dihedrals (one thread
-// evaluates a step's CVs); the window's coordinates are double buffered in
+// form takes walkers whose CVs are all COM distances, dihedrals or RMSDs of at
+// most 4 atoms (one thread evaluates a step's CVs, and a step's Jacobian
+// factors fit its record); the window's coordinates are double buffered in
 // rows of natoms | 1 records (an odd row stride keeps the threads of a warp,
 // one row each, on distinct banks).
 __host__ __device__ inline int window_steps(int natoms, const CvDev *cv, int d, int rsz) {
   for (int k = 0; k < d; ++k)
-    if (cv[k].type != ABP_CV_COM_DIST && cv[k].type != ABP_CV_DIHEDRAL) return 0;
+    if (cv[k].type != ABP_CV_COM_DIST && cv[k].type != ABP_CV_DIHEDRAL &&
+        !(cv[k].type == ABP_CV_RMSD && cv[k].na <= 4))
+      return 0;
   const long long row = (long long)(natoms | 1) * rsz;
   for (int W = kWinMax; W >= 4; W >>= 1)
     if (2 * W * row <= kWinBytes) return W;

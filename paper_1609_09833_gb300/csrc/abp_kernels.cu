@@ -107,9 +107,11 @@ __device__ void deposit_step(const Grp &g, GroupFixed<Real> *fx, const GroupLayo
   const WalkerDev &wd = fx->wd;
   build_tables<Real>(g, fx);
   if (g.warp == 0) {
-    double V0 = height_interp<Real, TILE>(fx, L, tile, g.lane);
+    // mABP hills have the fixed height w; WT hills the well-tempered height
+    const bool mabp = wd.method == ABP_METHOD_MABP;
+    double V0 = mabp ? 0.0 : height_interp<Real, TILE>(fx, L, tile, g.lane);
     if (g.lane == 0) {
-      double h = wd.w * exp(-V0 * wd.inv_dT);
+      double h = mabp ? wd.w : wd.w * exp(-V0 * wd.inv_dT);
       fx->hf = (Real)h;
       fx->flags |= ABP_WFLAG_DEPOSIT;
       if (log.rec) {
@@ -366,6 +368,13 @@ __device__ __forceinline__ void interp_one(const WalkerDev &wd, StepRec<Real> &s
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc[q] += w[c] * v[c][q];
     }
+  if (wd.method == ABP_METHOD_MABP) {  // the nearest node's histograms (weight 1 on corner 0)
+    Real V, dvm[3] = {0, 0, 0};
+    mabp_bias<Real>(wd, acc, V, dvm);
+    acc[0] = V;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) acc[1 + k] = dvm[k];
+  }
   st.V = acc[0];
 #pragma unroll
   for (int k = 0; k < 3; ++k)
@@ -376,6 +385,37 @@ __device__ __forceinline__ void interp_one(const WalkerDev &wd, StepRec<Real> &s
       const int nj = wd.cv[k].type == ABP_CV_COM_DIST ? 3 : 12;
       for (int q = 0; q < nj; ++q) st.jac[k][q] *= dv;
     }
+}
+
+// RMSD of one step by one thread (SI "Definition of the RMSD"):
+// s = (sum_i |x_i - x0_i|^2 / N + 0.01)^(1/2), no fit, and ds/dx_i =
+// (x_i - x0_i) / (N s) for the N <= 4 atoms into J[3 i ..].
+template <typename Real>
+__device__ __forceinline__ int rmsd_thread(const CvDev &c, const int32_t *ia, const typename Rec4<Real>::T *x,
+                                           Real &s, Real *J) {
+  const Real *ref;
+  if constexpr (sizeof(Real) == 4)
+    ref = c.ref;
+  else
+    ref = c.ref64;
+  Real dx[4][3], acc = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    if (i < c.na) {
+      const auto p = x[ia[i]];
+      dx[i][0] = p.x - ref[3 * i];
+      dx[i][1] = p.y - ref[3 * i + 1];
+      dx[i][2] = p.z - ref[3 * i + 2];
+      acc += dx[i][0] * dx[i][0] + dx[i][1] * dx[i][1] + dx[i][2] * dx[i][2];
+    }
+  const Real N = (Real)c.na;
+  s = sqrt(acc / N + (Real)0.01);
+  const Real inv = (Real)1 / (N * s);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    if (i < c.na)
+      for (int q = 0; q < 3; ++q) J[3 * i + q] = dx[i][q] * inv;
+  return 0;
 }
 
 // Phase A task: CV k of one step (row x of the window), its Jacobian
@@ -389,10 +429,12 @@ __device__ __forceinline__ void window_cv(const GroupFixed<Real> *fx, const type
   int fl;
   if (c.type == ABP_CV_COM_DIST)
     fl = com_thread<Real>(c, fx->ia[k], fx->ib[k], fx->wa[k], fx->wb[k], x, sk, st.jac[k]);
-  else
+  else if (c.type == ABP_CV_DIHEDRAL)
     fl = dihedral_eval<Real>(c, fx->ia[k], x, sk, reinterpret_cast<Real(*)[3]>(st.jac[k]));
+  else
+    fl = rmsd_thread<Real>(c, fx->ia[k], x, sk, st.jac[k]);
   st.s[k] = sk;
-  AxisSt<Real> ax = axis_eval<Real>(wd.g, wd.R[k], k, sk, (Real)0, dep);
+  AxisSt<Real> ax = axis_state<Real>(wd, k, sk, (Real)0, dep);
   st.i0[k] = ax.i0;
   st.i1[k] = ax.i1;
   st.f[k] = ax.f;
@@ -410,7 +452,7 @@ template <typename Real>
 __device__ void window_height(GroupFixed<Real> *fx, const StepRec<Real> &st, long long step, const DepositLog &log) {
   const WalkerDev &wd = fx->wd;
   const GridDev &gd = wd.g;
-  const int d = gd.d, nc = 1 << d;
+  const int d = gd.d, nc = wd.method == ABP_METHOD_MABP ? 0 : 1 << d;  // mABP hills: fixed height w
   const unsigned char *rec = reinterpret_cast<const unsigned char *>(gd.rec);
   double t[8];
 #pragma unroll
@@ -432,7 +474,7 @@ __device__ void window_height(GroupFixed<Real> *fx, const StepRec<Real> &st, lon
     }
   }
   const double V0 = ((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7]));
-  const double h = wd.w * exp(-V0 * wd.inv_dT);
+  const double h = nc ? wd.w * exp(-V0 * wd.inv_dT) : wd.w;
   fx->hV = V0;
   fx->hf = (Real)h;
   if (log.rec) {
@@ -478,7 +520,7 @@ __device__ __forceinline__ void step_flags(int d, bool dep, StepRec<Real> &st) {
 
 // Per atom, its a5 terms in the order they are added (CV by CV, list A
 // before list B): COM distance list A w_i, list B -w_i (both on the unit
-// separation); dihedral atom a: -1 on its gradient row.
+// separation); dihedral or RMSD atom i: -1 on its gradient row.
 template <typename Real>
 __device__ void build_atom_terms(const Grp &g, const GroupFixed<Real> *fx, int *cnt, AtomTerm<Real> *terms) {
   const WalkerDev &wd = fx->wd;
@@ -489,7 +531,7 @@ __device__ void build_atom_terms(const Grp &g, const GroupFixed<Real> *fx, int *
       const CvDev &c = wd.cv[k];
       const bool com = c.type == ABP_CV_COM_DIST;
       for (int l = 0; l < (com ? 2 : 1); ++l) {
-        const int n = l ? c.nb : (com ? c.na : 4);
+        const int n = l ? c.nb : (c.type == ABP_CV_DIHEDRAL ? 4 : c.na);
         const int32_t *list = l ? fx->ib[k] : fx->ia[k];
         for (int i = 0; i < n; ++i) {
           const int at = list[i];

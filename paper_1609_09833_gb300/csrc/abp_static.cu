@@ -91,6 +91,7 @@ extern "C" abp_status abp_step_static(int device, void *cuda_stream, const abp_g
        reinterpret_cast<uintptr_t>(grid_records_dev)) & (align - 1))
     return sfail(ABP_ERR_INVALID_ARG, "abp_step_static: buffers must be 16-byte (FP64: 32-byte) aligned");
   if (w->natoms < 1) return sfail(ABP_ERR_INVALID_ARG, "abp_step_static: natoms must be >= 1");
+  if (w->method != ABP_METHOD_WT) return sfail(ABP_ERR_UNSUPPORTED, "abp_step_static: well-tempered walkers only");
   if (!(w->gamma > 1) || !(w->kT > 0) || w->stride < 1 || !(w->w >= 0) || !std::isfinite(w->w) || !(w->cutoff > 0))
     return sfail(ABP_ERR_INVALID_ARG, "abp_step_static: need gamma > 1, kT > 0, w >= 0, cutoff > 0, stride >= 1");
 

@@ -341,3 +341,48 @@ def shared256_templates(seed: int, nw: int = 32, n_lig: int = 200, n_env: int = 
         env = r.uniform(0.0, box, size=(n_env, 3))
         out.append(np.concatenate([lig, env]))
     return out
+
+
+# ---------------------------------------------------------------- the paper's RMSD setup (mABP, 480^2 grid)
+
+
+def paper_rmsd_specs(nw: int = 64, n: int = 480, lo: float = 0.0, hi: float = 12.0, a_bins: float = 10.0,
+                     p: int = 20, b: float = 0.9, c: float = 0.001, kT: float = 2.5, stride: int = 1,
+                     seed: int = 11):
+    """Walkers shaped like the paper's ligand runs: two RMSD CVs (4 atoms
+    each, to seeded reference positions) on a 480 x 480 grid over [0, 12] nm,
+    mABP with compact hills a = 10 grid spacings, p = 20, b = 0.9, c = 0.001,
+    updated every step."""
+    r = rng(seed)
+    g = grid((lo, lo), (hi, hi), (n, n), (False, False))
+    a = [bins(g, k, a_bins) for k in range(2)]
+    specs = []
+    for _ in range(nw):
+        ref = _ball(r, 8, 0.4)
+        cvs = [{"type": "rmsd", "a": np.arange(0, 4), "ref": ref[:4].copy()},
+               {"type": "rmsd", "a": np.arange(4, 8), "ref": ref[4:].copy()}]
+        specs.append({"natoms": 8, "cvs": cvs, "grid": g, "hill": mabp_hill(a, p, b, c, kT, stride)})
+    return specs
+
+
+class RmsdFrames:
+    """Frames for paper_rmsd_specs walkers: each 4-atom group is its reference
+    shifted along a slow closed path (its RMSD sweeps about 0.1 to 3 nm),
+    plus N(0, jitter^2) per atom and frame."""
+
+    def __init__(self, specs, seed: int, amp=(0.3, 3.0), period=(400, 1600), jitter: float = 0.02):
+        r = rng(seed)
+        self.ref = np.concatenate([np.concatenate([c["ref"] for c in sp["cvs"]]) for sp in specs])  # [nw*8, 3]
+        ng = 2 * len(specs)
+        self.amp = r.uniform(amp[0], amp[1], size=(ng, 3)) / math.sqrt(3.0)
+        self.per = r.uniform(period[0], period[1], size=(ng, 3))
+        self.phase = r.uniform(0, 2 * math.pi, size=(ng, 3))
+        self.seed = seed
+        self.jitter = jitter
+
+    def frames(self, step0: int, T: int, dtype=np.float32) -> np.ndarray:
+        t = np.arange(step0, step0 + T, dtype=np.float64)[:, None, None]
+        shift = self.amp[None] * np.sin(2 * math.pi * t / self.per[None] + self.phase[None])  # [T, ng, 3]
+        shift = np.repeat(shift, 4, axis=1)
+        noise = rng(self.seed * 1_000_003 + step0 + 31).normal(scale=self.jitter, size=(T,) + self.ref.shape)
+        return (self.ref[None] + shift + noise).astype(dtype)
