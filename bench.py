@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--tile", default="auto", choices=["auto", "on", "off"])
     ap.add_argument("--group-threads", type=int, default=0)
     ap.add_argument("--no-extra", action="store_true", help="skip the other workloads")
-    ap.add_argument("--only", default=None, choices=["double_well", "uneven", "shared", "serve"],
+    ap.add_argument("--only", default=None, choices=["double_well", "uneven", "shared", "serve", "paper_rmsd"],
                     help="run just one of the other workloads (for profiling) and print its record")
     return ap.parse_args()
 
@@ -313,6 +313,48 @@ def bench_double_well(abp, synth, torch, dev):
         ctx.close()
 
 
+def bench_paper_rmsd(abp, synth, torch, dev):
+    """64 walkers shaped like the paper's ligand runs: two 4-atom RMSD CVs on a
+    480 x 480 grid over [0, 12] nm, mABP with compact hills (a = 10 grid
+    spacings, p = 20, b = 0.9, c = 0.001), histograms updated every step."""
+    ctx = abp.Context(dev)
+    try:
+        nw, C, chunks = 64, 1000, 4
+        specs = synth.paper_rmsd_specs(nw=nw)
+        rec = abp.to_records(synth.RmsdFrames(specs, seed=41).frames(0, chunks * C)).cuda()
+        A = rec.shape[1]
+        offs = torch.tensor(synth.offsets_of(specs), dtype=torch.int64, device="cuda")
+        walkers = ctx.make_walkers(specs)
+        F = torch.zeros(C, A, 4, device="cuda")
+        st = {"md": 0}
+
+        def run():
+            fi = (st["md"] // C) % chunks * C
+            abp.abp_run(ctx.handle, walkers, rec[fi:], abp.ABP_F32, offs, A, F, offs, A, abp.ABP_FORCES_OVERWRITE,
+                        st["md"], C)
+            st["md"] += C
+
+        ms = _time_loop(torch, run, 5)
+        g = specs[0]["grid"]
+        R = [int(math.floor(specs[0]["hill"]["a"][k] / ((g["hi"][k] - g["lo"][k]) / (g["n"][k] - 1)))) for k in
+             range(2)]
+        box = (2 * R[0] + 1) * (2 * R[1] + 1)
+        # coordinates + forces, the look-up node, the stencil read and written every step
+        per_step = 8 * 16 * 2 + NODE_BYTES + box * NODE_BYTES * 2
+        peaks, src = load_peaks()
+        achieved = per_step * nw * C / (ms / 1e3) / 1e9
+        return {"workload": "64 walkers, 2 RMSD CVs (4 atoms each), 480x480 grid on [0,12] nm, mABP compact hills "
+                            "a = 10 spacings, p = 20, b = 0.9, c = 0.001, update every step",
+                "value": nw * C / (ms / 1e3), "unit": "bias steps/s", "ms_per_launch": ms, "md_steps_per_launch": C,
+                "stencil_nodes": box,
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                             "frac": achieved / peaks["hbm_gbs"], "bytes_per_walker_step": per_step,
+                             "kernel": "k_win<float> (windowed form)", "peak_source": src}}
+    finally:
+        torch.cuda.synchronize()
+        ctx.close()
+
+
 def bench_uneven(abp, synth, torch, dev, sm_mhz):
     """1000 walkers: 40 % 1D / 50 % 2D / 10 % 3D grids, CN 40 x 400 each."""
     from paper_1609_09833_gb300 import autotune
@@ -555,7 +597,8 @@ def main():
         fn = {"double_well": lambda: bench_double_well(abp, synth, torch, 0),
               "uneven": lambda: bench_uneven(abp, synth, torch, 0, 2070.0),
               "shared": lambda: bench_shared(abp, synth, torch, 0, 2070.0),
-              "serve": lambda: bench_serve(abp, synth, torch, 0)}[args.only]
+              "serve": lambda: bench_serve(abp, synth, torch, 0),
+              "paper_rmsd": lambda: bench_paper_rmsd(abp, synth, torch, 0)}[args.only]
         print(json.dumps({"only": args.only, **fn()}), flush=True)
         return 0
 
@@ -692,7 +735,8 @@ def main():
         for name, fn in (("double_well_fp64", lambda: bench_double_well(abp, synth, torch, dev)),
                          ("uneven1000", lambda: bench_uneven(abp, synth, torch, dev, sm)),
                          ("shared256", lambda: bench_shared(abp, synth, torch, dev, sm)),
-                         ("serve4096", lambda: bench_serve(abp, synth, torch, dev))):
+                         ("serve4096", lambda: bench_serve(abp, synth, torch, dev)),
+                         ("paper_rmsd_mabp64", lambda: bench_paper_rmsd(abp, synth, torch, dev))):
             try:
                 extra[name] = fn()
             except Exception as e:  # report, do not hide the headline

@@ -132,6 +132,7 @@ struct AtomTerm {
 
 constexpr int kWinMax = 32;             // MD steps per window of the windowed form
 constexpr int kAtomTerms = 2 * kMaxCv;  // per atom: up to 2 list entries per CV
+constexpr int kMabpBoxBytes = 96 * 1024;  // windowed mABP: the union of a window's stencil boxes, at most
 constexpr int kWinBytes = 64 * 1024;    // its coordinate double buffer, at most
 
 // Steps per window for a walker in the windowed form (0: not eligible). The
@@ -162,7 +163,8 @@ __host__ __device__ inline int window_steps(int natoms, const CvDev *cv, int d, 
 //   atoms     per atom, its a5 terms: counts, then AtomTerm[natoms][kAtomTerms] (windowed form)
 //   lists     per-CV atom index lists (+ COM weights)
 //   cn        per COORD CV: dCN/dx per list entry and per-warp partials
-//   tile      optional copy of a box of the walker's grid (node records)
+//   tile      optional copy of a box of the walker's grid (node records); in
+//             the windowed form of an mABP walker, the window's stencil boxes
 struct GroupLayout {
   int xs0, xs1, fs, steps, atoms, lists, cn, tile, total;
   int win, xstride;  // windowed form: steps per window (0 = per-step form), row stride in records
@@ -191,9 +193,10 @@ __host__ __device__ inline void tile_dims(const GridDev &g, const int *R, int bu
 }
 
 // window: the fused batched form, which runs eligible walkers windowed (and
-// gives them no grid tile).
+// gives them no grid tile); mabp: the walker is an mABP walker.
 __host__ __device__ inline GroupLayout group_layout(int natoms, const CvDev *cv, const GridDev &g, const int *R,
-                                                    int nwarps, int rsz, int tile_budget, bool window = false) {
+                                                    int nwarps, int rsz, int tile_budget, bool window = false,
+                                                    bool mabp = false) {
   GroupLayout L;
   const int real = rsz / 4;
   int off = 0;
@@ -235,6 +238,7 @@ __host__ __device__ inline GroupLayout group_layout(int natoms, const CvDev *cv,
   if (L.win) {
     for (int k = 0; k < 3; ++k) L.T[k] = 0;
     L.tile_nodes = 0;
+    if (mabp) off += kMabpBoxBytes;
     L.total = align32(off);
     return L;
   }

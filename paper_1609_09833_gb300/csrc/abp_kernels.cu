@@ -32,7 +32,7 @@ template <typename Real>
 __device__ __forceinline__ GroupLayout layout_of(const GroupFixed<Real> *fx, int nwarps, int tile_budget,
                                                  bool window) {
   return group_layout(fx->wd.natoms, fx->wd.cv, fx->wd.g, fx->wd.R, nwarps, (int)sizeof(typename Rec4<Real>::T),
-                      tile_budget, window);
+                      tile_budget, window, fx->wd.method == ABP_METHOD_MABP);
 }
 
 // Copy each CV's atom lists (and COM weights as Real) into shared memory and
@@ -324,6 +324,30 @@ __device__ __forceinline__ int com_thread(const CvDev &c, const int32_t *ia, con
   return ABP_WFLAG_SINGULAR;
 }
 
+// The end of a4 for one step: V and dV/dxi from the interpolated fields (for
+// mABP, the nearest node's histograms turned into the bias), a zero gradient
+// on a clamped axis, and the Jacobian factors scaled for a5.
+template <typename Real>
+__device__ __forceinline__ void finish_lookup(const WalkerDev &wd, StepRec<Real> &st, Real *acc) {
+  const int d = wd.g.d;
+  if (wd.method == ABP_METHOD_MABP) {
+    Real V, dvm[3] = {0, 0, 0};
+    mabp_bias<Real>(wd, acc, V, dvm);
+    acc[0] = V;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) acc[1 + k] = dvm[k];
+  }
+  st.V = acc[0];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    if (k < d) {
+      const Real dv = ((st.clamped >> k) & 1) ? (Real)0 : acc[1 + k];
+      st.dv[k] = dv;
+      const int nj = wd.cv[k].type == ABP_CV_COM_DIST ? 3 : 12;
+      for (int q = 0; q < nj; ++q) st.jac[k][q] *= dv;
+    }
+}
+
 // a4 of one step: the 2^d corners' records loaded together, then combined in
 // corner order.
 template <typename Real>
@@ -368,23 +392,7 @@ __device__ __forceinline__ void interp_one(const WalkerDev &wd, StepRec<Real> &s
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc[q] += w[c] * v[c][q];
     }
-  if (wd.method == ABP_METHOD_MABP) {  // the nearest node's histograms (weight 1 on corner 0)
-    Real V, dvm[3] = {0, 0, 0};
-    mabp_bias<Real>(wd, acc, V, dvm);
-    acc[0] = V;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) acc[1 + k] = dvm[k];
-  }
-  st.V = acc[0];
-#pragma unroll
-  for (int k = 0; k < 3; ++k)
-    if (k < d) {
-      const Real dv = ((st.clamped >> k) & 1) ? (Real)0 : acc[1 + k];
-      st.dv[k] = dv;
-      // the Jacobian factor, scaled for a5
-      const int nj = wd.cv[k].type == ABP_CV_COM_DIST ? 3 : 12;
-      for (int q = 0; q < nj; ++q) st.jac[k][q] *= dv;
-    }
+  finish_lookup<Real>(wd, st, acc);
 }
 
 // RMSD of one step by one thread (SI "Definition of the RMSD"):
@@ -592,6 +600,16 @@ __device__ __forceinline__ void store_force_stream<double>(D4 *fo, const D4 &f, 
   }
 }
 
+__device__ __forceinline__ float4 lds128(unsigned a) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ void sts128(unsigned a, const float4 &v) {
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+               : "memory");
+}
+
 // Deposit steps of a window (bit j: step t0 + j).
 __device__ __forceinline__ unsigned window_dmask(long long step0, int t0, int nt, long long stride) {
   const long long rem = (step0 + t0) % stride;
@@ -620,6 +638,7 @@ struct WindowCtx {
   int W, nwin, mode;
   bool serial_out;
   unsigned long long stream;
+  unsigned char *box;    // mABP: the union of a window's stencil boxes (NULL: not staged)
 
   __device__ __forceinline__ int nt_of(int w) const { return min(W, nsteps - w * W); }
   __device__ __forceinline__ StepRec<Real> *steps_of(int w) const { return steps + (w % 3) * W; }
@@ -686,6 +705,222 @@ struct WindowCtx {
   // formed while the steps before it interpolate (same grid for both)
   template <int UNR>
   __device__ __forceinline__ void chain(const Grp &g, int w) const {
+    if (fx->wd.method == ABP_METHOD_MABP && box) {
+      const int d = fx->wd.g.d;
+      if (d == 1 ? chain_mabp<1>(g, w) : d == 2 ? chain_mabp<2>(g, w) : chain_mabp<3>(g, w)) return;
+    }
+    chain_seq<UNR>(g, w);
+  }
+
+  // mABP: the window's deposits through shared memory. Every hill has the
+  // fixed height w and sits on its step's nearest node, so no deposit depends
+  // on a look-up: the union of the window's stencil boxes is copied into
+  // shared memory, the hills are applied there one after another (the same
+  // compensated additions as chain_seq's, so the same bits), each step reads
+  // its node there once the hills up to its own are in, and the box is
+  // written back. Steps whose node lies outside the union read the grid.
+  // Returns false (nothing done) when the union does not fit.
+  template <int DIM>
+  __device__ bool chain_mabp(const Grp &g, int w) const {
+    const WalkerDev &wd = fx->wd;
+    const GridDev &gd = wd.g;
+    constexpr int d = DIM;
+    const int nt = nt_of(w), t0 = w * W, rb = gd.rec_bytes;
+    StepRec<Real> *st = steps_of(w);
+    const unsigned bad = fx->winbad[w % 3];
+    const unsigned gdep = window_dmask(step0, t0, nt, wd.stride) & ~bad;
+    const int first = gdep ? __ffs(gdep) - 1 : nt;
+    int org[3] = {0, 0, 0}, span[3] = {1, 1, 1};
+    long long nodes = gdep ? 1 : 0;
+    if (gdep) {
+      for (int k = 0; k < d; ++k) {
+        const int n = gd.n[k], c0 = st[first].da[k];
+        int lo = 0, hi = 0;
+        for (unsigned m = gdep; m; m &= m - 1) {
+          int dd = st[__ffs(m) - 1].da[k] - c0;
+          if (gd.periodic[k]) {
+            dd %= n;
+            if (dd < 0) dd += n;
+            if (2 * dd > n) dd -= n;
+          }
+          lo = min(lo, dd);
+          hi = max(hi, dd);
+        }
+        lo -= wd.R[k];
+        hi += wd.R[k];
+        if (gd.periodic[k]) {
+          if (hi - lo + 1 >= n) {
+            org[k] = 0;
+            span[k] = n;
+          } else {
+            org[k] = ((c0 + lo) % n + n) % n;
+            span[k] = hi - lo + 1;
+          }
+        } else {
+          org[k] = max(c0 + lo, 0);
+          span[k] = min(c0 + hi, n - 1) - org[k] + 1;
+        }
+        nodes *= span[k];
+      }
+      if (nodes * rb > kMabpBoxBytes) return false;
+    }
+    // box index of a node, or -1 outside the box
+    auto box_index = [&](const int *j) -> int {
+      int idx = 0, mul = 1;
+      for (int k = 0; k < d; ++k) {
+        int r = j[k] - org[k];
+        if (gd.periodic[k] && r < 0) r += gd.n[k];
+        if (r < 0 || r >= span[k]) return -1;
+        idx += mul * r;
+        mul *= span[k];
+      }
+      return idx;
+    };
+    // raw histograms of a step's node, kept in V / dv until the window's end
+    auto raw_copy = [&](StepRec<Real> &s, const unsigned char *p) {
+      Real v[4] = {0, 0, 0, 0};
+      rec_values<Real>(gd, p, v);
+      s.V = v[0];
+      for (int k = 0; k < 3; ++k) s.dv[k] = v[1 + k];
+    };
+    const unsigned char *rec = reinterpret_cast<const unsigned char *>(gd.rec);
+    auto node_ptr = [&](int idx) -> const unsigned char * {
+      long long node = 0, mul = 1;
+      int r = idx;
+      for (int k = 0; k < d; ++k) {
+        const int q = r % span[k];
+        r /= span[k];
+        int j = org[k] + q;
+        if (j >= gd.n[k]) j -= gd.n[k];
+        node += mul * j;
+        mul *= gd.n[k];
+      }
+      return rec + node * rb;
+    };
+    // steps read from the box (bit j), the rest from the grid
+    unsigned inbox = 0;
+    if (gdep)
+      for (int j = 0; j < nt; ++j)
+        if (!((bad >> j) & 1) && box_index(st[j].da) >= 0) inbox |= 1u << j;
+    // tables of the node-centred hill (the same for every deposit)
+    if (g.t < d) {
+      fx->da[g.t] = 0;
+      fx->dc[g.t] = 0;
+      fx->df[g.t] = 0;
+    }
+    g.sync();
+    build_tables<Real>(g, fx);
+    // the box in; steps outside it read the grid
+    for (int i = g.t; i < nodes; i += g.G) {
+      const float4 *src = reinterpret_cast<const float4 *>(node_ptr(i));
+      float4 *dst = reinterpret_cast<float4 *>(box + (size_t)i * rb);
+      dst[0] = src[0];
+      if (rb == 32) dst[1] = src[1];
+    }
+    for (int j = g.t; j < nt; j += g.G)
+      if (!((bad >> j) & 1) && !((inbox >> j) & 1)) interp_one<Real>(wd, st[j]);
+    g.sync();
+    for (int j = g.t; j < first; j += g.G)
+      if ((inbox >> j) & 1) raw_copy(st[j], box + (size_t)box_index(st[j].da) * rb);
+    const Real h = (Real)wd.w;
+    const int s0 = 2 * wd.R[0] + 1, s1 = d > 1 ? 2 * wd.R[1] + 1 : 1, s2 = d > 2 ? 2 * wd.R[2] + 1 : 1;
+    const int sp01 = s0 * s1;
+    for (unsigned m = gdep; m; m &= m - 1) {
+      const int j = __ffs(m) - 1;
+      const unsigned rest = m & (m - 1);
+      const int next = rest ? __ffs(rest) - 1 : nt;
+      g.sync();  // the hills and look-ups before this hill are done
+      // box-relative position of the hill's first node, per axis
+      // (on a periodic axis taken into [0, n), so that one wrap suffices below)
+      int base[3] = {0, 0, 0};
+      for (int k = 0; k < d; ++k) {
+        base[k] = st[j].da[k] - wd.R[k] - org[k];
+        if (gd.periodic[k]) base[k] = ((base[k] % gd.n[k]) + gd.n[k]) % gd.n[k];
+      }
+      const bool centre_in = (inbox >> j) & 1;
+      // stencil positions (o0 fastest), advanced without division
+      Iter2 it(g.t, g.G, s0);
+      for (int idx = g.t; idx < sp01 * s2; idx += g.G, it.next()) {
+        const int o0 = it.i, o12 = it.j, o1 = d > 2 ? o12 % s1 : o12, o2 = d > 2 ? o12 / s1 : 0;
+        const int o[3] = {o0, o1, o2};
+        int bi = 0, mul = 1;
+        bool in = true;
+        for (int k = 0; k < d; ++k) {
+          const int n = gd.n[k];
+          int r = base[k] + o[k];  // node - org
+          if (gd.periodic[k]) {
+            if (r >= n) r -= n;
+          } else {
+            const int jn = r + org[k];
+            in = in && jn >= 0 && jn < n;
+          }
+          in = in && r >= 0 && r < span[k];
+          bi += mul * r;
+          mul *= span[k];
+        }
+        if (!in) continue;
+        Real G = h * fx->tabG[0][o0];
+        if (d > 1) G = G * fx->tabG[1][o1];
+        if (d > 2) G = G * fx->tabG[2][o2];
+        const Real d0 = fx->tabD[0][o0], d1 = d > 1 ? fx->tabD[1][o1] : (Real)0,
+                   d2 = d > 2 ? fx->tabD[2][o2] : (Real)0;
+        unsigned char *p = box + (size_t)bi * rb;
+        // the record through shared-memory loads and stores
+        const unsigned sa = (unsigned)__cvta_generic_to_shared(p);
+        float4 ra = lds128(sa), rbv = rb == 32 ? lds128(sa + 16) : make_float4(0, 0, 0, 0);
+        rmw_regs<Real>(d, ra, rbv, G, d0, d1, d2);
+        sts128(sa, ra);
+        if (rb == 32) sts128(sa + 16, rbv);
+        // the hill's own step reads its centre right after it
+        if (centre_in && o0 == wd.R[0] && (d < 2 || o1 == wd.R[1]) && (d < 3 || o2 == wd.R[2])) raw_copy(st[j], p);
+      }
+      if (g.t == g.G - 1 && log.rec) window_height<Real>(fx, st[j], step0 + t0 + j, log);
+      if (next > j + 1) {  // steps between this hill and the next read after it
+        g.sync();
+        for (int q = j + 1 + g.t; q < next; q += g.G)
+          if ((inbox >> q) & 1) raw_copy(st[q], box + (size_t)box_index(st[q].da) * rb);
+      }
+    }
+    g.sync();
+    // the box out; the raw histograms of the steps read in it become the bias
+    for (int i = g.t; i < nodes; i += g.G) {
+      float4 *dst = reinterpret_cast<float4 *>(const_cast<unsigned char *>(node_ptr(i)));
+      const float4 *src = reinterpret_cast<const float4 *>(box + (size_t)i * rb);
+      dst[0] = src[0];
+      if (rb == 32) dst[1] = src[1];
+    }
+    for (int j = g.t; j < nt; j += g.G)
+      if ((inbox >> j) & 1) {
+        Real acc[4] = {st[j].V, st[j].dv[0], st[j].dv[1], st[j].dv[2]};
+        finish_lookup<Real>(wd, st[j], acc);
+      }
+    g.sync();
+    if (w + 1 == nwin && g.t == 0) write_state(st, nt, bad);
+    return true;
+  }
+
+  // the walker's state after the call's last step
+  __device__ __forceinline__ void write_state(const StepRec<Real> *st, int nt, unsigned bad) const {
+    const WalkerDev &wd = fx->wd;
+    const StepRec<Real> &s = st[nt - 1];
+    if ((bad >> (nt - 1)) & 1) {
+      wd.state->flags = ABP_WFLAG_NONFINITE;
+    } else {
+      WalkerState ws;
+      for (int k = 0; k < 3; ++k) {
+        ws.s[k] = k < wd.g.d ? (double)s.s[k] : 0.0;
+        ws.dV[k] = k < wd.g.d ? (double)s.dv[k] : 0.0;
+      }
+      ws.V = (double)s.V;
+      ws.flags = s.flags;
+      ws.pad = 0;
+      ws.step = step0 + last;
+      *wd.state = ws;
+    }
+  }
+
+  template <int UNR>
+  __device__ __forceinline__ void chain_seq(const Grp &g, int w) const {
     const WalkerDev &wd = fx->wd;
     const int nt = nt_of(w), t0 = w * W;
     StepRec<Real> *st = steps_of(w);
@@ -722,23 +957,7 @@ struct WindowCtx {
     for (int q = seg + g.t; q < nt; q += g.G)
       if (!((bad >> q) & 1)) interp_one<Real>(wd, st[q]);
     g.sync();
-    if (w + 1 == nwin && g.t == 0) {
-      const StepRec<Real> &s = st[nt - 1];
-      if ((bad >> (nt - 1)) & 1) {
-        wd.state->flags = ABP_WFLAG_NONFINITE;
-      } else {
-        WalkerState ws;
-        for (int k = 0; k < 3; ++k) {
-          ws.s[k] = k < wd.g.d ? (double)s.s[k] : 0.0;
-          ws.dV[k] = k < wd.g.d ? (double)s.dv[k] : 0.0;
-        }
-        ws.V = (double)s.V;
-        ws.flags = s.flags;
-        ws.pad = 0;
-        ws.step = step0 + last;
-        *wd.state = ws;
-      }
-    }
+    if (w + 1 == nwin && g.t == 0) write_state(st, nt, bad);
   }
 
   // C: a5 per (step, atom), stored as it is formed
@@ -808,6 +1027,7 @@ __device__ void walker_window(const Grp &g, GroupFixed<Real> *fx, unsigned char 
   c.mode = a.forces ? a.mode : ABP_FORCES_OVERWRITE;
   c.serial_out = a.forces && a.fstride == 0;
   c.stream = l2_evict_first();
+  c.box = fx->wd.method == ABP_METHOD_MABP ? dyn + L.tile : nullptr;
   // the two halves (or the whole warp twice)
   const bool split = g.G >= 64;
   Grp gx = g, gy = g;
@@ -956,7 +1176,8 @@ bool window_eligible(const WalkerDev &hd, int fp64) {
 }
 
 int run_group_bytes(const WalkerDev &hd, int fp64, int G, int tile_budget, bool window) {
-  GroupLayout L = group_layout(hd.natoms, hd.cv, hd.g, hd.R, G / 32, fp64 ? 32 : 16, tile_budget, window);
+  GroupLayout L = group_layout(hd.natoms, hd.cv, hd.g, hd.R, G / 32, fp64 ? 32 : 16, tile_budget, window,
+                               hd.method == ABP_METHOD_MABP);
   return align32(group_fixed_bytes(fp64) + L.total);
 }
 

@@ -367,10 +367,11 @@ def paper_rmsd_specs(nw: int = 64, n: int = 480, lo: float = 0.0, hi: float = 12
 
 class RmsdFrames:
     """Frames for paper_rmsd_specs walkers: each 4-atom group is its reference
-    shifted along a slow closed path (its RMSD sweeps about 0.1 to 3 nm),
-    plus N(0, jitter^2) per atom and frame."""
+    shifted along a slow closed path (its RMSD sweeps about 0.1 to 3 nm over
+    `period` steps: by default tens of thousands, a drift far slower than the
+    atoms' N(0, jitter^2) vibration, as for a ligand's pose in MD)."""
 
-    def __init__(self, specs, seed: int, amp=(0.3, 3.0), period=(400, 1600), jitter: float = 0.02):
+    def __init__(self, specs, seed: int, amp=(0.3, 3.0), period=(20_000, 80_000), jitter: float = 0.02):
         r = rng(seed)
         self.ref = np.concatenate([np.concatenate([c["ref"] for c in sp["cvs"]]) for sp in specs])  # [nw*8, 3]
         ng = 2 * len(specs)

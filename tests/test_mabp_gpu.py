@@ -164,7 +164,7 @@ def test_rmsd_cvs_on_the_paper_grid(abp, ctx):
     a = 10 grid spacings and p = 20 (the paper's ligand-binding setup), and
     the same CVs with well-tempered Gaussian hills."""
     specs = synth.paper_rmsd_specs(nw=6, c=0.05)
-    frames = synth.RmsdFrames(specs, seed=4).frames(0, 200)
+    frames = synth.RmsdFrames(specs, seed=4, period=(400, 1600)).frames(0, 200)  # fast sweeps for coverage
     walkers = ctx.make_walkers(specs)
     abp.abp_deposit_log_enable(ctx.handle, 1 << 16)
     Fg = gpu_replay(abp, ctx, walkers, frames, 0, chunks=2)
