@@ -79,6 +79,8 @@ class OrHill(C.Structure):
         ("p", C.c_int),
         ("b", C.c_double),
         ("c", C.c_double),
+        ("smax", C.c_double * 3),
+        ("kwall", C.c_double),
     ]
 
 
@@ -200,6 +202,10 @@ class Walker:
             s.hill.gamma = float(hl["gamma"])
         s.hill.kT = float(hl["kT"])
         s.hill.stride = int(hl["stride"])
+        if hl.get("kwall", 0.0) > 0:
+            s.hill.kwall = float(hl["kwall"])
+            for k in range(d):
+                s.hill.smax[k] = float(hl["smax"][k])
         cvs = spec["cvs"]
         if len(cvs) != d:
             raise ValueError("one CV per grid axis")

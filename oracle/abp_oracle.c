@@ -63,6 +63,12 @@
  * dh/dxi_i.
  * The RMSD CV (SI "Definition of the RMSD") is offset by 0.01 so that it is
  * never zero: s = (sum_i |x_i - x0_i|^2 / N + 0.01)^(1/2), no fit.
+ *
+ * The CV range limit (the restraint "which limits the maximum value of the
+ * CVs", Applications section; the paper gives no form) is read as a
+ * flat-bottomed harmonic wall per CV, U = kwall/2 (s_k - smax_k)^2 for
+ * s_k > smax_k: its gradient is added to dV_b/ds_k before the chain rule
+ * (dV reports the sum), kwall = 0 turns it off.
  */
 #include <math.h>
 #include <stdint.h>
@@ -115,6 +121,8 @@ typedef struct {
   double a[3];          /* compact hill half-width per CV */
   int p;                /* compact hill shape exponent, >= 1 */
   double b, c;          /* mABP parameters of Eq. (apfm) */
+  double smax[3];       /* CV range limit: wall above smax_k ... */
+  double kwall;         /* ... with force constant kwall (0: no wall) */
 } or_hill;
 
 typedef struct {
@@ -569,6 +577,11 @@ int or_lookup_mabp(const or_grid *g, const or_hill *hl, const double *field, con
   return flag;
 }
 
+/* dU/ds_k of the CV range limit: kwall (s - smax_k) above smax_k, else 0. */
+double or_wall_grad(const or_hill *hl, int k, double s) {
+  return (hl->kwall > 0 && s > hl->smax[k]) ? hl->kwall * (s - hl->smax[k]) : 0.0;
+}
+
 /* ------------------------------------------------------------------ */
 /* one MD step for a batch of walkers                                   */
 /* ------------------------------------------------------------------ */
@@ -636,6 +649,7 @@ int or_batch_step(int nw, const or_walker *wk, double *const *fields, const doub
       flags[w] |= or_lookup_mabp(&wk[w].g, &wk[w].hill, fields[w], &s[3 * w], &V[w], g3);
     else
       flags[w] |= or_interp(&wk[w].g, fields[w], &s[3 * w], &V[w], g3);
+    for (int k = 0; k < d; ++k) g3[k] += or_wall_grad(&wk[w].hill, k, s[3 * w + k]);
     for (int k = 0; k < 3; ++k) dV[3 * w + k] = g3[k];
     double *Fw = F[w];
     for (int a = 0; a < 3 * wk[w].natoms; ++a) {

@@ -102,6 +102,12 @@ def mabp_hill(a, p, b, c, kT=2.5, stride=1, w=1.0):
             "kT": float(kT), "stride": int(stride), "w": float(w)}
 
 
+def with_wall(hill: dict, smax, kwall: float) -> dict:
+    """The hill parameters plus the CV range limit: a harmonic wall of force
+    constant kwall above smax_k on each CV."""
+    return dict(hill, smax=list(map(float, smax)), kwall=float(kwall))
+
+
 def bins(g: dict, k: int, nbins: float) -> float:
     """Width of `nbins` grid spacings along axis k (the node convention)."""
     n = g["n"][k]

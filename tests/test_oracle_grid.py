@@ -329,3 +329,53 @@ def test_well_tempered_limit_on_double_well():
     assert rms < 0.5 * kT, rms
     # and it did cross the barrier many times
     assert np.sum(np.diff(np.sign(s_hist)) != 0) > 100
+
+
+# ---------------------------------------------------------------- CV range limit
+
+
+def test_range_limit_wall_force_is_minus_gradient_of_its_energy():
+    """The wall kwall/2 (s - smax)^2 above smax: on an empty bias the force on
+    the atoms equals minus the finite-difference gradient of the wall energy
+    of s(x) (COM distance CV), is zero below smax and continuous at it."""
+    spec = _spec([0.0], [3.0], [301], [False], [0.05], natoms=4,
+                 cvs=[{"type": "com_dist", "a": [0, 1], "b": [2, 3]}])
+    spec["hill"] = synth.with_wall(spec["hill"], [1.2], 40.0)
+    spec["hill"]["stride"] = 10 ** 9  # no hill: the force is the wall's alone
+    w = oracle.Walker(spec)
+    r = np.random.default_rng(2)
+    x = np.concatenate([r.normal(scale=0.1, size=(2, 3)), r.normal(scale=0.1, size=(2, 3)) + [1.5, 0.2, 0.0]])
+    res = oracle.run([w], x[None], [0], step0=1, T=1)
+    s = res["s"][0, 0, 0]
+    assert s > 1.2
+    assert res["dV"][0, 0, 0] == pytest.approx(40.0 * (s - 1.2), rel=1e-12)
+
+    def U(xx):
+        sv = oracle.cv_eval(w, 0, xx)[0]
+        return 0.5 * 40.0 * max(sv - 1.2, 0.0) ** 2
+
+    e = 1e-6
+    for a, k in ((0, 0), (2, 1), (3, 2)):
+        xp, xm = x.copy(), x.copy()
+        xp[a, k] += e
+        xm[a, k] -= e
+        assert res["F"][0, a, k] == pytest.approx(-(U(xp) - U(xm)) / (2 * e), rel=1e-6)
+    # below the limit: no force; the wall starts from zero at smax
+    x2 = x.copy()
+    x2[2:] -= [0.5, 0.0, 0.0]
+    res2 = oracle.run([w], x2[None], [0], step0=1, T=1)
+    assert res2["s"][0, 0, 0] < 1.2 and np.all(res2["F"] == 0.0)
+    spec0 = dict(spec, hill=dict(spec["hill"], kwall=0.0))
+    res0 = oracle.run([oracle.Walker(spec0)], x[None], [0], step0=1, T=1)
+    assert np.all(res0["F"] == 0.0)
+
+
+def test_range_limit_adds_to_the_bias_gradient():
+    spec = _spec([-2.0], [2.0], [401], [False], [0.1], w=1.0, stride=1)
+    spec["hill"] = synth.with_wall(spec["hill"], [0.3], 25.0)
+    w = oracle.Walker(spec)
+    x = np.array([[0.55, 0.0, 0.0]])
+    ref = oracle.run([oracle.Walker(_spec([-2.0], [2.0], [401], [False], [0.1], w=1.0, stride=1))], x[None], [0], 0, 1)
+    res = oracle.run([w], x[None], [0], 0, 1)
+    assert res["dV"][0, 0, 0] == pytest.approx(ref["dV"][0, 0, 0] + 25.0 * (0.55 - 0.3), rel=1e-12)
+    assert res["V"][0, 0] == ref["V"][0, 0]  # V reports the bias alone
