@@ -144,6 +144,10 @@ typedef struct {
   double a[3];           /* mABP: compact hill half-width per CV (CV units); stencil half-width floor(a_k / D_k) */
   int p;                 /* mABP: compact hill shape exponent, >= 1 (Eq. (compacthill)) */
   double b, c;           /* mABP: the parameters of Eq. (apfm), 0 < b < 1, c > 0 */
+  double smax[3];        /* CV range limit (the restraint "which limits the maximum value of the CVs",
+                            Applications section; the paper gives no form): a harmonic wall */
+  double kwall;          /* kwall/2 (s_k - smax_k)^2 above smax_k, added to dV_b/ds_k for the forces
+                            (walker readouts report the sum); 0 = no wall */
 } abp_walker_desc;
 
 /* One deposited hill (the deposit log). */

@@ -52,7 +52,8 @@ class CvDesc(C.Structure):
 class WalkerDesc(C.Structure):
     _fields_ = [("natoms", C.c_int), ("cv", CvDesc * 3), ("w", C.c_double), ("sigma", C.c_double * 3),
                 ("cutoff", C.c_double), ("gamma", C.c_double), ("kT", C.c_double), ("stride", C.c_int64),
-                ("method", C.c_int), ("a", C.c_double * 3), ("p", C.c_int), ("b", C.c_double), ("c", C.c_double)]
+                ("method", C.c_int), ("a", C.c_double * 3), ("p", C.c_int), ("b", C.c_double), ("c", C.c_double),
+                ("smax", C.c_double * 3), ("kwall", C.c_double)]
 
 
 class DepositRec(C.Structure):
@@ -436,6 +437,10 @@ def walker_desc(spec: dict):
     d.w = float(hl["w"])
     d.kT = float(hl["kT"])
     d.stride = int(hl["stride"])
+    if hl.get("kwall", 0.0) > 0:
+        d.kwall = float(hl["kwall"])
+        for k, v in enumerate(hl["smax"]):
+            d.smax[k] = float(v)
     if hl.get("method", "wt") == "mabp":
         d.method = ABP_METHOD_MABP
         for k, a in enumerate(hl["a"]):

@@ -596,6 +596,18 @@ abp_status abp_walker_create(abp_ctx *ctx, abp_grid *grid, const abp_walker_desc
     return fail(ABP_ERR_UNSUPPORTED, "mABP walkers need their own grid");
   }
   hd.method = d->method;
+  if (!(d->kwall >= 0) || !std::isfinite(d->kwall)) {
+    delete w;
+    return fail(ABP_ERR_INVALID_ARG, "kwall must be finite and >= 0");
+  }
+  hd.kwall = d->kwall;
+  for (int k = 0; k < 3; ++k) {
+    if (d->kwall > 0 && k < ncv && !std::isfinite(d->smax[k])) {
+      delete w;
+      return fail(ABP_ERR_INVALID_ARG, "smax[%d] must be finite when kwall > 0", k);
+    }
+    hd.smax[k] = d->kwall > 0 && k < ncv ? d->smax[k] : 0.0;
+  }
   long long stencil = 1;
   for (int k = 0; k < ncv; ++k) {
     double sig = mabp ? d->a[k] : d->sigma[k];

@@ -1046,6 +1046,12 @@ __device__ __forceinline__ void mabp_bias(const WalkerDev &wd, const Real *acc, 
   for (int k = 0; k < wd.g.d; ++k) dv[k] = (Real)wd.mabp_g * acc[1 + k] / den;
 }
 
+// dU/ds_k of the CV range limit: kwall (s - smax_k) above smax_k, else 0.
+template <typename Real>
+__device__ __forceinline__ Real wall_grad(const WalkerDev &wd, int k, Real s) {
+  return (wd.kwall > 0 && s > (Real)wd.smax[k]) ? (Real)wd.kwall * (s - (Real)wd.smax[k]) : (Real)0;
+}
+
 // a4: V and dV/ds_k at s after the deposit, by warp 0's first 2^d lanes,
 // combined with a fixed xor-butterfly; a clamped axis gets a zero gradient.
 // (For mABP the corners all sit on the nearest node with weight 1 on the
@@ -1074,6 +1080,7 @@ __device__ void interp_step(const Grp &g, GroupFixed<Real> *fx, const GroupLayou
       fx->V = acc[0];
       for (int k = 0; k < gd.d; ++k) {
         Real dv = ((fx->clamped >> k) & 1) ? (Real)0 : acc[1 + k];
+        dv += wall_grad<Real>(fx->wd, k, fx->sh[k] + fx->sl[k]);
         fx->dvds[k] = dv;
         fx->dV[k] = dv;
       }

@@ -83,6 +83,8 @@ struct WalkerDev {
   double mabp_k;     // mABP: kT b / (1 - b)   (Eq. (apfm): V = mabp_k ln(mabp_h h + 1))
   double mabp_g;     // mABP: c b kT           (Eq. (btraj-grad): dV = mabp_g h' / (1 + mabp_h h))
   double mabp_h;     // mABP: c (1 - b)
+  double smax[3];    // CV range limit: wall above smax_k ...
+  double kwall;      // ... of force constant kwall (0: none)
   void *fbuf;        // library-owned force records (abp_step -> abp_forces)
   void *jscratch;    // library-owned Jacobian scratch (plain form)
   WalkerState *state;

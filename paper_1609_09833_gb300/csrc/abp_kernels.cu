@@ -341,7 +341,7 @@ __device__ __forceinline__ void finish_lookup(const WalkerDev &wd, StepRec<Real>
 #pragma unroll
   for (int k = 0; k < 3; ++k)
     if (k < d) {
-      const Real dv = ((st.clamped >> k) & 1) ? (Real)0 : acc[1 + k];
+      const Real dv = (((st.clamped >> k) & 1) ? (Real)0 : acc[1 + k]) + wall_grad<Real>(wd, k, st.s[k]);
       st.dv[k] = dv;
       const int nj = wd.cv[k].type == ABP_CV_COM_DIST ? 3 : 12;
       for (int q = 0; q < nj; ++q) st.jac[k][q] *= dv;

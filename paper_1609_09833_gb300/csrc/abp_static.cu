@@ -92,6 +92,8 @@ extern "C" abp_status abp_step_static(int device, void *cuda_stream, const abp_g
     return sfail(ABP_ERR_INVALID_ARG, "abp_step_static: buffers must be 16-byte (FP64: 32-byte) aligned");
   if (w->natoms < 1) return sfail(ABP_ERR_INVALID_ARG, "abp_step_static: natoms must be >= 1");
   if (w->method != ABP_METHOD_WT) return sfail(ABP_ERR_UNSUPPORTED, "abp_step_static: well-tempered walkers only");
+  if (!(w->kwall >= 0) || !std::isfinite(w->kwall))
+    return sfail(ABP_ERR_INVALID_ARG, "abp_step_static: kwall must be finite and >= 0");
   if (!(w->gamma > 1) || !(w->kT > 0) || w->stride < 1 || !(w->w >= 0) || !std::isfinite(w->w) || !(w->cutoff > 0))
     return sfail(ABP_ERR_INVALID_ARG, "abp_step_static: need gamma > 1, kT > 0, w >= 0, cutoff > 0, stride >= 1");
 
@@ -128,6 +130,12 @@ extern "C" abp_status abp_step_static(int device, void *cuda_stream, const abp_g
   // hills
   hd.natoms = w->natoms;
   hd.id = -1;
+  hd.kwall = w->kwall;
+  for (int k = 0; k < d; ++k) {
+    if (w->kwall > 0 && !std::isfinite(w->smax[k]))
+      return sfail(ABP_ERR_INVALID_ARG, "abp_step_static: smax must be finite when kwall > 0");
+    hd.smax[k] = w->kwall > 0 ? w->smax[k] : 0.0;
+  }
   for (int k = 0; k < d; ++k) {
     double sig = w->sigma[k];
     if (!(sig > 0) || !std::isfinite(sig)) return sfail(ABP_ERR_INVALID_ARG, "abp_step_static: sigma must be > 0");

@@ -214,3 +214,43 @@ def test_unsupported_combinations_are_reported(abp, ctx):
     with pytest.raises(abp.AbpError) as e:
         ctx.make_walkers([bad])
     assert e.value.code == abp.ABP_ERR_INVALID_ARG
+
+
+def test_range_limit_wall_in_every_form(abp, ctx):
+    """The CV range limit (harmonic wall above smax) on the windowed form
+    (COM distance + dihedral, WT and mABP) and the per-step form (CN), with
+    limits the trajectories cross, against the oracle."""
+    specs = synth.mb64_specs(nw=4, stride=5)
+    specs = [dict(sp, hill=synth.with_wall(sp["hill"], [1.0, 1.5], 30.0)) for sp in specs]
+    specs += [dict(sp, hill=synth.with_wall(sp["hill"], [1.1, 0.0], 10.0))
+              for sp in _mabp(synth.mb64_specs(nw=2, stride=2), a_bins=6.0, c=0.1, stride=2)]
+    frames = synth.SweepFrames(6, seed=13, period=(100, 200)).frames(0, 120)
+    walkers = ctx.make_walkers(specs)
+    abp.abp_deposit_log_enable(ctx.handle, 1 << 16)
+    Fg = gpu_replay(abp, ctx, walkers, frames, 0, chunks=2)
+    _, ref = oracle_replay(specs, frames, 0)
+    assert np.any(ref["s"][:, :4, 0] > 1.0) and np.any(ref["s"][:, :4, 0] < 1.0)
+    off = synth.offsets_of(specs)
+    log = abp.abp_deposit_log_readout(ctx.handle, 1 << 20)
+    ids = {w.id: i for i, w in enumerate(walkers)}
+    ties = P.compare_deposits(specs, log, ref["deposits"], ids)
+    for i, sp in enumerate(specs):
+        if i in ties:
+            continue
+        sl = slice(off[i], off[i] + sp["natoms"])
+        keep = ~_lookup_tie_steps(sp, ref["s"][:, i]) if i >= 4 else np.ones(len(frames), bool)
+        assert P.force_err(Fg[keep][:, sl], ref["F"][keep][:, sl]) < P.TOL_F, i
+    cn = [dict(sp, hill=synth.with_wall(sp["hill"], [0.9, 300.0, 300.0][: len(sp["grid"]["n"])], 20.0))
+          for sp in synth.uneven1000_specs(seed=7, nw=4, stride=3, sizes_2d=(48,), n1d=200, n3d=20)]
+    tm = synth.uneven1000_templates(7, nw=4)
+    cframes = synth.JitterFrames(tm, seed=8, jitter=0.05).frames(0, 30)
+    ctx2 = abp.Context(0)
+    try:
+        w2 = ctx2.make_walkers(cn)
+        F2 = gpu_replay(abp, ctx2, w2, cframes, 0)
+        _, r2 = oracle_replay(cn, cframes, 0)
+        assert np.any(r2["dV"] != 0)
+        assert P.force_err(F2, r2["F"]) < P.TOL_F
+    finally:
+        torch.cuda.synchronize()
+        ctx2.close()
