@@ -352,9 +352,125 @@ __device__ void cv_dihedral(const Grp &g, GroupFixed<Real> *fx, int k, const typ
 // A entries are read from shared memory in chunks of 4 and their gradients
 // are reduced over the warp, then summed over warps in a fixed order.
 // jA / jB receive ds/dx per list entry.
+// Coordination number for a group A of at most 4 * MAXA atoms, tiled over
+// the group's threads: lane & 3 picks one of four A-groups (A atoms i with
+// i % 4 == lane & 3, held in registers with their gradients) and t >> 2 one
+// of G/4 B-groups (B atoms j with j % (G/4) == t >> 2, streamed). Every pair
+// is evaluated once. A B atom's gradient is summed over its four A-groups by
+// two lane exchanges; A gradients over the B-groups once, at the end (lane
+// exchanges, then warps in index order). Four compensated chains per thread.
+template <typename Real, int MAXA>
+__device__ void cv_coord_tiled(const Grp &g, GroupFixed<Real> *fx, int k, const typename Rec4<Real>::T *xs,
+                               typename Rec4<Real>::T *jA, typename Rec4<Real>::T *jB, Real *lig) {
+  using R4 = typename Rec4<Real>::T;
+  const CvDev &c = fx->wd.cv[k];
+  const int32_t *ia = fx->ia[k], *ib = fx->ib[k];
+  const Real k2 = (Real)c.inv_r0sq;
+  const Real c6 = (Real)-6 * k2;
+  const bool pbc = c.pbc != 0;
+  const Real bx = (Real)c.box[0], by = (Real)c.box[1], bz = (Real)c.box[2];
+  const Real ibx = (Real)c.inv_box[0], iby = (Real)c.inv_box[1], ibz = (Real)c.inv_box[2];
+  const int ag = g.lane & 3, bgrp = g.t >> 2, nbg = g.G >> 2;
+  Real ax[MAXA], ay[MAXA], az[MAXA], gx[MAXA], gy[MAXA], gz[MAXA];
+#pragma unroll
+  for (int q = 0; q < MAXA; ++q) {
+    const int i = ag + 4 * q;
+    gx[q] = gy[q] = gz[q] = 0;
+    ax[q] = ay[q] = az[q] = 0;
+    if (i < c.na) {
+      const R4 p = xs[ia[i]];
+      ax[q] = p.x;
+      ay[q] = p.y;
+      az[q] = p.z;
+    }
+  }
+  Real sacc[4] = {0, 0, 0, 0}, scomp[4] = {0, 0, 0, 0};
+  // every lane runs the same number of B rounds (the lane exchanges need the
+  // whole warp); a lane past the end of B evaluates its last atom with weight 0
+  const int rounds = (c.nb + nbg - 1) / nbg;
+  for (int rj = 0; rj < rounds; ++rj) {
+    const int j = bgrp + rj * nbg;
+    const bool okj = j < c.nb;
+    const R4 p = xs[ib[okj ? j : c.nb - 1]];
+    Real gjx = 0, gjy = 0, gjz = 0;
+#pragma unroll
+    for (int q = 0; q < MAXA; ++q) {
+      const int i = ag + 4 * q;
+      if (4 * q < c.na) {  // uniform over the warp: the A-group rows in use
+        Real dx = ax[q] - p.x, dy = ay[q] - p.y, dz = az[q] - p.z;
+        if (pbc) {
+          dx = min_image(dx, bx, ibx);
+          dy = min_image(dy, by, iby);
+          dz = min_image(dz, bz, ibz);
+        }
+        const Real qq = (dx * dx + dy * dy + dz * dz) * k2;
+        const Real q2 = qq * qq;
+        const Real sw = rcp_fast<Real>((Real)1 + q2 * qq);
+        const Real m = (okj && i < c.na) ? (Real)1 : (Real)0;
+        Real tsum, terr;
+        two_sum<Real>(sacc[q & 3], m * sw, tsum, terr);
+        sacc[q & 3] = tsum;
+        scomp[q & 3] += terr;
+        const Real gf = c6 * m * q2 * sw * sw;
+        gx[q] += gf * dx;
+        gy[q] += gf * dy;
+        gz[q] += gf * dz;
+        gjx -= gf * dx;
+        gjy -= gf * dy;
+        gjz -= gf * dz;
+      }
+    }
+    gjx += __shfl_xor_sync(0xffffffffu, gjx, 1);
+    gjy += __shfl_xor_sync(0xffffffffu, gjy, 1);
+    gjz += __shfl_xor_sync(0xffffffffu, gjz, 1);
+    gjx += __shfl_xor_sync(0xffffffffu, gjx, 2);
+    gjy += __shfl_xor_sync(0xffffffffu, gjy, 2);
+    gjz += __shfl_xor_sync(0xffffffffu, gjz, 2);
+    if (ag == 0 && okj) jB[j] = make_rec<Real>(gjx, gjy, gjz, (Real)0);
+  }
+  // A gradients: over the warp's B-groups (lanes of one A-group), then warps
+  Real *mylig = lig + g.warp * c.na * 3;
+#pragma unroll
+  for (int q = 0; q < MAXA; ++q) {
+    if (4 * q < c.na) {
+      Real v[3] = {gx[q], gy[q], gz[q]};
+#pragma unroll
+      for (int e = 0; e < 3; ++e)
+        for (int o = 4; o < 32; o <<= 1) v[e] += __shfl_xor_sync(0xffffffffu, v[e], o);
+      const int i = ag + 4 * q;
+      if (g.lane < 4 && i < c.na)
+        for (int e = 0; e < 3; ++e) mylig[i * 3 + e] = v[e];
+    }
+  }
+  Real sh, sl;
+  two_sum<Real>(sacc[0], scomp[0], sh, sl);
+#pragma unroll
+  for (int jj = 1; jj < 4; ++jj) ff_add<Real>(sh, sl, sacc[jj], scomp[jj]);
+  grp_sum_ff<Real>(g, sh, sl, fx->red);
+  if (g.t == 0) {
+    fx->sh[k] = sh;
+    fx->sl[k] = sl;
+  }
+  g.sync();
+  for (int i = g.t; i < c.na; i += g.G) {
+    Real a0 = 0, a1 = 0, a2 = 0;
+    for (int w = 0; w < g.nwarps; ++w) {
+      const Real *L = lig + w * c.na * 3 + i * 3;
+      a0 += L[0];
+      a1 += L[1];
+      a2 += L[2];
+    }
+    jA[i] = make_rec<Real>(a0, a1, a2, (Real)0);
+  }
+}
+
 template <typename Real>
 __device__ void cv_coord(const Grp &g, GroupFixed<Real> *fx, int k, const typename Rec4<Real>::T *xs,
                          typename Rec4<Real>::T *jA, typename Rec4<Real>::T *jB, Real *lig) {
+  if (fx->wd.cv[k].na <= 4 * 10) {
+    cv_coord_tiled<Real, 10>(g, fx, k, xs, jA, jB, lig);
+    return;
+  }
   using R4 = typename Rec4<Real>::T;
   const CvDev &c = fx->wd.cv[k];
   const int32_t *ia = fx->ia[k], *ib = fx->ib[k];
