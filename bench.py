@@ -386,7 +386,8 @@ def bench_uneven(abp, synth, torch, dev, sm_mhz):
                 "value": nw * C / (ms / 1e3), "unit": "bias steps/s", "ms_per_launch": ms,
                 "tuned": tuned["best"],
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                             "frac": achieved / peak, "kernel": "k_run<float> (CN pairs)",
+                             "frac": achieved / peak, "kernel": "k_run / k_run_lean (per-step form, CN pairs)",
+                             "traffic": captured_traffic("k_run_uneven1000", nw * C),
                              "peak_source": f"derived: 152 SM x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz"}}
     finally:
         torch.cuda.synchronize()
