@@ -254,6 +254,18 @@ abp_status abp_bias_readout(abp_ctx *ctx, const abp_grid *grid, void *dst, int d
  * an FP64 source is split exactly into value + compensation on FP32_COMP
  * grids. Syncs. */
 abp_status abp_bias_upload(abp_ctx *ctx, abp_grid *grid, const void *src, int src_is_device, int dtype);
+
+/* Checkpoint and restart (not a paper operation: the bias is state a long
+ * run saves and reloads). abp_grid_save copies the grid's node records as
+ * stored (value and compensation words of FP32_COMP grids, then for a grid
+ * created with shared = 1 its FP64 accumulator shadow), abp_grid_record_bytes
+ * of them, to dst; abp_grid_restore writes such bytes back into a grid of
+ * the same description. A walker whose grid is restored resumes its run bit
+ * for bit (abp_bias_readout / abp_bias_upload go through FP64 values and
+ * agree only to rounding). Both sync. */
+size_t abp_grid_record_bytes(const abp_grid *grid);
+abp_status abp_grid_save(abp_ctx *ctx, const abp_grid *grid, void *dst, int dst_is_device);
+abp_status abp_grid_restore(abp_ctx *ctx, abp_grid *grid, const void *src, int src_is_device);
 /* s_t[3], V_b(s_t), dV_b/ds[3] and flags of the walker's last step. Syncs.
  * Returns ABP_ERR_NONFINITE if that step saw non-finite coordinates. */
 abp_status abp_walker_readout(abp_ctx *ctx, const abp_walker *walker, double *s, double *V, double *dV,

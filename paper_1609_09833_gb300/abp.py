@@ -98,6 +98,9 @@ _SIGS = {
                          C.POINTER(C.c_size_t)],
     "abp_grid_apply_hills": [_vp, _vp, _vp, C.c_size_t],
     "abp_shared_forces": [_vp, C.POINTER(_vp), C.c_int, _vp, C.c_int, _vp, C.c_int, C.c_int64],
+    "abp_grid_record_bytes": [_vp],
+    "abp_grid_save": [_vp, _vp, _vp, C.c_int],
+    "abp_grid_restore": [_vp, _vp, _vp, C.c_int],
     "abp_bias_readout": [_vp, _vp, _vp, C.c_int, C.c_int],
     "abp_bias_upload": [_vp, _vp, _vp, C.c_int, C.c_int],
     "abp_walker_readout": [_vp, _vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
@@ -144,6 +147,7 @@ def load():
             f.argtypes = args
             f.restype = None if name in _VOID else (C.c_char_p if name in _STR else C.c_int)
         L.abp_walker_id.restype = C.c_int32
+        L.abp_grid_record_bytes.restype = C.c_size_t
         L.abp_server_now.restype = C.c_double
         _lib_handle = L
     return _lib_handle
@@ -273,6 +277,24 @@ def abp_grid_apply_hills(ctx, shape_walker, hills: np.ndarray):
 def abp_shared_forces(ctx, walkers, forces, forces_dtype, force_offsets, mode, step: int):
     _check(load().abp_shared_forces(ctx, _walkers(walkers), len(walkers), _ptr(forces), forces_dtype,
                                     _ptr(force_offsets), int(mode), int(step)))
+
+
+def abp_grid_record_bytes(grid) -> int:
+    return int(load().abp_grid_record_bytes(grid))
+
+
+def abp_grid_save(ctx, grid) -> np.ndarray:
+    """The grid's raw node records (and shadow) as host bytes."""
+    out = np.zeros(abp_grid_record_bytes(grid), dtype=np.uint8)
+    _check(load().abp_grid_save(ctx, grid, out.ctypes.data, 0))
+    return out
+
+
+def abp_grid_restore(ctx, grid, data: np.ndarray):
+    data = np.ascontiguousarray(data, dtype=np.uint8)
+    if data.nbytes != abp_grid_record_bytes(grid):
+        raise ValueError("record bytes do not match the grid")
+    _check(load().abp_grid_restore(ctx, grid, data.ctypes.data, 0))
 
 
 def abp_bias_readout(ctx, grid, dst, dst_is_device: bool, dtype: int):

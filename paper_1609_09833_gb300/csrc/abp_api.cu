@@ -1170,6 +1170,34 @@ abp_status abp_shared_forces(abp_ctx *ctx, abp_walker *const *walkers, int n, vo
 
 // ---------------------------------------------------------------- readouts
 
+size_t abp_grid_record_bytes(const abp_grid *g) { return g ? g->bytes + g->shadow_bytes : 0; }
+
+abp_status abp_grid_save(abp_ctx *ctx, const abp_grid *g, void *dst, int dst_is_device) {
+  if (!ctx || !g || !dst || g->ctx != ctx) return fail(ABP_ERR_INVALID_ARG, "bad argument");
+  abp_status st = set_device(ctx);
+  if (st) return st;
+  const cudaMemcpyKind kind = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CUDA_TRY(cudaMemcpyAsync(dst, g->g.rec, g->bytes, kind, ctx->stream));
+  if (g->shadow_bytes)
+    CUDA_TRY(cudaMemcpyAsync(static_cast<unsigned char *>(dst) + g->bytes, g->g.shadow, g->shadow_bytes, kind,
+                             ctx->stream));
+  CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return ABP_OK;
+}
+
+abp_status abp_grid_restore(abp_ctx *ctx, abp_grid *g, const void *src, int src_is_device) {
+  if (!ctx || !g || !src || g->ctx != ctx) return fail(ABP_ERR_INVALID_ARG, "bad argument");
+  abp_status st = set_device(ctx);
+  if (st) return st;
+  const cudaMemcpyKind kind = src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CUDA_TRY(cudaMemcpyAsync(g->g.rec, src, g->bytes, kind, ctx->stream));
+  if (g->shadow_bytes)
+    CUDA_TRY(cudaMemcpyAsync(g->g.shadow, static_cast<const unsigned char *>(src) + g->bytes, g->shadow_bytes, kind,
+                             ctx->stream));
+  CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return ABP_OK;
+}
+
 abp_status abp_bias_readout(abp_ctx *ctx, const abp_grid *g, void *dst, int dst_is_device, int dtype) {
   if (!ctx || !g || !dst || g->ctx != ctx) return fail(ABP_ERR_INVALID_ARG, "bad argument");
   if (dtype != ABP_F32 && dtype != ABP_F64) return fail(ABP_ERR_INVALID_ARG, "bad dtype");

@@ -448,3 +448,70 @@ def test_full_size_64_walker_workload_sampled(abp, ctx):
         assert np.all(P.rel_field_err(ctx.bias(walkers[i]), ref["fields"][j]) < P.TOL_V)
         fe = P.force_err(Fg[:, off[i]:off[i] + 36], ref["F"][:, j * 36:(j + 1) * 36])
         assert np.all(fe < P.TOL_F)
+
+
+def test_all_steps_accumulated_into_one_force_buffer(abp, ctx):
+    """force_step_stride = 0 with ACCUMULATE: every step's force is added to
+    the same records, in step order (windowed form and per-step form)."""
+    for specs, frames in ((synth.mb64_specs(nw=3, stride=4), synth.SweepFrames(3, seed=14).frames(0, 45)),
+                          (synth.uneven1000_specs(seed=9, nw=3, stride=4, sizes_2d=(48,), n1d=200, n3d=20),
+                           synth.JitterFrames(synth.uneven1000_templates(9, nw=3), seed=10).frames(0, 12))):
+        wa = ctx.make_walkers(specs)
+        Fa = gpu_replay(abp, ctx, wa, frames, 0)  # one force record set per step
+        wb = ctx.make_walkers(specs)
+        rec = abp.to_records(frames).cuda()
+        A = rec.shape[1]
+        offs = torch.tensor(synth.offsets_of(specs), dtype=torch.int64, device="cuda")
+        base = torch.randn(A, 4, device="cuda")
+        F = base.clone()
+        abp.abp_run(ctx.handle, wb, rec, abp.ABP_F32, offs, A, F, offs, 0, abp.ABP_FORCES_ACCUMULATE, 0,
+                    frames.shape[0])
+        torch.cuda.synchronize()
+        want = base.cpu().numpy()[:, :3].astype(np.float64) + Fa.sum(axis=0)
+        np.testing.assert_allclose(F.cpu().numpy()[:, :3], want, rtol=1e-5, atol=1e-5 * np.abs(Fa).max())
+        for x, y in zip(wa, wb):
+            assert np.array_equal(ctx.bias(x), ctx.bias(y))
+
+
+def test_checkpoint_and_resume_is_bit_exact(abp, ctx):
+    """Save a walker's grid after step k (abp_grid_save), restore it into a
+    new walker (abp_grid_restore) and continue: the forces and the grid equal
+    an uninterrupted run bit for bit (a walker on its own grid; windowed and
+    per-step forms, mABP and WT). Through FP64 values (abp_bias_readout /
+    abp_bias_upload) the resumed run agrees to rounding."""
+    cases = (synth.mb64_specs(nw=2, stride=3),
+             [dict(sp, hill=synth.mabp_hill([synth.bins(sp["grid"], k, 6.0) for k in range(2)], 20, 0.9, 0.2,
+                                            stride=2)) for sp in synth.mb64_specs(nw=2)],
+             synth.uneven1000_specs(seed=4, nw=2, stride=3, sizes_2d=(48,), n1d=200, n3d=20))
+    for specs in cases:
+        if specs[0]["cvs"][-1]["type"] == "coord":
+            frames = synth.JitterFrames(synth.uneven1000_templates(4, nw=2), seed=5).frames(0, 30)
+        else:
+            frames = synth.SweepFrames(2, seed=15).frames(0, 30)
+        wa = ctx.make_walkers(specs)
+        Fa = gpu_replay(abp, ctx, wa, frames, 0)
+        k = 17
+        wb = ctx.make_walkers(specs)
+        gpu_replay(abp, ctx, wb, frames[:k], 0)
+        saved = [abp.abp_grid_save(ctx.handle, w.grid) for w in wb]
+        values = [ctx.bias(w) for w in wb]
+        wc = ctx.make_walkers(specs)
+        for w, g in zip(wc, saved):
+            abp.abp_grid_restore(ctx.handle, w.grid, g)
+        wv = ctx.make_walkers(specs)
+        for w, g in zip(wv, values):
+            ctx.upload_bias(w, g)
+        rec = abp.to_records(frames[k:]).cuda()
+        A = rec.shape[1]
+        offs = torch.tensor(synth.offsets_of(specs), dtype=torch.int64, device="cuda")
+        F = torch.zeros_like(rec)
+        Fv = torch.zeros_like(rec)
+        abp.abp_run(ctx.handle, wc, rec, abp.ABP_F32, offs, A, F, offs, A, abp.ABP_FORCES_OVERWRITE, k,
+                    frames.shape[0] - k)
+        abp.abp_run(ctx.handle, wv, rec, abp.ABP_F32, offs, A, Fv, offs, A, abp.ABP_FORCES_OVERWRITE, k,
+                    frames.shape[0] - k)
+        torch.cuda.synchronize()
+        assert np.array_equal(F.cpu().numpy()[..., :3].astype(np.float64), Fa[k:])
+        for x, y in zip(wa, wc):
+            assert np.array_equal(ctx.bias(x), ctx.bias(y))
+        assert P.force_err(Fv.cpu().numpy()[..., :3].astype(np.float64), Fa[k:]) < 1e-6
