@@ -385,39 +385,41 @@ __device__ void cv_coord_tiled(const Grp &g, GroupFixed<Real> *fx, int k, const 
     }
   }
   Real sacc[4] = {0, 0, 0, 0}, scomp[4] = {0, 0, 0, 0};
+  // rows of A atoms this lane holds (the last row may be short)
+  const int nrow = (c.na - ag + 3) >> 2;
   // every lane runs the same number of B rounds (the lane exchanges need the
-  // whole warp); a lane past the end of B evaluates its last atom with weight 0
+  // whole warp); in the last round a lane past the end of B skips the pairs
   const int rounds = (c.nb + nbg - 1) / nbg;
   for (int rj = 0; rj < rounds; ++rj) {
     const int j = bgrp + rj * nbg;
     const bool okj = j < c.nb;
-    const R4 p = xs[ib[okj ? j : c.nb - 1]];
     Real gjx = 0, gjy = 0, gjz = 0;
+    if (okj) {
+      const R4 p = xs[ib[j]];
 #pragma unroll
-    for (int q = 0; q < MAXA; ++q) {
-      const int i = ag + 4 * q;
-      if (4 * q < c.na) {  // uniform over the warp: the A-group rows in use
-        Real dx = ax[q] - p.x, dy = ay[q] - p.y, dz = az[q] - p.z;
-        if (pbc) {
-          dx = min_image(dx, bx, ibx);
-          dy = min_image(dy, by, iby);
-          dz = min_image(dz, bz, ibz);
+      for (int q = 0; q < MAXA; ++q) {
+        if (q < nrow) {
+          Real dx = ax[q] - p.x, dy = ay[q] - p.y, dz = az[q] - p.z;
+          if (pbc) {
+            dx = min_image(dx, bx, ibx);
+            dy = min_image(dy, by, iby);
+            dz = min_image(dz, bz, ibz);
+          }
+          const Real qq = (dx * dx + dy * dy + dz * dz) * k2;
+          const Real q2 = qq * qq;
+          const Real sw = rcp_fast<Real>((Real)1 + q2 * qq);
+          Real tsum, terr;
+          two_sum<Real>(sacc[q & 3], sw, tsum, terr);
+          sacc[q & 3] = tsum;
+          scomp[q & 3] += terr;
+          const Real gf = c6 * q2 * (sw * sw);
+          gx[q] += gf * dx;
+          gy[q] += gf * dy;
+          gz[q] += gf * dz;
+          gjx -= gf * dx;
+          gjy -= gf * dy;
+          gjz -= gf * dz;
         }
-        const Real qq = (dx * dx + dy * dy + dz * dz) * k2;
-        const Real q2 = qq * qq;
-        const Real sw = rcp_fast<Real>((Real)1 + q2 * qq);
-        const Real m = (okj && i < c.na) ? (Real)1 : (Real)0;
-        Real tsum, terr;
-        two_sum<Real>(sacc[q & 3], m * sw, tsum, terr);
-        sacc[q & 3] = tsum;
-        scomp[q & 3] += terr;
-        const Real gf = c6 * m * q2 * sw * sw;
-        gx[q] += gf * dx;
-        gy[q] += gf * dy;
-        gz[q] += gf * dz;
-        gjx -= gf * dx;
-        gjy -= gf * dy;
-        gjz -= gf * dz;
       }
     }
     gjx += __shfl_xor_sync(0xffffffffu, gjx, 1);
