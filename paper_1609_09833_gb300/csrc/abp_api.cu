@@ -61,7 +61,7 @@ struct abp_ctx {
   size_t used = 0;
   DevCounters *ctr = nullptr;
   DepositLog log{nullptr, nullptr, 0};
-  TableCache tables[4];
+  TableCache tables[6];
   unsigned long long use_clock = 0;
   int next_id = 0;
   int sms = 0;  // multiprocessors of the device
@@ -832,33 +832,35 @@ static abp_status run_common(abp_ctx *ctx, abp_walker *const *walkers, int n, co
     return fail(ABP_ERR_INVALID_ARG, "FP64 coordinate and force buffers must be 32-byte aligned");
   st = set_device(ctx);
   if (st) return st;
-  // three forms: windowed (k_win), per-step fused (k_run), phased (big)
-  std::vector<abp_walker *> ww, fw, bw;
-  std::vector<int> wi, fi, bi;
+  // three forms: windowed (k_win, one launch per grid dimension), per-step
+  // fused (k_run), phased (big)
+  std::vector<abp_walker *> ww[3], fw, bw;
+  std::vector<int> wi[3], fi, bi;
   for (int i = 0; i < n; ++i) {
     if (walkers[i]->big) {
       bw.push_back(walkers[i]);
       bi.push_back(i);
     } else if (walkers[i]->win) {
-      ww.push_back(walkers[i]);
-      wi.push_back(i);
+      ww[walkers[i]->hd.g.d - 1].push_back(walkers[i]);
+      wi[walkers[i]->hd.g.d - 1].push_back(i);
     } else {
       fw.push_back(walkers[i]);
       fi.push_back(i);
     }
   }
-  for (int form = 0; form < 2; ++form) {
-    std::vector<abp_walker *> &lw = form ? fw : ww;
-    std::vector<int> &li = form ? fi : wi;
+  for (int form = 0; form < 4; ++form) {  // windowed d = 1, 2, 3, then per-step
+    const bool win = form < 3;
+    std::vector<abp_walker *> &lw = win ? ww[form] : fw;
+    std::vector<int> &li = win ? wi[form] : fi;
     if (lw.empty()) continue;
     RunArgs a{};
     if ((st = sub_table(ctx, lw, li, &a.table))) return st;
-    if ((st = pick_shape(ctx, lw.data(), (int)lw.size(), fp64, nsteps, form == 0, &a.G, &a.groups_per_cta,
+    if ((st = pick_shape(ctx, lw.data(), (int)lw.size(), fp64, nsteps, win, &a.G, &a.groups_per_cta,
                          &a.group_bytes, &a.tile_budget)))
       return st;
-    a.window = form == 0;
+    a.window = win ? form + 1 : 0;
     a.nw = (int)lw.size();
-    a.lean = ctx->tune_lean && !fp64 && form == 1;
+    a.lean = ctx->tune_lean && !fp64 && !win;
     a.coords = coords;
     a.coff = reinterpret_cast<const long long *>(coff);
     a.cstride = cstride;

@@ -136,6 +136,7 @@ constexpr int kWinMax = 32;             // MD steps per window of the windowed f
 constexpr int kAtomTerms = 2 * kMaxCv;  // per atom: up to 2 list entries per CV
 constexpr int kMabpBoxBytes = 96 * 1024;  // windowed mABP: the union of a window's stencil boxes, at most
 constexpr int kWinBytes = 64 * 1024;    // its coordinate double buffer, at most
+constexpr int kWtBoxBytes = 64 * 1024;  // windowed WT: a deposit's stencil box, at most
 
 // Steps per window for a walker in the windowed form (0: not eligible). The
 // form takes walkers whose CVs are all COM distances, dihedrals or RMSDs of at
@@ -166,10 +167,12 @@ __host__ __device__ inline int window_steps(int natoms, const CvDev *cv, int d, 
 //   lists     per-CV atom index lists (+ COM weights)
 //   cn        per COORD CV: dCN/dx per list entry and per-warp partials
 //   tile      optional copy of a box of the walker's grid (node records); in
-//             the windowed form of an mABP walker, the window's stencil boxes
+//             the windowed form, a deposit's stencil box (WT walkers whose box
+//             fits kWtBoxBytes) or the union of a window's boxes (mABP)
 struct GroupLayout {
   int xs0, xs1, fs, steps, atoms, lists, cn, tile, total;
   int win, xstride;  // windowed form: steps per window (0 = per-step form), row stride in records
+  int box;           // windowed form: bytes of the stencil-box region at `tile` (0: none)
   int T[3];          // tile nodes per axis (all 0 = no tile)
   int tile_nodes;
 };
@@ -237,10 +240,18 @@ __host__ __device__ inline GroupLayout group_layout(int natoms, const CvDev *cv,
     if (cv[k].type == ABP_CV_COORD) off += (cv[k].na + cv[k].nb) * rsz + align32(nwarps * cv[k].na * 3 * real);
   off = align32(off);
   L.tile = off;
+  L.box = 0;
   if (L.win) {
     for (int k = 0; k < 3; ++k) L.T[k] = 0;
     L.tile_nodes = 0;
-    if (mabp) off += kMabpBoxBytes;
+    if (mabp) {
+      L.box = kMabpBoxBytes;
+    } else {
+      long long nodes = 1;
+      for (int k = 0; k < g.d; ++k) nodes *= 2 * R[k] + 1;
+      if (nodes * g.rec_bytes <= kWtBoxBytes) L.box = (int)(nodes * g.rec_bytes);
+    }
+    off += align16(L.box);
     L.total = align32(off);
     return L;
   }

@@ -348,50 +348,113 @@ __device__ __forceinline__ void finish_lookup(const WalkerDev &wd, StepRec<Real>
     }
 }
 
+// A node record as two 16-byte halves: both for the 32-byte records of a
+// 2D or 3D grid, the first for the 16-byte records of a 1D grid.
+template <int DIM>
+__device__ __forceinline__ void rec_load(const unsigned char *p, float4 &a, float4 &b) {
+  const float4 *q = reinterpret_cast<const float4 *>(p);
+  a = q[0];
+  b = DIM > 1 ? q[1] : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// The 1 + d values of a record held in registers, formed as rec_values forms
+// them from memory: an FP32 grid (Real = float) holds value + compensation
+// per field, an FP64 grid (Real = double) the values.
+template <typename Real, int DIM, typename Acc>
+__device__ __forceinline__ void rec_vals(const float4 &a, const float4 &b, Acc *v) {
+  if constexpr (sizeof(Real) == 4) {
+    if constexpr (DIM == 1) {
+      v[0] = (Acc)a.x + (Acc)a.z;
+      v[1] = (Acc)a.y + (Acc)a.w;
+    } else {
+      v[0] = (Acc)a.x + (Acc)b.x;
+      v[1] = (Acc)a.y + (Acc)b.y;
+      v[2] = (Acc)a.z + (Acc)b.z;
+      if (DIM > 2) v[3] = (Acc)a.w + (Acc)b.w;
+    }
+  } else {
+    union U {
+      float4 f;
+      double2 v;
+    };
+    U ua, ub;
+    ua.f = a;
+    ub.f = b;
+    v[0] = (Acc)ua.v.x;
+    v[1] = (Acc)ua.v.y;
+    if (DIM > 1) v[2] = (Acc)ub.v.x;
+    if (DIM > 2) v[3] = (Acc)ub.v.y;
+  }
+}
+
+// Grid node of corner c of a step (bit k of c selects i1 on axis k).
+template <typename Real, int DIM>
+__device__ __forceinline__ long long corner_node(const GridDev &gd, const StepRec<Real> &st, int c) {
+  long long node = 0, mul = 1;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    node += mul * (((c >> k) & 1) ? st.i1[k] : st.i0[k]);
+    mul *= gd.n[k];
+  }
+  return node;
+}
+
+// Multilinear weight of corner c.
+template <typename Real, int DIM>
+__device__ __forceinline__ Real corner_weight(const StepRec<Real> &st, int c) {
+  Real wc = 1;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) wc *= ((c >> k) & 1) ? st.f[k] : (Real)1 - st.f[k];
+  return wc;
+}
+
+template <int DIM>
+__device__ __forceinline__ const unsigned char *node_ptr(const GridDev &gd, long long node) {
+  return reinterpret_cast<const unsigned char *>(gd.rec) + node * (DIM > 1 ? 32 : 16);
+}
+
+// a4 of one step, part 1: the 2^d corners' records, loaded together.
+template <typename Real, int DIM>
+__device__ __forceinline__ void interp_load(const WalkerDev &wd, const StepRec<Real> &st, float4 *ca, float4 *cb) {
+#pragma unroll
+  for (int c = 0; c < (1 << DIM); ++c) rec_load<DIM>(node_ptr<DIM>(wd.g, corner_node<Real, DIM>(wd.g, st, c)), ca[c], cb[c]);
+}
+
+// a4 of one step, part 2: the corners combined in corner order.
+template <typename Real, int DIM>
+__device__ __forceinline__ void interp_combine(const WalkerDev &wd, StepRec<Real> &st, const float4 *ca,
+                                               const float4 *cb) {
+  Real acc[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int c = 0; c < (1 << DIM); ++c) {
+    const Real wc = corner_weight<Real, DIM>(st, c);
+    Real v[4];
+    rec_vals<Real, DIM>(ca[c], cb[c], v);
+#pragma unroll
+    for (int q = 0; q <= DIM; ++q) acc[q] += wc * v[q];
+  }
+  finish_lookup<Real>(wd, st, acc);
+}
+
 // a4 of one step: the 2^d corners' records loaded together, then combined in
 // corner order.
-template <typename Real>
+template <typename Real, int DIM>
 __device__ __forceinline__ void interp_one(const WalkerDev &wd, StepRec<Real> &st) {
-  const GridDev &gd = wd.g;
-  const int d = gd.d, nc = 1 << d;
-  const unsigned char *rec = reinterpret_cast<const unsigned char *>(gd.rec);
-  Real f[3] = {0, 0, 0};
-  int i0[3] = {0, 0, 0}, i1[3] = {0, 0, 0};
+  constexpr int NC = 1 << DIM;
+  Real v[NC][4];
 #pragma unroll
-  for (int k = 0; k < 3; ++k)
-    if (k < d) {
-      f[k] = st.f[k];
-      i0[k] = st.i0[k];
-      i1[k] = st.i1[k];
-    }
-  Real v[8][4];
-  Real w[8];
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    w[c] = 0;
-    v[c][0] = v[c][1] = v[c][2] = v[c][3] = 0;
-    if (c < nc) {
-      Real wc = 1;
-      long long node = 0, mul = 1;
-#pragma unroll
-      for (int k = 0; k < 3; ++k)
-        if (k < d) {
-          const bool hi = (c >> k) & 1;
-          wc *= hi ? f[k] : (Real)1 - f[k];
-          node += mul * (hi ? i1[k] : i0[k]);
-          mul *= gd.n[k];
-        }
-      w[c] = wc;
-      rec_values<Real>(gd, rec + node * gd.rec_bytes, v[c]);
-    }
+  for (int c = 0; c < NC; ++c) {
+    float4 a, b;
+    rec_load<DIM>(node_ptr<DIM>(wd.g, corner_node<Real, DIM>(wd.g, st, c)), a, b);
+    rec_vals<Real, DIM>(a, b, v[c]);
   }
   Real acc[4] = {0, 0, 0, 0};
 #pragma unroll
-  for (int c = 0; c < 8; ++c)
-    if (c < nc) {
+  for (int c = 0; c < NC; ++c) {
+    const Real wc = corner_weight<Real, DIM>(st, c);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] += w[c] * v[c][q];
-    }
+    for (int q = 0; q <= DIM; ++q) acc[q] += wc * v[c][q];
+  }
   finish_lookup<Real>(wd, st, acc);
 }
 
@@ -453,34 +516,13 @@ __device__ __forceinline__ void window_cv(const GroupFixed<Real> *fx, const type
   st.cfl[k] = fl | (ax.clamped << 16);
 }
 
-// a2 of a window deposit, by one thread: V_b(s_t) from the grid before the
-// deposit in FP64 (the 2^d corners' value fields, combined pairwise in corner
-// order), the height h = w exp(-V / dT), and the deposit log record.
+// a2's end: V_b(s_t) from the corner terms t (pairwise, in corner order), the
+// height, and the deposit log record.
 template <typename Real>
-__device__ void window_height(GroupFixed<Real> *fx, const StepRec<Real> &st, long long step, const DepositLog &log) {
+__device__ __forceinline__ void window_height_out(GroupFixed<Real> *fx, const StepRec<Real> &st, const double *t,
+                                                  long long step, const DepositLog &log) {
   const WalkerDev &wd = fx->wd;
-  const GridDev &gd = wd.g;
-  const int d = gd.d, nc = wd.method == ABP_METHOD_MABP ? 0 : 1 << d;  // mABP hills: fixed height w
-  const unsigned char *rec = reinterpret_cast<const unsigned char *>(gd.rec);
-  double t[8];
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    t[c] = 0;
-    if (c < nc) {
-      double w = 1;
-      long long node = 0, mul = 1;
-      for (int k = 0; k < d; ++k) {
-        const bool hi = (c >> k) & 1;
-        const double f = (double)st.f[k];
-        w *= hi ? f : 1.0 - f;
-        node += mul * (hi ? st.i1[k] : st.i0[k]);
-        mul *= gd.n[k];
-      }
-      double v[4];
-      rec_values<double>(gd, rec + node * gd.rec_bytes, v);
-      t[c] = w * v[0];
-    }
-  }
+  const int d = wd.g.d, nc = wd.method == ABP_METHOD_MABP ? 0 : 1 << d;
   const double V0 = ((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7]));
   const double h = nc ? wd.w * exp(-V0 * wd.inv_dT) : wd.w;
   fx->hV = V0;
@@ -499,6 +541,41 @@ __device__ void window_height(GroupFixed<Real> *fx, const StepRec<Real> &st, lon
       log.rec[slot] = r;
     }
   }
+}
+
+// a2 of a window deposit, by one thread, from the deposit step's 2^d corner
+// records before the deposit: V_b(s_t) in FP64 (the corners' value fields,
+// combined pairwise in corner order), the height h = w exp(-V / dT), and the
+// deposit log record.
+template <typename Real, int DIM>
+__device__ __forceinline__ void window_height_regs(GroupFixed<Real> *fx, const StepRec<Real> &st, const float4 *ca,
+                                                   const float4 *cb, long long step, const DepositLog &log) {
+  const bool wt = fx->wd.method != ABP_METHOD_MABP;  // mABP hills: fixed height w
+  double t[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    t[c] = 0;
+    if (c < (1 << DIM) && wt) {
+      double w = 1;
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) {
+        const double f = (double)st.f[k];
+        w *= ((c >> k) & 1) ? f : 1.0 - f;
+      }
+      double v[4];
+      rec_vals<Real, DIM>(ca[c], cb[c], v);
+      t[c] = w * v[0];
+    }
+  }
+  window_height_out<Real>(fx, st, t, step, log);
+}
+
+// a2 of a window deposit, reading the corners from the grid.
+template <typename Real, int DIM>
+__device__ void window_height(GroupFixed<Real> *fx, const StepRec<Real> &st, long long step, const DepositLog &log) {
+  float4 ca[1 << DIM], cb[1 << DIM];
+  if (fx->wd.method != ABP_METHOD_MABP) interp_load<Real, DIM>(fx->wd, st, ca, cb);
+  window_height_regs<Real, DIM>(fx, st, ca, cb, step, log);
 }
 
 // The deposit's axis state into the group's fixed state (threads k < d), for
@@ -618,6 +695,30 @@ __device__ __forceinline__ unsigned window_dmask(long long step0, int t0, int nt
   return m;
 }
 
+// Grid byte offset of node (b0 + o0, b1 + o1) of a stencil box whose first
+// node is (b0, b1) (unwrapped; one wrap on a periodic axis), or -1 where it
+// falls outside a non-periodic axis.
+template <int DIM>
+__device__ __forceinline__ long long box_node_off(const GridDev &gd, int b0, int b1, int o0, int o1, int rb) {
+  int j0 = b0 + o0, j1 = b1 + o1;
+  bool in = true;
+  if (gd.periodic[0]) {
+    if (j0 < 0) j0 += gd.n[0];
+    if (j0 >= gd.n[0]) j0 -= gd.n[0];
+  } else {
+    in = j0 >= 0 && j0 < gd.n[0];
+  }
+  if (DIM > 1) {
+    if (gd.periodic[1]) {
+      if (j1 < 0) j1 += gd.n[1];
+      if (j1 >= gd.n[1]) j1 -= gd.n[1];
+    } else {
+      in = in && j1 >= 0 && j1 < gd.n[1];
+    }
+  }
+  return in ? (j0 + (DIM > 1 ? (long long)gd.n[0] * j1 : 0)) * rb : -1;
+}
+
 // Phases of one window, each run by a (sub)group `g` that ends synchronised.
 template <typename Real>
 struct WindowCtx {
@@ -638,7 +739,7 @@ struct WindowCtx {
   int W, nwin, mode;
   bool serial_out;
   unsigned long long stream;
-  unsigned char *box;    // mABP: the union of a window's stencil boxes (NULL: not staged)
+  unsigned char *box;    // a deposit's stencil box (WT) or the union of a window's boxes (mABP); NULL: none
 
   __device__ __forceinline__ int nt_of(int w) const { return min(W, nsteps - w * W); }
   __device__ __forceinline__ StepRec<Real> *steps_of(int w) const { return steps + (w % 3) * W; }
@@ -703,13 +804,112 @@ struct WindowCtx {
   // a2 .. a4 of window w on the grid: deposits in step order, each preceded
   // by a4 of the steps before it; the first deposit's tables and height are
   // formed while the steps before it interpolate (same grid for both)
-  template <int UNR>
+  template <int UNR, int DIM>
   __device__ __forceinline__ void chain(const Grp &g, int w) const {
-    if (fx->wd.method == ABP_METHOD_MABP && box) {
-      const int d = fx->wd.g.d;
-      if (d == 1 ? chain_mabp<1>(g, w) : d == 2 ? chain_mabp<2>(g, w) : chain_mabp<3>(g, w)) return;
+    if (fx->wd.method == ABP_METHOD_MABP) {
+      if (box && chain_mabp<DIM>(g, w)) return;
+    } else if constexpr (DIM < 3) {
+      if (box && chain_one<DIM>(g, w)) return;
     }
-    chain_seq<UNR>(g, w);
+    chain_seq<UNR, DIM>(g, w);
+  }
+
+  // A well-tempered window with exactly one deposit whose stencil box has at
+  // most one node per thread: every grid read of the window in one round --
+  // each step's 2^d corners into registers, the deposit's box into shared
+  // memory by cp.async -- all from the grid before the deposit. The deposit
+  // step's corners give the height (a2); the box is updated from shared
+  // memory and stored to the grid (a3); steps before the deposit interpolate
+  // their corners as read, steps from it on after applying the deposit to
+  // the corners inside its box, with the same arithmetic as the stored nodes
+  // (the same bits as reading them back). Returns false (nothing done) for
+  // any other window. (Larger boxes go through chain_seq: measured faster,
+  // the per-thread copies then cost more than the round trips they save.)
+  template <int DIM>
+  __device__ bool chain_one(const Grp &g, int w) const {
+    static_assert(DIM <= 2, "one-round chain: 1D and 2D grids");
+    const WalkerDev &wd = fx->wd;
+    const GridDev &gd = wd.g;
+    constexpr int d = DIM, NC = 1 << DIM;
+    constexpr int rb = DIM > 1 ? 32 : 16;  // node record bytes
+    const int nt = nt_of(w), t0 = w * W;
+    StepRec<Real> *st = steps_of(w);
+    const unsigned bad = fx->winbad[w % 3];
+    const unsigned gdep = window_dmask(step0, t0, nt, wd.stride) & ~bad;
+    if (__popc(gdep) != 1) return false;
+    const int first = __ffs(gdep) - 1;
+    const int s0 = 2 * wd.R[0] + 1, s1 = d > 1 ? 2 * wd.R[1] + 1 : 1;
+    if (s0 * s1 > g.G) return false;
+    // first node of the box per axis (unwrapped: the node below u, plus the
+    // centre offset, minus R)
+    const int b0 = st[first].da[0] + st[first].dc[0] - wd.R[0];
+    const int b1 = d > 1 ? st[first].da[1] + st[first].dc[1] - wd.R[1] : 0;
+    window_dep_axis<Real>(g, fx, st[first]);
+    unsigned char *grid = reinterpret_cast<unsigned char *>(gd.rec);
+    // the round: the box (node o0 + s0 o1 at that record of `box`) ...
+    for (Iter2 it(g.t, g.G, s0); it.j < s1; it.next()) {
+      const long long off = box_node_off<DIM>(gd, b0, b1, it.i, it.j, rb);
+      if (off < 0) continue;
+      unsigned char *dst = box + (size_t)(it.i + s0 * it.j) * rb;
+      cp_async16(dst, grid + off);
+      if (rb == 32) cp_async16(dst + 16, grid + off + 16);
+    }
+    cp_async_commit();
+    // ... and the corners of this thread's step
+    const int jstep = g.t;
+    const bool mine = jstep < nt && !((bad >> jstep) & 1);
+    float4 ca[NC], cb[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) ca[c] = cb[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (mine) interp_load<Real, DIM>(wd, st[jstep], ca, cb);
+    g.sync();  // the deposit's axis state
+    build_tables<Real>(g, fx);
+    if (jstep == first) window_height_regs<Real, DIM>(fx, st[first], ca, cb, step0 + t0 + first, log);
+    cp_async_wait_all();
+    g.sync();  // tables, height and box
+    const Real h = fx->hf;
+    for (Iter2 it(g.t, g.G, s0); it.j < s1; it.next()) {
+      const int o0 = it.i, o1 = it.j;
+      const long long off = box_node_off<DIM>(gd, b0, b1, o0, o1, rb);
+      if (off < 0) continue;
+      const unsigned sa = (unsigned)__cvta_generic_to_shared(box + (size_t)(o0 + s0 * o1) * rb);
+      float4 ra = lds128(sa), rbv = rb == 32 ? lds128(sa + 16) : make_float4(0.f, 0.f, 0.f, 0.f);
+      Real G = h * fx->tabG[0][o0];
+      if (d > 1) G = G * fx->tabG[1][o1];
+      rmw_regs<Real>(d, ra, rbv, G, fx->tabD[0][o0], d > 1 ? fx->tabD[1][o1] : (Real)0, (Real)0);
+      float4 *q = reinterpret_cast<float4 *>(grid + off);
+      q[0] = ra;
+      if (rb == 32) q[1] = rbv;
+    }
+    if (mine) {
+      StepRec<Real> &sj = st[jstep];
+      if (jstep >= first) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          int o[2] = {0, 0};
+          bool in = true;
+#pragma unroll
+          for (int k = 0; k < d; ++k) {
+            const int n = gd.n[k];
+            int r = (((c >> k) & 1) ? sj.i1[k] : sj.i0[k]) - (k ? b1 : b0);
+            if (gd.periodic[k]) {
+              if (r < 0) r += n;
+              if (r >= n) r -= n;
+            }
+            in = in && r >= 0 && r <= 2 * wd.R[k];
+            o[k] = r;
+          }
+          if (!in) continue;
+          Real G = h * fx->tabG[0][o[0]];
+          if (d > 1) G = G * fx->tabG[1][o[1]];
+          rmw_regs<Real>(d, ca[c], cb[c], G, fx->tabD[0][o[0]], d > 1 ? fx->tabD[1][o[1]] : (Real)0, (Real)0);
+        }
+      }
+      interp_combine<Real, DIM>(wd, sj, ca, cb);
+    }
+    g.sync();
+    if (w + 1 == nwin && g.t == 0) write_state(st, nt, bad);
+    return true;
   }
 
   // mABP: the window's deposits through shared memory. Every hill has the
@@ -779,7 +979,9 @@ struct WindowCtx {
     // raw histograms of a step's node, kept in V / dv until the window's end
     auto raw_copy = [&](StepRec<Real> &s, const unsigned char *p) {
       Real v[4] = {0, 0, 0, 0};
-      rec_values<Real>(gd, p, v);
+      float4 ra, rbv;
+      rec_load<DIM>(p, ra, rbv);
+      rec_vals<Real, DIM>(ra, rbv, v);
       s.V = v[0];
       for (int k = 0; k < 3; ++k) s.dv[k] = v[1 + k];
     };
@@ -818,7 +1020,7 @@ struct WindowCtx {
       if (rb == 32) dst[1] = src[1];
     }
     for (int j = g.t; j < nt; j += g.G)
-      if (!((bad >> j) & 1) && !((inbox >> j) & 1)) interp_one<Real>(wd, st[j]);
+      if (!((bad >> j) & 1) && !((inbox >> j) & 1)) interp_one<Real, DIM>(wd, st[j]);
     g.sync();
     for (int j = g.t; j < first; j += g.G)
       if ((inbox >> j) & 1) raw_copy(st[j], box + (size_t)box_index(st[j].da) * rb);
@@ -874,7 +1076,7 @@ struct WindowCtx {
         // the hill's own step reads its centre right after it
         if (centre_in && o0 == wd.R[0] && (d < 2 || o1 == wd.R[1]) && (d < 3 || o2 == wd.R[2])) raw_copy(st[j], p);
       }
-      if (g.t == g.G - 1 && log.rec) window_height<Real>(fx, st[j], step0 + t0 + j, log);
+      if (g.t == g.G - 1 && log.rec) window_height<Real, DIM>(fx, st[j], step0 + t0 + j, log);
       if (next > j + 1) {  // steps between this hill and the next read after it
         g.sync();
         for (int q = j + 1 + g.t; q < next; q += g.G)
@@ -919,7 +1121,7 @@ struct WindowCtx {
     }
   }
 
-  template <int UNR>
+  template <int UNR, int DIM>
   __device__ __forceinline__ void chain_seq(const Grp &g, int w) const {
     const WalkerDev &wd = fx->wd;
     const int nt = nt_of(w), t0 = w * W;
@@ -932,10 +1134,10 @@ struct WindowCtx {
       g.sync();
     }
     for (int j = g.t; j < first; j += g.G)
-      if (!((bad >> j) & 1)) interp_one<Real>(wd, st[j]);
+      if (!((bad >> j) & 1)) interp_one<Real, DIM>(wd, st[j]);
     if (gdep) {
       build_tables<Real>(g, fx);
-      if (g.t == g.G - 1) window_height<Real>(fx, st[first], step0 + t0 + first, log);
+      if (g.t == g.G - 1) window_height<Real, DIM>(fx, st[first], step0 + t0 + first, log);
     }
     g.sync();
     int seg = first;
@@ -943,11 +1145,11 @@ struct WindowCtx {
       const int j = __ffs(m) - 1;
       if (j != first) {
         for (int q = seg + g.t; q < j; q += g.G)
-          if (!((bad >> q) & 1)) interp_one<Real>(wd, st[q]);
+          if (!((bad >> q) & 1)) interp_one<Real, DIM>(wd, st[q]);
         window_dep_axis<Real>(g, fx, st[j]);
         g.sync();
         build_tables<Real>(g, fx);
-        if (g.t == g.G - 1) window_height<Real>(fx, st[j], step0 + t0 + j, log);
+        if (g.t == g.G - 1) window_height<Real, DIM>(fx, st[j], step0 + t0 + j, log);
         g.sync();
       }
       deposit_stencil<Real, false, UNR>(g, fx, L, nullptr);
@@ -955,7 +1157,7 @@ struct WindowCtx {
       seg = j;
     }
     for (int q = seg + g.t; q < nt; q += g.G)
-      if (!((bad >> q) & 1)) interp_one<Real>(wd, st[q]);
+      if (!((bad >> q) & 1)) interp_one<Real, DIM>(wd, st[q]);
     g.sync();
     if (w + 1 == nwin && g.t == 0) write_state(st, nt, bad);
   }
@@ -992,15 +1194,15 @@ struct WindowCtx {
   }
 };
 
-// The windowed form's driver. Iteration w runs A of window w + 1 and C of
-// window w - 1 (grid-independent) beside the grid chain of window w; the
-// three touch different StepRec arrays. A group of two or more warps splits
-// in halves on their own named barriers, the first half taking A and C (and
-// the coordinate copies), the second the chain; a one-warp group runs the
-// three in turn.
-template <typename Real, int UNR>
-__device__ void walker_window(const Grp &g, GroupFixed<Real> *fx, unsigned char *dyn, const GroupLayout &L,
-                              const RunArgs &a, int widx) {
+// The windowed form's driver. Iteration w runs A of window w + 1 beside the
+// grid chain of window w and C of window w - 1; the three touch different
+// StepRec arrays. A group of two or more warps splits in halves on their own
+// named barriers, the first half taking A (and the coordinate copies), the
+// second the chain, then C (the chain waits on grid reads, A on shared
+// memory); a one-warp group runs the three in turn.
+template <typename Real, int UNR, int DIM>
+__device__ __forceinline__ void walker_window(const Grp &g, GroupFixed<Real> *fx, unsigned char *dyn,
+                                              const GroupLayout &L, const RunArgs &a, int widx) {
   using R4 = typename Rec4<Real>::T;
   WindowCtx<Real> c;
   c.fx = fx;
@@ -1027,7 +1229,7 @@ __device__ void walker_window(const Grp &g, GroupFixed<Real> *fx, unsigned char 
   c.mode = a.forces ? a.mode : ABP_FORCES_OVERWRITE;
   c.serial_out = a.forces && a.fstride == 0;
   c.stream = l2_evict_first();
-  c.box = fx->wd.method == ABP_METHOD_MABP ? dyn + L.tile : nullptr;
+  c.box = L.box ? dyn + L.tile : nullptr;
   // the two halves (or the whole warp twice)
   const bool split = g.G >= 64;
   Grp gx = g, gy = g;
@@ -1039,7 +1241,7 @@ __device__ void walker_window(const Grp &g, GroupFixed<Real> *fx, unsigned char 
     gy.t = g.t - gx.G;
     gy.warp = g.warp - gx.nwarps;
   }
-  const bool isx = !split || g.t < g.G / 2, isy = !split || !isx;
+  const bool isx = !split || g.t < g.G / 2;
   build_atom_terms<Real>(g, fx, c.cnt, c.terms);
   if (isx) {
     c.prefetch(gx, 0);
@@ -1052,18 +1254,28 @@ __device__ void walker_window(const Grp &g, GroupFixed<Real> *fx, unsigned char 
     c.cvs(gx, 0);
   }
   g.sync();
-  for (int w = 0; w <= c.nwin; ++w) {
-    if (isx) {
+  // each half in a loop of its own (one g.sync per iteration in both), so
+  // that each keeps only its own state live
+  if (isx) {
+    for (int w = 0; w <= c.nwin; ++w) {
       if (w + 1 < c.nwin) {
         cp_async_wait_all();  // window w + 1's coordinates
         gx.sync();
         if (w + 2 < c.nwin) c.prefetch(gx, w + 2);  // into the buffer window w used
         c.cvs(gx, w + 1);
       }
-      if (w >= 1) c.forces(gx, w - 1);
+      if (!split) {
+        if (w < c.nwin) c.template chain<UNR, DIM>(gy, w);
+        if (w >= 1) c.forces(gy, w - 1);
+      }
+      g.sync();
     }
-    if (isy && w < c.nwin) c.template chain<UNR>(gy, w);
-    g.sync();
+  } else {
+    for (int w = 0; w <= c.nwin; ++w) {
+      if (w < c.nwin) c.template chain<UNR, DIM>(gy, w);
+      if (w >= 1) c.forces(gy, w - 1);
+      g.sync();
+    }
   }
 }
 
@@ -1105,9 +1317,10 @@ __global__ void __launch_bounds__(256, 1) k_run(RunArgs a) {
 // walkers are busy in long CN pair loops. Chosen by ABP_TUNE_LEAN.
 __global__ void __launch_bounds__(256, 2) k_run_lean(RunArgs a) { run_body<float, false>(a); }
 
-// The windowed form (walkers whose CVs are COM distances and dihedrals), in
-// its own kernel: its code alone fills the instruction cache.
-template <typename Real, int UNR>
+// The windowed form (walkers whose CVs are COM distances, dihedrals or small
+// RMSDs), in kernels of its own, one per grid dimension DIM: each keeps only
+// its own code in the instruction cache.
+template <typename Real, int UNR, int DIM>
 __global__ void __launch_bounds__(256, 1) k_win(RunArgs a) {
   extern __shared__ __align__(32) unsigned char smem[];
   const int gid = threadIdx.x / a.G;
@@ -1127,10 +1340,10 @@ __global__ void __launch_bounds__(256, 1) k_win(RunArgs a) {
   copy_desc<Real>(g, &fx->wd, te.wd);
   g.sync();
   const GroupLayout L = layout_of<Real>(fx, g.nwarps, 0, true);
-  if (L.win == 0) return;  // the host sends only eligible walkers here
+  if (L.win == 0 || fx->wd.g.d != DIM) return;  // the host sends only eligible walkers of DIM CVs here
   setup_lists<Real>(g, fx, dyn + L.lists);
   g.sync();
-  walker_window<Real, UNR>(g, fx, dyn, L, a, te.idx);
+  walker_window<Real, UNR, DIM>(g, fx, dyn, L, a, te.idx);
 }
 
 cudaError_t launch_run(const RunArgs &a, int fp64, cudaStream_t st) {
@@ -1140,15 +1353,14 @@ cudaError_t launch_run(const RunArgs &a, int fp64, cudaStream_t st) {
   if (a.nw == 0) return cudaSuccess;
   cudaError_t e;
   if (a.window) {
-    if (fp64) {
-      e = cudaFuncSetAttribute(k_win<double, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      k_win<double, 8><<<blocks, threads, smem, st>>>(a);
-    } else {
-      e = cudaFuncSetAttribute(k_win<float, 13>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      k_win<float, 13><<<blocks, threads, smem, st>>>(a);
-    }
+    void (*k)(RunArgs);
+    if (fp64)
+      k = a.window == 1 ? k_win<double, 8, 1> : a.window == 2 ? k_win<double, 8, 2> : k_win<double, 8, 3>;
+    else
+      k = a.window == 1 ? k_win<float, 13, 1> : a.window == 2 ? k_win<float, 13, 2> : k_win<float, 13, 3>;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<blocks, threads, smem, st>>>(a);
     return cudaGetLastError();
   }
   if (fp64) {

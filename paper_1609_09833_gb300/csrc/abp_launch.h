@@ -34,7 +34,7 @@ struct RunArgs {
   int nsteps;
   int tile_budget;     // >0: dynamic shared bytes per group, the rest of which holds a grid tile
   int lean;            // use the 128-register instantiation (FP32, no tile)
-  int window;          // every walker runs in the windowed form (k_win)
+  int window;          // d > 0: every walker has d CVs and runs in the windowed form (k_win)
   DepositLog log;
   DevCounters *ctr;
 };
