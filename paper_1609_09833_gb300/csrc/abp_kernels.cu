@@ -286,42 +286,69 @@ struct Iter2 {
   }
 };
 
+// Rounded arithmetic with no contraction left to the compiler, so that every
+// inlined copy of a CV computes the same bits.
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// One group's part of a COM distance: the group's first atom r0 and the
+// weighted offsets of its atoms from r0, summed in list order.
+template <typename Real>
+__device__ __forceinline__ void com_sum(const int32_t *list, const Real *wts, int n,
+                                        const typename Rec4<Real>::T *x, Real *r0, Real *acc) {
+  const auto p0 = x[list[0]];
+  Real a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll 4
+  for (int i = 0; i < n; ++i) {
+    Real w = wts[i];
+    auto p = x[list[i]];
+    a0 = fma_rn(w, sub_rn(p.x, p0.x), a0);
+    a1 = fma_rn(w, sub_rn(p.y, p0.y), a1);
+    a2 = fma_rn(w, sub_rn(p.z, p0.z), a2);
+  }
+  r0[0] = p0.x;
+  r0[1] = p0.y;
+  r0[2] = p0.z;
+  acc[0] = a0;
+  acc[1] = a1;
+  acc[2] = a2;
+}
+
+// The end of a COM distance from the two groups' parts: s = |R_B - R_A|
+// (minimum image in a periodic box) and u = d / s.
+template <typename Real>
+__device__ __forceinline__ int com_finish(const CvDev &c, const Real *ra, const Real *a, const Real *rb,
+                                          const Real *b, Real &s, Real *u) {
+  Real d[3];
+  for (int q = 0; q < 3; ++q) d[q] = add_rn(sub_rn(rb[q], ra[q]), sub_rn(b[q], a[q]));
+  if (c.pbc)
+    for (int q = 0; q < 3; ++q) d[q] = min_image(d[q], c.box[q], c.inv_box[q]);
+  Real r = sqrt(fma_rn(d[2], d[2], fma_rn(d[1], d[1], mul_rn(d[0], d[0]))));
+  s = r;
+  if (r > 0) {
+    Real ir = rcp_fast<Real>(r);
+    for (int q = 0; q < 3; ++q) u[q] = mul_rn(d[q], ir);
+    return 0;
+  }
+  for (int q = 0; q < 3; ++q) u[q] = 0;
+  return ABP_WFLAG_SINGULAR;
+}
+
 // COM distance of one step by one thread: each group's weighted offsets from
 // its first atom summed in list order, then s = |R_B - R_A| and u = d / s.
 template <typename Real>
 __device__ __forceinline__ int com_thread(const CvDev &c, const int32_t *ia, const int32_t *ib, const Real *wa,
                                           const Real *wb, const typename Rec4<Real>::T *x, Real &s, Real *u) {
-  const auto ra = x[ia[0]];
-  const auto rb = x[ib[0]];
-  Real a0 = 0, a1 = 0, a2 = 0, b0 = 0, b1 = 0, b2 = 0;
-#pragma unroll 4
-  for (int i = 0; i < c.na; ++i) {
-    Real w = wa[i];
-    auto p = x[ia[i]];
-    a0 += w * (p.x - ra.x);
-    a1 += w * (p.y - ra.y);
-    a2 += w * (p.z - ra.z);
-  }
-#pragma unroll 4
-  for (int i = 0; i < c.nb; ++i) {
-    Real w = wb[i];
-    auto p = x[ib[i]];
-    b0 += w * (p.x - rb.x);
-    b1 += w * (p.y - rb.y);
-    b2 += w * (p.z - rb.z);
-  }
-  Real d[3] = {(rb.x - ra.x) + (b0 - a0), (rb.y - ra.y) + (b1 - a1), (rb.z - ra.z) + (b2 - a2)};
-  if (c.pbc)
-    for (int q = 0; q < 3; ++q) d[q] = min_image(d[q], c.box[q], c.inv_box[q]);
-  Real r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-  s = r;
-  if (r > 0) {
-    Real ir = rcp_fast<Real>(r);
-    for (int q = 0; q < 3; ++q) u[q] = d[q] * ir;
-    return 0;
-  }
-  for (int q = 0; q < 3; ++q) u[q] = 0;
-  return ABP_WFLAG_SINGULAR;
+  Real ra[3], a[3], rb[3], b[3];
+  com_sum<Real>(ia, wa, c.na, x, ra, a);
+  com_sum<Real>(ib, wb, c.nb, x, rb, b);
+  return com_finish<Real>(c, ra, a, rb, b, s, u);
 }
 
 // The end of a4 for one step: V and dV/dxi from the interpolated fields (for
@@ -489,6 +516,22 @@ __device__ __forceinline__ int rmsd_thread(const CvDev &c, const int32_t *ia, co
   return 0;
 }
 
+// The step record's CV k: the value, flags and axis state.
+template <typename Real>
+__device__ __forceinline__ void window_cv_rec(const WalkerDev &wd, int k, Real sk, int fl, bool dep,
+                                              StepRec<Real> &st) {
+  st.s[k] = sk;
+  AxisSt<Real> ax = axis_state<Real>(wd, k, sk, (Real)0, dep);
+  st.i0[k] = ax.i0;
+  st.i1[k] = ax.i1;
+  st.f[k] = ax.f;
+  st.da[k] = ax.da;
+  st.dc[k] = ax.dc;
+  st.df[k] = ax.df;
+  st.ic_log[k] = ax.ic_log;
+  st.cfl[k] = fl | (ax.clamped << 16);
+}
+
 // Phase A task: CV k of one step (row x of the window), its Jacobian
 // factors and axis state.
 template <typename Real>
@@ -504,16 +547,33 @@ __device__ __forceinline__ void window_cv(const GroupFixed<Real> *fx, const type
     fl = dihedral_eval<Real>(c, fx->ia[k], x, sk, reinterpret_cast<Real(*)[3]>(st.jac[k]));
   else
     fl = rmsd_thread<Real>(c, fx->ia[k], x, sk, st.jac[k]);
-  st.s[k] = sk;
-  AxisSt<Real> ax = axis_state<Real>(wd, k, sk, (Real)0, dep);
-  st.i0[k] = ax.i0;
-  st.i1[k] = ax.i1;
-  st.f[k] = ax.f;
-  st.da[k] = ax.da;
-  st.dc[k] = ax.dc;
-  st.df[k] = ax.df;
-  st.ic_log[k] = ax.ic_log;
-  st.cfl[k] = fl | (ax.clamped << 16);
+  window_cv_rec<Real>(wd, k, sk, fl, dep, st);
+}
+
+// A COM-distance task of the windowed form on two lanes (2i: group A, 2i + 1:
+// group B, the same sums as com_thread's), finished by the even lane. Every
+// lane of the warp calls it (the odd lanes' parts travel by shuffle); `live`
+// is false on lanes past the window's steps.
+template <typename Real>
+__device__ __forceinline__ void window_com2(const GroupFixed<Real> *fx, const typename Rec4<Real>::T *x, int k,
+                                            bool dep, bool live, bool odd, StepRec<Real> &st) {
+  const WalkerDev &wd = fx->wd;
+  const CvDev &c = wd.cv[k];
+  Real r0[3], acc[3];
+  if (odd)
+    com_sum<Real>(fx->ib[k], fx->wb[k], c.nb, x, r0, acc);
+  else
+    com_sum<Real>(fx->ia[k], fx->wa[k], c.na, x, r0, acc);
+  Real o0[3], oa[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    o0[q] = __shfl_xor_sync(0xffffffffu, r0[q], 1);
+    oa[q] = __shfl_xor_sync(0xffffffffu, acc[q], 1);
+  }
+  if (odd || !live) return;
+  Real sk;
+  const int fl = com_finish<Real>(c, r0, acc, o0, oa, sk, st.jac[k]);
+  window_cv_rec<Real>(wd, k, sk, fl, dep, st);
 }
 
 // a2's end: V_b(s_t) from the corner terms t (pairwise, in corner order), the
@@ -758,19 +818,29 @@ struct WindowCtx {
     cp_async_commit();
   }
 
-  // A: non-finite check, then a1 and the axis state, one thread per (CV, step)
+  // A: a1 and the axis state, one thread per (CV, step) -- two for a COM
+  // distance, one per atom group -- and the non-finite check, on the threads
+  // the tasks leave free while they run, else before them. (A step's CVs are
+  // evaluated either way; those of a non-finite step are not used.)
   __device__ __forceinline__ void cvs(const Grp &g, int w) const {
     const WalkerDev &wd = fx->wd;
     const int nt = nt_of(w), natoms = wd.natoms, d = wd.g.d;
     const R4 *xs = xb[w & 1];
     StepRec<Real> *st = steps_of(w);
     unsigned *badp = &fx->winbad[w % 3];
+    const unsigned dmask = window_dmask(step0, w * W, nt, wd.stride);
+    // first thread of each CV's tasks (whole warps per CV)
+    int base[kMaxCv + 1];
+    base[0] = 0;
+    for (int k = 0; k < d; ++k) base[k + 1] = base[k] + align32((wd.cv[k].type == ABP_CV_COM_DIST ? 2 : 1) * nt);
+    const int ntask = base[d];
+    const bool overlap = ntask < g.G;
     if (g.t == 0) *badp = 0;
     g.sync();
-    {
-      // a mask per thread, OR-ed over the warp, one shared-memory OR per warp
+    // a mask per thread, OR-ed over the warp, one shared-memory OR per warp
+    auto finite = [&](int t, int T) {
       unsigned mine = 0;
-      Iter2 it(g.t, g.G, natoms);
+      Iter2 it(t, T, natoms);
       while (it.j < nt) {
         R4 p[4];
         int jj[4];
@@ -788,14 +858,28 @@ struct WindowCtx {
       }
       mine = __reduce_or_sync(0xffffffffu, mine);
       if (g.lane == 0 && mine) atomicOr(badp, mine);
+    };
+    if (!overlap) {
+      finite(g.t, g.G);
+      g.sync();
+      for (Iter2 it(g.t, g.G, nt); it.j < d; it.next())
+        window_cv<Real>(fx, xs + it.i * xst, it.j, (dmask >> it.i) & 1, st[it.i]);
+    } else if (g.t < ntask) {
+      int k = 0;
+      while (k + 1 < d && g.t >= base[k + 1]) ++k;
+      const int r = g.t - base[k];
+      if (wd.cv[k].type == ABP_CV_COM_DIST) {
+        const int j = min(r >> 1, nt - 1);
+        window_com2<Real>(fx, xs + j * xst, k, (dmask >> j) & 1, (r >> 1) < nt, r & 1, st[j]);
+      } else if (r < nt) {
+        window_cv<Real>(fx, xs + r * xst, k, (dmask >> r) & 1, st[r]);
+      }
+    } else {
+      finite(g.t - ntask, g.G - ntask);
     }
     g.sync();
     const unsigned bad = *badp;
     if (g.t == 0 && bad) atomicAdd(&ctr->nonfinite, __popc(bad));
-    const unsigned dmask = window_dmask(step0, w * W, nt, wd.stride);
-    for (Iter2 it(g.t, g.G, nt); it.j < d; it.next())
-      if (!((bad >> it.i) & 1)) window_cv<Real>(fx, xs + it.i * xst, it.j, (dmask >> it.i) & 1, st[it.i]);
-    g.sync();
     for (int j = g.t; j < nt; j += g.G)
       if (!((bad >> j) & 1)) step_flags<Real>(d, (dmask >> j) & 1, st[j]);
     g.sync();
@@ -1194,12 +1278,12 @@ struct WindowCtx {
   }
 };
 
-// The windowed form's driver. Iteration w runs A of window w + 1 beside the
-// grid chain of window w and C of window w - 1; the three touch different
-// StepRec arrays. A group of two or more warps splits in halves on their own
-// named barriers, the first half taking A (and the coordinate copies), the
-// second the chain, then C (the chain waits on grid reads, A on shared
-// memory); a one-warp group runs the three in turn.
+// The windowed form's driver. Iteration w runs A of window w + 1 and C of
+// window w - 1 (grid-independent) beside the grid chain of window w; the
+// three touch different StepRec arrays. A group of two or more warps splits
+// in halves on their own named barriers, the first half taking A and C (and
+// the coordinate copies), the second the chain; a one-warp group runs the
+// three in turn.
 template <typename Real, int UNR, int DIM>
 __device__ __forceinline__ void walker_window(const Grp &g, GroupFixed<Real> *fx, unsigned char *dyn,
                                               const GroupLayout &L, const RunArgs &a, int widx) {
@@ -1241,41 +1325,24 @@ __device__ __forceinline__ void walker_window(const Grp &g, GroupFixed<Real> *fx
     gy.t = g.t - gx.G;
     gy.warp = g.warp - gx.nwarps;
   }
-  const bool isx = !split || g.t < g.G / 2;
+  const bool isx = !split || g.t < g.G / 2, isy = !split || !isx;
   build_atom_terms<Real>(g, fx, c.cnt, c.terms);
-  if (isx) {
-    c.prefetch(gx, 0);
-    if (c.nwin > 1) c.prefetch(gx, 1);
-    if (c.nwin > 1)
-      asm volatile("cp.async.wait_group 1;" ::: "memory");
-    else
-      cp_async_wait_all();
-    gx.sync();
-    c.cvs(gx, 0);
-  }
-  g.sync();
-  // each half in a loop of its own (one g.sync per iteration in both), so
-  // that each keeps only its own state live
-  if (isx) {
-    for (int w = 0; w <= c.nwin; ++w) {
+  // Each phase has one call site, so that one copy of its code computes
+  // every window's steps (the same bits whichever window a step falls in).
+  // Iteration -1 only evaluates window 0's CVs.
+  if (isx) c.prefetch(gx, 0);
+  for (int w = -1; w <= c.nwin; ++w) {
+    if (isx) {
       if (w + 1 < c.nwin) {
         cp_async_wait_all();  // window w + 1's coordinates
         gx.sync();
         if (w + 2 < c.nwin) c.prefetch(gx, w + 2);  // into the buffer window w used
         c.cvs(gx, w + 1);
       }
-      if (!split) {
-        if (w < c.nwin) c.template chain<UNR, DIM>(gy, w);
-        if (w >= 1) c.forces(gy, w - 1);
-      }
-      g.sync();
+      if (w >= 1) c.forces(gx, w - 1);
     }
-  } else {
-    for (int w = 0; w <= c.nwin; ++w) {
-      if (w < c.nwin) c.template chain<UNR, DIM>(gy, w);
-      if (w >= 1) c.forces(gy, w - 1);
-      g.sync();
-    }
+    if (isy && w >= 0 && w < c.nwin) c.template chain<UNR, DIM>(gy, w);
+    g.sync();
   }
 }
 
