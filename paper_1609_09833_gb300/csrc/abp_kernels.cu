@@ -1424,7 +1424,7 @@ cudaError_t launch_run(const RunArgs &a, int fp64, cudaStream_t st) {
     if (fp64)
       k = a.window == 1 ? k_win<double, 8, 1> : a.window == 2 ? k_win<double, 8, 2> : k_win<double, 8, 3>;
     else
-      k = a.window == 1 ? k_win<float, 13, 1> : a.window == 2 ? k_win<float, 13, 2> : k_win<float, 13, 3>;
+      k = a.window == 1 ? k_win<float, 7, 1> : a.window == 2 ? k_win<float, 7, 2> : k_win<float, 7, 3>;
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<blocks, threads, smem, st>>>(a);
