@@ -779,6 +779,16 @@ __device__ __forceinline__ long long box_node_off(const GridDev &gd, int b0, int
   return in ? (j0 + (DIM > 1 ? (long long)gd.n[0] * j1 : 0)) * rb : -1;
 }
 
+// Named barrier `id` of `n` threads: arrive without waiting (after this
+// thread's shared-memory writes), or wait for the phase to complete.
+__device__ __forceinline__ void bar_arrive(int id, int n) {
+  __threadfence_block();
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void bar_wait(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
 // Phases of one window, each run by a (sub)group `g` that ends synchronised.
 template <typename Real>
 struct WindowCtx {
@@ -1329,7 +1339,49 @@ __device__ __forceinline__ void walker_window(const Grp &g, GroupFixed<Real> *fx
   build_atom_terms<Real>(g, fx, c.cnt, c.terms);
   // Each phase has one call site, so that one copy of its code computes
   // every window's steps (the same bits whichever window a step falls in).
-  // Iteration -1 only evaluates window 0's CVs.
+  if (split && a.groups_per_cta == 1) {
+    // The halves decoupled: A hands window i to the chain through barrier
+    // FULL[i % 3] (A arrives, the chain waits), the chain hands it back for
+    // C through DONE[i % 3]; A runs up to two windows ahead of C, so a
+    // window whose chain is long (a deposit) and one whose A is long even
+    // out. (The three StepRec slots are free again by the time A reuses
+    // them: A has waited on DONE for window i - 3 and run its C.)
+    // FP64 walkers: A's FP64 arithmetic is the long half, so the chain half
+    // runs C (measured on the one-walker FP64 workload; FP32 the other way)
+    constexpr bool kCForChain = sizeof(Real) == 8;
+    const int full0 = 3 * a.groups_per_cta + 1, done0 = full0 + 3;
+    if (isx) {
+      c.prefetch(gx, 0);
+      if (c.nwin > 1) c.prefetch(gx, 1);
+      for (int i = 0; i < c.nwin + 2; ++i) {
+        if (i < c.nwin) {
+          // window i's coordinates (window i + 1's may still be in flight)
+          if (i + 1 < c.nwin)
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+          else
+            cp_async_wait_all();
+          gx.sync();
+          c.cvs(gx, i);
+          if (i + 2 < c.nwin) c.prefetch(gx, i + 2);  // into window i's buffer, read by now
+          bar_arrive(full0 + i % 3, g.G);
+        }
+        if (i >= 2) {
+          bar_wait(done0 + (i - 2) % 3, g.G);
+          if (!kCForChain) c.forces(gx, i - 2);
+        }
+      }
+    } else {
+      for (int w = 0; w < c.nwin; ++w) {
+        bar_wait(full0 + w % 3, g.G);
+        c.template chain<UNR, DIM>(gy, w);
+        if (kCForChain) c.forces(gy, w);
+        bar_arrive(done0 + w % 3, g.G);
+      }
+    }
+    return;
+  }
+  // Lockstep: iteration w runs A of window w + 1 and C of window w - 1
+  // beside the chain of window w; iteration -1 only evaluates window 0's CVs.
   if (isx) c.prefetch(gx, 0);
   for (int w = -1; w <= c.nwin; ++w) {
     if (isx) {
@@ -1422,7 +1474,7 @@ cudaError_t launch_run(const RunArgs &a, int fp64, cudaStream_t st) {
   if (a.window) {
     void (*k)(RunArgs);
     if (fp64)
-      k = a.window == 1 ? k_win<double, 8, 1> : a.window == 2 ? k_win<double, 8, 2> : k_win<double, 8, 3>;
+      k = a.window == 1 ? k_win<double, 4, 1> : a.window == 2 ? k_win<double, 4, 2> : k_win<double, 4, 3>;
     else
       k = a.window == 1 ? k_win<float, 7, 1> : a.window == 2 ? k_win<float, 7, 2> : k_win<float, 7, 3>;
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
