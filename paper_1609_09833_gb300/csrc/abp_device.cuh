@@ -384,7 +384,9 @@ __device__ void cv_coord_tiled(const Grp &g, GroupFixed<Real> *fx, int k, const 
       az[q] = p.z;
     }
   }
-  Real sacc[4] = {0, 0, 0, 0}, scomp[4] = {0, 0, 0, 0};
+  // s: each B round's switch values summed in A order, the round's sum then
+  // added to a compensated (two-sum) accumulator
+  Real sacc = 0, scomp = 0;
   // rows of A atoms this lane holds (the last row may be short)
   const int nrow = (c.na - ag + 3) >> 2;
   // every lane runs the same number of B rounds (the lane exchanges need the
@@ -396,6 +398,7 @@ __device__ void cv_coord_tiled(const Grp &g, GroupFixed<Real> *fx, int k, const 
     Real gjx = 0, gjy = 0, gjz = 0;
     if (okj) {
       const R4 p = xs[ib[j]];
+      Real part = 0;
 #pragma unroll
       for (int q = 0; q < MAXA; ++q) {
         if (q < nrow) {
@@ -408,10 +411,7 @@ __device__ void cv_coord_tiled(const Grp &g, GroupFixed<Real> *fx, int k, const 
           const Real qq = (dx * dx + dy * dy + dz * dz) * k2;
           const Real q2 = qq * qq;
           const Real sw = rcp_fast<Real>((Real)1 + q2 * qq);
-          Real tsum, terr;
-          two_sum<Real>(sacc[q & 3], sw, tsum, terr);
-          sacc[q & 3] = tsum;
-          scomp[q & 3] += terr;
+          part += sw;
           const Real gf = c6 * q2 * (sw * sw);
           gx[q] += gf * dx;
           gy[q] += gf * dy;
@@ -421,6 +421,10 @@ __device__ void cv_coord_tiled(const Grp &g, GroupFixed<Real> *fx, int k, const 
           gjz -= gf * dz;
         }
       }
+      Real tsum, terr;
+      two_sum<Real>(sacc, part, tsum, terr);
+      sacc = tsum;
+      scomp += terr;
     }
     gjx += __shfl_xor_sync(0xffffffffu, gjx, 1);
     gjy += __shfl_xor_sync(0xffffffffu, gjy, 1);
@@ -445,9 +449,7 @@ __device__ void cv_coord_tiled(const Grp &g, GroupFixed<Real> *fx, int k, const 
     }
   }
   Real sh, sl;
-  two_sum<Real>(sacc[0], scomp[0], sh, sl);
-#pragma unroll
-  for (int jj = 1; jj < 4; ++jj) ff_add<Real>(sh, sl, sacc[jj], scomp[jj]);
+  two_sum<Real>(sacc, scomp, sh, sl);
   grp_sum_ff<Real>(g, sh, sl, fx->red);
   if (g.t == 0) {
     fx->sh[k] = sh;
