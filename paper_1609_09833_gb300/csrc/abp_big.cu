@@ -123,12 +123,14 @@ __global__ void __launch_bounds__(kBigThreads) k_big_cn(const BigItem *items, co
     mj[jj] = ok ? 1.f : 0.f;
     gxj[jj] = gyj[jj] = gzj[jj] = 0.f;
   }
-  float sacc[kBigJB], scomp[kBigJB];  // compensated (two-sum per term), one chain per B entry
-#pragma unroll
-  for (int jj = 0; jj < kBigJB; ++jj) sacc[jj] = scomp[jj] = 0.f;
+  // the thread's CN terms: each block of 4 A atoms x kBigJB B entries summed
+  // in (A, B) order, the block's sum added to a compensated (two-sum)
+  // accumulator
+  float sacc = 0.f, scomp = 0.f;
   float *mylig = lig + warp * na * 3;
   for (int i0 = 0; i0 < na; i0 += 4) {
     float gi[4][3];
+    float part = 0.f;
 #pragma unroll
     for (int ii = 0; ii < 4; ++ii) {
       gi[ii][0] = gi[ii][1] = gi[ii][2] = 0.f;
@@ -147,10 +149,7 @@ __global__ void __launch_bounds__(kBigThreads) k_big_cn(const BigItem *items, co
         float q2 = q * q;
         float sw = __fdividef(1.f, 1.f + q2 * q);
         float m = oki ? mj[jj] : 0.f;
-        float term = m * sw, tsum, terr;
-        two_sum<float>(sacc[jj], term, tsum, terr);
-        sacc[jj] = tsum;
-        scomp[jj] += terr;
+        part += m * sw;
         float gf = c6 * m * q2 * sw * sw;
         gi[ii][0] += gf * dx;
         gi[ii][1] += gf * dy;
@@ -159,6 +158,12 @@ __global__ void __launch_bounds__(kBigThreads) k_big_cn(const BigItem *items, co
         gyj[jj] -= gf * dy;
         gzj[jj] -= gf * dz;
       }
+    }
+    {
+      float tsum, terr;
+      two_sum<float>(sacc, part, tsum, terr);
+      sacc = tsum;
+      scomp += terr;
     }
 #pragma unroll
     for (int ii = 0; ii < 4; ++ii)
@@ -180,9 +185,7 @@ __global__ void __launch_bounds__(kBigThreads) k_big_cn(const BigItem *items, co
   }
   // this chunk's CN as hi + lo: warps in order, lanes by butterfly
   float sh, sl;
-  two_sum<float>(sacc[0], scomp[0], sh, sl);
-#pragma unroll
-  for (int jj = 1; jj < kBigJB; ++jj) ff_add<float>(sh, sl, sacc[jj], scomp[jj]);
+  two_sum<float>(sacc, scomp, sh, sl);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     float oh = __shfl_xor_sync(0xffffffffu, sh, o), ol = __shfl_xor_sync(0xffffffffu, sl, o);
