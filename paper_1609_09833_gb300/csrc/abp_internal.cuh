@@ -167,8 +167,9 @@ __host__ __device__ inline int window_steps(int natoms, const CvDev *cv, int d, 
 //   lists     per-CV atom index lists (+ COM weights)
 //   cn        per COORD CV: dCN/dx per list entry and per-warp partials
 //   tile      optional copy of a box of the walker's grid (node records); in
-//             the windowed form, a deposit's stencil box (WT walkers whose box
-//             fits kWtBoxBytes) or the union of a window's boxes (mABP)
+//             the windowed form, a deposit's stencil box (WT walkers of 1 or 2
+//             CVs whose box has at most one node per chain-half thread) or
+//             the union of a window's boxes (mABP)
 struct GroupLayout {
   int xs0, xs1, fs, steps, atoms, lists, cn, tile, total;
   int win, xstride;  // windowed form: steps per window (0 = per-step form), row stride in records
@@ -247,9 +248,13 @@ __host__ __device__ inline GroupLayout group_layout(int natoms, const CvDev *cv,
     if (mabp) {
       L.box = kMabpBoxBytes;
     } else {
+      // only a box the chain half can hold one node per thread of
+      // (the window's single-round chain); larger boxes go round by round
       long long nodes = 1;
       for (int k = 0; k < g.d; ++k) nodes *= 2 * R[k] + 1;
-      if (nodes * g.rec_bytes <= kWtBoxBytes) L.box = (int)(nodes * g.rec_bytes);
+      const int chain_threads = nwarps >= 2 ? nwarps * 16 : 32;
+      if (g.d < 3 && nodes <= chain_threads && nodes * g.rec_bytes <= kWtBoxBytes)
+        L.box = (int)(nodes * g.rec_bytes);
     }
     off += align16(L.box);
     L.total = align32(off);

@@ -515,3 +515,42 @@ def test_checkpoint_and_resume_is_bit_exact(abp, ctx):
         for x, y in zip(wa, wc):
             assert np.array_equal(ctx.bias(x), ctx.bias(y))
         assert P.force_err(Fv.cpu().numpy()[..., :3].astype(np.float64), Fa[k:]) < 1e-6
+
+
+@pytest.mark.parametrize("kind", ["wt", "mabp", "fp64"])
+def test_windowed_launch_shapes_give_the_same_bits(abp, ctx, kind):
+    """The windowed form's result does not depend on its launch shape: one
+    256-thread group per CTA (CV and chain halves decoupled by named
+    barriers), two 128-thread groups per CTA (lockstep halves), 64-thread
+    groups and one-warp groups (the three phases in turn) give the same
+    forces and grids, over calls of several windows."""
+    from tests.test_mabp_gpu import _mabp
+
+    dtype = np.float32
+    if kind == "fp64":
+        specs = [synth.double_well_com_spec(stride=7)] * 3
+        x0 = synth.double_well_com_coords(5)
+        frames = x0[None] + np.cumsum(synth.rng(6).normal(scale=0.03, size=(150, 16, 3)), axis=0)
+        frames = np.concatenate([frames + 0.1 * i for i in range(3)], axis=1)
+        dtype = np.float64
+    else:
+        specs = synth.mb64_specs(nw=4, stride=9)
+        if kind == "mabp":
+            specs = _mabp(specs, a_bins=8.0, c=0.2, stride=3)
+        frames = synth.SweepFrames(4, seed=12, period=(100, 200)).frames(0, 150)
+    runs = []
+    for G, gpc in ((256, 1), (128, 2), (64, 1), (32, 4)):
+        abp.abp_ctx_tune(ctx.handle, abp.ABP_TUNE_GROUP_THREADS, G)
+        abp.abp_ctx_tune(ctx.handle, abp.ABP_TUNE_GROUPS_PER_CTA, gpc)
+        prec = abp.ABP_PREC_FP64 if kind == "fp64" else abp.ABP_PREC_FP32_COMP
+        w = ctx.make_walkers(specs, precision=prec)
+        F = gpu_replay(abp, ctx, w, frames, 0, chunks=2, dtype=dtype)
+        runs.append((G, gpc, F, [ctx.bias(x) for x in w]))
+    abp.abp_ctx_tune(ctx.handle, abp.ABP_TUNE_GROUP_THREADS, 0)
+    abp.abp_ctx_tune(ctx.handle, abp.ABP_TUNE_GROUPS_PER_CTA, 0)
+    G0, p0, F0, B0 = runs[0]
+    assert np.count_nonzero(F0) > 0
+    for G, gpc, F, B in runs[1:]:
+        assert np.array_equal(F, F0), (G, gpc, np.argwhere(F != F0)[:3])
+        for a, b in zip(B, B0):
+            assert np.array_equal(a, b), (G, gpc)
