@@ -59,7 +59,7 @@ typedef int abp_status;
 #define ABP_ERR_ADMISSION (-4)    /* the allocation would exceed the context's HBM budget */
 #define ABP_ERR_NONFINITE (-5)    /* non-finite coordinates were seen; those walkers were left unchanged */
 #define ABP_ERR_TIMEOUT (-6)      /* a bounded device or host wait ran out */
-#define ABP_ERR_UNSUPPORTED (-7)  /* a combination this build does not implement */
+#define ABP_ERR_UNSUPPORTED (-7)  /* a combination the library does not implement */
 
 /* CV types (step a1). */
 #define ABP_CV_COM_DIST 0 /* |R_B - R_A|, R_G the mass-weighted centre of group G */
@@ -123,7 +123,7 @@ typedef struct {
   const double *mass_a;  /* COM masses (NULL = unit masses); ignored otherwise */
   const double *mass_b;
   double r0;             /* COORD switching radius (nm) */
-  int nn, mm;            /* COORD exponents; this build supports nn = 6, mm = 12 */
+  int nn, mm;            /* COORD exponents; nn = 6, mm = 12 are supported */
   int pbc;               /* minimum image on difference vectors (orthorhombic box) */
   double box[3];
   const double *ref;     /* RMSD: reference positions of the atoms idx_a, 3 n_a values (host) */

@@ -492,7 +492,7 @@ abp_status build_cv(abp_walker *w, const abp_cv_desc &c, int k, int natoms, CvDe
       cv.nb = 0;
       break;
     case ABP_CV_RMSD:
-      if (c.n_a < 1 || c.n_a > 4) return fail(ABP_ERR_UNSUPPORTED, "CV %d: this build takes RMSDs of 1 to 4 atoms", k);
+      if (c.n_a < 1 || c.n_a > 4) return fail(ABP_ERR_UNSUPPORTED, "CV %d: RMSDs of 1 to 4 atoms are supported", k);
       if (!c.ref) return fail(ABP_ERR_INVALID_ARG, "CV %d: an RMSD needs reference positions", k);
       for (int i = 0; i < 3 * c.n_a; ++i)
         if (!std::isfinite(c.ref[i])) return fail(ABP_ERR_INVALID_ARG, "CV %d: reference positions must be finite", k);

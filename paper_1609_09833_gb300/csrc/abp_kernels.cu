@@ -249,23 +249,25 @@ __device__ void walker_steps(const Grp &g, GroupFixed<Real> *fx, unsigned char *
 
 // ---------------------------------------------------------------- windowed form
 //
-// Walkers whose CVs are all COM distances and dihedrals run their nsteps MD
-// steps in windows of L.win steps. The coordinates of a whole window arrive
-// by cp.async while the previous window runs; within a window:
-//   A  the non-finite check of every (step, atom), then one thread per step:
-//      a1 (CVs and their Jacobian factors) and the axis state into the step's
-//      StepRec, and a4 at once for the steps before the window's first
-//      deposit (the grid cannot change before it); the thread of a deposit
-//      step starts an L2 prefetch of its stencil box;
-//   B  the window's deposits in step order, each by the whole group (a2 + a3
-//      as in the per-step form), each followed by a4 of the steps up to the
-//      next one, one thread per step;
+// Walkers whose CVs are all COM distances, dihedrals or RMSDs of at most 4
+// atoms run their nsteps MD steps in windows of L.win steps. A window's
+// coordinates arrive by cp.async two windows ahead; each window goes through
+// three phases:
+//   A  a1 (CVs, Jacobian factors, axis state) into the window's StepRecs,
+//      one lane per (CV, step) -- two for a COM distance -- and the
+//      non-finite check of every (step, atom);
+//   B  the grid chain: a4 for the steps before the window's first deposit,
+//      then each deposit in step order (a2 + a3) followed by a4 of the steps
+//      up to the next one (windows with one deposit and a small box: one
+//      round of grid reads for all of it, see chain_one);
 //   C  a5 for every (step, atom) pair from the atom's list entries, summed
 //      in registers in CV order and stored.
-// Every step reads the grid with exactly the deposits of the steps before it
-// and its own: the per-step order of the method, with the step-independent
-// work of a window done side by side. A step's arithmetic does not depend on
-// the window it falls in, so chunked calls give the same bits.
+// A group's two halves run A and C, and B, on three StepRec slots (see
+// walker_window). Every step reads the grid with exactly the deposits of the
+// steps before it and its own: the per-step order of the method, with the
+// step-independent work of a window done side by side. A step's arithmetic
+// does not depend on the window it falls in or on the launch shape, so
+// chunked calls and different group sizes give the same bits.
 
 // (j, i) = divmod(t, n), advanced by G each time without a division.
 struct Iter2 {
