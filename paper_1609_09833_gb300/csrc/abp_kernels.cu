@@ -1264,7 +1264,44 @@ struct WindowCtx {
     const StepRec<Real> *st = steps_of(w);
     const unsigned bad = fx->winbad[w % 3];
     R4 *fout = out ? reinterpret_cast<R4 *>(out) : reinterpret_cast<R4 *>(fx->wd.fbuf);
-    if (!serial_out) {
+    // FP32 walkers: one atom per thread (its terms in registers) over every
+    // nl-th step; FP64 walkers, whose C runs on the chain half, measured
+    // faster with one (step, atom) pair per thread
+    if (sizeof(Real) == 4 && !serial_out && natoms <= g.G) {
+      const int nl = g.G / natoms, a = g.t % natoms, lane0 = g.t / natoms;
+      if (lane0 < nl) {
+        const AtomTerm<Real> *ta = terms + a * kAtomTerms;
+        const int ne = cnt[a];
+        Real tw[kAtomTerms];
+        int toff[kAtomTerms];
+#pragma unroll
+        for (int q = 0; q < kAtomTerms; ++q) {
+          tw[q] = q < ne ? ta[q].w : (Real)0;
+          toff[q] = q < ne ? ta[q].off : 0;
+        }
+        for (int j = lane0; j < nt; j += nl) {
+          const long long t = (long long)t0 + j;
+          if (!out && t != last) continue;  // the walker's own buffer keeps the last step
+          R4 *fo = fout + foff + (out ? t * fstride : 0) + a;
+          if ((bad >> j) & 1) {
+            if (mode == ABP_FORCES_OVERWRITE) *fo = make_rec<Real>(0, 0, 0, 0);
+            continue;
+          }
+          // the atom's terms in order, as atom_force sums them
+          const Real *J = &st[j].jac[0][0];
+          Real f0 = 0, f1 = 0, f2 = 0;
+#pragma unroll
+          for (int q = 0; q < kAtomTerms; ++q)
+            if (q < ne) {
+              const Real *v = J + toff[q];
+              f0 += tw[q] * v[0];
+              f1 += tw[q] * v[1];
+              f2 += tw[q] * v[2];
+            }
+          store_force_stream<Real>(fo, make_rec<Real>(f0, f1, f2, 0), mode);
+        }
+      }
+    } else if (!serial_out) {
       for (Iter2 it(g.t, g.G, natoms); it.j < nt; it.next()) {
         const long long t = (long long)t0 + it.j;
         if (!out && t != last) continue;  // the walker's own buffer keeps the last step
