@@ -690,6 +690,20 @@ abp_status abp_walker_create(abp_ctx *ctx, abp_grid *grid, const abp_walker_desc
   }
   if (st == ABP_OK && w->big && big_cn_smem(hd) > 200 * 1024)
     st = fail(ABP_ERR_UNSUPPORTED, "a coordination number with more than ~2000 A atoms is not built");
+  if (st == ABP_OK && w->big) {
+    // the force phase's per-atom term table, into the walker's scratch
+    std::vector<int32_t> terms;
+    std::vector<uint8_t> cnt;
+    if (big_atom_terms(hd, d, terms, cnt))
+      st = fail(ABP_ERR_UNSUPPORTED, "an atom takes part in more than %d CV list entries", kAtomTerms);
+    unsigned char *js = static_cast<unsigned char *>(hd.jscratch);
+    if (st == ABP_OK && cudaMemcpy(js + big_terms_offset(hd), terms.data(), terms.size() * sizeof(int32_t),
+                                   cudaMemcpyHostToDevice) != cudaSuccess)
+      st = fail(ABP_ERR_CUDA, "term table upload failed");
+    if (st == ABP_OK &&
+        cudaMemcpy(js + big_nterm_offset(hd), cnt.data(), cnt.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      st = fail(ABP_ERR_CUDA, "term table upload failed");
+  }
   if (st == ABP_OK) {
     hd.id = ctx->next_id++;
     if ((st = walker_alloc(w, sizeof(WalkerDev), &p)) == ABP_OK) {
@@ -766,11 +780,12 @@ static abp_status sub_table(abp_ctx *ctx, const std::vector<abp_walker *> &ws, c
 static abp_status big_items(abp_ctx *ctx, const std::vector<abp_walker *> &ws, const std::vector<int> &idx,
                             BigArgs *a) {
   std::vector<BigItem> key;
-  int max_stencil = 0, any_shared = 0;
+  int max_stencil = 0, any_shared = 0, max_atoms = 0;
   size_t cn_smem = 0;
   for (size_t i = 0; i < ws.size(); ++i) {
     key.push_back(BigItem{ws[i]->dd, idx[i], 0});
     const WalkerDev &hd = ws[i]->hd;
+    max_atoms = std::max(max_atoms, hd.natoms);
     int box = 1;
     for (int k = 0; k < hd.g.d; ++k) box *= 2 * hd.R[k] + 1;
     max_stencil = std::max(max_stencil, box);
@@ -803,6 +818,7 @@ static abp_status big_items(abp_ctx *ctx, const std::vector<abp_walker *> &ws, c
   a->cn_smem = cn_smem;
   a->max_stencil = max_stencil;
   a->any_shared = any_shared;
+  a->max_atoms = max_atoms;
   return ABP_OK;
 }
 

@@ -19,6 +19,8 @@
 // (one CPU rank), SI "Minimization of Interprocess Communications".
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "abp_device.cuh"
 #include "abp_launch.h"
 
@@ -63,7 +65,7 @@ __host__ __device__ inline int big_nchunks(const WalkerDev &wd) {
 }
 
 struct BigLayout {
-  size_t head, jA, jB, part_s, part_g, total;
+  size_t head, jA, jB, part_s, part_g, terms, nterm, total;
 };
 
 __host__ __device__ inline BigLayout big_layout(const WalkerDev &wd) {
@@ -76,11 +78,45 @@ __host__ __device__ inline BigLayout big_layout(const WalkerDev &wd) {
   L.jB = L.jA + (size_t)na * 16;
   L.part_s = up256(L.jB + (size_t)nb * 16);
   L.part_g = up256(L.part_s + (size_t)nc * 8);
-  L.total = up256(L.part_g + (size_t)nc * na * 12);
+  // per atom, its a5 terms (big_atom_terms) and their count
+  L.terms = up256(L.part_g + (size_t)nc * na * 12);
+  L.nterm = up256(L.terms + (size_t)wd.natoms * kAtomTerms * 4);
+  L.total = up256(L.nterm + (size_t)wd.natoms);
   return L;
 }
 
+// Term codes of the force phase: kind | k << 3 | list position << 5.
+enum { kTermComA = 0, kTermComB = 1, kTermDih = 2, kTermCnA = 3, kTermCnB = 4 };
+
+int big_atom_terms(const WalkerDev &hd, const abp_walker_desc *d, std::vector<int32_t> &terms,
+                   std::vector<uint8_t> &cnt) {
+  const int n = hd.natoms;
+  terms.assign((size_t)n * kAtomTerms, 0);
+  cnt.assign((size_t)n, 0);
+  auto add = [&](int atom, int kind, int k, int pos) -> int {
+    if (atom < 0 || atom >= n || cnt[atom] >= kAtomTerms || pos >= (1 << 26)) return -1;
+    terms[(size_t)atom * kAtomTerms + cnt[atom]] = kind | (k << 3) | (pos << 5);
+    cnt[atom] += 1;
+    return 0;
+  };
+  // CV by CV, list A before list B: the order in which a5 adds them
+  for (int k = 0; k < hd.g.d; ++k) {
+    const abp_cv_desc &c = d->cv[k];
+    const bool com = c.type == ABP_CV_COM_DIST, cn = c.type == ABP_CV_COORD;
+    if (!com && !cn && c.type != ABP_CV_DIHEDRAL) return -1;
+    const int na = c.type == ABP_CV_DIHEDRAL ? 4 : c.n_a;
+    for (int i = 0; i < na; ++i)
+      if (add(c.idx_a[i], com ? kTermComA : cn ? kTermCnA : kTermDih, k, i)) return -1;
+    if (com || cn)
+      for (int i = 0; i < c.n_b; ++i)
+        if (add(c.idx_b[i], com ? kTermComB : kTermCnB, k, i)) return -1;
+  }
+  return 0;
+}
+
 size_t big_scratch_bytes(const WalkerDev &hd) { return big_layout(hd).total; }
+size_t big_terms_offset(const WalkerDev &hd) { return big_layout(hd).terms; }
+size_t big_nterm_offset(const WalkerDev &hd) { return big_layout(hd).nterm; }
 int big_cn_count(const WalkerDev &hd) {
   int n = 0;
   for (int k = 0; k < hd.g.d; ++k) n += hd.cv[k].type == ABP_CV_COORD;
@@ -539,13 +575,20 @@ __global__ void __launch_bounds__(kBigThreads) k_big_refresh(const BigItem *walk
 
 // ---------------------------------------------------------------- k_big_force
 
+// a4 + a5 of one walker's atoms [blockIdx.x * kBigThreads, + kBigThreads):
+// each CTA forms the walker's dV/ds (a few corner reads), then each thread
+// sums its atom's terms in the walker's fixed order (CV by CV, list A before
+// list B) and writes the walker's force buffer and, when given, the
+// caller's.
 __global__ void __launch_bounds__(kBigThreads) k_big_force(const BigItem *walkers, void *forces,
                                                            const long long *foff, long long force_step_off, int mode,
                                                            long long step) {
   extern __shared__ __align__(32) unsigned char smem[];
   Grp g = big_group();
   GroupFixed<float> *fx = reinterpret_cast<GroupFixed<float> *>(smem);
-  const BigItem it = walkers[blockIdx.x];
+  const BigItem it = walkers[blockIdx.y];
+  const int i0 = blockIdx.x * kBigThreads;
+  if (i0 >= it.wd->natoms) return;  // the whole CTA: past this walker's atoms
   big_load_desc(g, fx, it.wd);
   const WalkerDev &wd = fx->wd;
   unsigned char *js = reinterpret_cast<unsigned char *>(wd.jscratch);
@@ -553,10 +596,10 @@ __global__ void __launch_bounds__(kBigThreads) k_big_force(const BigItem *walker
   float4 *fb = reinterpret_cast<float4 *>(wd.fbuf);
   float4 *fo = forces ? reinterpret_cast<float4 *>(forces) + foff[it.widx] + force_step_off : fb;
   const int fmode = forces ? mode : ABP_FORCES_OVERWRITE;
+  const int i = i0 + g.t;
   if (head->bad) {
-    if (fmode == ABP_FORCES_OVERWRITE)
-      for (int i = g.t; i < wd.natoms; i += g.G) fo[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (g.t == 0) wd.state->flags = ABP_WFLAG_NONFINITE;
+    if (fmode == ABP_FORCES_OVERWRITE && i < wd.natoms) fo[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (blockIdx.x == 0 && g.t == 0) wd.state->flags = ABP_WFLAG_NONFINITE;
     return;
   }
   if (g.t < kMaxCv) {
@@ -572,75 +615,54 @@ __global__ void __launch_bounds__(kBigThreads) k_big_force(const BigItem *walker
   g.sync();
   GroupLayout Ldummy{};
   interp_step<float, false>(g, fx, Ldummy, nullptr);
-  // a5 into the walker's force buffer, one list per phase (fixed order)
-  for (int i = g.t; i < wd.natoms; i += g.G) fb[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-  g.sync();
-  const BigLayout L = big_layout(wd);
-  for (int k = 0; k < wd.g.d; ++k) {
-    const CvDev &c = wd.cv[k];
-    const float dv = fx->dvds[k];
-    if (c.type == ABP_CV_COM_DIST) {
-      const float ux = fx->com_u[k][0] * dv, uy = fx->com_u[k][1] * dv, uz = fx->com_u[k][2] * dv;
-      for (int i = g.t; i < c.na; i += g.G) {
-        float w = c.wa[i];
-        float4 &f = fb[c.ia[i]];
-        f.x += w * ux;
-        f.y += w * uy;
-        f.z += w * uz;
+  if (i < wd.natoms) {
+    const BigLayout L = big_layout(wd);
+    const int32_t *tt = reinterpret_cast<const int32_t *>(js + L.terms) + (size_t)i * kAtomTerms;
+    const int ne = js[L.nterm + i];
+    const float4 *jA = reinterpret_cast<const float4 *>(js + L.jA);
+    const float4 *jB = reinterpret_cast<const float4 *>(js + L.jB);
+    float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+    for (int q = 0; q < ne; ++q) {
+      const int code = tt[q], kind = code & 7, k = (code >> 3) & 3, pos = code >> 5;
+      const float dv = fx->dvds[k];
+      if (kind == kTermComA || kind == kTermComB) {
+        const float ux = fx->com_u[k][0] * dv, uy = fx->com_u[k][1] * dv, uz = fx->com_u[k][2] * dv;
+        if (kind == kTermComA) {
+          const float w = wd.cv[k].wa[pos];
+          f0 += w * ux;
+          f1 += w * uy;
+          f2 += w * uz;
+        } else {
+          const float w = wd.cv[k].wb[pos];
+          f0 -= w * ux;
+          f1 -= w * uy;
+          f2 -= w * uz;
+        }
+      } else if (kind == kTermDih) {
+        f0 -= dv * fx->dih_g[k][pos][0];
+        f1 -= dv * fx->dih_g[k][pos][1];
+        f2 -= dv * fx->dih_g[k][pos][2];
+      } else {
+        const float4 j = kind == kTermCnA ? jA[pos] : jB[pos];
+        f0 -= dv * j.x;
+        f1 -= dv * j.y;
+        f2 -= dv * j.z;
       }
-      g.sync();
-      for (int i = g.t; i < c.nb; i += g.G) {
-        float w = c.wb[i];
-        float4 &f = fb[c.ib[i]];
-        f.x -= w * ux;
-        f.y -= w * uy;
-        f.z -= w * uz;
-      }
-      g.sync();
-    } else if (c.type == ABP_CV_DIHEDRAL) {
-      if (g.t < 4) {
-        float4 &f = fb[c.ia[g.t]];
-        f.x -= dv * fx->dih_g[k][g.t][0];
-        f.y -= dv * fx->dih_g[k][g.t][1];
-        f.z -= dv * fx->dih_g[k][g.t][2];
-      }
-      g.sync();
-    } else {
-      const float4 *jA = reinterpret_cast<const float4 *>(js + L.jA);
-      const float4 *jB = reinterpret_cast<const float4 *>(js + L.jB);
-      for (int i = g.t; i < c.na; i += g.G) {
-        float4 j = jA[i];
-        float4 &f = fb[c.ia[i]];
-        f.x -= dv * j.x;
-        f.y -= dv * j.y;
-        f.z -= dv * j.z;
-      }
-      g.sync();
-      for (int i = g.t; i < c.nb; i += g.G) {
-        float4 j = jB[i];
-        float4 &f = fb[c.ib[i]];
-        f.x -= dv * j.x;
-        f.y -= dv * j.y;
-        f.z -= dv * j.z;
-      }
-      g.sync();
     }
-  }
-  if (fo != fb) {
-    for (int i = g.t; i < wd.natoms; i += g.G) {
-      float4 f = fb[i];
+    fb[i] = make_float4(f0, f1, f2, 0.f);
+    if (fo != fb) {
       if (fmode == ABP_FORCES_ACCUMULATE) {
         float4 o = fo[i];
-        o.x += f.x;
-        o.y += f.y;
-        o.z += f.z;
+        o.x += f0;
+        o.y += f1;
+        o.z += f2;
         fo[i] = o;
       } else {
-        fo[i] = make_float4(f.x, f.y, f.z, 0.f);
+        fo[i] = make_float4(f0, f1, f2, 0.f);
       }
     }
   }
-  if (g.t == 0) {
+  if (blockIdx.x == 0 && g.t == 0) {
     WalkerState st;
     for (int k = 0; k < 3; ++k) {
       st.s[k] = k < wd.g.d ? (double)fx->sh[k] + (double)fx->sl[k] : 0.0;
@@ -671,7 +693,8 @@ cudaError_t launch_big_step(const BigArgs &a, cudaStream_t st) {
   if (ph & 4) k_big_deposit<<<grid, kBigThreads, fixed, st>>>(a.walkers);
   if ((ph & 8) && a.any_shared) k_big_refresh<<<grid, kBigThreads, fixed, st>>>(a.walkers);
   if (ph & 16)
-    k_big_force<<<a.nw, kBigThreads, fixed, st>>>(a.walkers, a.forces, a.foff, a.force_step_off, a.mode, a.step);
+    k_big_force<<<dim3((a.max_atoms + kBigThreads - 1) / kBigThreads, a.nw), kBigThreads, fixed, st>>>(
+        a.walkers, a.forces, a.foff, a.force_step_off, a.mode, a.step);
   return cudaGetLastError();
 }
 

@@ -2,6 +2,8 @@
 // kernel translation units.
 #pragma once
 
+#include <vector>
+
 #include <cuda_runtime.h>
 
 #include "abp_internal.cuh"
@@ -78,6 +80,7 @@ struct BigArgs {
   int mode;
   long long step;
   int max_stencil;           // largest stencil box (nodes) among the walkers
+  int max_atoms;             // most atoms of a walker (the force phase's CTAs per walker)
   int any_shared;
   int phases;                // bits: 1 pairs, 2 CVs + heights, 4 deposit, 8 refresh, 16 forces (0 = all)
   DepositLog log;
@@ -85,6 +88,13 @@ struct BigArgs {
 };
 
 size_t big_scratch_bytes(const WalkerDev &hd);
+// The force phase's per-atom term table of a phased-form walker (host side;
+// uploaded into its scratch): per atom, codes kind | k << 3 | position << 5
+// in the order a5 adds them. Returns -1 if an atom has more than kAtomTerms.
+int big_atom_terms(const WalkerDev &hd, const abp_walker_desc *d, std::vector<int32_t> &terms,
+                   std::vector<uint8_t> &cnt);
+size_t big_terms_offset(const WalkerDev &hd);
+size_t big_nterm_offset(const WalkerDev &hd);
 int big_cn_count(const WalkerDev &hd);
 int big_chunks(const WalkerDev &hd);
 size_t big_cn_smem(const WalkerDev &hd);
