@@ -164,35 +164,66 @@ __global__ void __launch_bounds__(kBigThreads) k_big_cn(const BigItem *items, co
   // accumulator
   float sacc = 0.f, scomp = 0.f;
   float *mylig = lig + warp * na * 3;
+  // every B entry of this CTA in range: blocks of 4 A atoms need no mask
+  // (a mask of 1 would change no bit)
+  const bool fullj = j0 + kBigJB * kBigThreads <= nb;
   for (int i0 = 0; i0 < na; i0 += 4) {
     float gi[4][3];
     float part = 0.f;
+    if (fullj && i0 + 4 <= na) {
 #pragma unroll
-    for (int ii = 0; ii < 4; ++ii) {
-      gi[ii][0] = gi[ii][1] = gi[ii][2] = 0.f;
-      int i = i0 + ii;
-      bool oki = i < na;
-      float4 a = As[oki ? i : 0];
+      for (int ii = 0; ii < 4; ++ii) {
+        gi[ii][0] = gi[ii][1] = gi[ii][2] = 0.f;
+        float4 a = As[i0 + ii];
 #pragma unroll
-      for (int jj = 0; jj < kBigJB; ++jj) {
-        float dx = a.x - xj[jj], dy = a.y - yj[jj], dz = a.z - zj[jj];
-        if (pbc) {
-          dx = min_image(dx, bx, ibx);
-          dy = min_image(dy, by, iby);
-          dz = min_image(dz, bz, ibz);
+        for (int jj = 0; jj < kBigJB; ++jj) {
+          float dx = a.x - xj[jj], dy = a.y - yj[jj], dz = a.z - zj[jj];
+          if (pbc) {
+            dx = min_image(dx, bx, ibx);
+            dy = min_image(dy, by, iby);
+            dz = min_image(dz, bz, ibz);
+          }
+          float q = (dx * dx + dy * dy + dz * dz) * k2;
+          float q2 = q * q;
+          float sw = __fdividef(1.f, 1.f + q2 * q);
+          part += sw;
+          float gf = c6 * q2 * sw * sw;
+          gi[ii][0] += gf * dx;
+          gi[ii][1] += gf * dy;
+          gi[ii][2] += gf * dz;
+          gxj[jj] -= gf * dx;
+          gyj[jj] -= gf * dy;
+          gzj[jj] -= gf * dz;
         }
-        float q = (dx * dx + dy * dy + dz * dz) * k2;
-        float q2 = q * q;
-        float sw = __fdividef(1.f, 1.f + q2 * q);
-        float m = oki ? mj[jj] : 0.f;
-        part += m * sw;
-        float gf = c6 * m * q2 * sw * sw;
-        gi[ii][0] += gf * dx;
-        gi[ii][1] += gf * dy;
-        gi[ii][2] += gf * dz;
-        gxj[jj] -= gf * dx;
-        gyj[jj] -= gf * dy;
-        gzj[jj] -= gf * dz;
+      }
+    } else {
+#pragma unroll
+      for (int ii = 0; ii < 4; ++ii) {
+        gi[ii][0] = gi[ii][1] = gi[ii][2] = 0.f;
+        int i = i0 + ii;
+        bool oki = i < na;
+        float4 a = As[oki ? i : 0];
+#pragma unroll
+        for (int jj = 0; jj < kBigJB; ++jj) {
+          float dx = a.x - xj[jj], dy = a.y - yj[jj], dz = a.z - zj[jj];
+          if (pbc) {
+            dx = min_image(dx, bx, ibx);
+            dy = min_image(dy, by, iby);
+            dz = min_image(dz, bz, ibz);
+          }
+          float q = (dx * dx + dy * dy + dz * dz) * k2;
+          float q2 = q * q;
+          float sw = __fdividef(1.f, 1.f + q2 * q);
+          float m = oki ? mj[jj] : 0.f;
+          part += m * sw;
+          float gf = c6 * m * q2 * sw * sw;
+          gi[ii][0] += gf * dx;
+          gi[ii][1] += gf * dy;
+          gi[ii][2] += gf * dz;
+          gxj[jj] -= gf * dx;
+          gyj[jj] -= gf * dy;
+          gzj[jj] -= gf * dz;
+        }
       }
     }
     {
