@@ -88,6 +88,53 @@ class OrWalker(C.Structure):
     _fields_ = [("g", OrGrid), ("hill", OrHill), ("cv", OrCv * MAXCV), ("natoms", C.c_int)]
 
 
+class OrMd(C.Structure):
+    _fields_ = [
+        ("dt", C.c_double),
+        ("mu", C.c_double),
+        ("kT", C.c_double),
+        ("seed", C.c_uint64),
+        ("pot", C.c_int),
+        ("dw_a", C.c_double),
+        ("dw_b", C.c_double),
+        ("mb_scale", C.c_double),
+        ("mb_map", C.c_double * 4),
+        ("mb_A", C.c_double * 4),
+        ("mb_a", C.c_double * 4),
+        ("mb_b", C.c_double * 4),
+        ("mb_c", C.c_double * 4),
+        ("mb_x0", C.c_double * 4),
+        ("mb_y0", C.c_double * 4),
+        ("state_f32", C.c_int),
+    ]
+
+
+POTENTIALS = {"none": 0, "double_well": 1, "muller_brown": 2}
+
+
+def md_struct(md: dict) -> OrMd:
+    """An or_md from a closed-loop dynamics dict (see synth.md_params)."""
+    m = OrMd()
+    m.dt, m.mu, m.kT = float(md["dt"]), float(md["mu"]), float(md["kT"])
+    m.seed = int(md["seed"]) & ((1 << 64) - 1)
+    m.pot = POTENTIALS[md.get("potential", "none")]
+    m.state_f32 = int(bool(md.get("state_f32", False)))
+    if m.pot == POTENTIALS["double_well"]:
+        m.dw_a, m.dw_b = float(md["dw"][0]), float(md["dw"][1])
+    elif m.pot == POTENTIALS["muller_brown"]:
+        mb = md["mb"]
+        m.mb_scale = float(mb["scale"])
+        for q in range(4):
+            m.mb_map[q] = float(mb["map"][q])
+            for key in ("A", "a", "b", "c", "x0", "y0"):
+                getattr(m, "mb_" + key)[q] = float(mb[key][q])
+    return m
+
+
+class OrStepAux(C.Structure):
+    _fields_ = [("H", C.c_double * 9), ("A", C.c_double * 4), ("sb", C.c_double * 3)]
+
+
 class OrDeposit(C.Structure):
     _fields_ = [
         ("step", C.c_int64),
@@ -135,14 +182,33 @@ def lib():
         L.or_check.restype = C.c_int
         L.or_batch_step.argtypes = [
             C.c_int, C.POINTER(OrWalker), C.POINTER(dp), C.POINTER(dp), C.c_int64,
-            dp, dp, dp, C.POINTER(dp), ip, C.POINTER(OrDeposit),
+            dp, dp, dp, C.POINTER(dp), ip, C.POINTER(OrDeposit), C.POINTER(OrMd), C.POINTER(C.c_uint32),
+            C.POINTER(dp), C.POINTER(OrStepAux), C.POINTER(dp),
         ]
         L.or_batch_step.restype = C.c_int
+        u32p = C.POINTER(C.c_uint32)
         L.or_run.argtypes = [
             C.c_int, C.POINTER(OrWalker), C.POINTER(dp), dp, C.POINTER(C.c_int64), C.c_int64,
             C.c_int64, C.c_int64, dp, dp, dp, dp, ip, C.POINTER(OrDeposit), C.c_int64,
-            C.POINTER(C.c_int64),
+            C.POINTER(C.c_int64), C.POINTER(OrMd), u32p, dp, C.POINTER(OrStepAux), dp,
         ]
+        L.or_interp_aux.argtypes = [C.POINTER(OrGrid), dp, dp, dp, dp]
+        L.or_interp_aux.restype = None
+        L.or_cv_round_bound.argtypes = [C.POINTER(OrCv), dp]
+        L.or_cv_round_bound.restype = C.c_double
+        L.or_md_run.argtypes = [
+            C.c_int, C.POINTER(OrWalker), C.POINTER(dp), dp, C.POINTER(C.c_int64), C.c_int64, C.POINTER(OrMd),
+            u32p, C.c_int64, C.c_int64, dp, dp, dp, C.POINTER(OrDeposit), C.c_int64, C.POINTER(C.c_int64),
+        ]
+        L.or_md_run.restype = C.c_int
+        L.or_philox4x32_10.argtypes = [u32p, u32p, u32p]
+        L.or_philox4x32_10.restype = None
+        L.or_uniform24.argtypes = [C.c_uint32]
+        L.or_uniform24.restype = C.c_double
+        L.or_md_normals.argtypes = [C.c_uint64, C.c_uint32, C.c_int64, C.c_int, dp]
+        L.or_md_normals.restype = None
+        L.or_md_potential.argtypes = [C.POINTER(OrMd), dp, dp]
+        L.or_md_potential.restype = C.c_double
         L.or_run.restype = C.c_int
         L.or_langevin_double_well.argtypes = [
             C.POINTER(OrWalker), dp, dp, C.c_int64, C.c_double, C.c_double, C.c_double, dp, dp,
@@ -316,7 +382,7 @@ def lookup_mabp(walker: Walker, field: np.ndarray, s):
 
 
 def run(walkers, frames, atom_offsets, step0: int, T: int, fields=None, record_forces=True,
-        dep_cap: int | None = None):
+        dep_cap: int | None = None, md: dict | None = None, streams=None, error_model: bool = False):
     """Open-loop replay of T steps (step0 .. step0+T-1) for a batch of walkers.
 
     walkers: list of Walker. frames: float array [T, total_atoms, 3] (any
@@ -325,7 +391,14 @@ def run(walkers, frames, atom_offsets, step0: int, T: int, fields=None, record_f
     [nodes, 1+d]); walkers given the same array object share that grid. New
     zeroed grids are made when fields is None. Returns a dict with s, V, dV
     ([T, nw, 3] / [T, nw]), F ([T, total_atoms, 3] or None), flags, the deposit
-    log and the final fields.
+    log and the final fields. With md (closed-loop dynamics, see md_struct)
+    and streams (one noise stream per walker) it also returns Xn
+    [T, total_atoms, 3]: for every step, the coordinates after that step's
+    move predicted from the recorded frame. With error_model it also returns
+    the per-step error-analysis outputs: H [T, nw, 3, 3] (slope of the
+    interpolated dV_k along s_j), A [T, nw, 4] (absolute interpolation
+    scale), sb [T, nw, 3] (CV rounding bound in units of the unit roundoff)
+    and Jn [T, total_atoms, 3] (|ds_k/dx| per atom).
     """
     nw = len(walkers)
     frames = np.ascontiguousarray(frames, dtype=np.float64)
@@ -347,9 +420,19 @@ def run(walkers, frames, atom_offsets, step0: int, T: int, fields=None, record_f
         dep_cap = sum(T // w.struct.hill.stride + 1 for w in walkers)
     deps = (OrDeposit * max(dep_cap, 1))()
     nd = C.c_int64()
+    mds, st, Xn = None, None, None
+    if md is not None:
+        mds = md_struct(md)
+        st = np.ascontiguousarray(np.asarray(streams, dtype=np.uint32))
+        assert st.shape == (nw,)
+        Xn = np.zeros((T, total, 3))
+    aux = (OrStepAux * (T * nw))() if error_model else None
+    Jn = np.zeros((T, total, 3)) if error_model else None
     rc = lib().or_run(
         nw, arr, fptrs, _dptr(frames), offs.ctypes.data_as(C.POINTER(C.c_int64)), total * 3, int(step0), int(T),
         _dptr(s), _dptr(V), _dptr(dV), _dptr(F) if F is not None else None, _iptr(flags), deps, dep_cap, C.byref(nd),
+        C.byref(mds) if mds is not None else None, st.ctypes.data_as(C.POINTER(C.c_uint32)) if st is not None else None,
+        _dptr(Xn) if Xn is not None else None, aux, _dptr(Jn) if Jn is not None else None,
     )
     if rc:
         raise RuntimeError(f"oracle run failed ({rc})")
@@ -361,7 +444,12 @@ def run(walkers, frames, atom_offsets, step0: int, T: int, fields=None, record_f
         "s": np.array([list(deps[i].s) for i in range(n)]).reshape(n, 3),
         "height": np.array([deps[i].height for i in range(n)]),
     }
-    return {"s": s, "V": V, "dV": dV, "F": F, "flags": flags, "deposits": log, "fields": fields}
+    out = {"s": s, "V": V, "dV": dV, "F": F, "flags": flags, "deposits": log, "fields": fields, "Xn": Xn}
+    if error_model:
+        a = np.ctypeslib.as_array(aux).view(np.float64).reshape(T, nw, 16)
+        out.update(H=a[:, :, 0:9].reshape(T, nw, 3, 3).copy(), A=a[:, :, 9:13].copy(), sb=a[:, :, 13:16].copy(),
+                   Jn=Jn)
+    return out
 
 
 def langevin_double_well(walker: Walker, field: np.ndarray, x0: np.ndarray, T: int, dt: float, mu: float,
@@ -378,3 +466,94 @@ def langevin_double_well(walker: Walker, field: np.ndarray, x0: np.ndarray, T: i
     if rc:
         raise RuntimeError(f"oracle langevin failed ({rc})")
     return x, s_hist
+
+
+# ---------------------------------------------------------------- closed-loop dynamics
+
+
+def philox4x32_10(ctr, key):
+    """Philox-4x32-10 of a 4-word counter and a 2-word key (Salmon et al., SC'11)."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    u32p = C.POINTER(C.c_uint32)
+    lib().or_philox4x32_10(c.ctypes.data_as(u32p), k.ctypes.data_as(u32p), out.ctypes.data_as(u32p))
+    return out
+
+
+def uniform24(r: int) -> float:
+    return float(lib().or_uniform24(int(r) & 0xFFFFFFFF))
+
+
+def md_normals(seed: int, stream: int, step: int, atom: int) -> np.ndarray:
+    """The three standard normals of one atom at one MD step."""
+    n = np.zeros(3)
+    lib().or_md_normals(int(seed) & ((1 << 64) - 1), int(stream), int(step), int(atom), _dptr(n))
+    return n
+
+
+def md_potential(md: dict, s):
+    """U(s) and dU/ds of the closed-loop dynamics' CV potential."""
+    m = md_struct(md)
+    s3 = np.zeros(3)
+    s3[: len(s)] = s
+    dU = np.zeros(3)
+    U = lib().or_md_potential(C.byref(m), _dptr(s3), _dptr(dU))
+    return float(U), dU
+
+
+def md_run(walkers, x0, atom_offsets, md: dict, streams, step0: int, T: int, fields=None, record_x=False,
+           dep_cap: int | None = None):
+    """Closed-loop run of T steps (step0 .. step0+T-1) from coordinates x0
+    [total_atoms, 3]. Returns a dict with the final x, X (the coordinates each
+    step's bias was evaluated at, [T, total_atoms, 3], when record_x), s, V,
+    the deposit log and the fields."""
+    nw = len(walkers)
+    x = np.ascontiguousarray(x0, dtype=np.float64).copy()
+    total = x.shape[0]
+    if fields is None:
+        fields = [w.new_field() for w in walkers]
+    arr = (OrWalker * nw)(*[w.struct for w in walkers])
+    fptrs = (C.POINTER(C.c_double) * nw)(*[_dptr(f) for f in fields])
+    offs = np.ascontiguousarray(np.asarray(atom_offsets, dtype=np.int64) * 3)
+    mds = md_struct(md)
+    st = np.ascontiguousarray(np.asarray(streams, dtype=np.uint32))
+    X = np.zeros((T, total, 3)) if record_x else None
+    s = np.zeros((T, nw, 3))
+    V = np.zeros((T, nw))
+    if dep_cap is None:
+        dep_cap = sum(T // w.struct.hill.stride + 1 for w in walkers)
+    deps = (OrDeposit * max(dep_cap, 1))()
+    nd = C.c_int64()
+    rc = lib().or_md_run(nw, arr, fptrs, _dptr(x), offs.ctypes.data_as(C.POINTER(C.c_int64)), total * 3,
+                         C.byref(mds), st.ctypes.data_as(C.POINTER(C.c_uint32)), int(step0), int(T),
+                         _dptr(X) if X is not None else None, _dptr(s), _dptr(V), deps, dep_cap, C.byref(nd))
+    if rc:
+        raise RuntimeError(f"oracle md run failed ({rc})")
+    n = min(nd.value, dep_cap)
+    log = {
+        "step": np.array([deps[i].step for i in range(n)], dtype=np.int64),
+        "walker": np.array([deps[i].walker for i in range(n)], dtype=np.int32),
+        "s": np.array([list(deps[i].s) for i in range(n)]).reshape(n, 3),
+        "height": np.array([deps[i].height for i in range(n)]),
+    }
+    return {"x": x, "X": X, "s": s, "V": V, "deposits": log, "fields": fields}
+
+
+# ---------------------------------------------------------------- error analysis (test tolerances)
+
+
+def interp_aux(walker: Walker, field: np.ndarray, s):
+    """Slopes H[k, j] = d(dV_k)/ds_j of the interpolant and its absolute scale A."""
+    s3 = np.zeros(3)
+    s3[: walker.d] = s
+    H = np.zeros(9)
+    A = np.zeros(4)
+    lib().or_interp_aux(C.byref(walker.struct.g), _dptr(field), _dptr(s3), _dptr(H), _dptr(A))
+    return H.reshape(3, 3)[: walker.d, : walker.d].copy(), A[: 1 + walker.d].copy()
+
+
+def cv_round_bound(walker: Walker, k: int, x: np.ndarray) -> float:
+    """First-order rounding bound of CV k at x, in units of the unit roundoff."""
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+    return float(lib().or_cv_round_bound(C.byref(walker.struct.cv[k]), _dptr(x)))

@@ -132,6 +132,32 @@ typedef struct {
   int natoms;
 } or_walker;
 
+/* The model dynamics of a closed-loop run (see or_md_move). */
+enum { OR_POT_NONE = 0, OR_POT_DOUBLE_WELL = 1, OR_POT_MULLER_BROWN = 2 };
+typedef struct {
+  double dt;            /* time step (ps) */
+  double mu;            /* mobility (nm^2 / (kJ/mol ps)) */
+  double kT;            /* thermal energy of the noise (kJ/mol) */
+  uint64_t seed;        /* Philox key */
+  int pot;              /* OR_POT_* */
+  double dw_a, dw_b;    /* double well A (s_0^2 - B^2)^2 */
+  double mb_scale;      /* Mueller-Brown: energy scale */
+  double mb_map[4];     /* X = map[0] s_0 + map[1], Y = map[2] s_1 + map[3] */
+  double mb_A[4], mb_a[4], mb_b[4], mb_c[4], mb_x0[4], mb_y0[4];
+  int state_f32;        /* nonzero: positions are stored in binary32 after every
+                           move (an engine that keeps FP32 coordinates) */
+} or_md;
+
+/* Per-walker error-analysis outputs of one step (or_batch_step): the slopes
+ * and absolute scale of the interpolation (or_interp_aux; a CV range wall
+ * adds kwall to H[4k] above smax) and each CV's rounding bound in units of
+ * the unit roundoff (or_cv_round_bound). */
+typedef struct {
+  double H[9];
+  double A[4];
+  double sb[3];
+} or_stepaux;
+
 /* What the step deposited (one record per hill). */
 typedef struct {
   int64_t step;
@@ -405,6 +431,166 @@ int or_interp(const or_grid *g, const double *field, const double *s, double *V,
   return flag;
 }
 
+/* Error-analysis companions of or_interp (test infrastructure: they scale
+ * the tolerance of a per-step comparison, they are not part of the method).
+ * At s, with the corners, weights and clamping of or_interp:
+ *   H[3*k + j] = d(dV_k)/ds_j, the slope of the interpolated derivative field
+ *                k along axis j (0 on a clamped axis j or for a clamped k);
+ *   A[q]       = sum over corners of weight * |field q at the corner|, the
+ *                scale of the rounding error of the interpolation itself. */
+void or_interp_aux(const or_grid *g, const double *field, const double *s, double *H, double *A) {
+  int d = g->d, nf = 1 + d;
+  int i0[3] = {0, 0, 0}, i1[3] = {0, 0, 0}, clamped[3] = {0, 0, 0};
+  double f[3] = {0, 0, 0}, D[3] = {1, 1, 1};
+  for (int k = 0; k < d; ++k) {
+    D[k] = grid_spacing(g, k);
+    double u = (s[k] - g->lo[k]) / D[k];
+    if (g->periodic[k]) {
+      u = wrap_u(u, g->n[k]);
+      int a = (int)floor(u);
+      if (a > g->n[k] - 1) a = g->n[k] - 1;
+      i0[k] = a;
+      i1[k] = (a + 1) % g->n[k];
+      f[k] = u - a;
+    } else {
+      if (u < 0.0) { u = 0.0; clamped[k] = 1; }
+      if (u > g->n[k] - 1) { u = g->n[k] - 1; clamped[k] = 1; }
+      int a = (int)floor(u);
+      if (a > g->n[k] - 2) a = g->n[k] - 2;
+      i0[k] = a;
+      i1[k] = a + 1;
+      f[k] = u - a;
+    }
+  }
+  for (int q = 0; q < 9; ++q) H[q] = 0.0;
+  for (int q = 0; q < 4; ++q) A[q] = 0.0;
+  for (int corner = 0; corner < (1 << d); ++corner) {
+    double wgt = 1.0, dw[3] = {1, 1, 1};
+    long node = 0, mul = 1;
+    for (int k = 0; k < d; ++k) {
+      int hi = (corner >> k) & 1;
+      double wk = hi ? f[k] : 1.0 - f[k];
+      wgt *= wk;
+      /* d(weight)/ds_j: the factor of axis j replaced by its derivative */
+      for (int j = 0; j < d; ++j) dw[j] *= (j == k) ? (hi ? 1.0 : -1.0) / D[k] : wk;
+      node += mul * (hi ? i1[k] : i0[k]);
+      mul *= g->n[k];
+    }
+    for (int q = 0; q < nf; ++q) A[q] += wgt * fabs(field[node * nf + q]);
+    for (int k = 0; k < d; ++k)
+      for (int j = 0; j < d; ++j)
+        if (!clamped[k] && !clamped[j]) H[3 * k + j] += dw[j] * field[node * nf + 1 + k];
+  }
+}
+
+/* First-order bound on the rounding error of an evaluation of CV c at x in
+ * a binary floating-point format of unit roundoff u, in units of u (multiply
+ * by u). The evaluation forms coordinate differences first and then follows
+ * the definition; every rounding of an operation is counted at the operands'
+ * magnitude (test infrastructure: the tolerance of a CV comparison).
+ *   COM distance: the group sums over offsets from each group's first atom
+ *     (n + 3 roundings per term), the difference of the first atoms, the
+ *     norm (6 |s|); a minimum image adds 3 L per axis;
+ *   dihedral: bond vectors rounded (each a shift of 1/sin of the adjacent
+ *     bond angle, twice for the middle bond), then the two atan2 arguments,
+ *     each within 10 roundings of |b1| |b2|^2 |b3| while their norm is
+ *     |m| |n| = |b1| |b2|^2 |b3| sin(theta1) sin(theta2);
+ *   coordination number: per pair q = r^2 / r0^2 within (7 q + 2 sum_q |v_q|
+ *     |dx_q| / r0^2) roundings (dx before and v after a minimum image), the
+ *     switch within 5 more, dsw/dq = -3 q^2 sw^2; the partial sums 16 |s|;
+ *   RMSD: the reference rounded (|x0|), each difference, the sum of 3N
+ *     squares and the square root. */
+double or_cv_round_bound(const or_cv *c, const double *x) {
+  if (c->type == OR_CV_COM_DIST) {
+    double ra[3] = {0, 0, 0}, rb[3] = {0, 0, 0}, Ma = 0, Mb = 0, ea = 0, eb = 0;
+    for (int i = 0; i < c->na; ++i) Ma += c->ma ? c->ma[i] : 1.0;
+    for (int i = 0; i < c->nb; ++i) Mb += c->mb ? c->mb[i] : 1.0;
+    const double *xa0 = x + 3 * c->ia[0], *xb0 = x + 3 * c->ib[0];
+    for (int i = 0; i < c->na; ++i) {
+      double m = (c->ma ? c->ma[i] : 1.0) / Ma;
+      for (int k = 0; k < 3; ++k) {
+        ra[k] += m * x[3 * c->ia[i] + k];
+        ea += m * fabs(x[3 * c->ia[i] + k] - xa0[k]);
+      }
+    }
+    for (int i = 0; i < c->nb; ++i) {
+      double m = (c->mb ? c->mb[i] : 1.0) / Mb;
+      for (int k = 0; k < 3; ++k) {
+        rb[k] += m * x[3 * c->ib[i] + k];
+        eb += m * fabs(x[3 * c->ib[i] + k] - xb0[k]);
+      }
+    }
+    double dv[3], d0 = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      dv[k] = rb[k] - ra[k];
+      d0 += fabs(xb0[k] - xa0[k]);
+    }
+    min_image(dv, c);
+    double s = sqrt(dot(dv, dv));
+    double b = (c->na + 3) * ea + (c->nb + 3) * eb + 3.0 * d0 + 6.0 * s;
+    if (c->pbc) b += 3.0 * (c->box[0] + c->box[1] + c->box[2]);
+    return b;
+  }
+  if (c->type == OR_CV_DIHEDRAL) {
+    const double *x1 = x + 3 * c->ia[0], *x2 = x + 3 * c->ia[1];
+    const double *x3 = x + 3 * c->ia[2], *x4 = x + 3 * c->ia[3];
+    double b1[3], b2[3], b3[3], m[3], n[3];
+    for (int k = 0; k < 3; ++k) {
+      b1[k] = x2[k] - x1[k];
+      b2[k] = x3[k] - x2[k];
+      b3[k] = x4[k] - x3[k];
+    }
+    min_image(b1, c);
+    min_image(b2, c);
+    min_image(b3, c);
+    cross(b1, b2, m);
+    cross(b2, b3, n);
+    double l1 = sqrt(dot(b1, b1)), l2 = sqrt(dot(b2, b2)), l3 = sqrt(dot(b3, b3));
+    double lm = sqrt(dot(m, m)), ln = sqrt(dot(n, n));
+    if (lm == 0.0 || ln == 0.0) return INFINITY;
+    double i1 = l1 * l2 / lm, i2 = l2 * l3 / ln; /* 1/sin of the two bond angles */
+    double b = 4.0 * (i1 + i2) + 20.0 * i1 * i2;
+    /* with a minimum image a bond component is rounded at the magnitude of
+     * the raw difference (up to the box edge); |d phi/d b1| = i1 / |b1|,
+     * |d phi/d b3| = i2 / |b3|, |d phi/d b2| <= (i1 + i2) / |b2| */
+    if (c->pbc) {
+      double L = fmax(c->box[0], fmax(c->box[1], c->box[2]));
+      b += 2.0 * sqrt(3.0) * L * (i1 / l1 + i2 / l3 + (i1 + i2) / l2);
+    }
+    return b;
+  }
+  if (c->type == OR_CV_COORD) {
+    double k2 = 1.0 / (c->r0 * c->r0), acc = 0.0, s = 0.0;
+    for (int a = 0; a < c->na; ++a) {
+      const double *xi = x + 3 * c->ia[a];
+      for (int bb = 0; bb < c->nb; ++bb) {
+        const double *xj = x + 3 * c->ib[bb];
+        double raw[3] = {xi[0] - xj[0], xi[1] - xj[1], xi[2] - xj[2]};
+        double v[3] = {raw[0], raw[1], raw[2]};
+        min_image(v, c);
+        double q = dot(v, v) * k2;
+        double sw = 1.0 / (1.0 + q * q * q);
+        double dq = 7.0 * q + 2.0 * k2 * (fabs(v[0] * raw[0]) + fabs(v[1] * raw[1]) + fabs(v[2] * raw[2]));
+        acc += 3.0 * q * q * sw * sw * dq + 5.0 * sw;
+        s += sw;
+      }
+    }
+    return acc + 16.0 * s;
+  }
+  if (c->type == OR_CV_RMSD) {
+    double acc = 0.0, e = 0.0;
+    for (int i = 0; i < c->na; ++i)
+      for (int k = 0; k < 3; ++k) {
+        double xv = x[3 * c->ia[i] + k], x0 = c->ref[3 * i + k], dd = xv - x0;
+        acc += dd * dd;
+        e += 2.0 * fabs(dd) * (fabs(x0) + fabs(dd));
+      }
+    double s = sqrt(acc / c->na + 0.01);
+    return (e / c->na + (3.0 * c->na + 3.0) * (acc / c->na + 0.01)) / (2.0 * s) + s;
+  }
+  return 0.0; /* OR_CV_POS_X: a coordinate, exact */
+}
+
 /* ------------------------------------------------------------------ */
 /* a2 + a3: well-tempered height and Gaussian deposit in a cutoff box   */
 /* ------------------------------------------------------------------ */
@@ -583,6 +769,123 @@ double or_wall_grad(const or_hill *hl, int k, double s) {
 }
 
 /* ------------------------------------------------------------------ */
+/* closed-loop dynamics: counter-based noise, CV potentials, moves      */
+/* ------------------------------------------------------------------ */
+
+/* The model MD engine of the closed-loop workloads (not part of the paper's
+ * method, which receives coordinates from an MD code and returns the bias
+ * force): every CV atom moves by overdamped Langevin dynamics,
+ *   x_i <- x_i + dt mu F_i + sqrt(2 mu kT dt) xi_i,
+ *   F_i = -sum_k (dV_b/ds_k + dU/ds_k) ds_k/dx_i,
+ * F_i the bias force of the step plus the force of a potential U(s) of the
+ * walker's CVs, xi_i three standard normals per atom and step. */
+
+/* Philox-4x32 with 10 rounds (Salmon, Moraes, Dror and Shaw, "Parallel
+ * random numbers: as easy as 1, 2, 3", SC'11). A round multiplies counter
+ * words 0 and 2 by the two round multipliers; the new counter is
+ *   (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)),
+ * and the key advances by the two Weyl increments before every round but
+ * the first. */
+void or_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += W0;
+      k1 += W1;
+    }
+    uint64_t p0 = (uint64_t)M0 * c0, p1 = (uint64_t)M1 * c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    c0 = hi1 ^ c1 ^ k0;
+    c1 = lo1;
+    c2 = hi0 ^ c3 ^ k1;
+    c3 = lo0;
+  }
+  out[0] = c0;
+  out[1] = c1;
+  out[2] = c2;
+  out[3] = c3;
+}
+
+/* A 32-bit word's top 24 bits as a uniform number in (0, 1): (j + 1/2) 2^-24,
+ * exact in single and double precision. */
+double or_uniform24(uint32_t r) { return ((double)(r >> 8) + 0.5) * (1.0 / 16777216.0); }
+
+/* Three standard normals for one atom of one walker at one MD step:
+ * Philox with counter (atom, step low word, step high word, stream) and key
+ * (seed low word, seed high word); the four uniforms u0..u3 give
+ *   n0 = r0 cos(2 pi u1), n1 = r0 sin(2 pi u1), n2 = r2 cos(2 pi u3),
+ *   r = sqrt(-2 ln u) (Box and Muller, Ann. Math. Stat. 29 (1958)). */
+void or_md_normals(uint64_t seed, uint32_t stream, int64_t step, int atom, double *n) {
+  uint32_t ctr[4] = {(uint32_t)atom, (uint32_t)((uint64_t)step & 0xffffffffu), (uint32_t)((uint64_t)step >> 32),
+                     stream};
+  uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+  uint32_t r[4];
+  or_philox4x32_10(ctr, key, r);
+  double u0 = or_uniform24(r[0]), u1 = or_uniform24(r[1]), u2 = or_uniform24(r[2]), u3 = or_uniform24(r[3]);
+  const double two_pi = 6.283185307179586476925286766559;
+  double r0 = sqrt(-2.0 * log(u0)), r2 = sqrt(-2.0 * log(u2));
+  n[0] = r0 * cos(two_pi * u1);
+  n[1] = r0 * sin(two_pi * u1);
+  n[2] = r2 * cos(two_pi * u3);
+}
+
+/* U(s) of the walker's CVs and dU/ds_k (k < 3; unused entries 0):
+ *   OR_POT_DOUBLE_WELL   U = A (s_0^2 - B^2)^2;
+ *   OR_POT_MULLER_BROWN  U = scale sum_{i<4} A_i exp(a_i X'^2 + b_i X' Y' + c_i Y'^2),
+ *                        X' = X - x0_i, Y' = Y - y0_i, X = mx s_0 + cx, Y = my s_1 + cy
+ *                        (the four-term surface of Mueller and Brown,
+ *                        Theor. Chim. Acta 53 (1979), on an affine image of
+ *                        the CV box). */
+double or_md_potential(const or_md *md, const double *s, double *dU) {
+  dU[0] = dU[1] = dU[2] = 0.0;
+  if (md->pot == OR_POT_DOUBLE_WELL) {
+    double q = s[0] * s[0] - md->dw_b * md->dw_b;
+    dU[0] = 4.0 * md->dw_a * s[0] * q;
+    return md->dw_a * q * q;
+  }
+  if (md->pot == OR_POT_MULLER_BROWN) {
+    double X = md->mb_map[0] * s[0] + md->mb_map[1], Y = md->mb_map[2] * s[1] + md->mb_map[3];
+    double U = 0.0, dX = 0.0, dY = 0.0;
+    for (int i = 0; i < 4; ++i) {
+      double xp = X - md->mb_x0[i], yp = Y - md->mb_y0[i];
+      double e = md->mb_A[i] * exp(md->mb_a[i] * xp * xp + md->mb_b[i] * xp * yp + md->mb_c[i] * yp * yp);
+      U += e;
+      dX += e * (2.0 * md->mb_a[i] * xp + md->mb_b[i] * yp);
+      dY += e * (md->mb_b[i] * xp + 2.0 * md->mb_c[i] * yp);
+    }
+    dU[0] = md->mb_scale * md->mb_map[0] * dX;
+    dU[1] = md->mb_scale * md->mb_map[2] * dY;
+    return md->mb_scale * U;
+  }
+  return 0.0;
+}
+
+/* One move of one walker's atoms (see the section head): xn = x + dt mu
+ * (Fb - sum_k dU/ds_k J_k) + sqrt(2 mu kT dt) xi, with Fb the step's bias
+ * force and J_k = ds_k/dx at x. */
+void or_md_move(const or_walker *wk, const or_md *md, uint32_t stream, int64_t step, const double *x,
+                const double *Fb, const double *s, const double *const *J, double *xn) {
+  double dU[3];
+  or_md_potential(md, s, dU);
+  double amp = sqrt(2.0 * md->mu * md->kT * md->dt);
+  for (int i = 0; i < wk->natoms; ++i) {
+    double nz[3];
+    or_md_normals(md->seed, stream, step, i, nz);
+    for (int q = 0; q < 3; ++q) {
+      int a = 3 * i + q;
+      double f = Fb[a];
+      for (int k = 0; k < wk->g.d; ++k) f -= dU[k] * J[k][a];
+      xn[a] = x[a] + md->dt * md->mu * f + amp * nz[q];
+      if (md->state_f32) xn[a] = (double)(float)xn[a];
+    }
+  }
+}
+
+/* ------------------------------------------------------------------ */
 /* one MD step for a batch of walkers                                   */
 /* ------------------------------------------------------------------ */
 
@@ -593,7 +896,8 @@ double or_wall_grad(const or_hill *hl, int k, double s) {
  * Returns 0, or OR_FLAG_BADARG on an unusable walker. */
 int or_batch_step(int nw, const or_walker *wk, double *const *fields, const double *const *x,
                   int64_t step, double *s, double *V, double *dV, double *const *F, int *flags,
-                  or_deposit *dep) {
+                  or_deposit *dep, const or_md *md, const uint32_t *streams, double *const *xn,
+                  or_stepaux *aux, double *const *Jn) {
   for (int w = 0; w < nw; ++w)
     if (or_check(&wk[w].g, &wk[w].hill)) return OR_FLAG_BADARG;
 
@@ -608,6 +912,7 @@ int or_batch_step(int nw, const or_walker *wk, double *const *fields, const doub
       int fl = or_cv_eval(&wk[w].cv[k], wk[w].natoms, x[w], &s[3 * w + k], J[w * OR_MAXCV + k]);
       if (fl & OR_FLAG_BADARG) bad = 1;
       flags[w] |= fl;
+      if (aux) aux[w].sb[k] = or_cv_round_bound(&wk[w].cv[k], x[w]);
     }
     for (int k = wk[w].g.d; k < 3; ++k) s[3 * w + k] = 0.0;
   }
@@ -650,12 +955,41 @@ int or_batch_step(int nw, const or_walker *wk, double *const *fields, const doub
     else
       flags[w] |= or_interp(&wk[w].g, fields[w], &s[3 * w], &V[w], g3);
     for (int k = 0; k < d; ++k) g3[k] += or_wall_grad(&wk[w].hill, k, s[3 * w + k]);
+    if (aux) {
+      for (int k = d; k < 3; ++k) aux[w].sb[k] = 0.0;
+      if (wk[w].hill.method == OR_METHOD_MABP_COMPACT) {
+        /* a node look-up: no slope inside a cell; the rounding scale is the
+         * bias and its gradient themselves */
+        for (int q = 0; q < 9; ++q) aux[w].H[q] = 0.0;
+        aux[w].A[0] = fabs(V[w]);
+        for (int k = 0; k < 3; ++k) aux[w].A[1 + k] = k < d ? fabs(g3[k]) : 0.0;
+      } else {
+        or_interp_aux(&wk[w].g, fields[w], &s[3 * w], aux[w].H, aux[w].A);
+      }
+      for (int k = 0; k < d; ++k)
+        if (or_wall_grad(&wk[w].hill, k, s[3 * w + k]) != 0.0) aux[w].H[4 * k] += wk[w].hill.kwall;
+    }
+    if (Jn && Jn[w])
+      for (int i = 0; i < wk[w].natoms; ++i)
+        for (int k = 0; k < 3; ++k) {
+          double n2 = 0.0;
+          if (k < d)
+            for (int q = 0; q < 3; ++q) n2 += J[w * OR_MAXCV + k][3 * i + q] * J[w * OR_MAXCV + k][3 * i + q];
+          Jn[w][3 * i + k] = sqrt(n2);
+        }
     for (int k = 0; k < 3; ++k) dV[3 * w + k] = g3[k];
     double *Fw = F[w];
     for (int a = 0; a < 3 * wk[w].natoms; ++a) {
       double acc = 0.0;
       for (int k = 0; k < d; ++k) acc += g3[k] * J[w * OR_MAXCV + k][a];
       Fw[a] = -acc;
+    }
+    /* closed loop: the move of this step from x, the bias force and the
+     * force of the CV potential (this step's CVs and Jacobians) */
+    if (md) {
+      const double *Jw[OR_MAXCV] = {NULL, NULL, NULL};
+      for (int k = 0; k < d; ++k) Jw[k] = J[w * OR_MAXCV + k];
+      or_md_move(&wk[w], md, streams ? streams[w] : 0u, step, x[w], Fw, &s[3 * w], Jw, xn[w]);
     }
     for (int k = 0; k < d; ++k) free(J[w * OR_MAXCV + k]);
   }
@@ -673,11 +1007,19 @@ int or_batch_step(int nw, const or_walker *wk, double *const *fields, const doub
  * (NULL to skip): s_hist [T][nw][3], V_hist [T][nw], dV_hist [T][nw][3],
  * F_hist [T][frame_stride] (forces at the same offsets as the frames),
  * flag_hist [T][nw], dep_log (capacity dep_cap; *n_dep receives the count).
+ * With md (and Xn_hist [T][frame_stride]) the replay also predicts, for each
+ * step, the coordinates after that step's closed-loop move from the recorded
+ * ones (or_md_move; streams[w] is walker w's noise stream): a recorded
+ * closed-loop trajectory is checked one step at a time against it.
+ * aux_hist [T][nw] and Jn_hist [T][frame_stride] (optional) receive each
+ * step's or_stepaux and, per atom, |ds_k/dx| of each CV k (error-analysis
+ * outputs for per-step comparisons).
  * Returns 0 or OR_FLAG_BADARG. */
 int or_run(int nw, const or_walker *wk, double *const *fields, const double *frames,
            const int64_t *atom_off, int64_t frame_stride, int64_t step0, int64_t T,
            double *s_hist, double *V_hist, double *dV_hist, double *F_hist, int *flag_hist,
-           or_deposit *dep_log, int64_t dep_cap, int64_t *n_dep) {
+           or_deposit *dep_log, int64_t dep_cap, int64_t *n_dep, const or_md *md, const uint32_t *streams,
+           double *Xn_hist, or_stepaux *aux_hist, double *Jn_hist) {
   const double **x = (const double **)malloc(sizeof(double *) * (size_t)nw);
   double **F = (double **)malloc(sizeof(double *) * (size_t)nw);
   double *s = (double *)malloc(sizeof(double) * 3 * (size_t)nw);
@@ -688,12 +1030,17 @@ int or_run(int nw, const or_walker *wk, double *const *fields, const double *fra
   double *Fscratch = F_hist ? NULL : (double *)malloc(sizeof(double) * (size_t)frame_stride);
   int64_t nd = 0;
   int rc = 0;
+  double **Xn = (double **)malloc(sizeof(double *) * (size_t)nw);
+  double **Jn = (double **)malloc(sizeof(double *) * (size_t)nw);
   for (int64_t t = 0; t < T && rc == 0; ++t) {
     for (int w = 0; w < nw; ++w) {
       x[w] = frames + t * frame_stride + atom_off[w];
       F[w] = (F_hist ? F_hist + t * frame_stride : Fscratch) + atom_off[w];
+      Xn[w] = (md && Xn_hist) ? Xn_hist + t * frame_stride + atom_off[w] : NULL;
+      Jn[w] = Jn_hist ? Jn_hist + t * frame_stride + atom_off[w] : NULL;
     }
-    rc = or_batch_step(nw, wk, fields, x, step0 + t, s, V, dV, F, fl, dep);
+    rc = or_batch_step(nw, wk, fields, x, step0 + t, s, V, dV, F, fl, dep, (md && Xn_hist) ? md : NULL, streams,
+                       Xn, aux_hist ? aux_hist + t * nw : NULL, Jn_hist ? Jn : NULL);
     for (int w = 0; w < nw; ++w) {
       if (s_hist) for (int k = 0; k < 3; ++k) s_hist[(t * nw + w) * 3 + k] = s[3 * w + k];
       if (V_hist) V_hist[t * nw + w] = V[w];
@@ -704,6 +1051,8 @@ int or_run(int nw, const or_walker *wk, double *const *fields, const double *fra
     }
   }
   if (n_dep) *n_dep = nd;
+  free(Xn);
+  free(Jn);
   free(x);
   free(F);
   free(s);
@@ -712,6 +1061,58 @@ int or_run(int nw, const or_walker *wk, double *const *fields, const double *fra
   free(fl);
   free(dep);
   free(Fscratch);
+  return rc;
+}
+
+/* Closed-loop run: steps step0..step0+T-1 of nw walkers whose atoms start
+ * in x (one frame laid out as in or_run: walker w's atoms at atom_off[w],
+ * frame_stride doubles), each step's move (or_md_move) applied in place.
+ * Optional outputs (NULL to skip): X_hist [T][frame_stride], the coordinates
+ * each step's bias was evaluated at; s_hist [T][nw][3]; V_hist [T][nw];
+ * the deposit log as in or_run. Returns 0 or OR_FLAG_BADARG. */
+int or_md_run(int nw, const or_walker *wk, double *const *fields, double *x, const int64_t *atom_off,
+              int64_t frame_stride, const or_md *md, const uint32_t *streams, int64_t step0, int64_t T,
+              double *X_hist, double *s_hist, double *V_hist, or_deposit *dep_log, int64_t dep_cap,
+              int64_t *n_dep) {
+  const double **xs = (const double **)malloc(sizeof(double *) * (size_t)nw);
+  double **F = (double **)malloc(sizeof(double *) * (size_t)nw);
+  double **Xn = (double **)malloc(sizeof(double *) * (size_t)nw);
+  double *Fbuf = (double *)malloc(sizeof(double) * (size_t)frame_stride);
+  double *xnext = (double *)malloc(sizeof(double) * (size_t)frame_stride);
+  double *s = (double *)malloc(sizeof(double) * 3 * (size_t)nw);
+  double *V = (double *)malloc(sizeof(double) * (size_t)nw);
+  double *dV = (double *)malloc(sizeof(double) * 3 * (size_t)nw);
+  int *fl = (int *)malloc(sizeof(int) * (size_t)nw);
+  or_deposit *dep = (or_deposit *)malloc(sizeof(or_deposit) * (size_t)nw);
+  int64_t nd = 0;
+  int rc = 0;
+  for (int w = 0; w < nw; ++w) {
+    xs[w] = x + atom_off[w];
+    F[w] = Fbuf + atom_off[w];
+    Xn[w] = xnext + atom_off[w];
+  }
+  for (int64_t t = 0; t < T && rc == 0; ++t) {
+    if (X_hist) memcpy(X_hist + t * frame_stride, x, sizeof(double) * (size_t)frame_stride);
+    rc = or_batch_step(nw, wk, fields, xs, step0 + t, s, V, dV, F, fl, dep, md, streams, Xn, NULL, NULL);
+    for (int w = 0; w < nw; ++w) {
+      memcpy(x + atom_off[w], Xn[w], sizeof(double) * 3 * (size_t)wk[w].natoms);
+      if (s_hist) for (int k = 0; k < 3; ++k) s_hist[(t * nw + w) * 3 + k] = s[3 * w + k];
+      if (V_hist) V_hist[t * nw + w] = V[w];
+      if ((fl[w] & OR_FLAG_DEPOSIT) && dep_log && nd < dep_cap) dep_log[nd] = dep[w];
+      if (fl[w] & OR_FLAG_DEPOSIT) ++nd;
+    }
+  }
+  if (n_dep) *n_dep = nd;
+  free(xs);
+  free(F);
+  free(Xn);
+  free(Fbuf);
+  free(xnext);
+  free(s);
+  free(V);
+  free(dV);
+  free(fl);
+  free(dep);
   return rc;
 }
 
@@ -738,7 +1139,7 @@ int or_langevin_double_well(const or_walker *wk, double *field, double *x, int64
   int rc = 0;
   double amp = sqrt(2.0 * mu * wk->hill.kT * dt);
   for (int64_t t = 0; t < T && rc == 0; ++t) {
-    rc = or_batch_step(1, wk, fields, xs, t, s, &V, dV, Fs, &fl, &dep);
+    rc = or_batch_step(1, wk, fields, xs, t, s, &V, dV, Fs, &fl, &dep, NULL, NULL, NULL, NULL, NULL);
     if (s_hist) s_hist[t] = s[0];
     double sv;
     or_cv_eval(&wk->cv[0], wk->natoms, x, &sv, J);

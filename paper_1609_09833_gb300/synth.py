@@ -200,6 +200,40 @@ class SweepFrames:
         return (tmpl + noise).astype(dtype)
 
 
+# ---------------------------------------------------------------- closed-loop dynamics (plain data)
+
+# The four-term surface of Mueller and Brown (Theor. Chim. Acta 53, 1979):
+# U(X, Y) = sum_i A_i exp(a_i (X - x0_i)^2 + b_i (X - x0_i)(Y - y0_i) + c_i (Y - y0_i)^2).
+MULLER_BROWN = {"A": (-200.0, -100.0, -170.0, 15.0), "a": (-1.0, -1.0, -6.5, 0.7), "b": (0.0, 0.0, 11.0, 0.6),
+                "c": (-10.0, -10.0, -6.5, 0.7), "x0": (1.0, 0.0, -0.5, -1.0), "y0": (0.0, 0.5, 1.5, 1.0)}
+
+
+def md_params(dt: float = 0.002, mu: float = 1.0, kT: float = 2.5, seed: int = 1, potential: str = "none", **kw):
+    """Closed-loop dynamics: overdamped Langevin of every CV atom, time step
+    dt (ps), mobility mu (nm^2 / (kJ/mol ps)), noise at kT, Philox key seed,
+    under the bias plus an optional potential of the CVs."""
+    p = {"dt": float(dt), "mu": float(mu), "kT": float(kT), "seed": int(seed), "potential": potential}
+    p.update(kw)
+    return p
+
+
+def md_double_well(seed: int = 1, A: float = 5.0, B: float = 1.0, **kw):
+    """U(s) = A (s_0^2 - B^2)^2 on the first CV (A = 5 kJ/mol, B = 1 nm)."""
+    return md_params(seed=seed, potential="double_well", dw=(float(A), float(B)), **kw)
+
+
+def md_muller_brown(seed: int = 1, s_box=((0.2, 2.0), (-math.pi, math.pi)), xy_box=((-1.5, 1.2), (-0.2, 2.0)),
+                    scale: float = 0.1, mu: float = 0.1, **kw):
+    """The Mueller-Brown surface times `scale` on the affine image of the CV
+    box s_box onto xy_box (X = mx s_0 + cx, Y = my s_1 + cy)."""
+    (s0a, s0b), (s1a, s1b) = s_box
+    (xa, xb), (ya, yb) = xy_box
+    mx = (xb - xa) / (s0b - s0a)
+    my = (yb - ya) / (s1b - s1a)
+    mb = dict(MULLER_BROWN, scale=float(scale), map=(mx, xa - mx * s0a, my, ya - my * s1a))
+    return md_params(seed=seed, potential="muller_brown", mb=mb, mu=mu, **kw)
+
+
 # ---------------------------------------------------------------- double well (one walker, FP64)
 
 
