@@ -1,18 +1,23 @@
 """Benchmark: bias steps/s of the batched ABP force call on one GB300.
 
-Workload (one "step" of this benchmark = C consecutive MD steps of the whole
-hot path a1..a5 for every walker, one launch of the fused kernel):
+Headline workload (one "step" of this benchmark = C consecutive closed-loop
+MD steps of every walker, one launch of the closed-loop kernel):
   64 walkers, each with its own 256 x 256 FP32 grid (value + compensation,
   3 fields), CVs = centre-of-mass distance of two 16-atom groups in
   [0.2, 2.0] nm and a periodic dihedral, sigma = (0.04 nm, 0.1 rad),
-  w = 0.5 kJ/mol every 50 steps, gamma = 15; seeded open-loop frames
-  (template path + 0.02 nm jitter) resident in HBM, 4000 frames (147 MB,
-  larger than L2) cycled.
+  w = 0.5 kJ/mol every 50 steps, gamma = 15; every atom moves by overdamped
+  Langevin dynamics (dt = 0.002 ps, mu = 0.1 nm^2/(kJ/mol ps), kT = 2.5)
+  under the bias and the Mueller-Brown surface x 0.1 on the CV box, so each
+  step's coordinates come from the previous step's force on the device.
+  L2 is flushed before every timed launch (the grids, 134 MB, exceed it
+  too).
 
-Reported beside the batched number: the plain one-walker-per-launch form
-(three launches per walker per MD step), per-call latency percentiles, an
+Reported beside the closed-loop number: the open-loop replay of recorded
+frames (the windowed form, 1000-step launches; the method's throughput when
+future coordinates are known), the plain one-walker-per-launch form (three
+launches per walker per MD step), per-call latency percentiles, an
 end-to-end figure through the same public call with host buffers, the
-roofline of the fused kernel and the FP64 oracle timed on the host cores.
+roofline of the kernel and the FP64 oracle timed on the host cores.
 
 Multi-GPU (torchrun): every rank runs its own independent 64 walkers
 (replicas; no data-path collective), value = all ranks' bias steps / the
@@ -42,14 +47,22 @@ NW = 64
 NATOMS = 36
 FRAMES = 4000
 SEED = 2024
-# algorithmic bytes per walker-step of this workload (see the design notes):
-# coordinates read + forces written as 16-byte records, interpolation corners
-# (4 nodes x 3 fields x value+compensation x 4 B), and per deposit the stencil
-# read-modify-write (47 x 35 nodes x 3 fields x 2 words x 4 B x 2) plus the
-# height's corner read, every 50 steps.
+# Algorithmic bytes per walker-step of the 64-walker workload: the grid
+# traffic -- interpolation corners (4 nodes x 3 fields x value +
+# compensation x 4 B) and, every 50 steps, the deposit's stencil
+# read-modify-write (47 x 35 nodes x 3 fields x 2 words x 4 B, read and
+# written) plus the height's corner read -- and the atoms: an open-loop
+# replay reads each step's coordinates and writes its forces (36 records of
+# 16 B each way); a closed-loop launch keeps the atoms on chip and reads and
+# writes them once per launch of C steps.
 STENCIL_NODES = 47 * 35
 NODE_BYTES = 3 * 2 * 4
-BYTES_PER_WALKER_STEP = NATOMS * 16 * 2 + 4 * NODE_BYTES + (STENCIL_NODES * NODE_BYTES * 2 + 4 * NODE_BYTES) / 50.0
+GRID_BYTES_PER_WALKER_STEP = 4 * NODE_BYTES + (STENCIL_NODES * NODE_BYTES * 2 + 4 * NODE_BYTES) / 50.0
+BYTES_PER_WALKER_STEP = NATOMS * 16 * 2 + GRID_BYTES_PER_WALKER_STEP
+
+
+def closed_loop_bytes_per_walker_step(C):
+    return GRID_BYTES_PER_WALKER_STEP + NATOMS * 16 * 2 / C
 
 
 def parse():
@@ -64,7 +77,8 @@ def parse():
     ap.add_argument("--tile", default="auto", choices=["auto", "on", "off"])
     ap.add_argument("--group-threads", type=int, default=0)
     ap.add_argument("--no-extra", action="store_true", help="skip the other workloads")
-    ap.add_argument("--only", default=None, choices=["double_well", "uneven", "shared", "serve", "paper_rmsd"],
+    ap.add_argument("--only", default=None, choices=["double_well", "uneven", "shared", "serve", "paper_rmsd",
+                                                      "headline"],
                     help="run just one of the other workloads (for profiling) and print its record")
     return ap.parse_args()
 
@@ -198,6 +212,18 @@ def workload(seed):
     return specs, synth.SweepFrames(NW, seed=seed)
 
 
+HEADLINE_WORKLOAD = ("64 walkers, own 256x256 FP32+comp grids, COM distance + periodic dihedral, closed loop: "
+                     "overdamped Langevin of every atom on the bias + scaled Mueller-Brown surface")
+
+
+def dynamics(seed):
+    """The headline's closed-loop dynamics: Langevin on the scaled
+    Mueller-Brown surface mapped to the CV box."""
+    from paper_1609_09833_gb300 import synth
+
+    return synth.md_muller_brown(seed=seed, mu=0.1)
+
+
 # ---------------------------------------------------------------- reference arm (the oracle)
 
 
@@ -213,14 +239,16 @@ def run_reference(args):
     fields = [w.new_field() for w in ws]
     per = 5  # MD steps per reference step (a bounded sample of the workload)
     off = synth.offsets_of(specs)
-    frames = fr.frames(0, per * (args.warmup + args.steps)).astype(np.float64)
+    md = dynamics(SEED)
+    streams = np.arange(NW)
+    x = fr.frames(0, 1)[0].astype(np.float64)
     step = 0
     for _ in range(args.warmup):
-        oracle.run(ws, frames[step:step + per], off, step, per, fields=fields, record_forces=False)
+        x = oracle.md_run(ws, x, off, md, streams, step, per, fields=fields)["x"]
         step += per
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.run(ws, frames[step:step + per], off, step, per, fields=fields, record_forces=False)
+        x = oracle.md_run(ws, x, off, md, streams, step, per, fields=fields)["x"]
         step += per
     dt = time.perf_counter() - t0
     value = NW * per * args.steps / dt
@@ -229,10 +257,10 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "64 walkers, own 256x256 grids, COM distance + dihedral, open-loop frames",
-                   "md_steps_per_step": per},
+        "config": {"workload": HEADLINE_WORKLOAD, "md_steps_per_step": per},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{per} MD steps x {NW} walkers per step, FP64 C oracle, OpenMP over walkers"},
+                         "sample": f"{per} closed-loop MD steps x {NW} walkers per step, FP64 C oracle, OpenMP "
+                                   "over walkers"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -248,30 +276,51 @@ def cpu_baseline(seconds: float):
     ws = [oracle.Walker(s) for s in specs]
     fields = [w.new_field() for w in ws]
     off = synth.offsets_of(specs)
+    md = dynamics(SEED)
+    streams = np.arange(NW)
     pilot = 40
-    frames = fr.frames(0, pilot).astype(np.float64)
     t0 = time.perf_counter()
-    oracle.run(ws, frames, off, 0, pilot, fields=fields, record_forces=False)
+    x = oracle.md_run(ws, fr.frames(0, 1)[0].astype(np.float64), off, md, streams, 0, pilot, fields=fields)["x"]
     per_step = (time.perf_counter() - t0) / pilot
     T = int(max(50, min(20000, seconds / max(per_step, 1e-9))))
-    frames = fr.frames(pilot, T).astype(np.float64)
     t0 = time.perf_counter()
-    oracle.run(ws, frames, off, pilot, T, fields=fields, record_forces=False)
+    oracle.md_run(ws, x, off, md, streams, pilot, T, fields=fields)
     dt = time.perf_counter() - t0
     return {"value": NW * T / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"MD steps {pilot}..{pilot + T - 1} of the same 64-walker workload ({NW * T} bias steps, "
-                      f"{dt:.1f} s), FP64 C oracle, OpenMP over walkers"}
+            "sample": f"closed-loop MD steps {pilot}..{pilot + T - 1} of the same 64-walker workload ({NW * T} "
+                      f"bias steps, {dt:.1f} s), FP64 C oracle, OpenMP over walkers"}
 
 
 # ---------------------------------------------------------------- the other workloads
 
-CN_FLOPS = 30          # flops per CN pair, no minimum image (see the design notes)
-CN_FLOPS_PBC = 39      # with the minimum image
+# Flops of one coordination-number pair as the defined formula has them
+# (s = sum 1 / (1 + q^3), q = r^2 / r0^2, and dCN/dx for both atoms):
+# differences 3, r^2 5, q 1, q^2 and q^3 2, 1 + q^3 1, the reciprocal 1, the
+# sum 1, the gradient factor -6 q^2 sw^2 / r0^2 3, the two 3-vector updates
+# 12 (one FMA each, 2 flops) = 29; a minimum image adds d / L and d - L k per
+# component, 6 = 35. The ALU rooflines of both CN workloads use these counts.
+CN_PAIR_FLOPS = 29
+CN_PAIR_FLOPS_PBC = 35
 
 
-def fp32_peak_tflops(sm_mhz):
-    """FP32 FMA peak: 152 SMs x 128 lanes x 2 flops x SM clock."""
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+class Fp32Peak:
+    """The device's FP32 FMA throughput, measured by the library's FMA kernel
+    (abp_fp32_fma_peak) with the SM clock sampled while it runs; the peak at
+    another clock scales with the clock."""
+
+    def __init__(self, abp, dev):
+        with Clocks(dev) as clk:
+            flops, secs = abp.abp_fp32_fma_peak(dev, None, 40000)
+        self.tflops = flops / 1e12
+        self.seconds = secs
+        self.mhz = clk.summary()["sm_mhz"] or 2070.0
+
+    def at(self, sm_mhz):
+        return self.tflops * (sm_mhz or self.mhz) / self.mhz
+
+    def source(self, sm_mhz):
+        return (f"measured: FMA-chain kernel {self.tflops:.1f} TFLOP/s at {self.mhz:.0f} MHz "
+                f"({self.seconds * 1e3:.0f} ms), scaled to {sm_mhz or self.mhz:.0f} MHz")
 
 
 def _time_loop(torch, fn, reps):
@@ -287,27 +336,42 @@ def _time_loop(torch, fn, reps):
 
 
 def bench_double_well(abp, synth, torch, dev):
-    """One FP64 walker, COM distance of two 8-atom groups, 512-node grid."""
+    """One FP64 walker, COM distance of two 8-atom groups, 512-node grid:
+    closed loop on U = 5 (s^2 - 1)^2 (overdamped Langevin, mu = 1, dt =
+    0.002, kT = 2.5), and the open-loop replay of a random-walk trajectory."""
     ctx = abp.Context(dev)
     try:
         spec = synth.double_well_com_spec()
-        w = ctx.make_walkers([spec], precision=abp.ABP_PREC_FP64)
         T = 2000
+        offs = torch.zeros(1, dtype=torch.int64, device="cuda")
+        wc = ctx.make_walkers([spec], precision=abp.ABP_PREC_FP64)
+        x = abp.to_records(synth.double_well_com_coords(5)[None], torch.float64).cuda()[0]
+        md = synth.md_double_well(seed=5)
+        st = {"md": 0}
+
+        def closed():
+            abp.abp_md_run(ctx.handle, wc, x, abp.ABP_F64, offs, md, [0], step0=st["md"], nsteps=T)
+            st["md"] += T
+
+        ms_closed = _time_loop(torch, closed, 5)
+        w = ctx.make_walkers([spec], precision=abp.ABP_PREC_FP64)
         x0 = synth.double_well_com_coords(5)
         frames = x0[None] + np.cumsum(synth.rng(6).normal(scale=0.03, size=(T, 16, 3)), axis=0)
         rec = abp.to_records(frames, torch.float64).cuda()
-        offs = torch.zeros(1, dtype=torch.int64, device="cuda")
         F = torch.zeros_like(rec)
-        st = {"md": 0}
+        so = {"md": 0}
 
         def run():
-            abp.abp_run(ctx.handle, w, rec, abp.ABP_F64, offs, 16, F, offs, 16, abp.ABP_FORCES_OVERWRITE, st["md"], T)
-            st["md"] += T
+            abp.abp_run(ctx.handle, w, rec, abp.ABP_F64, offs, 16, F, offs, 16, abp.ABP_FORCES_OVERWRITE, so["md"], T)
+            so["md"] += T
 
         ms = _time_loop(torch, run, 5)
-        return {"workload": "1 walker, FP64 end to end, COM distance 2x8 atoms, 512-node grid, stride 100",
-                "value": T / (ms / 1e3), "unit": "bias steps/s", "us_per_step": 1e3 * ms / T,
-                "md_steps_per_launch": T, "dtype": "f64", "bound": "latency (one walker)"}
+        return {"workload": "1 walker, FP64 end to end, COM distance 2x8 atoms, 512-node grid, stride 100; "
+                            "closed loop on U = 5 (s^2-1)^2",
+                "value": T / (ms_closed / 1e3), "unit": "bias steps/s", "us_per_step": 1e3 * ms_closed / T,
+                "md_steps_per_launch": T, "dtype": "f64", "bound": "latency (one walker's dependent step chain)",
+                "open_loop_replay": {"value": T / (ms / 1e3), "us_per_step": 1e3 * ms / T,
+                                     "form": "windowed, recorded random-walk frames"}}
     finally:
         torch.cuda.synchronize()
         ctx.close()
@@ -355,7 +419,7 @@ def bench_paper_rmsd(abp, synth, torch, dev):
         ctx.close()
 
 
-def bench_uneven(abp, synth, torch, dev, sm_mhz):
+def bench_uneven(abp, synth, torch, dev, sm_mhz, fp32):
     """1000 walkers: 40 % 1D / 50 % 2D / 10 % 3D grids, CN 40 x 400 each."""
     from paper_1609_09833_gb300 import autotune
 
@@ -378,9 +442,9 @@ def bench_uneven(abp, synth, torch, dev, sm_mhz):
             st["md"] += C
 
         ms = _time_loop(torch, run, 6)
-        flops = nw * C * 40 * 400 * CN_FLOPS
+        flops = nw * C * 40 * 400 * CN_PAIR_FLOPS
         achieved = flops / (ms / 1e3) / 1e12
-        peak = fp32_peak_tflops(sm_mhz)
+        peak = fp32.at(sm_mhz)
         return {"workload": "1000 walkers (40% 1D 1024, 50% 2D 128^2/256^2/512^2, 10% 3D 64^3), CN 40x400, "
                             "jitter frames, one launch per 25 MD steps",
                 "value": nw * C / (ms / 1e3), "unit": "bias steps/s", "ms_per_launch": ms,
@@ -388,14 +452,18 @@ def bench_uneven(abp, synth, torch, dev, sm_mhz):
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                              "frac": achieved / peak, "kernel": "k_run / k_run_lean (per-step form, CN pairs)",
                              "traffic": captured_traffic("k_run_uneven1000", nw * C),
-                             "peak_source": f"derived: 152 SM x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz"}}
+                             "flops_per_pair": CN_PAIR_FLOPS, "peak_source": fp32.source(sm_mhz)}}
     finally:
         torch.cuda.synchronize()
         ctx.close()
 
 
-def bench_shared(abp, synth, torch, dev, sm_mhz):
-    """32 walkers on one shared 256^3 grid, 200 x 10,000-atom CN each."""
+def bench_shared(abp, synth, torch, dev, sm_mhz, fp32):
+    """32 walkers on one shared 256^3 grid, 200 x 10,000-atom CN each: the
+    closed loop (free overdamped Langevin of every atom under the bias, the
+    phased form's five launches plus the move per MD step), replayed as a
+    CUDA graph of C steps; the open-loop replay of jitter frames beside it;
+    the pair kernel's own time from the library's per-kernel timing."""
     ctx = abp.Context(dev)
     try:
         nw, C = 32, 10
@@ -404,48 +472,71 @@ def bench_shared(abp, synth, torch, dev, sm_mhz):
         rec = abp.to_records(synth.JitterFrames(tm, seed=42).frames(0, C)).cuda()
         A = rec.shape[1]
         offs = torch.tensor(synth.offsets_of(specs), dtype=torch.int64, device="cuda")
-        walkers = ctx.make_walkers(specs)
-        F = torch.zeros_like(rec)
+        md = synth.md_params(seed=43, mu=0.05)
+        streams = np.arange(nw)
+        # closed loop
+        wc = ctx.make_walkers(specs)
+        x = rec[0].clone()
         abp.abp_deposit_log_enable(ctx.handle, 1 << 16)
-        # direct calls (also uploads the walker tables before capture)
         st = {"md": 0}
 
-        def run():
-            abp.abp_run(ctx.handle, walkers, rec, abp.ABP_F32, offs, A, F, offs, A, abp.ABP_FORCES_OVERWRITE,
-                        st["md"], C)
+        def closed():
+            abp.abp_md_run(ctx.handle, wc, x, abp.ABP_F32, offs, md, streams, step0=st["md"], nsteps=C)
             st["md"] += C
 
-        ms_direct = _time_loop(torch, run, 3)
-        # CUDA-graph replay of the same call (5 launches per MD step captured)
+        ms_direct = _time_loop(torch, closed, 3)
         s = torch.cuda.Stream()
         ctx.set_stream(s.cuda_stream)
         g = torch.cuda.CUDAGraph()
         torch.cuda.synchronize()
         with torch.cuda.graph(g, stream=s):
-            abp.abp_run(ctx.handle, walkers, rec, abp.ABP_F32, offs, A, F, offs, A, abp.ABP_FORCES_OVERWRITE,
-                        10 ** 6, C)
+            abp.abp_md_run(ctx.handle, wc, x, abp.ABP_F32, offs, md, streams, step0=10 ** 6, nsteps=C)
         ctx.set_stream(torch.cuda.current_stream().cuda_stream)
         ms_graph = _time_loop(torch, g.replay, 5)
         log = abp.abp_deposit_log_readout(ctx.handle, 1 << 16)
-        flops = nw * C * 200 * 10_000 * CN_FLOPS_PBC
-        achieved = flops / (ms_graph / 1e3) / 1e12
-        peak = fp32_peak_tflops(sm_mhz)
-        # overlap of the hills of one deposit step (atomic contention)
+        # the pair kernel's own time, direct calls with per-kernel timing
+        abp.abp_ctx_tune(ctx.handle, abp.ABP_TUNE_TIMING, 1)
+        abp.abp_kernel_times(ctx.handle)
+        for _ in range(3):
+            closed()
+        times = abp.abp_kernel_times(ctx.handle)
+        abp.abp_ctx_tune(ctx.handle, abp.ABP_TUNE_TIMING, 0)
+        n_cn, ms_cn_total = times.get("k_big_cn", (0, float("nan")))
+        ms_cn = ms_cn_total / max(n_cn, 1)
+        step_ms = sum(v[1] for v in times.values()) / max(n_cn, 1)
+        flops_launch = nw * 200 * 10_000 * CN_PAIR_FLOPS_PBC
+        achieved = flops_launch / (ms_cn / 1e3) / 1e12
+        peak = fp32.at(sm_mhz)
+        # the open loop on jitter frames (the same walkers' shape)
+        wo = ctx.make_walkers(specs)
+        F = torch.zeros_like(rec)
+        so = {"md": 0}
+
+        def run():
+            abp.abp_run(ctx.handle, wo, rec, abp.ABP_F32, offs, A, F, offs, A, abp.ABP_FORCES_OVERWRITE,
+                        so["md"], C)
+            so["md"] += C
+
+        ms_open = _time_loop(torch, run, 3)
         overlap = None
         if len(log["step"]):
             st0 = log["step"][0]
             ic = log["ic"][log["step"] == st0]
             R = 8
-            pairs = sum(1 for a in range(len(ic)) for b in range(a + 1, len(ic))
-                        if np.all(np.abs(ic[a] - ic[b]) <= 2 * R))
+            pairs = sum(1 for a in range(len(ic)) for b2 in range(a + 1, len(ic))
+                        if np.all(np.abs(ic[a] - ic[b2]) <= 2 * R))
             overlap = {"hills_per_deposit_step": int(len(ic)), "overlapping_box_pairs": int(pairs)}
         return {"workload": "32 walkers, one shared 256^3 grid (FP64 shadow), 200 ligand + 10,000 environment "
-                            "atoms, 6 nm periodic box, stride 10; 10 MD steps per call, CUDA-graph replay",
+                            "atoms, 6 nm periodic box, stride 10; closed loop (free overdamped Langevin, mu = 0.05), "
+                            "10 MD steps per call, CUDA-graph replay",
                 "value": nw * C / (ms_graph / 1e3), "unit": "bias steps/s", "ms_per_md_step": ms_graph / C,
-                "value_direct_calls": nw * C / (ms_direct / 1e3), "gpu_launches_per_md_step": 5,
+                "value_direct_calls": nw * C / (ms_direct / 1e3), "gpu_launches_per_md_step": 6,
+                "open_loop_replay": {"value": nw * C / (ms_open / 1e3), "gpu_launches_per_md_step": 5},
+                "kernel_ms_per_md_step": {k: v[1] / max(v[0], 1) for k, v in times.items()},
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                             "frac": achieved / peak, "kernel": "whole step (CN pair kernel dominant)",
-                             "peak_source": f"derived: 152 SM x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz"},
+                             "frac": achieved / peak, "kernel": "k_big_cn (pair kernel), its own CUDA-event time",
+                             "kernel_share_of_step": ms_cn / step_ms if step_ms > 0 else None,
+                             "flops_per_pair": CN_PAIR_FLOPS_PBC, "peak_source": fp32.source(sm_mhz)},
                 "deposit_contention": overlap}
     finally:
         torch.cuda.synchronize()
@@ -521,34 +612,64 @@ def bench_serve(abp, synth, torch, dev, seconds=2.0, rate=20_000.0):
                    "p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
                    "mean_batch": float(batches.mean())}
         results.clear()
-        # saturation: a backlog of `depth` requests per simulation, queued in one call
+        # saturation: a backlog of `depth` requests per simulation, queued in
+        # one call; three repeats, the median reported with the spread
         depth = 8
-        order = [i for d in range(depth) for i in range(nsim)]
-        sim_ids = np.array([sims[i] for i in order], dtype=np.int64)
-        steps_arr = np.empty(len(order), dtype=np.int64)
-        chunks = []
-        for k, i in enumerate(order):
-            steps_arr[k] = step[i]
-            chunks.append(frames[i][step[i] % nf])
-            step[i] += 1
-        packed = np.ascontiguousarray(np.concatenate(chunks, axis=0))
-        out = np.zeros_like(packed)
-        t0 = time.perf_counter()
-        abp.abp_server_submit_many(srv, sim_ids, steps_arr, packed, out)
-        t_sub = time.perf_counter() - t0
-        while len(results) < nsim * depth and time.perf_counter() - t0 < 120:
-            time.sleep(0.005)
-        t_all = time.perf_counter() - t0
-        lat = np.array([x.t_done - x.t_submit for x in results]) * 1e6
-        sat = {"requests": nsim * depth, "completed": len(results), "throughput": len(results) / t_all,
-               "submit_seconds": t_sub, "mean_batch": float(np.mean([x.batch for x in results]))}
+        reps = []
+        for _ in range(3):
+            results.clear()
+            order = [i for d in range(depth) for i in range(nsim)]
+            sim_ids = np.array([sims[i] for i in order], dtype=np.int64)
+            steps_arr = np.empty(len(order), dtype=np.int64)
+            chunks = []
+            for k, i in enumerate(order):
+                steps_arr[k] = step[i]
+                chunks.append(frames[i][step[i] % nf])
+                step[i] += 1
+            packed = np.ascontiguousarray(np.concatenate(chunks, axis=0))
+            out = np.zeros_like(packed)
+            t0 = time.perf_counter()
+            abp.abp_server_submit_many(srv, sim_ids, steps_arr, packed, out)
+            t_sub = time.perf_counter() - t0
+            while len(results) < nsim * depth and time.perf_counter() - t0 < 120:
+                time.sleep(0.002)
+            t_all = time.perf_counter() - t0
+            reps.append({"completed": len(results), "throughput": len(results) / t_all, "submit_seconds": t_sub,
+                         "mean_batch": float(np.mean([x.batch for x in results]))})
+        tput = sorted(r["throughput"] for r in reps)
+        sat = {"requests_per_repeat": nsim * depth, "repeats": reps, "throughput": tput[1],
+               "spread": (tput[-1] - tput[0]) / tput[1]}
         done.set()
         th.join()
+        # the plain form on the same simulations' shapes: 256 of them as
+        # walkers of their own, three launches per walker per MD step
+        pctx = abp.Context(dev)
+        try:
+            np_ = 256
+            psp = specs[:np_]
+            pw = pctx.make_walkers(psp)
+            xs = np.concatenate([frames[i][0][:, :3] for i in range(np_)])
+            prec = abp.to_records(xs[None]).cuda()[0]
+            poffs = torch.tensor(synth.offsets_of(psp), dtype=torch.int64, device="cuda")
+            pF = torch.zeros_like(prec)
+            for t in range(2):
+                abp.abp_step_plain(pctx.handle, pw, prec, abp.ABP_F32, poffs, pF, poffs, abp.ABP_FORCES_OVERWRITE, t)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            n_plain = 5
+            for t in range(2, 2 + n_plain):
+                abp.abp_step_plain(pctx.handle, pw, prec, abp.ABP_F32, poffs, pF, poffs, abp.ABP_FORCES_OVERWRITE, t)
+            torch.cuda.synchronize()
+            plain = np_ * n_plain / (time.perf_counter() - t0)
+        finally:
+            pctx.close()
         st = abp.abp_server_stats(srv)
         return {"workload": "4096 simulations, 2D grids 64^2..1024^2 FP32+comp, 8..256 atoms, stride 20..500; "
                             "Poisson step requests (host coords in, host forces out)",
-                "value": sat["throughput"], "unit": "bias steps/s (served, saturated)",
+                "value": sat["throughput"], "unit": "bias steps/s (served, saturated; median of 3)",
                 "admitted": len(sims), "hbm_bytes": hbm, "poisson": poisson, "saturation": sat,
+                "plain": {"value": plain, "ratio": sat["throughput"] / plain,
+                          "form": "256 of the simulations as plain-form walkers, 3 launches per walker per step"},
                 "launches": st["launches"]}
     finally:
         if srv is not None:
@@ -592,12 +713,14 @@ def main():
 
     from paper_1609_09833_gb300 import abp, build, synth
 
+    if args.only == "headline":  # the headline line alone (profiling runs)
+        args.only, args.no_extra, args.no_cpu_baseline = None, True, True
     if args.only:
         torch.cuda.set_device(0)
         build.build()
         fn = {"double_well": lambda: bench_double_well(abp, synth, torch, 0),
-              "uneven": lambda: bench_uneven(abp, synth, torch, 0, 2070.0),
-              "shared": lambda: bench_shared(abp, synth, torch, 0, 2070.0),
+              "uneven": lambda: bench_uneven(abp, synth, torch, 0, 2070.0, Fp32Peak(abp, 0)),
+              "shared": lambda: bench_shared(abp, synth, torch, 0, 2070.0, Fp32Peak(abp, 0)),
               "serve": lambda: bench_serve(abp, synth, torch, 0),
               "paper_rmsd": lambda: bench_paper_rmsd(abp, synth, torch, 0)}[args.only]
         print(json.dumps({"only": args.only, **fn()}), flush=True)
@@ -618,28 +741,22 @@ def main():
     abp.abp_ctx_tune(ctx.handle, abp.ABP_TUNE_TILE, {"auto": -1, "on": 1, "off": 0}[args.tile])
     abp.abp_ctx_tune(ctx.handle, abp.ABP_TUNE_GROUP_THREADS, args.group_threads)
     specs, fr = workload(SEED + 7919 * rank)
+    md = dynamics(SEED + rank)
+    streams = np.arange(NW) + NW * rank
     C = args.md_steps
-    nframes = max(FRAMES // C, 1) * C
-    frames = abp.to_records(fr.frames(0, nframes)).cuda()  # [nframes, 64*36, 4]
-    A = frames.shape[1]
+    A = NW * NATOMS
     offs = torch.tensor(synth.offsets_of(specs), dtype=torch.int64, device="cuda")
-    tuned = None
-    if args.tile == "auto" and args.group_threads == 0:
-        from paper_1609_09833_gb300 import autotune
-
-        tuned = autotune.tune(ctx, specs, frames[:C], offs, C)["best"]
+    x0 = abp.to_records(fr.frames(0, 1)).cuda()[0]  # [64*36, 4]: the walkers' atoms at step 0
+    x = x0.clone()
     walkers = ctx.make_walkers(specs)
-    F = torch.zeros(C, A, 4, device="cuda")
     OVER = abp.ABP_FORCES_OVERWRITE
     state = {"md": 0}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # twice L2
 
-    def launch(out=F):
-        md = state["md"]
-        fi = md % nframes
-        if fi + C > nframes:
-            fi = 0
-        abp.abp_run(ctx.handle, walkers, frames[fi:], abp.ABP_F32, offs, A, out, offs, A, OVER, md, C)
-        state["md"] = md + C
+    def launch():
+        md0 = state["md"]
+        abp.abp_md_run(ctx.handle, walkers, x, abp.ABP_F32, offs, md, streams, step0=md0, nsteps=C)
+        state["md"] = md0 + C
 
     def barrier():
         torch.cuda.synchronize()
@@ -650,49 +767,48 @@ def main():
     for _ in range(max(args.warmup, 3)):
         launch()
     barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # each timed launch starts with L2 flushed (the flush itself untimed)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     with Clocks(dev) as clk:
         barrier()
-        e0.record(stream)
-        for _ in range(args.steps):
+        for a, b in ev:
+            flush.fill_(1)
+            a.record(stream)
             launch()
-        e1.record(stream)
+            b.record(stream)
         barrier()
-    ms = e0.elapsed_time(e1)
+    ms = float(sum(a.elapsed_time(b) for a, b in ev))
     if world > 1:
         t = torch.tensor([ms], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
     bias_steps = world * NW * C * args.steps
     value = bias_steps / (ms / 1e3)
-    kernel_ms = ms / args.steps  # one launch of the fused kernel per step
+    kernel_ms = ms / args.steps  # one launch of the closed-loop kernel per step
 
-    # single-MD-step call latency (one launch for all walkers), p50/p99
-    lat = []
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(200)]
-    F1 = torch.zeros(1, A, 4, device="cuda")
-    for a, b in ev:
-        md = state["md"]
+    # one MD step of all 64 walkers per call (a host-coupled MD step), p50/p99
+    evl = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(200)]
+    for a, b in evl:
+        md0 = state["md"]
         a.record(stream)
-        abp.abp_run(ctx.handle, walkers, frames[md % nframes:], abp.ABP_F32, offs, A, F1, offs, A, OVER, md, 1)
+        abp.abp_md_run(ctx.handle, walkers, x, abp.ABP_F32, offs, md, streams, step0=md0, nsteps=1)
         b.record(stream)
-        state["md"] = md + 1
+        state["md"] = md0 + 1
     torch.cuda.synchronize()
-    lat = np.array([a.elapsed_time(b) * 1e3 for a, b in ev])
+    lat = np.array([a.elapsed_time(b) * 1e3 for a, b in evl])
 
     # end to end through the same call with host buffers (pinned), per step:
-    # H2D of the step's C frames, the call, D2H of its forces
-    host_in = frames[:C].cpu().pin_memory()
-    host_out = torch.empty(C, A, 4).pin_memory()
-    dev_in = torch.empty_like(frames[:C])
+    # H2D of the walkers' atoms, C closed-loop steps, D2H of the moved atoms
+    host_in = x.cpu().pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
     n_e2e = max(3, min(args.steps, 30))
 
     def e2e_step():
-        md = state["md"]
-        dev_in.copy_(host_in, non_blocking=True)
-        abp.abp_run(ctx.handle, walkers, dev_in, abp.ABP_F32, offs, A, F, offs, A, OVER, md, C)
-        host_out.copy_(F, non_blocking=True)
-        state["md"] = md + C
+        md0 = state["md"]
+        x.copy_(host_in, non_blocking=True)
+        abp.abp_md_run(ctx.handle, walkers, x, abp.ABP_F32, offs, md, streams, step0=md0, nsteps=C)
+        host_out.copy_(x, non_blocking=True)
+        state["md"] = md0 + C
 
     for _ in range(2):
         e2e_step()
@@ -705,7 +821,38 @@ def main():
     e2e = {"value": NW * C * n_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(host_in.numel() * 4),
            "d2h_bytes_per_step": int(host_out.numel() * 4)}
 
-    # the plain one-walker-per-launch form on the same workload
+    # the open-loop replay of recorded frames (windowed form, the former
+    # headline) and the plain one-walker-per-launch form on those frames
+    nframes = max(FRAMES // C, 1) * C
+    frames = abp.to_records(fr.frames(0, nframes)).cuda()  # [nframes, 64*36, 4], larger than L2
+    tuned = None
+    if args.tile == "auto" and args.group_threads == 0:
+        from paper_1609_09833_gb300 import autotune
+
+        tuned = autotune.tune(ctx, specs, frames[:C], offs, C)["best"]
+    wo = ctx.make_walkers(specs)
+    F = torch.zeros(C, A, 4, device="cuda")
+    so = {"md": 0}
+
+    def launch_open():
+        md0 = so["md"]
+        fi = md0 % nframes
+        if fi + C > nframes:
+            fi = 0
+        abp.abp_run(ctx.handle, wo, frames[fi:], abp.ABP_F32, offs, A, F, offs, A, OVER, md0, C)
+        so["md"] = md0 + C
+
+    for _ in range(3):
+        launch_open()
+    torch.cuda.synchronize()
+    n_open = max(10, args.steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(n_open):
+        launch_open()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    open_ms = e0.elapsed_time(e1) / n_open
     wp = ctx.make_walkers(specs)
     Fp = torch.zeros(A, 4, device="cuda")
     for t in range(3):
@@ -719,12 +866,25 @@ def main():
     plain_value = NW * n_plain / (time.perf_counter() - t0)
 
     peaks, src = load_peaks()
-    achieved = BYTES_PER_WALKER_STEP * NW * C / (kernel_ms / 1e3) / 1e9
-    traffic = captured_traffic("k_win_mb64", NW * C)
+    psrc = f"{src} (MEASURED_PEAKS.json hbm_gbs, copy)" if src == "measured" else "fallback 6.8 TB/s"
+    cl_bytes = closed_loop_bytes_per_walker_step(C)
+    achieved = cl_bytes * NW * C / (kernel_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                "kernel": "k_win<float> (windowed form)", "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs, copy)"
-                if src == "measured" else "fallback 6.8 TB/s"}
+                "frac": achieved / peaks["hbm_gbs"], "traffic": captured_traffic("k_md_mb64", NW * C),
+                "kernel": "k_md<float, 2> (closed-loop form, one warp per walker)", "peak_source": psrc,
+                "bytes_per_walker_step": cl_bytes,
+                "limiter": "each walker's steps form a dependent chain (CVs, grid corners from L2, force, move); "
+                           "64 chains on 64 SMs",
+                "us_per_walker_step": 1e3 * kernel_ms / C}
+    open_achieved = BYTES_PER_WALKER_STEP * NW * C / (open_ms / 1e3) / 1e9
+    open_loop = {"workload": "the same 64 walkers replaying 4000 recorded open-loop frames (147 MB, larger than "
+                             "L2, cycled), windowed form", "value": NW * C / (open_ms / 1e3), "unit": UNIT,
+                 "ms_per_launch": open_ms, "md_steps_per_launch": C, "launch_shape": tuned,
+                 "roofline": {"bound": "hbm", "achieved": open_achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                              "frac": open_achieved / peaks["hbm_gbs"],
+                              "traffic": captured_traffic("k_win_mb64", NW * C),
+                              "kernel": "k_win<float> (windowed form)", "peak_source": psrc,
+                              "bytes_per_walker_step": BYTES_PER_WALKER_STEP}}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds)
@@ -732,10 +892,13 @@ def main():
     extra = None
     if rank == 0 and world == 1 and not args.no_extra:
         sm = clocks["sm_mhz"] or 2070.0
-        extra = {}
+        fp32 = Fp32Peak(abp, dev)
+        extra = {"open_loop_replay64": open_loop,
+                 "fp32_peak": {"tflops": fp32.tflops, "sm_mhz": fp32.mhz, "seconds": fp32.seconds,
+                               "how": "abp_fp32_fma_peak: 8 x SMs CTAs x 256 threads x 8 FMA chains"}}
         for name, fn in (("double_well_fp64", lambda: bench_double_well(abp, synth, torch, dev)),
-                         ("uneven1000", lambda: bench_uneven(abp, synth, torch, dev, sm)),
-                         ("shared256", lambda: bench_shared(abp, synth, torch, dev, sm)),
+                         ("uneven1000", lambda: bench_uneven(abp, synth, torch, dev, sm, fp32)),
+                         ("shared256", lambda: bench_shared(abp, synth, torch, dev, sm, fp32)),
                          ("serve4096", lambda: bench_serve(abp, synth, torch, dev)),
                          ("paper_rmsd_mabp64", lambda: bench_paper_rmsd(abp, synth, torch, dev))):
             try:
@@ -747,20 +910,20 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "64 walkers, own 256x256 FP32+comp grids, COM distance + periodic dihedral, "
-                                   "open-loop frames", "md_steps_per_step": C, "walkers_per_gpu": NW,
+            "config": {"workload": HEADLINE_WORKLOAD, "md_steps_per_step": C, "walkers_per_gpu": NW,
                        "atoms_per_walker": NATOMS, "grid": "256x256x3 fields", "deposit_stride": 50,
-                       "l2": "inputs larger than L2: 4000 resident frames (147 MB) cycled",
-                       "parallelism": f"replicas x{world}", "launch_shape": tuned},
+                       "dynamics": "overdamped Langevin, dt 0.002 ps, mu 0.1, kT 2.5, Mueller-Brown x 0.1",
+                       "l2": "flushed before every timed launch (256 MB write); grids 134 MB",
+                       "parallelism": f"replicas x{world}"},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clocks,
             "gpu_launches": args.steps,
             "plain": {"value": plain_value, "unit": UNIT, "ratio": value / plain_value,
-                      "form": "3 launches per walker per MD step from a host loop"},
+                      "form": "3 launches per walker per MD step from a host loop (open-loop frames)"},
             "latency_us": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                           "what": "one MD step of all 64 walkers, one call, CUDA events"},
+                           "what": "one closed-loop MD step of all 64 walkers, one call, CUDA events"},
             "other_workloads": extra,
         }
         print(json.dumps(line), flush=True)

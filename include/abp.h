@@ -170,9 +170,9 @@ abp_status abp_ctx_set_stream(abp_ctx *ctx, void *cuda_stream);
 /* Bytes currently allocated against the budget. */
 abp_status abp_ctx_bytes(const abp_ctx *ctx, size_t *used, size_t *budget);
 
-/* Launch-shape knobs of the batched form, for the autotuner (the paper has
- * no counterpart: its bias routine runs on one CPU rank). 0 (or -1 for
- * ABP_TUNE_TILE) restores the library's default choice. Knobs change only
+/* Launch-shape knobs of the batched form, for the autotuner, and the timing
+ * switch (the paper has no counterpart: its bias routine runs on one CPU
+ * rank). 0 (or -1 for ABP_TUNE_TILE) restores the library's default choice. Knobs change only
  * the schedule: results are bit-identical for every tile setting and every
  * number of groups per CTA; a different group width changes the order of
  * the CV sums, so results then agree to rounding.
@@ -189,7 +189,21 @@ abp_status abp_ctx_bytes(const abp_ctx *ctx, size_t *used, size_t *budget);
 #define ABP_TUNE_GROUPS_PER_CTA 2
 #define ABP_TUNE_TILE 3
 #define ABP_TUNE_LEAN 4
+#define ABP_TUNE_TIMING 5 /* 1 = bracket every kernel launch of the context with CUDA events (read by
+                             abp_kernel_times); 0 = off (the default). Changes no result. */
 abp_status abp_ctx_tune(abp_ctx *ctx, int knob, int value);
+
+/* Per-kernel device time of the context's launches since the last call
+ * (with ABP_TUNE_TIMING on): up to cap entries {kernel name, launches,
+ * milliseconds summed over the launches}; *n_out receives the count. Syncs
+ * the context stream; the totals restart after the call. With timing off,
+ * *n_out = 0. Launches captured into a CUDA graph are not timed. */
+typedef struct {
+  char name[32];
+  int64_t launches;
+  double ms;
+} abp_kernel_time;
+abp_status abp_kernel_times(abp_ctx *ctx, abp_kernel_time *out, int cap, int *n_out);
 void abp_ctx_destroy(abp_ctx *ctx);
 
 /* ---- grids and walkers ---------------------------------------------------- */
@@ -244,6 +258,65 @@ abp_status abp_run(abp_ctx *ctx, abp_walker *const *walkers, int n, const void *
 abp_status abp_step_plain(abp_ctx *ctx, abp_walker *const *walkers, int n, const void *coords_dev,
                           int coords_dtype, const int64_t *coord_offsets_dev, void *forces_dev,
                           const int64_t *force_offsets_dev, int mode, int64_t step);
+
+/* ---- closed-loop dynamics ------------------------------------------------------- */
+
+/* A model MD engine around the force call, on the device: the paper's bias
+ * routine sits inside the biased MD cycle (Figure "cycle": coordinates in,
+ * bias force out, added to the MD force), so the coordinates of step t + 1
+ * depend on the bias force of step t. abp_md_run closes that loop without
+ * leaving the GPU. Every CV atom moves by overdamped Langevin dynamics
+ *   x <- x + dt mu F + sqrt(2 mu kT dt) xi,
+ *   F  = F_bias - sum_k dU/ds_k ds_k/dx,
+ * F_bias the step's bias force (steps a1..a5, as abp_run computes it) and U
+ * an optional potential of the walker's CVs; xi three standard normals per
+ * atom and step: Philox-4x32-10 (Salmon et al., "Parallel random numbers: as
+ * easy as 1, 2, 3", SC'11) of the counter (atom index, step low 32 bits,
+ * step high 32 bits, the walker's stream) under the key (seed low 32 bits,
+ * seed high 32 bits); each output word's top 24 bits give u = (j + 1/2) 2^-24,
+ * and Box-Muller gives n0 = r0 cos(2 pi u1), n1 = r0 sin(2 pi u1),
+ * n2 = r2 cos(2 pi u3), r = sqrt(-2 ln u). The paper has no counterpart (its
+ * MD engine is GROMACS). */
+#define ABP_POT_NONE 0
+#define ABP_POT_DOUBLE_WELL 1  /* U = dw_a (s_0^2 - dw_b^2)^2 */
+#define ABP_POT_MULLER_BROWN 2 /* U = mb_scale sum_{i<4} mb_A[i] exp(mb_a[i] X'^2 + mb_b[i] X' Y' + mb_c[i] Y'^2),
+                                  X' = X - mb_x0[i], Y' = Y - mb_y0[i], X = mb_map[0] s_0 + mb_map[1],
+                                  Y = mb_map[2] s_1 + mb_map[3] (the surface of Mueller and Brown,
+                                  Theor. Chim. Acta 53 (1979), on an affine image of the CV box) */
+
+typedef struct {
+  double dt;        /* time step (ps) */
+  double mobility;  /* mu (nm^2 / (kJ/mol ps)) */
+  double kT;        /* thermal energy of the noise (kJ/mol) */
+  uint64_t seed;    /* Philox key */
+  int potential;    /* ABP_POT_* */
+  double dw_a, dw_b;
+  double mb_scale;
+  double mb_map[4];
+  double mb_A[4], mb_a[4], mb_b[4], mb_c[4], mb_x0[4], mb_y0[4];
+} abp_md_desc;
+
+/* nsteps closed-loop MD steps step0..step0+nsteps-1 of n walkers in one
+ * launch. coords_dev holds each walker's atoms at step0 (records at
+ * coord_offsets_dev[w] + i, dtype as for abp_run) and receives them after
+ * the last step's move (in place). streams (host, n values) are the walkers'
+ * noise streams. Optional outputs (NULL to skip): traj_dev, the coordinates
+ * each step's bias was evaluated at (records at traj_offsets_dev[w] +
+ * t * traj_step_stride + i); forces_dev, each step's bias force (records at
+ * force_offsets_dev[w] + t * force_step_stride + i, by mode; without it
+ * abp_forces delivers the last step's). Walkers whose CVs are COM
+ * distances, dihedrals or RMSDs run one warp each (steps chained on the
+ * device); walkers of the phased form (a shared grid or a large walker) run
+ * their step's launches followed by the move, and take ABP_POT_NONE only.
+ * Other walkers (a coordination number in the fused form) are rejected with
+ * ABP_ERR_UNSUPPORTED. A walker that meets non-finite coordinates stops
+ * there (its state reports ABP_WFLAG_NONFINITE; abp_sync returns
+ * ABP_ERR_NONFINITE). Asynchronous on the context stream. */
+abp_status abp_md_run(abp_ctx *ctx, abp_walker *const *walkers, int n, void *coords_dev, int coords_dtype,
+                      const int64_t *coord_offsets_dev, const abp_md_desc *md, const uint32_t *streams,
+                      void *traj_dev, const int64_t *traj_offsets_dev, int64_t traj_step_stride, void *forces_dev,
+                      const int64_t *force_offsets_dev, int64_t force_step_stride, int mode, int64_t step0,
+                      int nsteps);
 
 /* ---- readouts ------------------------------------------------------------ */
 
@@ -358,6 +431,10 @@ abp_status abp_server_admit(abp_server *srv, const abp_grid_desc *grid, const ab
                             int64_t *sim);
 /* Releases a simulation once its requests have finished (waits for them). */
 abp_status abp_server_release(abp_server *srv, int64_t sim);
+/* Copies a simulation's bias grid (as abp_bias_readout) once its queued and
+ * running requests have finished (waits for them, up to 60 s, then
+ * ABP_ERR_TIMEOUT): the free-energy estimate of a served simulation. */
+abp_status abp_server_bias_readout(abp_server *srv, int64_t sim, void *dst, int dst_is_device, int dtype);
 /* Queues MD step `step` of simulation `sim`: coords_host (natoms float
  * records x, y, z, pad) is copied before the call returns; the bias forces
  * are written (overwrite) to forces_host (natoms float records, caller-owned,
@@ -419,6 +496,18 @@ double abp_server_now(void);
 abp_status abp_step_static(int device, void *cuda_stream, const abp_grid_desc *grid_desc, void *grid_records_dev,
                            const abp_walker_desc *walker_desc, const void *coords_dev, int coords_dtype,
                            void *forces_dev, int mode, int64_t step);
+
+/* ---- measurement ------------------------------------------------------------ */
+
+/* The device's FP32 FMA throughput (the paper has no counterpart: it is the
+ * denominator of the arithmetic rooflines of the coordination-number pair
+ * loops): one launch of 8 x (multiprocessors) CTAs of 256 threads, each
+ * thread advancing 8 independent FMA chains for `iters` rounds (2 flops per
+ * FMA), timed with CUDA events on cuda_stream after a short warm-up launch.
+ * Writes FLOP/s to *flops_per_s and the timed seconds to *seconds (may be
+ * NULL). Allocates and frees a small output buffer; restores the caller's
+ * current device; synchronous. */
+abp_status abp_fp32_fma_peak(int device, void *cuda_stream, int iters, double *flops_per_s, double *seconds);
 
 /* Waits for the context stream; returns ABP_ERR_NONFINITE if any walker
  * stepped since the last sync saw non-finite coordinates. */

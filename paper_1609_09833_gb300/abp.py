@@ -67,6 +67,43 @@ HILL_DTYPE = np.dtype([("s", "<f8", (3,)), ("height", "<f8"), ("step", "<i8"), (
 assert HILL_DTYPE.itemsize == 48
 
 
+class MdDesc(C.Structure):
+    _fields_ = [("dt", C.c_double), ("mobility", C.c_double), ("kT", C.c_double), ("seed", C.c_uint64),
+                ("potential", C.c_int), ("dw_a", C.c_double), ("dw_b", C.c_double), ("mb_scale", C.c_double),
+                ("mb_map", C.c_double * 4), ("mb_A", C.c_double * 4), ("mb_a", C.c_double * 4),
+                ("mb_b", C.c_double * 4), ("mb_c", C.c_double * 4), ("mb_x0", C.c_double * 4),
+                ("mb_y0", C.c_double * 4)]
+
+
+ABP_POT_NONE, ABP_POT_DOUBLE_WELL, ABP_POT_MULLER_BROWN = 0, 1, 2
+_POTS = {"none": ABP_POT_NONE, "double_well": ABP_POT_DOUBLE_WELL, "muller_brown": ABP_POT_MULLER_BROWN}
+
+
+def md_desc(md: dict) -> MdDesc:
+    """MdDesc from a closed-loop dynamics dict (synth.md_params)."""
+    d = MdDesc()
+    d.dt, d.mobility, d.kT = float(md["dt"]), float(md["mu"]), float(md["kT"])
+    d.seed = int(md["seed"]) & ((1 << 64) - 1)
+    d.potential = _POTS[md.get("potential", "none")]
+    if d.potential == ABP_POT_DOUBLE_WELL:
+        d.dw_a, d.dw_b = float(md["dw"][0]), float(md["dw"][1])
+    elif d.potential == ABP_POT_MULLER_BROWN:
+        mb = md["mb"]
+        d.mb_scale = float(mb["scale"])
+        for q in range(4):
+            d.mb_map[q] = float(mb["map"][q])
+            for key in ("A", "a", "b", "c", "x0", "y0"):
+                getattr(d, "mb_" + key)[q] = float(mb[key][q])
+    return d
+
+
+class KernelTime(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("ms", C.c_double)]
+
+
+ABP_TUNE_TIMING = 5
+
+
 class ServerDesc(C.Structure):
     _fields_ = [("max_batch", C.c_int), ("max_atoms", C.c_int), ("nstreams", C.c_int)]
 
@@ -94,6 +131,8 @@ _SIGS = {
     "abp_run": [_vp, C.POINTER(_vp), C.c_int, _vp, C.c_int, _vp, C.c_int64, _vp, _vp, C.c_int64, C.c_int,
                 C.c_int64, C.c_int],
     "abp_step_plain": [_vp, C.POINTER(_vp), C.c_int, _vp, C.c_int, _vp, _vp, _vp, C.c_int, C.c_int64],
+    "abp_md_run": [_vp, C.POINTER(_vp), C.c_int, _vp, C.c_int, _vp, C.POINTER(MdDesc), C.POINTER(C.c_uint32), _vp,
+                   _vp, C.c_int64, _vp, _vp, C.c_int64, C.c_int, C.c_int64, C.c_int],
     "abp_shared_hills": [_vp, C.POINTER(_vp), C.c_int, _vp, C.c_int, _vp, C.c_int64, _vp, C.c_size_t,
                          C.POINTER(C.c_size_t)],
     "abp_grid_apply_hills": [_vp, _vp, _vp, C.c_size_t],
@@ -116,11 +155,14 @@ _SIGS = {
     "abp_server_destroy": [_vp],
     "abp_server_admit": [_vp, C.POINTER(GridDesc), C.POINTER(WalkerDesc), C.POINTER(C.c_int64)],
     "abp_server_release": [_vp, C.c_int64],
+    "abp_server_bias_readout": [_vp, C.c_int64, _vp, C.c_int, C.c_int],
     "abp_server_submit": [_vp, C.c_int64, C.c_int64, _vp, _vp, C.c_uint64],
     "abp_server_submit_many": [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp],
     "abp_server_poll": [_vp, C.POINTER(Result), C.c_int, C.POINTER(C.c_int), C.c_int],
     "abp_server_stats": [_vp, _i64p, _i64p, _i64p, _i64p],
     "abp_server_now": [],
+    "abp_fp32_fma_peak": [C.c_int, _vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)],
+    "abp_kernel_times": [_vp, C.POINTER(KernelTime), C.c_int, C.POINTER(C.c_int)],
     "abp_last_error": [],
     "abp_version": [],
 }
@@ -259,6 +301,19 @@ def abp_step_plain(ctx, walkers, coords, coords_dtype, coord_offsets, forces, fo
                                  _ptr(coord_offsets), _ptr(forces), _ptr(force_offsets), int(mode), int(step)))
 
 
+def abp_md_run(ctx, walkers, coords, coords_dtype, coord_offsets, md, streams, traj=None, traj_offsets=None,
+               traj_step_stride=0, forces=None, force_offsets=None, force_step_stride=0, mode=ABP_FORCES_OVERWRITE,
+               step0: int = 0, nsteps: int = 1):
+    """Closed-loop MD steps (coordinates moved in place). md: MdDesc or a
+    dynamics dict; streams: one noise stream per walker."""
+    desc = md if isinstance(md, MdDesc) else md_desc(md)
+    st = np.ascontiguousarray(np.asarray(streams, dtype=np.uint32))
+    _check(load().abp_md_run(ctx, _walkers(walkers), len(walkers), _ptr(coords), coords_dtype, _ptr(coord_offsets),
+                             C.byref(desc), st.ctypes.data_as(C.POINTER(C.c_uint32)), _ptr(traj), _ptr(traj_offsets),
+                             int(traj_step_stride), _ptr(forces), _ptr(force_offsets), int(force_step_stride),
+                             int(mode), int(step0), int(nsteps)))
+
+
 def abp_shared_hills(ctx, walkers, coords, coords_dtype, coord_offsets, step: int) -> np.ndarray:
     """Hill records (HILL_DTYPE) of this step's depositing walkers, in list order."""
     out = np.zeros(max(1, len(walkers)), dtype=HILL_DTYPE)
@@ -370,6 +425,14 @@ def abp_server_release(srv, sim: int):
     _check(load().abp_server_release(srv, int(sim)))
 
 
+def abp_server_bias_readout(srv, sim: int, spec_grid: dict) -> np.ndarray:
+    """A served simulation's grid fields [nodes, 1 + d] (FP64), after its requests."""
+    d = len(spec_grid["n"])
+    out = np.zeros((int(np.prod(spec_grid["n"])), 1 + d), dtype=np.float64)
+    _check(load().abp_server_bias_readout(srv, int(sim), _ptr(out), 0, ABP_F64))
+    return out
+
+
 def abp_server_submit(srv, sim: int, step: int, coords_host, forces_host, tag: int = 0):
     _check(load().abp_server_submit(srv, int(sim), int(step), _ptr(coords_host), _ptr(forces_host), int(tag)))
 
@@ -397,6 +460,21 @@ def abp_server_stats(srv):
 
 def abp_server_now() -> float:
     return float(load().abp_server_now())
+
+
+def abp_kernel_times(ctx) -> dict:
+    """Per-kernel {name: (launches, ms)} since the last call (ABP_TUNE_TIMING on)."""
+    buf = (KernelTime * 64)()
+    n = C.c_int()
+    _check(load().abp_kernel_times(ctx, buf, 64, C.byref(n)))
+    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].ms)) for i in range(n.value)}
+
+
+def abp_fp32_fma_peak(device: int = 0, stream=None, iters: int = 20000):
+    """Measured FP32 FMA throughput of the device: (FLOP/s, seconds timed)."""
+    f, s = C.c_double(), C.c_double()
+    _check(load().abp_fp32_fma_peak(int(device), stream, int(iters), C.byref(f), C.byref(s)))
+    return f.value, s.value
 
 
 def abp_last_error() -> str:

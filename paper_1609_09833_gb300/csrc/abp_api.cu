@@ -41,6 +41,72 @@ abp_status fail(abp_status code, const char *fmt, ...) {
     if (e_ != cudaSuccess) return fail(ABP_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
 
+// Per-kernel timing of a context: an event pair per launch, accumulated per
+// kernel name when read (abp_kernel_times).
+struct KernelTimer final : LaunchTimer {
+  struct Pending {
+    std::string name;
+    cudaEvent_t a, b;
+    bool open;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  std::vector<std::pair<std::string, std::pair<long long, double>>> totals;
+  cudaEvent_t take() {
+    cudaEvent_t e = nullptr;
+    if (!pool.empty()) {
+      e = pool.back();
+      pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+      e = nullptr;
+    }
+    return e;
+  }
+  void begin(const char *kernel, cudaStream_t st) override {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+    cudaEvent_t a = take(), b = take();
+    if (!a || !b) {
+      if (a) pool.push_back(a);
+      if (b) pool.push_back(b);
+      return;
+    }
+    cudaEventRecord(a, st);
+    pending.push_back(Pending{kernel, a, b, true});
+  }
+  void end(const char *kernel, cudaStream_t st) override {
+    if (!pending.empty() && pending.back().open && pending.back().name == kernel) {
+      cudaEventRecord(pending.back().b, st);
+      pending.back().open = false;
+    }
+  }
+  // accumulate the finished pairs (caller has synchronised)
+  void collect() {
+    for (auto &p : pending) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+        auto it = std::find_if(totals.begin(), totals.end(), [&](const auto &t) { return t.first == p.name; });
+        if (it == totals.end()) {
+          totals.push_back({p.name, {0, 0.0}});
+          it = totals.end() - 1;
+        }
+        it->second.first += 1;
+        it->second.second += ms;
+      }
+      pool.push_back(p.a);
+      pool.push_back(p.b);
+    }
+    pending.clear();
+  }
+  ~KernelTimer() override {
+    for (auto &p : pending) {
+      cudaEventDestroy(p.a);
+      cudaEventDestroy(p.b);
+    }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
 struct TableCache {
   std::vector<TableEntry> key;
   TableEntry *dev = nullptr;
@@ -72,6 +138,7 @@ struct abp_ctx {
   size_t big_cap = 0;
   HillDev *hill_dev = nullptr;  // hill records of the last abp_grid_apply_hills
   size_t hill_cap = 0;
+  KernelTimer *timer = nullptr;  // ABP_TUNE_TIMING
   std::mutex mu;
 };
 
@@ -322,6 +389,16 @@ abp_status abp_ctx_tune(abp_ctx *ctx, int knob, int value) {
       if (value < 0 || value > 1) return fail(ABP_ERR_INVALID_ARG, "lean knob must be 0 or 1");
       ctx->tune_lean = value;
       return ABP_OK;
+    case ABP_TUNE_TIMING:
+      if (value < 0 || value > 1) return fail(ABP_ERR_INVALID_ARG, "timing knob must be 0 or 1");
+      if (value && !ctx->timer) ctx->timer = new (std::nothrow) KernelTimer();
+      if (value && !ctx->timer) return fail(ABP_ERR_OOM, "timer");
+      if (!value && ctx->timer) {
+        cudaStreamSynchronize(ctx->stream);
+        delete ctx->timer;
+        ctx->timer = nullptr;
+      }
+      return ABP_OK;
   }
   return fail(ABP_ERR_INVALID_ARG, "unknown knob %d", knob);
 }
@@ -344,7 +421,30 @@ void abp_ctx_destroy(abp_ctx *ctx) {
   if (ctx->log.rec) cudaFree(ctx->log.rec);
   if (ctx->log.count) cudaFree(ctx->log.count);
   if (ctx->ctr) cudaFree(ctx->ctr);
+  delete ctx->timer;
   delete ctx;
+}
+
+abp_status abp_kernel_times(abp_ctx *ctx, abp_kernel_time *out, int cap, int *n_out) {
+  if (!ctx || !n_out || (cap > 0 && !out)) return fail(ABP_ERR_INVALID_ARG, "NULL argument");
+  *n_out = 0;
+  if (!ctx->timer) return ABP_OK;
+  abp_status st = set_device(ctx);
+  if (st) return st;
+  CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  ctx->timer->collect();
+  int n = 0;
+  for (const auto &t : ctx->timer->totals) {
+    if (n >= cap) break;
+    std::memset(&out[n], 0, sizeof(abp_kernel_time));
+    std::snprintf(out[n].name, sizeof out[n].name, "%s", t.first.c_str());
+    out[n].launches = t.second.first;
+    out[n].ms = t.second.second;
+    ++n;
+  }
+  ctx->timer->totals.clear();
+  *n_out = n;
+  return ABP_OK;
 }
 
 // ---------------------------------------------------------------- grids
@@ -740,9 +840,9 @@ int32_t abp_walker_id(const abp_walker *w) { return w ? w->hd.id : -1; }
 // Device table for a sub-list of the caller's walkers (entries keep the
 // caller's index, which selects coordinate and force offsets).
 static abp_status sub_table(abp_ctx *ctx, const std::vector<abp_walker *> &ws, const std::vector<int> &idx,
-                            const TableEntry **out) {
+                            const TableEntry **out, const uint32_t *streams = nullptr) {
   std::vector<TableEntry> key(ws.size());
-  for (size_t i = 0; i < ws.size(); ++i) key[i] = TableEntry{ws[i]->dd, idx[i], 0};
+  for (size_t i = 0; i < ws.size(); ++i) key[i] = TableEntry{ws[i]->dd, idx[i], streams ? streams[idx[i]] : 0u};
   std::vector<long long> cost(ws.size());
   std::vector<size_t> order(ws.size());
   for (size_t i = 0; i < ws.size(); ++i) order[i] = i;
@@ -778,12 +878,12 @@ static abp_status sub_table(abp_ctx *ctx, const std::vector<abp_walker *> &ws, c
 
 // Items of the phased form: one per walker, then one per CN chunk.
 static abp_status big_items(abp_ctx *ctx, const std::vector<abp_walker *> &ws, const std::vector<int> &idx,
-                            BigArgs *a) {
+                            BigArgs *a, const uint32_t *streams = nullptr) {
   std::vector<BigItem> key;
   int max_stencil = 0, any_shared = 0, max_atoms = 0;
   size_t cn_smem = 0;
   for (size_t i = 0; i < ws.size(); ++i) {
-    key.push_back(BigItem{ws[i]->dd, idx[i], 0});
+    key.push_back(BigItem{ws[i]->dd, idx[i], 0, streams ? streams[idx[i]] : 0u, 0});
     const WalkerDev &hd = ws[i]->hd;
     max_atoms = std::max(max_atoms, hd.natoms);
     int box = 1;
@@ -795,7 +895,7 @@ static abp_status big_items(abp_ctx *ctx, const std::vector<abp_walker *> &ws, c
   int ncn = 0;
   for (size_t i = 0; i < ws.size(); ++i) {
     int nc = big_chunks(ws[i]->hd);
-    for (int c = 0; c < nc; ++c) key.push_back(BigItem{ws[i]->dd, idx[i], c});
+    for (int c = 0; c < nc; ++c) key.push_back(BigItem{ws[i]->dd, idx[i], c, 0u, 0});
     ncn += nc;
   }
   if (key.size() != ctx->big_key.size() ||
@@ -888,7 +988,10 @@ static abp_status run_common(abp_ctx *ctx, abp_walker *const *walkers, int n, co
     a.nsteps = nsteps;
     a.log = ctx->log;
     a.ctr = ctx->ctr;
+    const char *kname = win ? "k_win" : (a.lean && a.tile_budget == 0 ? "k_run_lean" : "k_run");
+    if (ctx->timer) ctx->timer->begin(kname, ctx->stream);
     cudaError_t e = launch_run(a, fp64, ctx->stream);
+    if (ctx->timer) ctx->timer->end(kname, ctx->stream);
     if (e != cudaSuccess) return fail(ABP_ERR_CUDA, "fused launch: %s", cudaGetErrorString(e));
   }
   if (!bw.empty()) {
@@ -901,6 +1004,7 @@ static abp_status run_common(abp_ctx *ctx, abp_walker *const *walkers, int n, co
     b.mode = mode;
     b.log = ctx->log;
     b.ctr = ctx->ctr;
+    b.timer = ctx->timer;
     for (int t = 0; t < nsteps; ++t) {
       b.step = step0 + t;
       b.step_off = (long long)t * cstride;
@@ -920,6 +1024,145 @@ abp_status abp_run(abp_ctx *ctx, abp_walker *const *walkers, int n, const void *
     return fail(ABP_ERR_INVALID_ARG, "forces or force offsets are NULL");
   return run_common(ctx, walkers, n, coords_dev, coords_dtype, coord_offsets_dev, coord_step_stride, forces_dev,
                     force_offsets_dev, force_step_stride, mode, step0, nsteps);
+}
+
+abp_status abp_md_run(abp_ctx *ctx, abp_walker *const *walkers, int n, void *coords_dev, int coords_dtype,
+                      const int64_t *coord_offsets_dev, const abp_md_desc *md, const uint32_t *streams,
+                      void *traj_dev, const int64_t *traj_offsets_dev, int64_t traj_step_stride, void *forces_dev,
+                      const int64_t *force_offsets_dev, int64_t force_step_stride, int mode, int64_t step0,
+                      int nsteps) {
+  if (!ctx) return fail(ABP_ERR_INVALID_ARG, "ctx is NULL");
+  int fp64;
+  bool shared;
+  abp_status st = check_list(ctx, walkers, n, &fp64, &shared);
+  if (st) return st;
+  if (shared) {
+    std::set<const abp_grid *> seen;
+    for (int i = 0; i < n; ++i)
+      if (!seen.insert(walkers[i]->grid).second && !walkers[i]->grid->desc.shared)
+        return fail(ABP_ERR_INVALID_ARG, "walkers that deposit into one grid need a grid created with shared = 1");
+  }
+  if (n == 0 || nsteps == 0) return ABP_OK;
+  if (nsteps < 0) return fail(ABP_ERR_INVALID_ARG, "nsteps must be >= 0");
+  if (step0 < 0) return fail(ABP_ERR_INVALID_ARG, "step must be >= 0");
+  if (!coords_dev || !coord_offsets_dev) return fail(ABP_ERR_INVALID_ARG, "coordinates or offsets are NULL");
+  if (!md || !streams) return fail(ABP_ERR_INVALID_ARG, "dynamics descriptor or streams are NULL");
+  if (traj_dev && !traj_offsets_dev) return fail(ABP_ERR_INVALID_ARG, "trajectory offsets are NULL");
+  if (forces_dev && !force_offsets_dev) return fail(ABP_ERR_INVALID_ARG, "force offsets are NULL");
+  if (coords_dtype != (fp64 ? ABP_F64 : ABP_F32))
+    return fail(ABP_ERR_INVALID_ARG, "coordinate dtype must be %s for these walkers", fp64 ? "ABP_F64" : "ABP_F32");
+  if (mode != ABP_FORCES_ACCUMULATE && mode != ABP_FORCES_OVERWRITE) return fail(ABP_ERR_INVALID_ARG, "bad mode");
+  const uintptr_t amask = fp64 ? 31 : 15;
+  if ((reinterpret_cast<uintptr_t>(coords_dev) & amask) || (reinterpret_cast<uintptr_t>(traj_dev) & amask) ||
+      (reinterpret_cast<uintptr_t>(forces_dev) & amask))
+    return fail(ABP_ERR_INVALID_ARG, "coordinate, trajectory and force buffers must be %d-byte aligned",
+                (int)amask + 1);
+  if (!(md->dt > 0) || !(md->mobility >= 0) || !(md->kT >= 0) || !std::isfinite(md->dt) ||
+      !std::isfinite(md->mobility) || !std::isfinite(md->kT))
+    return fail(ABP_ERR_INVALID_ARG, "dynamics: dt > 0, mobility >= 0 and kT >= 0 (finite) are required");
+  if (md->potential < ABP_POT_NONE || md->potential > ABP_POT_MULLER_BROWN)
+    return fail(ABP_ERR_INVALID_ARG, "unknown potential %d", md->potential);
+  MdParams mp{};
+  mp.potential = md->potential;
+  mp.c1 = md->dt * md->mobility;
+  mp.c2 = std::sqrt(2.0 * md->mobility * md->kT * md->dt);
+  mp.seed = md->seed;
+  mp.dw_a = md->dw_a;
+  mp.dw_b = md->dw_b;
+  mp.mb_scale = md->mb_scale;
+  for (int q = 0; q < 4; ++q) {
+    mp.mb_map[q] = md->mb_map[q];
+    mp.mb_A[q] = md->mb_A[q];
+    mp.mb_a[q] = md->mb_a[q];
+    mp.mb_b[q] = md->mb_b[q];
+    mp.mb_c[q] = md->mb_c[q];
+    mp.mb_x0[q] = md->mb_x0[q];
+    mp.mb_y0[q] = md->mb_y0[q];
+  }
+  if (md->potential == ABP_POT_MULLER_BROWN)
+    for (int i = 0; i < n; ++i)
+      if (walkers[i]->hd.g.d < 2)
+        return fail(ABP_ERR_INVALID_ARG, "walker %d: the Mueller-Brown potential needs two CVs", i);
+  // the one-warp form (by grid dimension) and the phased form
+  std::vector<abp_walker *> ww[3], bw;
+  std::vector<int> wi[3], bi;
+  for (int i = 0; i < n; ++i) {
+    if (walkers[i]->big) {
+      if (md->potential != ABP_POT_NONE)
+        return fail(ABP_ERR_UNSUPPORTED, "walker %d runs in the phased form, which takes no CV potential", i);
+      bw.push_back(walkers[i]);
+      bi.push_back(i);
+    } else if (walkers[i]->win) {
+      ww[walkers[i]->hd.g.d - 1].push_back(walkers[i]);
+      wi[walkers[i]->hd.g.d - 1].push_back(i);
+    } else {
+      return fail(ABP_ERR_UNSUPPORTED,
+                  "walker %d: closed-loop runs take walkers whose CVs are COM distances, dihedrals or RMSDs, and "
+                  "walkers of the phased form",
+                  i);
+    }
+  }
+  if ((st = set_device(ctx))) return st;
+  for (int dim = 1; dim <= 3; ++dim) {
+    std::vector<abp_walker *> &lw = ww[dim - 1];
+    if (lw.empty()) continue;
+    MdRunArgs a{};
+    if ((st = sub_table(ctx, lw, wi[dim - 1], &a.r.table, streams))) return st;
+    int gb = 0;
+    for (abp_walker *w : lw) gb = std::max(gb, md_group_bytes(w->hd, fp64));
+    const int smem_max = 227 * 1024;
+    if (gb > smem_max) return fail(ABP_ERR_UNSUPPORTED, "a walker needs %d bytes of shared memory (max %d)", gb, smem_max);
+    // one warp per walker; with more walkers than multiprocessors, four per CTA
+    int wpc = ctx->tune_gpc ? std::min(ctx->tune_gpc, 4) : ((int)lw.size() > ctx->sms ? 4 : 1);
+    while (wpc > 1 && wpc * gb > smem_max) --wpc;
+    a.r.nw = (int)lw.size();
+    a.r.G = 32;
+    a.r.groups_per_cta = wpc;
+    a.r.group_bytes = gb;
+    a.r.coords = coords_dev;
+    a.r.coff = reinterpret_cast<const long long *>(coord_offsets_dev);
+    a.r.forces = forces_dev;
+    a.r.foff = reinterpret_cast<const long long *>(force_offsets_dev);
+    a.r.fstride = force_step_stride;
+    a.r.mode = mode;
+    a.r.step0 = step0;
+    a.r.nsteps = nsteps;
+    a.r.log = ctx->log;
+    a.r.ctr = ctx->ctr;
+    a.md = mp;
+    a.traj = traj_dev;
+    a.toff = reinterpret_cast<const long long *>(traj_offsets_dev);
+    a.tstride = traj_step_stride;
+    if (ctx->timer) ctx->timer->begin("k_md", ctx->stream);
+    cudaError_t e = launch_md(a, fp64, dim, ctx->stream);
+    if (ctx->timer) ctx->timer->end("k_md", ctx->stream);
+    if (e != cudaSuccess) return fail(ABP_ERR_CUDA, "closed-loop launch: %s", cudaGetErrorString(e));
+  }
+  if (!bw.empty()) {
+    BigArgs b{};
+    if ((st = big_items(ctx, bw, bi, &b, streams))) return st;
+    b.coords = coords_dev;
+    b.coff = reinterpret_cast<const long long *>(coord_offsets_dev);
+    b.forces = forces_dev;
+    b.foff = reinterpret_cast<const long long *>(force_offsets_dev);
+    b.mode = mode;
+    b.log = ctx->log;
+    b.ctr = ctx->ctr;
+    b.md = &mp;
+    b.timer = ctx->timer;
+    b.xio = coords_dev;
+    b.traj = traj_dev;
+    b.toff = reinterpret_cast<const long long *>(traj_offsets_dev);
+    for (int t = 0; t < nsteps; ++t) {
+      b.step = step0 + t;
+      b.step_off = 0;  // the coordinates stay where they are and move in place
+      b.force_step_off = (long long)t * force_step_stride;
+      b.traj_step_off = (long long)t * traj_step_stride;
+      cudaError_t e = launch_big_step(b, ctx->stream);
+      if (e != cudaSuccess) return fail(ABP_ERR_CUDA, "phased launch: %s", cudaGetErrorString(e));
+    }
+  }
+  return ABP_OK;
 }
 
 abp_status abp_step(abp_ctx *ctx, abp_walker *const *walkers, int n, const void *coords_dev, int coords_dtype,
@@ -1712,6 +1955,25 @@ abp_status abp_server_admit(abp_server *s, const abp_grid_desc *g, const abp_wal
   sm.natoms = w->natoms;
   *sim = id;
   return ABP_OK;
+}
+
+abp_status abp_server_bias_readout(abp_server *s, int64_t sim, void *dst, int dst_is_device, int dtype) {
+  if (!s || !dst) return fail(ABP_ERR_INVALID_ARG, "NULL argument");
+  abp_grid *grid = nullptr;
+  {
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->sims.find(sim);
+    if (it == s->sims.end()) return fail(ABP_ERR_INVALID_ARG, "unknown simulation %lld", (long long)sim);
+    if (!s->cv_done.wait_for(lk, std::chrono::seconds(60), [&] {
+          auto jt = s->sims.find(sim);
+          return jt == s->sims.end() || (!jt->second.busy && jt->second.pending.empty());
+        }))
+      return fail(ABP_ERR_TIMEOUT, "simulation %lld still has requests after 60 s", (long long)sim);
+    it = s->sims.find(sim);
+    if (it == s->sims.end()) return fail(ABP_ERR_INVALID_ARG, "simulation %lld was released", (long long)sim);
+    grid = it->second.grid;
+  }
+  return abp_bias_readout(s->ctx, grid, dst, dst_is_device, dtype);
 }
 
 abp_status abp_server_release(abp_server *s, int64_t sim) {

@@ -23,6 +23,7 @@
 
 #include "abp_device.cuh"
 #include "abp_launch.h"
+#include "abp_md.cuh"
 
 namespace abp {
 
@@ -707,25 +708,83 @@ __global__ void __launch_bounds__(kBigThreads) k_big_force(const BigItem *walker
   }
 }
 
+// ---------------------------------------------------------------- k_big_move
+
+// Closed loop (abp_md_run): after the force phase, the move of one walker's
+// atoms [blockIdx.x * kBigThreads, + kBigThreads): x += c1 F_bias + c2 xi
+// (this form takes no CV potential), the coordinates before the move to the
+// trajectory records when given. A walker whose step saw non-finite
+// coordinates does not move.
+__global__ void __launch_bounds__(kBigThreads) k_big_move(const BigItem *walkers, MdParams md, void *xio,
+                                                          const long long *coff, void *traj, const long long *toff,
+                                                          long long traj_step_off, long long step) {
+  const BigItem it = walkers[blockIdx.y];
+  const WalkerDev *wd = it.wd;
+  const int i = blockIdx.x * kBigThreads + threadIdx.x;
+  if (i >= wd->natoms) return;
+  const BigHead *head = reinterpret_cast<const BigHead *>(wd->jscratch);
+  if (head->bad) return;
+  float4 *x = reinterpret_cast<float4 *>(xio) + coff[it.widx] + i;
+  const float4 f = reinterpret_cast<const float4 *>(wd->fbuf)[i];
+  float4 p = *x;
+  if (traj) reinterpret_cast<float4 *>(traj)[toff[it.widx] + traj_step_off + i] = p;
+  float n[3];
+  md_normals(md.seed, it.stream, step, i, n);
+  const float c1 = (float)md.c1, c2 = (float)md.c2;
+  p.x += c1 * f.x + c2 * n[0];
+  p.y += c1 * f.y + c2 * n[1];
+  p.z += c1 * f.z + c2 * n[2];
+  *x = p;
+}
+
 // ---------------------------------------------------------------- launcher
 
 cudaError_t launch_big_step(const BigArgs &a, cudaStream_t st) {
   const size_t fixed = (size_t)fixed_bytes_f();
   const int ph = a.phases ? a.phases : 31;
+  LaunchTimer *tm = a.timer;
+  auto t0 = [&](const char *k) {
+    if (tm) tm->begin(k, st);
+  };
+  auto t1 = [&](const char *k) {
+    if (tm) tm->end(k, st);
+  };
   cudaError_t e;
   if ((ph & 1) && a.ncn_items > 0) {
     e = cudaFuncSetAttribute(k_big_cn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.cn_smem);
     if (e != cudaSuccess) return e;
+    t0("k_big_cn");
     k_big_cn<<<a.ncn_items, kBigThreads, a.cn_smem, st>>>(a.cn_items, a.coords, a.coff, a.step_off);
+    t1("k_big_cn");
   }
-  if (ph & 2)
+  if (ph & 2) {
+    t0("k_big_cvs");
     k_big_cvs<<<a.nw, kBigThreads, fixed, st>>>(a.walkers, a.coords, a.coff, a.step_off, a.step, a.log, a.ctr);
+    t1("k_big_cvs");
+  }
   dim3 grid(a.nw, (a.max_stencil + kStencilPerBlock - 1) / kStencilPerBlock);
-  if (ph & 4) k_big_deposit<<<grid, kBigThreads, fixed, st>>>(a.walkers);
-  if ((ph & 8) && a.any_shared) k_big_refresh<<<grid, kBigThreads, fixed, st>>>(a.walkers);
-  if (ph & 16)
+  if (ph & 4) {
+    t0("k_big_deposit");
+    k_big_deposit<<<grid, kBigThreads, fixed, st>>>(a.walkers);
+    t1("k_big_deposit");
+  }
+  if ((ph & 8) && a.any_shared) {
+    t0("k_big_refresh");
+    k_big_refresh<<<grid, kBigThreads, fixed, st>>>(a.walkers);
+    t1("k_big_refresh");
+  }
+  if (ph & 16) {
+    t0("k_big_force");
     k_big_force<<<dim3((a.max_atoms + kBigThreads - 1) / kBigThreads, a.nw), kBigThreads, fixed, st>>>(
         a.walkers, a.forces, a.foff, a.force_step_off, a.mode, a.step);
+    t1("k_big_force");
+  }
+  if ((ph & 16) && a.md) {
+    t0("k_big_move");
+    k_big_move<<<dim3((a.max_atoms + kBigThreads - 1) / kBigThreads, a.nw), kBigThreads, 0, st>>>(
+        a.walkers, *a.md, a.xio, a.coff, a.traj, a.toff, a.traj_step_off, a.step);
+    t1("k_big_move");
+  }
   return cudaGetLastError();
 }
 

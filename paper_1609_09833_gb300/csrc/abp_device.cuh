@@ -229,10 +229,64 @@ __device__ __forceinline__ void grp_sum_ff(const Grp &g, Real &h, Real &l, Real 
 
 // ---------------------------------------------------------------- a1: CVs
 
+// The end of an FP32 COM distance in hi + lo arithmetic: d = (r_B - r_A) +
+// (B - A), r_G each group's first atom and G + Gl its weighted offset sum
+// (hi + lo), the first atoms' difference and the sums' difference formed
+// exactly; a minimum image in a periodic box; r^2 = sum d^2 in hi + lo and
+// s = sqrt(r^2) with one Newton correction (sh + sl); u = d / s in FP32. A
+// hill two grid spacings wide on a fine grid needs s to ~1e-6 of its width,
+// below the resolution of one FP32 number near 1 nm.
+__device__ __forceinline__ int com_finish_ff(const CvDev &c, const float *ra, const float *ah, const float *al,
+                                             const float *rb, const float *bh, const float *bl, float &sh, float &sl,
+                                             float *u) {
+  float dh[3], dl[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    float rdh, rdl, t, te, s1, e1;
+    two_sum<float>(rb[q], -ra[q], rdh, rdl);
+    two_sum<float>(bh[q], -ah[q], t, te);
+    te = __fadd_rn(te, __fsub_rn(bl[q], al[q]));
+    two_sum<float>(rdh, t, s1, e1);
+    e1 = __fadd_rn(e1, __fadd_rn(rdl, te));
+    dh[q] = __fadd_rn(s1, e1);
+    dl[q] = __fsub_rn(e1, __fsub_rn(dh[q], s1));
+    if (c.pbc) {
+      const float shift = __fmul_rn((float)c.box[q], floorf(__fmaf_rn(dh[q], (float)c.inv_box[q], 0.5f)));
+      float t2, te2;
+      two_sum<float>(dh[q], -shift, t2, te2);
+      dh[q] = t2;
+      dl[q] = __fadd_rn(dl[q], te2);
+    }
+  }
+  float r2h = 0.f, r2l = 0.f;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const float p = __fmul_rn(dh[q], dh[q]);
+    const float e = __fmaf_rn(dh[q], dh[q], -p) + 2.f * dh[q] * dl[q];
+    ff_add<float>(r2h, r2l, p, e);
+  }
+  const float rh = sqrtf(r2h);
+  sh = rh;
+  if (rh > 0.f) {
+    sl = __fdiv_rn(__fadd_rn(__fmaf_rn(-rh, rh, r2h), r2l), 2.f * rh);
+    const float ir = __fdiv_rn(1.f, rh);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) u[q] = __fmul_rn(dh[q], ir);
+    return 0;
+  }
+  sl = 0.f;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) u[q] = 0.f;
+  return ABP_WFLAG_SINGULAR;
+}
+
 // Centre-of-mass distance s = |R_B - R_A| (minimum image if pbc). Each
 // group's weighted sum runs over offsets from the group's first atom, which
-// keeps the FP32 rounding at the scale of the group's extent rather than of
-// the absolute coordinates: R_G = r_G + sum_i w_i (x_i - r_G), sum_i w_i = 1.
+// keeps the rounding at the scale of the group's extent rather than of the
+// absolute coordinates: R_G = r_G + sum_i w_i (x_i - r_G), sum_i w_i = 1.
+// FP32 walkers sum compensated (Kahan per thread, hi + lo across the group)
+// and finish in hi + lo (com_finish_ff): a group of hundreds of atoms spread
+// over nanometres would otherwise lose ~1e-7 nm.
 template <typename Real>
 __device__ void cv_com(const Grp &g, GroupFixed<Real> *fx, int k, const typename Rec4<Real>::T *xs) {
   const CvDev &c = fx->wd.cv[k];
@@ -240,6 +294,48 @@ __device__ void cv_com(const Grp &g, GroupFixed<Real> *fx, int k, const typename
   const Real *wa = fx->wa[k], *wb = fx->wb[k];
   const auto ra = xs[ia[0]];
   const auto rb = xs[ib[0]];
+  if constexpr (sizeof(Real) == 4) {
+    float h[6] = {0, 0, 0, 0, 0, 0}, cm[6] = {0, 0, 0, 0, 0, 0};
+    auto kahan = [&](int q, float w, float dx) {
+      const float y = __fmaf_rn(w, dx, -cm[q]);
+      const float t = __fadd_rn(h[q], y);
+      cm[q] = __fsub_rn(__fsub_rn(t, h[q]), y);
+      h[q] = t;
+    };
+    for (int i = g.t; i < c.na; i += g.G) {
+      const float w = wa[i];
+      const auto p = xs[ia[i]];
+      kahan(0, w, __fsub_rn(p.x, ra.x));
+      kahan(1, w, __fsub_rn(p.y, ra.y));
+      kahan(2, w, __fsub_rn(p.z, ra.z));
+    }
+    for (int i = g.t; i < c.nb; i += g.G) {
+      const float w = wb[i];
+      const auto p = xs[ib[i]];
+      kahan(3, w, __fsub_rn(p.x, rb.x));
+      kahan(4, w, __fsub_rn(p.y, rb.y));
+      kahan(5, w, __fsub_rn(p.z, rb.z));
+    }
+    float l[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      // the running sum and its compensation as a normalised hi + lo pair
+      float s2, e2;
+      two_sum<float>(h[q], -cm[q], s2, e2);
+      h[q] = s2;
+      l[q] = e2;
+      grp_sum_ff<float>(g, h[q], l[q], fx->red);
+    }
+    if (g.t == 0) {
+      const float r0a[3] = {ra.x, ra.y, ra.z}, r0b[3] = {rb.x, rb.y, rb.z};
+      float sh, sl;
+      const int fl = com_finish_ff(c, r0a, h, l, r0b, h + 3, l + 3, sh, sl, fx->com_u[k]);
+      fx->sh[k] = sh;
+      fx->sl[k] = sl;
+      if (fl) fx->flags |= fl;
+    }
+    return;
+  }
   Real v[6] = {0, 0, 0, 0, 0, 0};
   for (int i = g.t; i < c.na; i += g.G) {
     Real w = wa[i];

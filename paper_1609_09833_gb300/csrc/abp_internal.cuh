@@ -90,6 +90,20 @@ struct WalkerDev {
   WalkerState *state;
 };
 
+// Closed-loop dynamics of abp_md_run (device copy of abp_md_desc, with the
+// move's two constants formed on the host in FP64).
+struct MdParams {
+  int potential;                 // ABP_POT_*
+  int pad;
+  double c1;                     // dt * mobility
+  double c2;                     // sqrt(2 mobility kT dt)
+  unsigned long long seed;
+  double dw_a, dw_b;
+  double mb_scale;
+  double mb_map[4];
+  double mb_A[4], mb_a[4], mb_b[4], mb_c[4], mb_x0[4], mb_y0[4];
+};
+
 // Deposit log (device side).
 struct DepositLog {
   abp_deposit_rec *rec;
@@ -110,7 +124,8 @@ __host__ __device__ inline int align32(int x) { return (x + 31) & ~31; }
 // CVs, Jacobian factors, axis state and interpolated bias.
 template <typename Real>
 struct StepRec {
-  Real s[kMaxCv];         // CV values
+  Real s[kMaxCv];         // CV values (FP32 walkers: the high part of a COM distance ...
+  Real sl[kMaxCv];        // ... whose low part is here; 0 for the other CVs)
   Real jac[kMaxCv][12];   // COM distance: unit separation (3); dihedral, RMSD: gradient (4 x 3)
   Real f[kMaxCv];         // interpolation weight of i1
   Real df[kMaxCv];        // deposit: u - da

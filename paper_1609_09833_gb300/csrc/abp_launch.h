@@ -10,12 +10,21 @@
 
 namespace abp {
 
+// Optional per-kernel timing of a context (abp_ctx_tune ABP_TUNE_TIMING): the
+// launchers bracket each kernel launch with begin/end, which record CUDA
+// events on the launch's stream (read back by abp_kernel_times).
+struct LaunchTimer {
+  virtual void begin(const char *kernel, cudaStream_t st) = 0;
+  virtual void end(const char *kernel, cudaStream_t st) = 0;
+  virtual ~LaunchTimer() = default;
+};
+
 // One walker of a batched launch: its device descriptor and its index in
 // the caller's walker list (which selects its coordinate/force offsets).
 struct TableEntry {
   const WalkerDev *wd;
   int idx;
-  int pad;
+  unsigned stream;  // the walker's noise stream in a closed-loop launch (0 otherwise)
 };
 
 struct RunArgs {
@@ -63,6 +72,8 @@ struct BigItem {
   const WalkerDev *wd;
   int widx;
   int chunk;
+  unsigned stream;  // walker items of a closed-loop call: the walker's noise stream
+  int pad;
 };
 
 struct BigArgs {
@@ -83,9 +94,29 @@ struct BigArgs {
   int max_atoms;             // most atoms of a walker (the force phase's CTAs per walker)
   int any_shared;
   int phases;                // bits: 1 pairs, 2 CVs + heights, 4 deposit, 8 refresh, 16 forces (0 = all)
+  LaunchTimer *timer;        // per-kernel timing (NULL: off)
+  const MdParams *md;        // closed loop: the force phase also moves the atoms (NULL: open loop)
+  void *xio;                 // closed loop: the coordinates, moved in place
+  void *traj;                // closed loop: records of the coordinates each step was evaluated at (or NULL)
+  const long long *toff;
+  long long traj_step_off;
   DepositLog log;
   DevCounters *ctr;
 };
+
+// A closed-loop launch (abp_md_run): the batched arguments (coords is
+// written in place), the dynamics, and the optional trajectory records.
+struct MdRunArgs {
+  RunArgs r;
+  MdParams md;
+  void *traj;               // NULL: not recorded
+  const long long *toff;
+  long long tstride;
+};
+
+// Closed-loop form of walkers whose CVs a thread evaluates (abp_md.cu).
+int md_group_bytes(const WalkerDev &hd, int fp64);
+cudaError_t launch_md(const MdRunArgs &a, int fp64, int dim, cudaStream_t st);
 
 size_t big_scratch_bytes(const WalkerDev &hd);
 // The force phase's per-atom term table of a phased-form walker (host side;

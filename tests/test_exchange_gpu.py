@@ -84,7 +84,8 @@ def test_two_replicas_equal_one_shared_grid(abp):
         # the single grid against the oracle run of all five walkers
         ws = [oracle.Walker(s) for s in specs]
         shared = ws[0].new_field()
-        ref = oracle.run(ws, frames.astype(np.float64), synth.offsets_of(specs), 0, T, fields=[shared] * len(ws))
+        ref = oracle.run(ws, frames.astype(np.float64), synth.offsets_of(specs), 0, T, fields=[shared] * len(ws),
+                         error_model=True)
         Fg = Fr.cpu().numpy()[..., :3].astype(np.float64)
         worst = check_run(abp, ctx_r, specs, wr, frames, 0, Fg, ref)
         print("worst errors", worst)

@@ -6,7 +6,9 @@ oracle, in the windowed and per-step fused forms and the plain form.
 mABP reads the bias at the nearest node, so a step whose CV lies within the
 tie band of a half-node may read a neighbouring node on one side: such steps
 are left out of the force comparison (and counted), as deposits whose
-centre ties are (tests/parity.py)."""
+centre ties are (tests/parity.py). The band of a step is 4 |u32 - u64| +
+1e-6 with |u32 - u64| bounded by the CV's rounding bound (the oracle's
+error model) over the node spacing."""
 import math
 
 import numpy as np
@@ -52,16 +54,23 @@ def _mabp(specs, a_bins=10.0, p=20, b=0.9, c=0.05, stride=1, w=1.0):
     return out
 
 
-def _lookup_tie_steps(spec, s):
-    """[T] mask of steps whose CV is within the tie band of a half-node."""
+def _lookup_tie_steps(spec, s, sb, unit=P.U32):
+    """[T] mask of steps whose CV is within the tie band of a half-node:
+    4 |u32 - u64| + 1e-6, |u32 - u64| <= unit sb / D (sb: the CVs' rounding
+    bounds of the steps, [T, 3])."""
+    g = spec["grid"]
+    d = len(g["n"])
+    D = np.array([(g["hi"][k] - g["lo"][k]) / (g["n"][k] if g["periodic"][k] else g["n"][k] - 1)
+                  for k in range(d)])
     u = np.array([P.grid_u(spec, st) for st in s])
-    return np.any(np.abs((u % 1.0) - 0.5) < P.TIE_BAND, axis=1)
+    band = 4 * unit * sb[:, :d] / D + 1e-6
+    return np.any(np.abs((u % 1.0) - 0.5) < band, axis=1)
 
 
-def check_mabp(abp, ctx, specs, walkers, Fg, ref):
+def check_mabp(abp, ctx, specs, walkers, Fg, ref, unit=P.U32):
     log = abp.abp_deposit_log_readout(ctx.handle, 1 << 20)
     ids = {w.id: i for i, w in enumerate(walkers)}
-    ties = P.compare_deposits(specs, log, ref["deposits"], ids)
+    ties = P.compare_deposits(specs, log, ref["deposits"], ids, sb=ref["sb"], unit=unit)
     assert len(ties) <= max(1, len(walkers) // 4), ties
     assert np.all(log["height"] == np.array([specs[ids[int(x)]]["hill"]["w"] for x in log["walker_id"]]))
     off = synth.offsets_of(specs)
@@ -72,13 +81,16 @@ def check_mabp(abp, ctx, specs, walkers, Fg, ref):
         e = P.rel_field_err(ctx.bias(w), ref["fields"][i])
         assert np.all(e < P.TOL_V), (i, e)
         worst["V"] = max(worst["V"], float(e.max()))
-        keep = ~_lookup_tie_steps(sp, ref["s"][:, i])
+        keep = ~_lookup_tie_steps(sp, ref["s"][:, i], ref["sb"][:, i], unit)
         worst["tie_steps"] += int((~keep).sum())
         sl = slice(off[i], off[i] + sp["natoms"])
         fe = P.force_err(Fg[keep][:, sl], ref["F"][keep][:, sl])
         assert fe < P.TOL_F, (i, fe)
         worst["F"] = max(worst["F"], float(fe))
-    # the tie band is 2e-4 wide in u: a small fraction of steps may fall in it
+        sub = {key: ref[key][keep] for key in ("F", "H", "A", "sb", "Jn")}
+        rel, ratio, _ = P.check_forces_per_step(Fg[keep], sub, i, sl, len(sp["grid"]["n"]), unit=unit)
+        worst["F_step"] = max(worst.get("F_step", 0.0), rel)
+    # the tie band is a few 1e-6 wide in u: a small fraction of steps may fall in it
     assert worst["tie_steps"] <= max(3, 0.005 * Fg.shape[0] * len(walkers)), worst
     return worst
 
@@ -156,7 +168,7 @@ def test_mabp_fp64_walker(abp, ctx):
     abp.abp_deposit_log_enable(ctx.handle, 1 << 16)
     Fg = gpu_replay(abp, ctx, walkers, frames, 0, chunks=2, dtype=np.float64)
     _, ref = oracle_replay([spec], frames, 0)
-    print("worst", check_mabp(abp, ctx, [spec], walkers, Fg, ref))
+    print("worst", check_mabp(abp, ctx, [spec], walkers, Fg, ref, unit=P.U64))
 
 
 def test_rmsd_cvs_on_the_paper_grid(abp, ctx):
@@ -186,6 +198,33 @@ def test_rmsd_cvs_on_the_paper_grid(abp, ctx):
         from tests.test_parity_gpu import check_run
 
         print("worst wt", check_run(abp, ctx2, wt, w2, frames, 0, Fw, rw))
+    finally:
+        torch.cuda.synchronize()
+        ctx2.close()
+
+
+def test_mabp_at_the_papers_constants(abp, ctx):
+    """b = 0.9, c = 0.001 (the paper's ligand-binding values), compact hills
+    a = 10 grid spacings, p = 20, updated every step: the RMSD walkers on the
+    paper's 480 x 480 grid (the benchmark's workload) and COM distance +
+    dihedral walkers, over 600 steps each."""
+    specs = synth.paper_rmsd_specs(nw=6)
+    assert all(s["hill"]["b"] == 0.9 and s["hill"]["c"] == 0.001 for s in specs)
+    frames = synth.RmsdFrames(specs, seed=5, period=(600, 2400)).frames(0, 600)
+    walkers = ctx.make_walkers(specs)
+    abp.abp_deposit_log_enable(ctx.handle, 1 << 16)
+    Fg = gpu_replay(abp, ctx, walkers, frames, 0, chunks=3)
+    _, ref = oracle_replay(specs, frames, 0)
+    print("worst rmsd", check_mabp(abp, ctx, specs, walkers, Fg, ref))
+    specs2 = _mabp(synth.mb64_specs(nw=6, stride=1), a_bins=10.0, c=0.001, b=0.9)
+    frames2 = synth.SweepFrames(6, seed=6, period=(200, 500), dihedral_period=(150, 400)).frames(0, 600)
+    ctx2 = abp.Context(0)
+    try:
+        w2 = ctx2.make_walkers(specs2)
+        abp.abp_deposit_log_enable(ctx2.handle, 1 << 16)
+        F2 = gpu_replay(abp, ctx2, w2, frames2, 0, chunks=3)
+        _, r2 = oracle_replay(specs2, frames2, 0)
+        print("worst com/dihedral", check_mabp(abp, ctx2, specs2, w2, F2, r2))
     finally:
         torch.cuda.synchronize()
         ctx2.close()
@@ -233,12 +272,12 @@ def test_range_limit_wall_in_every_form(abp, ctx):
     off = synth.offsets_of(specs)
     log = abp.abp_deposit_log_readout(ctx.handle, 1 << 20)
     ids = {w.id: i for i, w in enumerate(walkers)}
-    ties = P.compare_deposits(specs, log, ref["deposits"], ids)
+    ties = P.compare_deposits(specs, log, ref["deposits"], ids, sb=ref["sb"])
     for i, sp in enumerate(specs):
         if i in ties:
             continue
         sl = slice(off[i], off[i] + sp["natoms"])
-        keep = ~_lookup_tie_steps(sp, ref["s"][:, i]) if i >= 4 else np.ones(len(frames), bool)
+        keep = ~_lookup_tie_steps(sp, ref["s"][:, i], ref["sb"][:, i]) if i >= 4 else np.ones(len(frames), bool)
         assert P.force_err(Fg[keep][:, sl], ref["F"][keep][:, sl]) < P.TOL_F, i
     cn = [dict(sp, hill=synth.with_wall(sp["hill"], [0.9, 300.0, 300.0][: len(sp["grid"]["n"])], 20.0))
           for sp in synth.uneven1000_specs(seed=7, nw=4, stride=3, sizes_2d=(48,), n1d=200, n3d=20)]

@@ -1,0 +1,336 @@
+"""GPU parity of the closed-loop form (abp_md_run): the force call inside the
+model MD engine, step t + 1's coordinates from step t's bias force on the
+device.
+
+Against the oracle, one step at a time along the oracle's own closed-loop
+trajectory (the oracle's coordinates go in; nothing of the GPU's goes into
+the oracle): at every step the GPU's bias force, deposits and grid meet
+the open-loop tolerances, and its move lands where the oracle's did within
+the FP32 (or FP64) error of one move. Then the GPU's own closed loop:
+launches of many steps equal one-step calls bit for bit; the open-loop
+windowed form replayed on the GPU's own trajectory gives the same forces
+and grid; and the bias converges to the well-tempered limit of the
+COM-distance double well, -(1 - 1/gamma) (U(s) - 2 kT ln s) + C."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1609_09833_gb300 import synth
+from tests import parity as P
+from tests.test_parity_gpu import check_run, gpu_replay, oracle_replay
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def abp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1609_09833_gb300 import abp as A
+    from paper_1609_09833_gb300 import build
+
+    build.build()
+    A.load()
+    return A
+
+
+@pytest.fixture()
+def ctx(abp):
+    c = abp.Context(0)
+    yield c
+    torch.cuda.synchronize()
+    c.close()
+
+
+def _tdt(dtype):
+    return torch.float32 if dtype == np.float32 else torch.float64
+
+
+def gpu_steps_from(abp, ctx, walkers, frames, md, streams, step0=0, dtype=np.float32):
+    """One closed-loop call per step, each starting from frames[t] (the
+    oracle's trajectory): returns the moved coordinates and the bias forces,
+    [T, atoms, 3] each."""
+    specs = [w.spec for w in walkers]
+    rec = abp.to_records(frames.astype(dtype), _tdt(dtype)).cuda()
+    offs = torch.tensor(synth.offsets_of(specs), dtype=torch.int64, device="cuda")
+    cdt = abp.ABP_F32 if dtype == np.float32 else abp.ABP_F64
+    X = torch.zeros_like(rec)
+    F = torch.zeros_like(rec)
+    buf = torch.zeros_like(rec[0])
+    for t in range(frames.shape[0]):
+        buf.copy_(rec[t])
+        abp.abp_md_run(ctx.handle, walkers, buf, cdt, offs, md, streams, forces=F[t], force_offsets=offs,
+                       mode=abp.ABP_FORCES_OVERWRITE, step0=step0 + t, nsteps=1)
+        X[t].copy_(buf)
+    torch.cuda.synchronize()
+    return X.cpu().numpy()[..., :3].astype(np.float64), F.cpu().numpy()[..., :3].astype(np.float64)
+
+
+def gpu_run(abp, ctx, walkers, x0, md, streams, step0, nsteps, chunks=1, dtype=np.float32):
+    """The GPU's own closed loop from x0 in `chunks` calls: returns the
+    trajectory (coordinates each step was evaluated at), the bias forces and
+    the final coordinates."""
+    specs = [w.spec for w in walkers]
+    A = x0.shape[0]
+    tdt = _tdt(dtype)
+    buf = abp.to_records(x0[None].astype(dtype), tdt).cuda()[0]
+    offs = torch.tensor(synth.offsets_of(specs), dtype=torch.int64, device="cuda")
+    cdt = abp.ABP_F32 if dtype == np.float32 else abp.ABP_F64
+    traj = torch.zeros(nsteps, A, 4, dtype=tdt, device="cuda")
+    F = torch.zeros_like(traj)
+    bounds = np.linspace(0, nsteps, chunks + 1).astype(int)
+    for a, b in zip(bounds[:-1], bounds[1:]):
+        abp.abp_md_run(ctx.handle, walkers, buf, cdt, offs, md, streams, traj=traj[a:], traj_offsets=offs,
+                       traj_step_stride=A, forces=F[a:], force_offsets=offs, force_step_stride=A,
+                       mode=abp.ABP_FORCES_OVERWRITE, step0=step0 + a, nsteps=int(b - a))
+    torch.cuda.synchronize()
+    cv = lambda t: t.cpu().numpy()[..., :3].astype(np.float64)  # noqa: E731
+    return cv(traj), cv(F), cv(buf)
+
+
+def _potential_floor(md, ref, sl, w, d, unit):
+    """Per step and atom, the error the FP32 (FP64) CV potential's force may
+    carry: its slope (central differences of dU/ds) times the CVs' rounding
+    bounds, plus its own rounding; and a bound on the force's size."""
+    T = ref["s"].shape[0]
+    E = np.zeros((T, d))
+    G = np.zeros((T, d))
+    for t in range(T):
+        s = ref["s"][t, w, :d]
+        _, dU = oracle.md_potential(md, s)
+        G[t] = np.abs(dU[:d])
+        H = np.zeros((d, d))
+        for j in range(d):
+            e = 1e-6 * max(1.0, abs(s[j]))
+            sp, sm = s.copy(), s.copy()
+            sp[j] += e
+            sm[j] -= e
+            H[:, j] = (oracle.md_potential(md, sp)[1][:d] - oracle.md_potential(md, sm)[1][:d]) / (2 * e)
+        E[t] = np.abs(H) @ (unit * ref["sb"][t, w, :d]) + 16 * unit * G[t]
+    Jn = ref["Jn"][:, sl, :d]
+    return np.einsum("tak,tk->ta", Jn, E), np.einsum("tak,tk->ta", Jn, G)
+
+
+def check_moves(specs, md, streams, frames, X, ref, unit=P.U32, tol_f=P.TOL_F):
+    """The GPU's move of every step and atom against the oracle's next
+    frame: the rounding of the position (both sides), the step's force error
+    (the per-step force allowance of tests/parity.py for the bias, the
+    potential's own floor) times dt mu, and the noise's rounding."""
+    c1 = md["dt"] * md["mu"]
+    c2 = math.sqrt(2 * md["mu"] * md["kT"] * md["dt"])
+    off = synth.offsets_of(specs)
+    T = X.shape[0]
+    worst = 0.0
+    for w, sp in enumerate(specs):
+        d = len(sp["grid"]["n"])
+        sl = slice(off[w], off[w] + sp["natoms"])
+        xi = np.array([[oracle.md_normals(md["seed"], streams[w], t, i) for i in range(sp["natoms"])]
+                       for t in range(T)])
+        fU_floor, fU = _potential_floor(md, ref, sl, w, d, unit)
+        Fb = np.linalg.norm(ref["F"][:, sl], axis=-1)
+        scale = (Fb + fU).max(axis=-1, keepdims=True)
+        allowF = tol_f * scale + P.force_floor(ref, w, sl, d, unit) + fU_floor + 8 * unit * (Fb + fU)
+        xn = frames[1:T + 1, sl]
+        allow = (4 * unit * np.linalg.norm(xn, axis=-1) + c1 * allowF
+                 + 16 * unit * c2 * np.linalg.norm(xi, axis=-1))
+        err = np.linalg.norm(X[:, sl] - xn, axis=-1)
+        r = err / allow
+        t, i = np.unravel_index(np.argmax(r), r.shape)
+        assert r.max() <= 1.0, (w, int(t), int(i), float(err[t, i]), float(allow[t, i]))
+        worst = max(worst, float(r.max()))
+    return worst
+
+
+def _oracle_closed_loop(specs, x0, md, streams, T, shared=False):
+    ws = [oracle.Walker(s) for s in specs]
+    fields = [ws[0].new_field()] * len(ws) if shared else None
+    res = oracle.md_run(ws, x0.astype(np.float64), synth.offsets_of(specs), md, streams, 0, T, fields=fields,
+                        record_x=True)
+    return np.concatenate([res["X"], res["x"][None]])
+
+
+# ---------------------------------------------------------------- against the oracle, step by step
+
+
+def test_closed_loop_steps_match_the_oracle_fp32_mueller_brown(abp, ctx):
+    """Six COM-distance + dihedral walkers on their own 256 x 256 grids
+    under the scaled Mueller-Brown surface (the 64-walker workload's
+    dynamics), 150 steps, a deposit every 5 steps."""
+    nw, T = 6, 150
+    specs = synth.mb64_specs(nw=nw, stride=5)
+    md = synth.md_muller_brown(seed=5, state_f32=True)
+    streams = np.arange(nw) + 100
+    x0 = synth.SweepFrames(nw, seed=21).frames(0, 1)[0]
+    frames = _oracle_closed_loop(specs, x0, md, streams, T)
+    assert np.array_equal(frames.astype(np.float32).astype(np.float64), frames)
+    walkers = ctx.make_walkers(specs)
+    abp.abp_deposit_log_enable(ctx.handle, 1 << 16)
+    X, F = gpu_steps_from(abp, ctx, walkers, frames[:T], md, streams)
+    _, ref = oracle_replay(specs, frames[:T].astype(np.float32), 0)
+    worst = check_run(abp, ctx, specs, walkers, frames[:T], 0, F, ref)
+    worst["move"] = check_moves(specs, md, streams, frames, X, ref)
+    print("worst", worst)
+    # the walkers did move through the potential: the CVs changed
+    assert np.ptp(ref["s"][:, :, 0]) > 0.01 and np.ptp(ref["s"][:, :, 1]) > 0.05
+
+
+def test_closed_loop_steps_match_the_oracle_fp64_double_well(abp, ctx):
+    """The one-walker FP64 workload (COM distance of two 8-atom groups on
+    U = 5 (s^2 - 1)^2, mu = 1), two walkers, 300 steps, a deposit every 10."""
+    T = 300
+    specs = [synth.double_well_com_spec(stride=10), synth.double_well_com_spec(stride=10)]
+    md = synth.md_double_well(seed=9)
+    streams = [3, 4]
+    x0 = np.concatenate([synth.double_well_com_coords(21), synth.double_well_com_coords(22)])
+    frames = _oracle_closed_loop(specs, x0, md, streams, T)
+    walkers = ctx.make_walkers(specs, precision=abp.ABP_PREC_FP64)
+    abp.abp_deposit_log_enable(ctx.handle, 1 << 16)
+    X, F = gpu_steps_from(abp, ctx, walkers, frames[:T], md, streams, dtype=np.float64)
+    _, ref = oracle_replay(specs, frames[:T], 0)
+    log = abp.abp_deposit_log_readout(ctx.handle, 1 << 16)
+    ids = {w.id: i for i, w in enumerate(walkers)}
+    assert not P.compare_deposits(specs, log, ref["deposits"], ids, sb=ref["sb"], unit=P.U64)
+    for i, w in enumerate(walkers):
+        assert np.all(P.rel_field_err(ctx.bias(w), ref["fields"][i]) < 1e-10)
+        P.check_forces_per_step(F, ref, i, slice(16 * i, 16 * i + 16), 1, tol=1e-9, unit=P.U64)
+    print("worst move", check_moves(specs, md, streams, frames, X, ref, unit=P.U64, tol_f=1e-9))
+
+
+def test_closed_loop_phased_form_on_a_shared_grid(abp, ctx):
+    """Four walkers of the shared-grid workload's shape (COM distance,
+    dihedral, CN over 20 x 300 atoms in a 3 nm periodic box) depositing into
+    one 40^3 grid, free overdamped Langevin (no CV potential), 12 steps."""
+    nw, T = 4, 12
+    specs = synth.shared256_specs(nw=nw, n=40, n_lig=20, n_env=300, box=3.0, stride=2, cn_range=(60.0, 160.0))
+    md = synth.md_params(seed=13, mu=0.05, state_f32=True)
+    streams = np.arange(nw)
+    x0 = np.concatenate(synth.shared256_templates(9, nw=nw, n_lig=20, n_env=300, box=3.0)).astype(np.float32)
+    frames = _oracle_closed_loop(specs, x0, md, streams, T, shared=True)
+    walkers = ctx.make_walkers(specs)
+    abp.abp_deposit_log_enable(ctx.handle, 4096)
+    X, F = gpu_steps_from(abp, ctx, walkers, frames[:T], md, streams)
+    ws = [oracle.Walker(s) for s in specs]
+    shared = ws[0].new_field()
+    ref = oracle.run(ws, frames[:T], synth.offsets_of(specs), 0, T, fields=[shared] * nw, error_model=True)
+    worst = check_run(abp, ctx, specs, walkers, frames[:T], 0, F, ref)
+    worst["move"] = check_moves(specs, md, streams, frames, X, ref)
+    print("worst", worst)
+
+
+# ---------------------------------------------------------------- the GPU's own closed loop
+
+
+def test_launch_length_does_not_change_the_bits(abp, ctx):
+    """One launch of 120 steps, four launches, and 120 one-step calls give
+    the same trajectory, forces and grids bit for bit."""
+    nw, T = 5, 120
+    specs = synth.mb64_specs(nw=nw, stride=7)
+    md = synth.md_muller_brown(seed=17)
+    streams = np.arange(nw) * 7
+    x0 = synth.SweepFrames(nw, seed=23).frames(0, 1)[0]
+    runs = []
+    for chunks in (1, 4, T):
+        w = ctx.make_walkers(specs)
+        tr, F, xf = gpu_run(abp, ctx, w, x0, md, streams, 0, T, chunks=chunks)
+        runs.append((tr, F, xf, [ctx.bias(x) for x in w]))
+    for tr, F, xf, B in runs[1:]:
+        assert np.array_equal(tr, runs[0][0]) and np.array_equal(F, runs[0][1]) and np.array_equal(xf, runs[0][2])
+        for a, b in zip(B, runs[0][3]):
+            assert np.array_equal(a, b)
+
+
+def test_open_loop_replay_of_the_closed_loop_trajectory(abp, ctx):
+    """The windowed form (abp_run) replayed on the GPU's own closed-loop
+    trajectory computes the closed loop's bias forces and grids: the two
+    forms run a step through the same operations."""
+    nw, T = 6, 300
+    specs = synth.mb64_specs(nw=nw, stride=10)
+    md = synth.md_muller_brown(seed=19)
+    streams = np.arange(nw)
+    x0 = synth.SweepFrames(nw, seed=25).frames(0, 1)[0]
+    wm = ctx.make_walkers(specs)
+    traj, F, _ = gpu_run(abp, ctx, wm, x0, md, streams, 0, T, chunks=2)
+    ww = ctx.make_walkers(specs)
+    Fw = gpu_replay(abp, ctx, ww, traj.astype(np.float32), 0, chunks=2)
+    assert P.force_err(Fw, F) < 1e-6
+    for a, b in zip(wm, ww):
+        assert np.all(P.rel_field_err(ctx.bias(a), ctx.bias(b)) < 1e-6)
+    print("bitwise equal:", np.array_equal(Fw, F), all(np.array_equal(ctx.bias(a), ctx.bias(b)) for a, b in zip(wm, ww)))
+
+
+def test_well_tempered_limit_of_the_closed_loop_on_the_gpu(abp, ctx):
+    """Four FP64 walkers of the one-walker workload closed on the GPU (COM
+    distance of two 8-atom groups, U = 5 (s^2 - 1)^2, mu = 1, kT = 2.5,
+    gamma = 10, stride 100), 2e5 steps each: every walker's bias matches
+    -(1 - 1/gamma) (U(s) - 2 kT ln s) + C within 0.5 kT RMS on [0.3, 1.7]
+    (the free energy of the distance of two freely diffusing centres)."""
+    kT, gamma, nw, T = 2.5, 10.0, 4, 200_000
+    specs = [synth.double_well_com_spec() for _ in range(nw)]
+    md = synth.md_double_well(seed=31)
+    x0 = np.concatenate([synth.double_well_com_coords(40 + i) for i in range(nw)])
+    walkers = ctx.make_walkers(specs, precision=abp.ABP_PREC_FP64)
+    rec = abp.to_records(x0[None], torch.float64).cuda()[0]
+    offs = torch.tensor(synth.offsets_of(specs), dtype=torch.int64, device="cuda")
+    for c in range(10):
+        abp.abp_md_run(ctx.handle, walkers, rec, abp.ABP_F64, offs, md, np.arange(nw), step0=c * T // 10,
+                       nsteps=T // 10)
+    abp.abp_sync(ctx.handle)
+    xi = np.linspace(-2.0, 2.0, 512)
+    sel = (xi > 0.3) & (xi < 1.7)
+    Fs = 5.0 * (xi[sel] ** 2 - 1.0) ** 2 - 2.0 * kT * np.log(xi[sel])
+    for w in walkers:
+        resid = ctx.bias(w)[sel, 0] + (1 - 1 / gamma) * Fs
+        rms = np.sqrt(np.mean((resid - resid.mean()) ** 2))
+        print("rms / kT", rms / kT)
+        assert rms < 0.5 * kT, rms
+        st = ctx.readout(w)
+        assert st["flags"] & abp.WFLAG_NONFINITE == 0
+
+
+# ---------------------------------------------------------------- edge cases
+
+
+def test_closed_loop_rejections_and_non_finite_coordinates(abp, ctx):
+    md = synth.md_muller_brown()
+    cn = synth.uneven1000_specs(seed=3, nw=1, sizes_2d=(48,), n1d=200, n3d=20)
+    w = ctx.make_walkers(cn)
+    rec = torch.zeros(cn[0]["natoms"], 4, device="cuda")
+    offs = torch.zeros(1, dtype=torch.int64, device="cuda")
+    with pytest.raises(abp.AbpError) as e:  # a CN walker of the fused form
+        abp.abp_md_run(ctx.handle, w, rec, abp.ABP_F32, offs, md, [0])
+    assert e.value.code == abp.ABP_ERR_UNSUPPORTED
+    one = ctx.make_walkers([synth.double_well_com_spec()])
+    with pytest.raises(abp.AbpError) as e:  # Mueller-Brown needs two CVs
+        abp.abp_md_run(ctx.handle, one, torch.zeros(16, 4, device="cuda"), abp.ABP_F32, offs, md, [0])
+    assert e.value.code == abp.ABP_ERR_INVALID_ARG
+    with pytest.raises(abp.AbpError) as e:
+        abp.abp_md_run(ctx.handle, one, torch.zeros(16, 4, device="cuda"), abp.ABP_F32, offs,
+                       synth.md_params(dt=-1.0), [0])
+    assert e.value.code == abp.ABP_ERR_INVALID_ARG
+    shared = synth.shared256_specs(nw=2, n=24, n_lig=8, n_env=40, box=3.0, stride=2, cn_range=(0.0, 40.0))
+    sw = ctx.make_walkers(shared)
+    offs2 = torch.tensor(synth.offsets_of(shared), dtype=torch.int64, device="cuda")
+    with pytest.raises(abp.AbpError) as e:  # the phased form takes no CV potential
+        abp.abp_md_run(ctx.handle, sw, torch.zeros(96, 4, device="cuda"), abp.ABP_F32, offs2,
+                       synth.md_double_well(), [0, 1])
+    assert e.value.code == abp.ABP_ERR_UNSUPPORTED
+    # non-finite coordinates: that walker stops (its atoms stay as they were),
+    # the other runs on
+    specs = synth.mb64_specs(nw=2, stride=3)
+    walkers = ctx.make_walkers(specs)
+    x0 = synth.SweepFrames(2, seed=2).frames(0, 1)[0].copy()
+    x0[5, 1] = np.nan
+    buf = abp.to_records(x0[None]).cuda()[0]
+    before = buf.clone()
+    offs3 = torch.tensor([0, 36], dtype=torch.int64, device="cuda")
+    abp.abp_md_run(ctx.handle, walkers, buf, abp.ABP_F32, offs3, md, [0, 1], nsteps=5)
+    with pytest.raises(abp.AbpError) as e:
+        abp.abp_sync(ctx.handle)
+    assert e.value.code == abp.ABP_ERR_NONFINITE
+    assert torch.equal(torch.nan_to_num(buf[:36]), torch.nan_to_num(before[:36]))
+    assert not torch.equal(buf[36:], before[36:])
+    assert ctx.readout(walkers[0])["flags"] == abp.WFLAG_NONFINITE
+    assert np.all(ctx.bias(walkers[0]) == 0.0)

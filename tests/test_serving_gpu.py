@@ -120,3 +120,55 @@ def test_admission_by_hbm_budget(abp):
     finally:
         abp.abp_server_destroy(srv)
         ctx.close()
+
+
+def test_full_size_simulations_against_the_oracle(abp):
+    """The twelve simulations with the largest grids of the served workload
+    (sides up to 1024, hills two grid spacings wide, 8 to 256 atoms, its own
+    strides), 400 steps each through the server, against the oracle: every
+    deposit's CV values, centre and height, every step's forces (with the
+    per-step allowance of tests/parity.py) and the grids at the end."""
+    from tests.test_parity_gpu import check_run
+
+    specs_all = synth.serve_specs(seed=61, nsim=4096)
+    tmpl_all = synth.serve_templates(61, specs_all)
+    pick = sorted(range(len(specs_all)), key=lambda i: -specs_all[i]["grid"]["n"][0])[:12]
+    specs = [specs_all[i] for i in pick]
+    T = 400
+    ctx = abp.Context(0)
+    srv = abp.abp_server_create(ctx.handle, max_batch=64, max_atoms=256, nstreams=2)
+    try:
+        abp.abp_deposit_log_enable(ctx.handle, 1 << 16)
+        keep, sims = [], []
+        for sp in specs:
+            desc, k = abp.walker_desc(sp)
+            keep.append(k)
+            sims.append(abp.abp_server_admit(srv, abp.grid_desc(sp["grid"]), desc))
+        coords = [_records(_frames(tmpl_all[i], 500 + i, T)) for i in pick]
+        order = [(j, t) for t in range(T) for j in range(len(specs))]
+        out, _ = _serve(abp, srv, sims, coords, list(range(T)), order)
+        frames = np.concatenate([c[:, :, :3] for c in coords], axis=1).astype(np.float64)
+        Fg = np.concatenate([np.stack([out[(j, t)][:, :3] for t in range(T)]) for j in range(len(specs))],
+                            axis=1).astype(np.float64)
+        ws = [oracle.Walker(sp) for sp in specs]
+        ref = oracle.run(ws, frames, synth.offsets_of(specs), 0, T, error_model=True)
+        grids = [abp.abp_server_bias_readout(srv, s, sp["grid"]) for s, sp in zip(sims, specs)]
+
+        class _Fields:  # check_run reads each walker's grid through ctx.bias
+            def bias(self, w):
+                return grids[w.i]
+
+        class _W:
+            def __init__(self, i, wid):
+                self.id, self.i = wid, i
+
+        log = abp.abp_deposit_log_readout(ctx.handle, 1 << 16)
+        ids = sorted(set(int(x) for x in log["walker_id"]))
+        assert len(ids) == len(specs)  # every simulation deposited at step 0
+        # walker ids in admission order
+        walkers = [_W(i, wid) for i, wid in enumerate(ids)]
+        worst = check_run(abp, _Fields(), specs, walkers, frames, 0, Fg, ref, log=log)
+        print("sides", [sp["grid"]["n"][0] for sp in specs], "worst", worst)
+    finally:
+        abp.abp_server_destroy(srv)
+        ctx.close()

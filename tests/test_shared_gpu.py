@@ -39,7 +39,7 @@ def _shared_oracle(specs, frames, step0):
     ws = [oracle.Walker(s) for s in specs]
     shared = ws[0].new_field()
     return oracle.run(ws, frames.astype(np.float64), synth.offsets_of(specs), step0, frames.shape[0],
-                      fields=[shared] * len(ws))
+                      fields=[shared] * len(ws), error_model=True)
 
 
 def test_shared_grid_small(abp, ctx):
@@ -98,8 +98,8 @@ def test_large_walker_on_own_grid(abp, ctx):
     walkers = ctx.make_walkers([spec])
     abp.abp_deposit_log_enable(ctx.handle, 4096)
     Fg = gpu_replay(abp, ctx, walkers, frames, 0)
-    ref = oracle.run([wo], frames.astype(np.float64), [0], 0, frames.shape[0])
-    check_run(abp, ctx, [spec], walkers, frames, 0, Fg, ref)
+    ref = oracle.run([wo], frames.astype(np.float64), [0], 0, frames.shape[0], error_model=True)
+    print("worst errors", check_run(abp, ctx, [spec], walkers, frames, 0, Fg, ref))
     with pytest.raises(abp.AbpError):  # the plain form does not take it
         rec = abp.to_records(frames[:1]).cuda()
         offs = torch.zeros(1, dtype=torch.int64, device="cuda")
@@ -142,9 +142,14 @@ def test_full_size_shared_256_workload(abp, ctx):
     g = ctx.bias(walkers[0])
     assert np.all(P.rel_field_err(g, ref["fields"][0]) < P.TOL_V)
     off = synth.offsets_of(specs)
+    ids = {w.id: i for i, w in enumerate(walkers)}
+    assert not P.compare_deposits(specs, log, ref["deposits"], ids, sb=ref["sb"])
+    worst = 0.0
     for i in range(nw):
         sl = slice(off[i], off[i] + specs[i]["natoms"])
         assert P.force_err(Fg[:, sl], ref["F"][:, sl]) < P.TOL_F
+        worst = max(worst, P.check_forces_per_step(Fg, ref, i, sl, 3)[0])
+    print("worst per-step force error", worst)
 
 
 def test_cuda_graph_replay_equals_direct_calls(abp, ctx):
