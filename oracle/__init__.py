@@ -172,7 +172,7 @@ def lib():
         L.or_interp.restype = C.c_int
         L.or_height.argtypes = [C.POINTER(OrHill), C.c_double]
         L.or_height.restype = C.c_double
-        L.or_deposit_hill.argtypes = [C.POINTER(OrGrid), C.POINTER(OrHill), dp, dp, C.c_double, ip]
+        L.or_deposit_hill.argtypes = [C.POINTER(OrGrid), C.POINTER(OrHill), dp, dp, C.c_double, ip, dp]
         L.or_deposit_hill.restype = None
         L.or_grid_nodes.argtypes = [C.POINTER(OrGrid)]
         L.or_grid_nodes.restype = C.c_long
@@ -183,16 +183,16 @@ def lib():
         L.or_batch_step.argtypes = [
             C.c_int, C.POINTER(OrWalker), C.POINTER(dp), C.POINTER(dp), C.c_int64,
             dp, dp, dp, C.POINTER(dp), ip, C.POINTER(OrDeposit), C.POINTER(OrMd), C.POINTER(C.c_uint32),
-            C.POINTER(dp), C.POINTER(OrStepAux), C.POINTER(dp),
+            C.POINTER(dp), C.POINTER(OrStepAux), C.POINTER(dp), C.POINTER(dp),
         ]
         L.or_batch_step.restype = C.c_int
         u32p = C.POINTER(C.c_uint32)
         L.or_run.argtypes = [
             C.c_int, C.POINTER(OrWalker), C.POINTER(dp), dp, C.POINTER(C.c_int64), C.c_int64,
             C.c_int64, C.c_int64, dp, dp, dp, dp, ip, C.POINTER(OrDeposit), C.c_int64,
-            C.POINTER(C.c_int64), C.POINTER(OrMd), u32p, dp, C.POINTER(OrStepAux), dp,
+            C.POINTER(C.c_int64), C.POINTER(OrMd), u32p, dp, C.POINTER(OrStepAux), dp, C.POINTER(dp),
         ]
-        L.or_interp_aux.argtypes = [C.POINTER(OrGrid), dp, dp, dp, dp]
+        L.or_interp_aux.argtypes = [C.POINTER(OrGrid), dp, dp, dp, dp, dp]
         L.or_interp_aux.restype = None
         L.or_cv_round_bound.argtypes = [C.POINTER(OrCv), dp]
         L.or_cv_round_bound.restype = C.c_double
@@ -216,7 +216,7 @@ def lib():
         L.or_langevin_double_well.restype = C.c_int
         L.or_compact.argtypes = [C.c_double, C.c_double, C.c_int, dp]
         L.or_compact.restype = C.c_double
-        L.or_deposit_compact.argtypes = [C.POINTER(OrGrid), C.POINTER(OrHill), dp, dp, C.c_double, ip]
+        L.or_deposit_compact.argtypes = [C.POINTER(OrGrid), C.POINTER(OrHill), dp, dp, C.c_double, ip, dp]
         L.or_deposit_compact.restype = None
         L.or_lookup_mabp.argtypes = [C.POINTER(OrGrid), C.POINTER(OrHill), dp, dp, dp, dp]
         L.or_lookup_mabp.restype = C.c_int
@@ -356,7 +356,7 @@ def deposit(walker: Walker, field: np.ndarray, s, h: float):
     s3[: walker.d] = s
     ic = np.zeros(3, dtype=np.int32)
     fn = lib().or_deposit_compact if walker.struct.hill.method == METHODS["mabp"] else lib().or_deposit_hill
-    fn(C.byref(walker.struct.g), C.byref(walker.struct.hill), _dptr(field), _dptr(s3), float(h), _iptr(ic))
+    fn(C.byref(walker.struct.g), C.byref(walker.struct.hill), _dptr(field), _dptr(s3), float(h), _iptr(ic), None)
     return ic[: walker.d].copy()
 
 
@@ -396,8 +396,9 @@ def run(walkers, frames, atom_offsets, step0: int, T: int, fields=None, record_f
     [T, total_atoms, 3]: for every step, the coordinates after that step's
     move predicted from the recorded frame. With error_model it also returns
     the per-step error-analysis outputs: H [T, nw, 3, 3] (slope of the
-    interpolated dV_k along s_j), A [T, nw, 4] (absolute interpolation
-    scale), sb [T, nw, 3] (CV rounding bound in units of the unit roundoff)
+    interpolated dV_k along s_j), A [T, nw, 4] (the interpolated gross
+    fields: the rounding scale of the accumulated grid and of the
+    interpolation), sb [T, nw, 3] (CV rounding bound in units of the unit roundoff)
     and Jn [T, total_atoms, 3] (|ds_k/dx| per atom).
     """
     nw = len(walkers)
@@ -428,11 +429,19 @@ def run(walkers, frames, atom_offsets, step0: int, T: int, fields=None, record_f
         Xn = np.zeros((T, total, 3))
     aux = (OrStepAux * (T * nw))() if error_model else None
     Jn = np.zeros((T, total, 3)) if error_model else None
+    gptrs = None
+    if error_model:
+        # gross fields, shared where the fields are
+        by_id = {}
+        for f in fields:
+            by_id.setdefault(id(f), np.abs(f))  # what the grid already holds counts at its size
+        gross = [by_id[id(f)] for f in fields]
+        gptrs = (C.POINTER(C.c_double) * nw)(*[_dptr(g) for g in gross])
     rc = lib().or_run(
         nw, arr, fptrs, _dptr(frames), offs.ctypes.data_as(C.POINTER(C.c_int64)), total * 3, int(step0), int(T),
         _dptr(s), _dptr(V), _dptr(dV), _dptr(F) if F is not None else None, _iptr(flags), deps, dep_cap, C.byref(nd),
         C.byref(mds) if mds is not None else None, st.ctypes.data_as(C.POINTER(C.c_uint32)) if st is not None else None,
-        _dptr(Xn) if Xn is not None else None, aux, _dptr(Jn) if Jn is not None else None,
+        _dptr(Xn) if Xn is not None else None, aux, _dptr(Jn) if Jn is not None else None, gptrs,
     )
     if rc:
         raise RuntimeError(f"oracle run failed ({rc})")
@@ -549,7 +558,7 @@ def interp_aux(walker: Walker, field: np.ndarray, s):
     s3[: walker.d] = s
     H = np.zeros(9)
     A = np.zeros(4)
-    lib().or_interp_aux(C.byref(walker.struct.g), _dptr(field), _dptr(s3), _dptr(H), _dptr(A))
+    lib().or_interp_aux(C.byref(walker.struct.g), _dptr(field), None, _dptr(s3), _dptr(H), _dptr(A))
     return H.reshape(3, 3)[: walker.d, : walker.d].copy(), A[: 1 + walker.d].copy()
 
 

@@ -436,9 +436,14 @@ int or_interp(const or_grid *g, const double *field, const double *s, double *V,
  * At s, with the corners, weights and clamping of or_interp:
  *   H[3*k + j] = d(dV_k)/ds_j, the slope of the interpolated derivative field
  *                k along axis j (0 on a clamped axis j or for a clamped k);
- *   A[q]       = sum over corners of weight * |field q at the corner|, the
- *                scale of the rounding error of the interpolation itself. */
-void or_interp_aux(const or_grid *g, const double *field, const double *s, double *H, double *A) {
+ *   A[q]       = sum over corners of weight * the gross value of field q at
+ *                the corner (the sum of the absolute values of every
+ *                contribution deposited there, gross = NULL: |field|): the
+ *                scale of the rounding error of a node value accumulated
+ *                from single-precision contributions, and of the
+ *                interpolation itself. */
+void or_interp_aux(const or_grid *g, const double *field, const double *gross, const double *s, double *H,
+                   double *A) {
   int d = g->d, nf = 1 + d;
   int i0[3] = {0, 0, 0}, i1[3] = {0, 0, 0}, clamped[3] = {0, 0, 0};
   double f[3] = {0, 0, 0}, D[3] = {1, 1, 1};
@@ -476,7 +481,7 @@ void or_interp_aux(const or_grid *g, const double *field, const double *s, doubl
       node += mul * (hi ? i1[k] : i0[k]);
       mul *= g->n[k];
     }
-    for (int q = 0; q < nf; ++q) A[q] += wgt * fabs(field[node * nf + q]);
+    for (int q = 0; q < nf; ++q) A[q] += wgt * (gross ? gross[node * nf + q] : fabs(field[node * nf + q]));
     for (int k = 0; k < d; ++k)
       for (int j = 0; j < d; ++j)
         if (!clamped[k] && !clamped[j]) H[3 * k + j] += dw[j] * field[node * nf + 1 + k];
@@ -603,7 +608,7 @@ double or_height(const or_hill *hl, double Vb) {
 /* Adds h*G and h*dG/dxi_k at every node of the stencil box around s.
  * ic_out receives the box centre indices. */
 void or_deposit_hill(const or_grid *g, const or_hill *hl, double *field, const double *s,
-                     double h, int *ic_out) {
+                     double h, int *ic_out, double *gross) {
   int d = g->d, nf = 1 + d;
   int ic[3] = {0, 0, 0}, R[3] = {0, 0, 0};
   double D[3] = {1, 1, 1}, L[3] = {0, 0, 0};
@@ -647,8 +652,12 @@ void or_deposit_hill(const or_grid *g, const or_hill *hl, double *field, const d
         if (!inside) continue;
         double hG = h * exp(-r2);
         field[node * nf] += hG;
-        for (int k = 0; k < d; ++k)
-          field[node * nf + 1 + k] += hG * (-dist[k] / (hl->sigma[k] * hl->sigma[k]));
+        if (gross) gross[node * nf] += fabs(hG);
+        for (int k = 0; k < d; ++k) {
+          double v = hG * (-dist[k] / (hl->sigma[k] * hl->sigma[k]));
+          field[node * nf + 1 + k] += v;
+          if (gross) gross[node * nf + 1 + k] += fabs(v);
+        }
       }
 }
 
@@ -695,7 +704,7 @@ static void nearest_node(const or_grid *g, const double *s, int *ic, int *limite
  * h'_i += w dS(xi* - xi)/dxi_i on every node within a of xi* (per axis),
  * S the product of the one-dimensional compact hills. */
 void or_deposit_compact(const or_grid *g, const or_hill *hl, double *field, const double *s, double w,
-                        int *ic_out) {
+                        int *ic_out, double *gross) {
   int d = g->d, nf = 1 + d;
   int ic[3] = {0, 0, 0}, R[3] = {0, 0, 0}, lim[3];
   double D[3] = {1, 1, 1};
@@ -732,12 +741,14 @@ void or_deposit_compact(const or_grid *g, const or_hill *hl, double *field, cons
         if (!inside) continue;
         double prod = S[0] * S[1] * S[2];
         field[node * nf] += w * prod;
+        if (gross) gross[node * nf] += fabs(w * prod);
         for (int k = 0; k < d; ++k) {
           double other = 1.0;
           for (int q = 0; q < d; ++q)
             if (q != k) other *= S[q];
           /* d S(xi* - xi) / d xi_k = - S'(u_k) * prod of the other axes */
           field[node * nf + 1 + k] += w * (-dS[k]) * other;
+          if (gross) gross[node * nf + 1 + k] += fabs(w * dS[k] * other);
         }
       }
 }
@@ -897,7 +908,7 @@ void or_md_move(const or_walker *wk, const or_md *md, uint32_t stream, int64_t s
 int or_batch_step(int nw, const or_walker *wk, double *const *fields, const double *const *x,
                   int64_t step, double *s, double *V, double *dV, double *const *F, int *flags,
                   or_deposit *dep, const or_md *md, const uint32_t *streams, double *const *xn,
-                  or_stepaux *aux, double *const *Jn) {
+                  or_stepaux *aux, double *const *Jn, double *const *gross) {
   for (int w = 0; w < nw; ++w)
     if (or_check(&wk[w].g, &wk[w].hill)) return OR_FLAG_BADARG;
 
@@ -938,10 +949,11 @@ int or_batch_step(int nw, const or_walker *wk, double *const *fields, const doub
     dep[w].walker = w;
     dep[w].height = h[w];
     for (int k = 0; k < 3; ++k) dep[w].s[k] = s[3 * w + k];
+    double *gw = gross ? gross[w] : NULL;
     if (wk[w].hill.method == OR_METHOD_MABP_COMPACT)
-      or_deposit_compact(&wk[w].g, &wk[w].hill, fields[w], &s[3 * w], h[w], dep[w].ic);
+      or_deposit_compact(&wk[w].g, &wk[w].hill, fields[w], &s[3 * w], h[w], dep[w].ic, gw);
     else
-      or_deposit_hill(&wk[w].g, &wk[w].hill, fields[w], &s[3 * w], h[w], dep[w].ic);
+      or_deposit_hill(&wk[w].g, &wk[w].hill, fields[w], &s[3 * w], h[w], dep[w].ic, gw);
     flags[w] |= OR_FLAG_DEPOSIT;
   }
 
@@ -959,12 +971,24 @@ int or_batch_step(int nw, const or_walker *wk, double *const *fields, const doub
       for (int k = d; k < 3; ++k) aux[w].sb[k] = 0.0;
       if (wk[w].hill.method == OR_METHOD_MABP_COMPACT) {
         /* a node look-up: no slope inside a cell; the rounding scale is the
-         * bias and its gradient themselves */
+         * bias and its gradient themselves, and the gross histograms at the
+         * node through dV/dh' = c b kT / (1 + c (1-b) h) */
         for (int q = 0; q < 9; ++q) aux[w].H[q] = 0.0;
         aux[w].A[0] = fabs(V[w]);
-        for (int k = 0; k < 3; ++k) aux[w].A[1 + k] = k < d ? fabs(g3[k]) : 0.0;
+        int ic[3] = {0, 0, 0}, lim[3];
+        nearest_node(&wk[w].g, &s[3 * w], ic, lim);
+        long node = 0, mul = 1;
+        for (int k = 0; k < d; ++k) {
+          node += mul * ic[k];
+          mul *= wk[w].g.n[k];
+        }
+        const double *fw = fields[w];
+        const double den = 1.0 + wk[w].hill.c * (1.0 - wk[w].hill.b) * fw[node * (1 + d)];
+        const double gfac = wk[w].hill.c * wk[w].hill.b * wk[w].hill.kT / den;
+        for (int k = 0; k < 3; ++k)
+          aux[w].A[1 + k] = k < d ? fabs(g3[k]) + (gross ? gfac * gross[w][node * (1 + d) + 1 + k] : 0.0) : 0.0;
       } else {
-        or_interp_aux(&wk[w].g, fields[w], &s[3 * w], aux[w].H, aux[w].A);
+        or_interp_aux(&wk[w].g, fields[w], gross ? gross[w] : NULL, &s[3 * w], aux[w].H, aux[w].A);
       }
       for (int k = 0; k < d; ++k)
         if (or_wall_grad(&wk[w].hill, k, s[3 * w + k]) != 0.0) aux[w].H[4 * k] += wk[w].hill.kwall;
@@ -1013,13 +1037,15 @@ int or_batch_step(int nw, const or_walker *wk, double *const *fields, const doub
  * closed-loop trajectory is checked one step at a time against it.
  * aux_hist [T][nw] and Jn_hist [T][frame_stride] (optional) receive each
  * step's or_stepaux and, per atom, |ds_k/dx| of each CV k (error-analysis
- * outputs for per-step comparisons).
+ * outputs for per-step comparisons); gross (optional, laid out and shared
+ * like fields) accumulates the absolute values of every deposited
+ * contribution, the scale of the accumulated grid's rounding.
  * Returns 0 or OR_FLAG_BADARG. */
 int or_run(int nw, const or_walker *wk, double *const *fields, const double *frames,
            const int64_t *atom_off, int64_t frame_stride, int64_t step0, int64_t T,
            double *s_hist, double *V_hist, double *dV_hist, double *F_hist, int *flag_hist,
            or_deposit *dep_log, int64_t dep_cap, int64_t *n_dep, const or_md *md, const uint32_t *streams,
-           double *Xn_hist, or_stepaux *aux_hist, double *Jn_hist) {
+           double *Xn_hist, or_stepaux *aux_hist, double *Jn_hist, double *const *gross) {
   const double **x = (const double **)malloc(sizeof(double *) * (size_t)nw);
   double **F = (double **)malloc(sizeof(double *) * (size_t)nw);
   double *s = (double *)malloc(sizeof(double) * 3 * (size_t)nw);
@@ -1040,7 +1066,7 @@ int or_run(int nw, const or_walker *wk, double *const *fields, const double *fra
       Jn[w] = Jn_hist ? Jn_hist + t * frame_stride + atom_off[w] : NULL;
     }
     rc = or_batch_step(nw, wk, fields, x, step0 + t, s, V, dV, F, fl, dep, (md && Xn_hist) ? md : NULL, streams,
-                       Xn, aux_hist ? aux_hist + t * nw : NULL, Jn_hist ? Jn : NULL);
+                       Xn, aux_hist ? aux_hist + t * nw : NULL, Jn_hist ? Jn : NULL, gross);
     for (int w = 0; w < nw; ++w) {
       if (s_hist) for (int k = 0; k < 3; ++k) s_hist[(t * nw + w) * 3 + k] = s[3 * w + k];
       if (V_hist) V_hist[t * nw + w] = V[w];
@@ -1093,7 +1119,7 @@ int or_md_run(int nw, const or_walker *wk, double *const *fields, double *x, con
   }
   for (int64_t t = 0; t < T && rc == 0; ++t) {
     if (X_hist) memcpy(X_hist + t * frame_stride, x, sizeof(double) * (size_t)frame_stride);
-    rc = or_batch_step(nw, wk, fields, xs, step0 + t, s, V, dV, F, fl, dep, md, streams, Xn, NULL, NULL);
+    rc = or_batch_step(nw, wk, fields, xs, step0 + t, s, V, dV, F, fl, dep, md, streams, Xn, NULL, NULL, NULL);
     for (int w = 0; w < nw; ++w) {
       memcpy(x + atom_off[w], Xn[w], sizeof(double) * 3 * (size_t)wk[w].natoms);
       if (s_hist) for (int k = 0; k < 3; ++k) s_hist[(t * nw + w) * 3 + k] = s[3 * w + k];
@@ -1139,7 +1165,7 @@ int or_langevin_double_well(const or_walker *wk, double *field, double *x, int64
   int rc = 0;
   double amp = sqrt(2.0 * mu * wk->hill.kT * dt);
   for (int64_t t = 0; t < T && rc == 0; ++t) {
-    rc = or_batch_step(1, wk, fields, xs, t, s, &V, dV, Fs, &fl, &dep, NULL, NULL, NULL, NULL, NULL);
+    rc = or_batch_step(1, wk, fields, xs, t, s, &V, dV, Fs, &fl, &dep, NULL, NULL, NULL, NULL, NULL, NULL);
     if (s_hist) s_hist[t] = s[0];
     double sv;
     or_cv_eval(&wk->cv[0], wk->natoms, x, &sv, J);

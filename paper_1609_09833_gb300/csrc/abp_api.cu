@@ -701,12 +701,14 @@ abp_status abp_walker_create(abp_ctx *ctx, abp_grid *grid, const abp_walker_desc
     return fail(ABP_ERR_INVALID_ARG, "kwall must be finite and >= 0");
   }
   hd.kwall = d->kwall;
+  hd.kwall_f = (float)d->kwall;
   for (int k = 0; k < 3; ++k) {
     if (d->kwall > 0 && k < ncv && !std::isfinite(d->smax[k])) {
       delete w;
       return fail(ABP_ERR_INVALID_ARG, "smax[%d] must be finite when kwall > 0", k);
     }
     hd.smax[k] = d->kwall > 0 && k < ncv ? d->smax[k] : 0.0;
+    hd.smax_f[k] = (float)hd.smax[k];
   }
   long long stencil = 1;
   for (int k = 0; k < ncv; ++k) {
@@ -1112,12 +1114,13 @@ abp_status abp_md_run(abp_ctx *ctx, abp_walker *const *walkers, int n, void *coo
     for (abp_walker *w : lw) gb = std::max(gb, md_group_bytes(w->hd, fp64));
     const int smem_max = 227 * 1024;
     if (gb > smem_max) return fail(ABP_ERR_UNSUPPORTED, "a walker needs %d bytes of shared memory (max %d)", gb, smem_max);
-    // one warp per walker; with more walkers than multiprocessors, four per CTA
-    int wpc = ctx->tune_gpc ? std::min(ctx->tune_gpc, 4) : ((int)lw.size() > ctx->sms ? 4 : 1);
-    while (wpc > 1 && wpc * gb > smem_max) --wpc;
+    // four warps per walker; with more walkers than multiprocessors, two
+    // walker groups per CTA
+    int gpc = ctx->tune_gpc ? std::min(ctx->tune_gpc, 2) : ((int)lw.size() > ctx->sms ? 2 : 1);
+    while (gpc > 1 && gpc * gb > smem_max) --gpc;
     a.r.nw = (int)lw.size();
-    a.r.G = 32;
-    a.r.groups_per_cta = wpc;
+    a.r.G = 128;
+    a.r.groups_per_cta = gpc;
     a.r.group_bytes = gb;
     a.r.coords = coords_dev;
     a.r.coff = reinterpret_cast<const long long *>(coord_offsets_dev);

@@ -127,6 +127,45 @@ int big_chunks(const WalkerDev &hd) { return big_nchunks(hd); }
 
 // ---------------------------------------------------------------- k_big_cn
 
+// Minimum image d - L rint(d / L) with rint formed on the FMA pipe: adding
+// and subtracting 1.5 2^23 rounds d / L to the nearest integer exactly for
+// |d / L| < 2^22 (ties go to even, where either image has the same length).
+__device__ __forceinline__ float min_image_rn(float d, float L, float invL) {
+  const float M = 12582912.0f;
+  const float t = __fsub_rn(__fmaf_rn(d, invL, M), M);
+  return __fmaf_rn(-L, t, d);
+}
+
+// The A gradients of one block (4 A atoms x 3 components, this lane's part)
+// summed over the warp by a reduce-scatter: the half-warps exchange half of
+// the values (atoms 0, 1 | 2, 3), then the quarter-warps (one atom each),
+// then three butterfly levels over the remaining three; lane 8 q holds atom
+// q's sums, which it adds to the warp's accumulators.
+__device__ __forceinline__ void reduce_block_grads(const float (&gi)[4][3], int lane, int i0, int na, float *mylig) {
+  const bool h16 = (lane & 16) != 0, h8 = (lane & 8) != 0;
+  float w6[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const float lo = gi[j / 3][j % 3], hi = gi[2 + j / 3][j % 3];
+    const float send = h16 ? lo : hi;
+    w6[j] = (h16 ? hi : lo) + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  float w3[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const float send = h8 ? w6[j] : w6[3 + j];
+    w3[j] = (h8 ? w6[3 + j] : w6[j]) + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) w3[j] += __shfl_xor_sync(0xffffffffu, w3[j], o);
+  const int ii = (h16 ? 2 : 0) + (h8 ? 1 : 0);
+  if ((lane & 7) == 0 && i0 + ii < na)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) mylig[(i0 + ii) * 3 + q] += w3[q];
+}
+
 // One CTA: the A x (one chunk of B) pairs of one walker's CN.
 __global__ void __launch_bounds__(kBigThreads) k_big_cn(const BigItem *items, const void *coords,
                                                         const long long *coff, long long step_off) {
@@ -180,9 +219,9 @@ __global__ void __launch_bounds__(kBigThreads) k_big_cn(const BigItem *items, co
         for (int jj = 0; jj < kBigJB; ++jj) {
           float dx = a.x - xj[jj], dy = a.y - yj[jj], dz = a.z - zj[jj];
           if (pbc) {
-            dx = min_image(dx, bx, ibx);
-            dy = min_image(dy, by, iby);
-            dz = min_image(dz, bz, ibz);
+            dx = min_image_rn(dx, bx, ibx);
+            dy = min_image_rn(dy, by, iby);
+            dz = min_image_rn(dz, bz, ibz);
           }
           float q = (dx * dx + dy * dy + dz * dz) * k2;
           float q2 = q * q;
@@ -208,9 +247,9 @@ __global__ void __launch_bounds__(kBigThreads) k_big_cn(const BigItem *items, co
         for (int jj = 0; jj < kBigJB; ++jj) {
           float dx = a.x - xj[jj], dy = a.y - yj[jj], dz = a.z - zj[jj];
           if (pbc) {
-            dx = min_image(dx, bx, ibx);
-            dy = min_image(dy, by, iby);
-            dz = min_image(dz, bz, ibz);
+            dx = min_image_rn(dx, bx, ibx);
+            dy = min_image_rn(dy, by, iby);
+            dz = min_image_rn(dz, bz, ibz);
           }
           float q = (dx * dx + dy * dy + dz * dz) * k2;
           float q2 = q * q;
@@ -233,15 +272,7 @@ __global__ void __launch_bounds__(kBigThreads) k_big_cn(const BigItem *items, co
       sacc = tsum;
       scomp += terr;
     }
-#pragma unroll
-    for (int ii = 0; ii < 4; ++ii)
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        float v = gi[ii][q];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0 && i0 + ii < na) mylig[(i0 + ii) * 3 + q] += v;
-      }
+    reduce_block_grads(gi, lane, i0, na, mylig);
   }
   unsigned char *js = reinterpret_cast<unsigned char *>(wd->jscratch);
   const BigLayout L = big_layout(*wd);

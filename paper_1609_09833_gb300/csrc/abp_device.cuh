@@ -268,8 +268,10 @@ __device__ __forceinline__ int com_finish_ff(const CvDev &c, const float *ra, co
   const float rh = sqrtf(r2h);
   sh = rh;
   if (rh > 0.f) {
-    sl = __fdiv_rn(__fadd_rn(__fmaf_rn(-rh, rh, r2h), r2l), 2.f * rh);
-    const float ir = __fdiv_rn(1.f, rh);
+    // the correction is a few units in the last place of rh, and u only
+    // needs FP32 accuracy: a fast reciprocal serves both
+    const float ir = __fdividef(1.f, rh);
+    sl = __fmul_rn(__fadd_rn(__fmaf_rn(-rh, rh, r2h), r2l), 0.5f * ir);
 #pragma unroll
     for (int q = 0; q < 3; ++q) u[q] = __fmul_rn(dh[q], ir);
     return 0;
@@ -1265,7 +1267,10 @@ __device__ __forceinline__ void mabp_bias(const WalkerDev &wd, const Real *acc, 
 // dU/ds_k of the CV range limit: kwall (s - smax_k) above smax_k, else 0.
 template <typename Real>
 __device__ __forceinline__ Real wall_grad(const WalkerDev &wd, int k, Real s) {
-  return (wd.kwall > 0 && s > (Real)wd.smax[k]) ? (Real)wd.kwall * (s - (Real)wd.smax[k]) : (Real)0;
+  if constexpr (sizeof(Real) == 4)
+    return (wd.kwall_f > 0.f && s > wd.smax_f[k]) ? wd.kwall_f * (s - wd.smax_f[k]) : 0.f;
+  else
+    return (wd.kwall > 0 && s > (Real)wd.smax[k]) ? (Real)wd.kwall * (s - (Real)wd.smax[k]) : (Real)0;
 }
 
 // a4: V and dV/ds_k at s after the deposit, by warp 0's first 2^d lanes,

@@ -85,6 +85,8 @@ struct WalkerDev {
   double mabp_h;     // mABP: c (1 - b)
   double smax[3];    // CV range limit: wall above smax_k ...
   double kwall;      // ... of force constant kwall (0: none)
+  float smax_f[3];   // the same in FP32 (the FP32 kernels' copies)
+  float kwall_f;
   void *fbuf;        // library-owned force records (abp_step -> abp_forces)
   void *jscratch;    // library-owned Jacobian scratch (plain form)
   WalkerState *state;

@@ -4,15 +4,17 @@
 // cycle of the paper's Figure "cycle", with overdamped Langevin dynamics in
 // place of GROMACS).
 //
-//   k_md   one warp per walker, for walkers whose CVs are COM distances,
+//   k_md   four warps per walker, for walkers whose CVs are COM distances,
 //          dihedrals or RMSDs (the windowed form's walkers). A step is a
 //          dependent chain -- a1, a2 + a3 on deposit steps, a4, a5, the move --
-//          so a walker's steps cannot overlap one another; the warp keeps the
-//          walker's atoms in shared memory for the whole launch and runs each
-//          phase with the windowed form's per-step operations
-//          (abp_window_ops.cuh): the same CVs, axis state, height, stencil
-//          and interpolation arithmetic. The noise of a step is drawn while
-//          its interpolation corners are in flight.
+//          so a walker's steps cannot overlap one another; the group keeps
+//          the walker's atoms in shared memory for the whole launch, splits
+//          each step's independent work between the two warps of its step
+//          pair (the COM sums beside the other CVs, one atom per thread for
+//          the forces and the move), draws the noise a window of steps ahead
+//          on its two other warps, and runs each phase with the windowed
+//          form's per-step operations (abp_window_ops.cuh): the same axis
+//          state, height, stencil and interpolation arithmetic.
 #include <cuda_runtime.h>
 
 #include "abp_launch.h"
@@ -28,16 +30,25 @@ __host__ __device__ constexpr int md_fixed_bytes() {
   return (int)((sizeof(GroupFixed<Real>) + 31) & ~(size_t)31);
 }
 
-// Shared-memory layout of one walker's warp (bytes from the end of its
-// GroupFixed): the atoms, the step's record, the potential's Jacobian
-// factors, each atom's noise, the a5 term tables and the CV atom lists.
+// Steps per noise window of the closed-loop form: the producer warps fill
+// one window's noise while the step chain consumes the previous one; two
+// windows of a walker's noise take at most ~32 KB of shared memory.
+__host__ __device__ inline int md_window(int natoms, int real) {
+  int W = (32 * 1024) / (2 * natoms * 3 * real);
+  return W < 1 ? 1 : (W > 16 ? 16 : W);
+}
+
+// Shared-memory layout of one walker's group (bytes from the end of its
+// GroupFixed): the atoms, the step's record, the potential's gradient, two
+// windows of noise, the a5 term tables and the CV atom lists.
 struct MdLayout {
-  int xs, st, ju, nz, cnt, terms, lists, total;
+  int xs, st, ju, nz, nzwin, cnt, terms, lists, total, W;
 };
 
 __host__ __device__ inline MdLayout md_layout(int natoms, const CvDev *cv, int d, int fp64) {
   MdLayout L;
   const int rsz = fp64 ? 32 : 16, real = fp64 ? 8 : 4;
+  L.W = md_window(natoms, real);
   int off = 0;
   L.xs = off;
   off += natoms * rsz;
@@ -46,7 +57,8 @@ __host__ __device__ inline MdLayout md_layout(int natoms, const CvDev *cv, int d
   L.ju = off;
   off += align32(kMaxCv * 12 * real);
   L.nz = off;
-  off += align16(natoms * 3 * real);
+  L.nzwin = align16(L.W * natoms * 3 * real);
+  off += 2 * L.nzwin;
   L.cnt = off;
   off += align16(natoms * 4);
   L.terms = off;
@@ -60,23 +72,198 @@ __host__ __device__ inline MdLayout md_layout(int natoms, const CvDev *cv, int d
   return L;
 }
 
-template <typename Real, int DIM, int UNR>
-__global__ void __launch_bounds__(128) k_md(MdRunArgs a) {
-  using R4 = typename Rec4<Real>::T;
+// A COM distance by one warp: group A's atoms on lanes 0-15 and group B's on
+// lanes 16-31 (stride 16), each lane's weighted offsets from its group's
+// first atom summed (FP32: compensated, as com_sum), the half-warps' partial
+// sums combined by a butterfly (FP32: in hi + lo), then finished on lane 0
+// (com_finish). Every lane of the warp calls it; lane 0 returns the CV.
+template <typename Real>
+__device__ __forceinline__ int com_warp(const CvDev &c, const int32_t *ia, const int32_t *ib, const Real *wa,
+                                        const Real *wb, const typename Rec4<Real>::T *x, int lane, Real &s, Real &sl,
+                                        Real *u) {
+  const bool gb = lane >= 16;
+  const int32_t *list = gb ? ib : ia;
+  const Real *wts = gb ? wb : wa;
+  const int n = gb ? c.nb : c.na;
+  const auto p0 = x[list[0]];
+  Real h[3] = {0, 0, 0}, l[3] = {0, 0, 0};
+  for (int i = lane & 15; i < n; i += 16) {
+    const Real w = wts[i];
+    const auto p = x[list[i]];
+    const Real d[3] = {sub_rn(p.x, p0.x), sub_rn(p.y, p0.y), sub_rn(p.z, p0.z)};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      if constexpr (sizeof(Real) == 4) {
+        const Real y = fma_rn(w, d[q], -l[q]);
+        const Real t = add_rn(h[q], y);
+        l[q] = sub_rn(sub_rn(t, h[q]), y);
+        h[q] = t;
+      } else {
+        h[q] = fma_rn(w, d[q], h[q]);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    if constexpr (sizeof(Real) == 4) {
+      Real s2, e2;
+      two_sum<Real>(h[q], -l[q], s2, e2);  // Kahan's compensation holds minus the lost part
+      h[q] = s2;
+      l[q] = e2;
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) {
+        const Real oh = __shfl_xor_sync(0xffffffffu, h[q], o), ol = __shfl_xor_sync(0xffffffffu, l[q], o);
+        ff_add<Real>(h[q], l[q], oh, ol);
+      }
+    } else {
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) h[q] += __shfl_xor_sync(0xffffffffu, h[q], o);
+    }
+  }
+  Real bh[3], bl[3], b0[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    bh[q] = __shfl_sync(0xffffffffu, h[q], 16);
+    bl[q] = __shfl_sync(0xffffffffu, l[q], 16);
+  }
+  b0[0] = __shfl_sync(0xffffffffu, p0.x, 16);
+  b0[1] = __shfl_sync(0xffffffffu, p0.y, 16);
+  b0[2] = __shfl_sync(0xffffffffu, p0.z, 16);
+  if (lane != 0) return 0;
+  const Real a0[3] = {p0.x, p0.y, p0.z};
+  return com_finish<Real>(c, a0, h, l, b0, bh, bl, s, sl, u);
+}
+
+// The end of a4 in the closed-loop form: V and dV/ds_k (mABP: the nearest
+// node's histograms turned into the bias; zero on a clamped axis; plus the
+// CV range wall) into the step's record. The Jacobian factors stay unscaled:
+// the force phase weighs them by dV/ds_k + dU/ds_k.
+template <typename Real>
+__device__ __forceinline__ void md_finish(const WalkerDev &wd, StepRec<Real> &st, Real *acc) {
+  const int d = wd.g.d;
+  if (wd.method == ABP_METHOD_MABP) {
+    Real V, dvm[3] = {0, 0, 0};
+    mabp_bias<Real>(wd, acc, V, dvm);
+    acc[0] = V;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) acc[1 + k] = dvm[k];
+  }
+  st.V = acc[0];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    if (k < d) st.dv[k] = (((st.clamped >> k) & 1) ? (Real)0 : acc[1 + k]) + wall_grad<Real>(wd, k, st.s[k]);
+}
+
+// a4 by the warp: lane c < 2^DIM reads corner c and weighs its fields, the
+// corners are summed by a butterfly ((c0 + c1) + (c2 + c3), ...), and lane 0
+// finishes the look-up (md_finish). Every lane of the warp calls it.
+template <typename Real, int DIM>
+__device__ __forceinline__ void interp_warp(const WalkerDev &wd, StepRec<Real> &st, int lane) {
   constexpr int NC = 1 << DIM;
+  Real acc[4] = {0, 0, 0, 0};
+  if (lane < NC) {
+    float4 ra, rb;
+    rec_load<DIM>(node_ptr<DIM>(wd.g, corner_node<Real, DIM>(wd.g, st, lane)), ra, rb);
+    Real v[4];
+    rec_vals<Real, DIM>(ra, rb, v);
+    const Real wc = corner_weight<Real, DIM>(st, lane);
+#pragma unroll
+    for (int q = 0; q <= DIM; ++q) acc[q] = wc * v[q];
+  }
+#pragma unroll
+  for (int o = 1; o < NC; o <<= 1)
+#pragma unroll
+    for (int q = 0; q <= DIM; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+  if (lane == 0) md_finish<Real>(wd, st, acc);
+}
+
+// L1 prefetch of the grid records around a cell (lower corner c0 on axis 0,
+// c1 on axis 1): m0 nodes either side along axis 0, m1 rows either side
+// along axis 1 (wrapped on a periodic axis, limited on the others), one
+// 128-byte line per lane and request; lanes first..31 take part.
+template <int DIM>
+__device__ __forceinline__ void prefetch_cell(const GridDev &gd, int c0, int c1, int lane, int first) {
+  if (DIM > 2 || lane < first) return;
+  constexpr int rb = DIM > 1 ? 32 : 16;
+  const int m0 = 4, m1 = DIM > 1 ? 8 : 0;
+  int lo0 = c0 - m0, hi0 = c0 + 1 + m0;
+  lo0 = lo0 < 0 ? 0 : lo0;
+  hi0 = hi0 > gd.n[0] - 1 ? gd.n[0] - 1 : hi0;
+  const int lines = ((hi0 * rb) >> 7) - ((lo0 * rb) >> 7) + 1;
+  const int rows = 2 * m1 + 2;
+  const unsigned char *rec = reinterpret_cast<const unsigned char *>(gd.rec);
+  for (int r = lane - first; r < lines * rows; r += 32 - first) {
+    const int row = r / lines, ln = r - row * lines;
+    int j1 = 0;
+    if (DIM > 1) {
+      j1 = c1 - m1 + row;
+      if (gd.periodic[1]) {
+        if (j1 < 0) j1 += gd.n[1];
+        if (j1 >= gd.n[1]) j1 -= gd.n[1];
+      } else if (j1 < 0 || j1 >= gd.n[1]) {
+        continue;
+      }
+    }
+    const unsigned char *p = rec + ((long long)j1 * gd.n[0]) * rb + ((((lo0 * rb) >> 7) + ln) << 7);
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+  }
+}
+
+// a2 + a3 of a deposit step by the step pair (its own function: rarely run,
+// kept out of the step loop's code): the axis state of the deposit, the
+// tables, the height from the grid before the deposit, the stencil.
+template <typename Real, int DIM, int UNR>
+__device__ __noinline__ void md_deposit(const Grp &g, GroupFixed<Real> *fx, const StepRec<Real> &st, long long step,
+                                        const DepositLog &log) {
+  const GroupLayout Lnone{};
+  window_dep_axis<Real>(g, fx, st);
+  g.sync();
+  build_tables<Real>(g, fx);
+  if (g.t == 0) window_height<Real, DIM>(fx, st, step, log);
+  g.sync();
+  deposit_stencil<Real, false, UNR>(g, fx, Lnone, nullptr);
+  g.sync();
+}
+
+// The closed-loop kernel: a group of four warps per walker.
+//   warps 0 and 1, the step pair: each step's chain. Warp 0 evaluates the COM
+//   distances (com_warp), the CV potential's gradient and a4 (lane 0);
+//   warp 1 evaluates the other CVs (one lane per CV) beside warp 0's sums;
+//   both run a deposit's stencil and the forces and moves of the atoms.
+//   Named barrier gid + 1 (64 threads) separates the step's phases.
+//   warps 2 and 3, the producers: the Philox noise of the next window of W
+//   steps while the pair runs the current one (two noise buffers); the four
+//   warps meet at window boundaries (named barrier gpc + gid + 1).
+template <typename Real, int DIM, int UNR>
+__global__ void __launch_bounds__(256, 1) k_md(MdRunArgs a) {
+  using R4 = typename Rec4<Real>::T;
   extern __shared__ __align__(32) unsigned char smem[];
   const RunArgs &ra = a.r;
-  const int wpc = blockDim.x >> 5;  // walkers (warps) per CTA
-  const int gid = threadIdx.x >> 5;
-  const int slot = blockIdx.x * wpc + gid;
-  if (slot >= ra.nw) return;  // a whole warp
-  Grp g;
-  g.G = 32;
+  const int gpc = blockDim.x >> 7;  // walker groups per CTA
+  const int gid = threadIdx.x >> 7;
+  const int slot = blockIdx.x * gpc + gid;
+  if (slot >= ra.nw) return;  // the whole group
+  const int tg = threadIdx.x & 127;
+  Grp gg;  // the whole group
+  gg.G = 128;
+  gg.gid = gpc + gid;
+  gg.t = tg;
+  gg.lane = tg & 31;
+  gg.warp = tg >> 5;
+  gg.nwarps = 4;
+  // the step pair's barrier: bar.sync itself makes the participating
+  // threads' earlier shared and global accesses visible to one another
+  auto psync = [&]() { asm volatile("bar.sync %0, %1;" ::"r"(gid + 1), "r"(64) : "memory"); };
+  Grp g;  // the step pair (warps 0, 1) or the producer pair (warps 2, 3)
+  g.G = 64;
   g.gid = gid;
-  g.t = threadIdx.x & 31;
-  g.lane = g.t;
-  g.warp = 0;
-  g.nwarps = 1;
+  g.t = tg & 63;
+  g.lane = tg & 31;
+  g.warp = g.t >> 5;
+  g.nwarps = 2;
+  const bool producer = tg >= 64;
+  const bool w0 = !producer && g.warp == 0;
+  const int lane = g.lane;
   unsigned char *base = smem + (size_t)gid * ra.group_bytes;
   GroupFixed<Real> *fx = reinterpret_cast<GroupFixed<Real> *>(base);
   unsigned char *dyn = base + md_fixed_bytes<Real>();
@@ -84,9 +271,9 @@ __global__ void __launch_bounds__(128) k_md(MdRunArgs a) {
   {
     const int *s = reinterpret_cast<const int *>(te.wd);
     int *d = reinterpret_cast<int *>(&fx->wd);
-    for (int i = g.t; i < (int)(sizeof(WalkerDev) / 4); i += 32) d[i] = s[i];
+    for (int i = tg; i < (int)(sizeof(WalkerDev) / 4); i += 128) d[i] = s[i];
   }
-  __syncwarp();
+  gg.sync();
   const WalkerDev &wd = fx->wd;
   const int natoms = wd.natoms;
   const MdLayout L = md_layout(natoms, wd.cv, DIM, sizeof(Real) == 8);
@@ -97,148 +284,183 @@ __global__ void __launch_bounds__(128) k_md(MdRunArgs a) {
       const CvDev &c = wd.cv[k];
       int32_t *ia = reinterpret_cast<int32_t *>(cur);
       int32_t *ib = ia + c.na;
-      for (int i = g.t; i < c.na; i += 32) ia[i] = c.ia[i];
-      for (int i = g.t; i < c.nb; i += 32) ib[i] = c.ib[i];
+      for (int i = tg; i < c.na; i += 128) ia[i] = c.ia[i];
+      for (int i = tg; i < c.nb; i += 128) ib[i] = c.ib[i];
       cur += align16((c.na + c.nb) * 4);
-      Real *wa = nullptr, *wb = nullptr;
+      Real *w_a = nullptr, *w_b = nullptr;
       if (c.type == ABP_CV_COM_DIST) {
-        wa = reinterpret_cast<Real *>(cur);
-        wb = wa + c.na;
-        for (int i = g.t; i < c.na; i += 32) wa[i] = sizeof(Real) == 4 ? (Real)c.wa[i] : (Real)c.wa64[i];
-        for (int i = g.t; i < c.nb; i += 32) wb[i] = sizeof(Real) == 4 ? (Real)c.wb[i] : (Real)c.wb64[i];
+        w_a = reinterpret_cast<Real *>(cur);
+        w_b = w_a + c.na;
+        for (int i = tg; i < c.na; i += 128) w_a[i] = sizeof(Real) == 4 ? (Real)c.wa[i] : (Real)c.wa64[i];
+        for (int i = tg; i < c.nb; i += 128) w_b[i] = sizeof(Real) == 4 ? (Real)c.wb[i] : (Real)c.wb64[i];
         cur += align16((c.na + c.nb) * (int)sizeof(Real));
       }
-      if (g.t == 0) {
+      if (tg == 0) {
         fx->ia[k] = ia;
         fx->ib[k] = ib;
-        fx->wa[k] = wa;
-        fx->wb[k] = wb;
+        fx->wa[k] = w_a;
+        fx->wb[k] = w_b;
       }
     }
   }
-  __syncwarp();
+  gg.sync();
   R4 *xs = reinterpret_cast<R4 *>(dyn + L.xs);
   StepRec<Real> &st = *reinterpret_cast<StepRec<Real> *>(dyn + L.st);
-  Real(*ju)[12] = reinterpret_cast<Real(*)[12]>(dyn + L.ju);
-  Real *nz = reinterpret_cast<Real *>(dyn + L.nz);
   int *cnt = reinterpret_cast<int *>(dyn + L.cnt);
   AtomTerm<Real> *terms = reinterpret_cast<AtomTerm<Real> *>(dyn + L.terms);
-  build_atom_terms<Real>(g, fx, cnt, terms);
+  if (!producer) build_atom_terms<Real>(g, fx, cnt, terms);
   R4 *cio = reinterpret_cast<R4 *>(const_cast<void *>(ra.coords)) + ra.coff[te.idx];
-  for (int i = g.t; i < natoms; i += 32) xs[i] = cio[i];
+  for (int i = tg; i < natoms; i += 128) xs[i] = cio[i];
   R4 *fout = ra.forces ? reinterpret_cast<R4 *>(ra.forces) + ra.foff[te.idx] : reinterpret_cast<R4 *>(wd.fbuf);
   const int fmode = ra.forces ? ra.mode : ABP_FORCES_OVERWRITE;
   R4 *tout = a.traj ? reinterpret_cast<R4 *>(a.traj) + a.toff[te.idx] : nullptr;
   const long long step0 = ra.step0;
-  const Real c1 = (Real)a.md.c1, c2 = (Real)a.md.c2;
-  const GroupLayout Lnone{};
+  const MdCoef<Real> mc = md_coef<Real>(a.md);
+  const MdTerm<Real> mt = md_term<Real>(a.md, lane);
+  const int W = L.W, nwin = (ra.nsteps + W - 1) / W;
+  auto nzbuf = [&](int w) { return reinterpret_cast<Real *>(dyn + L.nz + (w & 1) * L.nzwin); };
+  // the producers: window w's noise, (step, atom) pairs over their 64 threads
+  auto draw = [&](int w) {
+    Real *nz = nzbuf(w);
+    const int t0 = w * W, nt = min(W, ra.nsteps - t0);
+    for (Iter2 it(g.t, 64, natoms); it.j < nt; it.next()) {
+      Real n3[3];
+      md_normals(a.md.seed, te.stream, step0 + t0 + it.j, it.i, n3);
+      Real *p = nz + (it.j * natoms + it.i) * 3;
+      p[0] = n3[0];
+      p[1] = n3[1];
+      p[2] = n3[2];
+    }
+  };
   long long rem = step0 % wd.stride;
   long long next_dep = rem == 0 ? 0 : wd.stride - rem;
-  int last = -1;  // the last step run
-  __syncwarp();
-  for (int t = 0; t < ra.nsteps; ++t) {
-    const long long step = step0 + t;
-    // the step's coordinates must be finite; a walker that meets non-finite
-    // ones stops (its state says so)
-    int bad = 0;
-    for (int i = g.t; i < natoms; i += 32) bad |= finite_rec<Real>(xs[i]) ? 0 : 1;
-    if (__any_sync(0xffffffffu, bad)) {
-      if (g.t == 0) {
-        wd.state->flags = ABP_WFLAG_NONFINITE;
-        atomicAdd(&ra.ctr->nonfinite, 1);
-      }
-      break;
-    }
-    const bool dep = t == next_dep;
-    if (dep) next_dep += wd.stride;
-    // a1: every CV of the step into its record (COM distances on a lane pair,
-    // the others on lane 0), then the step's flags
+  int last = -1;        // the last step run
+  bool stopped = false;  // non-finite coordinates met (the pair's decision)
+  int pc0 = 0, pc1 = 0;  // warp 1: the previous step's cell (its L1 prefetch)
+  Real *dUs = reinterpret_cast<Real *>(dyn + L.ju);  // the step's dU/ds_k (warp 1 -> the force phase)
+  int *badw = reinterpret_cast<int *>(fx->winbad);  // one flag per step-pair warp
+  if (producer && nwin > 0) draw(0);
+  gg.sync();
+  for (int w = 0; w < nwin; ++w) {
+    if (producer) {
+      if (w + 1 < nwin) draw(w + 1);
+    } else {
+      const Real *nzw = nzbuf(w);
+      const int t0 = w * W, nt = min(W, ra.nsteps - t0);
+      for (int j = 0; j < nt && !stopped; ++j) {
+        const int t = t0 + j;
+        const long long step = step0 + t;
+        const bool dep = t == next_dep;
+        if (dep) next_dep += wd.stride;
+        // a1, and each warp's half of the finiteness check
+        int bad = 0;
+        for (int i = g.t; i < natoms; i += 64) bad |= finite_rec<Real>(xs[i]) ? 0 : 1;
+        bad = __any_sync(0xffffffffu, bad);
+        if (lane == 0) badw[g.warp] = bad;
+        if (w0) {
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-      if (wd.cv[k].type == ABP_CV_COM_DIST)
-        window_com2<Real>(fx, xs, k, dep, g.t < 2, g.t & 1, st);
-      else if (g.t == 0)
-        window_cv<Real>(fx, xs, k, dep, st);
-    }
-    __syncwarp();
-    if (g.t == 0) {
-      step_flags<Real>(DIM, dep, st);
-      // the CV potential's factors: dU/ds_k times the CV's Jacobian factors
-      Real sk[3] = {0, 0, 0}, dU[3];
+          for (int k = 0; k < DIM; ++k)
+            if (wd.cv[k].type == ABP_CV_COM_DIST) {
+              Real sk, slk;
+              const int fl = com_warp<Real>(wd.cv[k], fx->ia[k], fx->ib[k], fx->wa[k], fx->wb[k], xs, lane, sk,
+                                            slk, st.jac[k]);
+              if (lane == 0) window_cv_rec<Real>(wd, k, sk, slk, fl, dep, st);
+            }
+        } else {
+          // the previous step's cell first (its corners likely to be read again)
+          if (t > 0) prefetch_cell<DIM>(wd.g, pc0, pc1, lane, 1);
+          int q = 0;
 #pragma unroll
-      for (int k = 0; k < DIM; ++k) sk[k] = st.s[k];
-      md_potential_grad<Real>(a.md, sk, dU);
+          for (int k = 0; k < DIM; ++k)
+            if (wd.cv[k].type != ABP_CV_COM_DIST) {
+              if (lane == q) window_cv<Real>(fx, xs, k, dep, st);
+              ++q;
+            }
+        }
+        psync();
+        if (badw[0] | badw[1]) {
+          // this walker stops here: its state says so, its atoms stay
+          if (g.t == 0) {
+            wd.state->flags = ABP_WFLAG_NONFINITE;
+            atomicAdd(&ra.ctr->nonfinite, 1);
+          }
+          stopped = true;
+          break;
+        }
+        if (w0 && lane == 0) step_flags<Real>(DIM, dep, st);
+        if (dep) {
+          psync();
+          md_deposit<Real, DIM, UNR>(g, fx, st, step, ra.log);
+        }
+        if (w0) {
+          // a4 by warp 0
+          interp_warp<Real, DIM>(wd, st, lane);
+        } else {
+          // beside it, the CV potential's gradient by warp 1
+          Real sk[3] = {0, 0, 0}, dU[3];
 #pragma unroll
-      for (int k = 0; k < DIM; ++k) {
-        const int nj = wd.cv[k].type == ABP_CV_COM_DIST ? 3 : 12;
-        for (int q = 0; q < nj; ++q) ju[k][q] = st.jac[k][q] * dU[k];
+          for (int k = 0; k < DIM; ++k) sk[k] = st.s[k];
+          md_potential_grad_warp<Real>(mc, mt, sk, lane, dU);
+          if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) dUs[k] = dU[k];
+          pc0 = st.i0[0];
+          pc1 = DIM > 1 ? st.i0[DIM > 1 ? 1 : 0] : 0;
+        }
+        psync();
+        // a5 and the move, one atom per thread of the pair: each of the
+        // atom's terms (CV k, weight w, Jacobian factor v) adds w v (dV_b/ds_k
+        // + dU/ds_k) to the total force, and w v dV_b/ds_k to the bias force
+        // when the caller keeps it; then x += c1 F + c2 xi
+        const Real *nz = nzw + j * natoms * 3;
+        const bool keep_f = ra.forces || t == ra.nsteps - 1;
+        Real dvk[3], dtk[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          dvk[k] = k < DIM ? st.dv[k] : (Real)0;
+          dtk[k] = dvk[k] + dUs[k];
+        }
+        for (int i = g.t; i < natoms; i += 64) {
+          const AtomTerm<Real> *ti = terms + i * kAtomTerms;
+          const int ne = cnt[i];
+          const Real *J = &st.jac[0][0];
+          Real f0 = 0, f1 = 0, f2 = 0, b0 = 0, b1 = 0, b2 = 0;
+          for (int q = 0; q < ne; ++q) {
+            const int off = ti[q].off;
+            const int k = off >= 24 ? 2 : (off >= 12 ? 1 : 0);
+            const Real *v = J + off;
+            const Real wt = ti[q].w * dtk[k];
+            f0 += wt * v[0];
+            f1 += wt * v[1];
+            f2 += wt * v[2];
+            if (keep_f) {
+              const Real wb = ti[q].w * dvk[k];
+              b0 += wb * v[0];
+              b1 += wb * v[1];
+              b2 += wb * v[2];
+            }
+          }
+          R4 x = xs[i];
+          if (tout) tout[(long long)t * a.tstride + i] = x;
+          if (keep_f) {
+            R4 *fo = fout + (ra.forces ? (long long)t * ra.fstride : 0) + i;
+            store_force<Real>(fo, make_rec<Real>(b0, b1, b2, 0), fmode);
+          }
+          x.x += mc.c1 * f0 + mc.c2 * nz[3 * i];
+          x.y += mc.c1 * f1 + mc.c2 * nz[3 * i + 1];
+          x.z += mc.c1 * f2 + mc.c2 * nz[3 * i + 2];
+          xs[i] = x;
+        }
+        last = t;
+        psync();
       }
     }
-    __syncwarp();
-    // a2 + a3 on a deposit step: height from the grid before the deposit,
-    // then the stencil by the whole warp
-    if (dep) {
-      window_dep_axis<Real>(g, fx, st);
-      __syncwarp();
-      build_tables<Real>(g, fx);
-      if (g.t == 0) window_height<Real, DIM>(fx, st, step, ra.log);
-      __syncwarp();
-      deposit_stencil<Real, false, UNR>(g, fx, Lnone, nullptr);
-      __syncwarp();
-    }
-    // a4: lane 0 reads the corners; the warp draws the step's noise while
-    // they are in flight
-    float4 ca[NC], cb[NC];
-    if (g.t == 0) interp_load<Real, DIM>(wd, st, ca, cb);
-    for (int i = g.t; i < natoms; i += 32) {
-      Real n3[3];
-      md_normals(a.md.seed, te.stream, step, i, n3);
-      nz[3 * i] = n3[0];
-      nz[3 * i + 1] = n3[1];
-      nz[3 * i + 2] = n3[2];
-    }
-    if (g.t == 0) interp_combine<Real, DIM>(wd, st, ca, cb);
-    __syncwarp();
-    // a5 and the move: each atom's bias force from its terms (as the
-    // windowed form sums them: -sum_k dV_b/ds_k ds_k/dx), the potential's
-    // force -sum_k dU/ds_k ds_k/dx from the same terms on the dU-scaled
-    // factors, then x += c1 (F_bias + F_U) + c2 xi
-    const bool keep_f = ra.forces || t == ra.nsteps - 1;
-    for (int i = g.t; i < natoms; i += 32) {
-      const AtomTerm<Real> *ti = terms + i * kAtomTerms;
-      const int ne = cnt[i];
-      const Real *J = &st.jac[0][0];
-      const Real *JU = &ju[0][0];
-      Real f0 = 0, f1 = 0, f2 = 0, u0 = 0, u1 = 0, u2 = 0;
-      for (int q = 0; q < ne; ++q) {
-        const Real w = ti[q].w;
-        const Real *v = J + ti[q].off;
-        const Real *vu = JU + ti[q].off;
-        f0 += w * v[0];
-        f1 += w * v[1];
-        f2 += w * v[2];
-        u0 += w * vu[0];
-        u1 += w * vu[1];
-        u2 += w * vu[2];
-      }
-      R4 x = xs[i];
-      if (tout) tout[(long long)t * a.tstride + i] = x;
-      if (keep_f) {
-        R4 *fo = fout + (ra.forces ? (long long)t * ra.fstride : 0) + i;
-        store_force<Real>(fo, make_rec<Real>(f0, f1, f2, 0), fmode);
-      }
-      x.x += c1 * (f0 + u0) + c2 * nz[3 * i];
-      x.y += c1 * (f1 + u1) + c2 * nz[3 * i + 1];
-      x.z += c1 * (f2 + u2) + c2 * nz[3 * i + 2];
-      xs[i] = x;
-    }
-    last = t;
-    __syncwarp();
+    gg.sync();
   }
   // the moved atoms back to the caller, and the walker's state after its
   // last step
-  for (int i = g.t; i < natoms; i += 32) cio[i] = xs[i];
-  if (g.t == 0 && last >= 0) {
+  for (int i = tg; i < natoms; i += 128) cio[i] = xs[i];
+  if (tg == 0 && last >= 0) {
     WalkerState ws;
     for (int k = 0; k < 3; ++k) {
       ws.s[k] = k < DIM ? (double)st.s[k] + (double)st.sl[k] : 0.0;
@@ -262,10 +484,10 @@ int md_group_bytes(const WalkerDev &hd, int fp64) {
 cudaError_t launch_md(const MdRunArgs &a, int fp64, int dim, cudaStream_t st) {
   const RunArgs &r = a.r;
   if (r.nw == 0) return cudaSuccess;
-  const int wpc = r.groups_per_cta;
-  const int threads = 32 * wpc;
-  const int blocks = (r.nw + wpc - 1) / wpc;
-  const size_t smem = (size_t)r.group_bytes * wpc;
+  const int gpc = r.groups_per_cta;
+  const int threads = 128 * gpc;
+  const int blocks = (r.nw + gpc - 1) / gpc;
+  const size_t smem = (size_t)r.group_bytes * gpc;
   void (*k)(MdRunArgs);
   if (fp64)
     k = dim == 1 ? k_md<double, 1, 4> : dim == 2 ? k_md<double, 2, 4> : k_md<double, 3, 4>;

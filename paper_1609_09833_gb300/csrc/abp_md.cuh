@@ -62,27 +62,73 @@ __device__ __forceinline__ void md_normals(unsigned long long seed, unsigned str
   n[2] = r2 * cospi(2.0 * u3);
 }
 
-// dU/ds_k of the run's CV potential (abp.h: ABP_POT_*).
+// The run's dynamics in the walker's precision, converted once per launch:
+// the move's constants and the CV potential's coefficients.
 template <typename Real>
-__device__ __forceinline__ void md_potential_grad(const MdParams &m, const Real *s, Real *dU) {
+struct MdCoef {
+  int pot;
+  Real c1, c2;               // dt mu, sqrt(2 mu kT dt)
+  Real dwa, dwb2;            // double well: A, B^2
+  Real mx, cx, my, cy;       // Mueller-Brown: the affine map of (s_0, s_1)
+  Real sx, sy;               // scale * mx, scale * my
+};
+
+template <typename Real>
+__device__ __forceinline__ MdCoef<Real> md_coef(const MdParams &m) {
+  MdCoef<Real> k;
+  k.pot = m.potential;
+  k.c1 = (Real)m.c1;
+  k.c2 = (Real)m.c2;
+  k.dwa = (Real)m.dw_a;
+  k.dwb2 = (Real)(m.dw_b * m.dw_b);
+  k.mx = (Real)m.mb_map[0];
+  k.cx = (Real)m.mb_map[1];
+  k.my = (Real)m.mb_map[2];
+  k.cy = (Real)m.mb_map[3];
+  k.sx = (Real)(m.mb_scale * m.mb_map[0]);
+  k.sy = (Real)(m.mb_scale * m.mb_map[2]);
+  return k;
+}
+
+// One lane's Mueller-Brown term (term lane & 3 of the four), read once per
+// launch so that the step loop indexes no array by lane.
+template <typename Real>
+struct MdTerm {
+  Real A, a, b, c, x0, y0;
+};
+
+template <typename Real>
+__device__ __forceinline__ MdTerm<Real> md_term(const MdParams &m, int lane) {
+  const int i = lane & 3;
+  return MdTerm<Real>{(Real)m.mb_A[i], (Real)m.mb_a[i], (Real)m.mb_b[i], (Real)m.mb_c[i], (Real)m.mb_x0[i],
+                      (Real)m.mb_y0[i]};
+}
+
+// dU/ds_k of the run's CV potential (abp.h: ABP_POT_*) by the warp: lane i <
+// 4 forms the i-th Mueller-Brown term (its coefficients in mt), the four are
+// summed by two lane exchanges ((t0 + t1) + (t2 + t3)); lane 0 returns the
+// gradient.
+template <typename Real>
+__device__ __forceinline__ void md_potential_grad_warp(const MdCoef<Real> &k, const MdTerm<Real> &mt, const Real *s,
+                                                       int lane, Real *dU) {
   dU[0] = dU[1] = dU[2] = 0;
-  if (m.potential == ABP_POT_DOUBLE_WELL) {
-    const Real b = (Real)m.dw_b, q = s[0] * s[0] - b * b;
-    dU[0] = (Real)4 * (Real)m.dw_a * s[0] * q;
-  } else if (m.potential == ABP_POT_MULLER_BROWN) {
-    const Real X = (Real)m.mb_map[0] * s[0] + (Real)m.mb_map[1];
-    const Real Y = (Real)m.mb_map[2] * s[1] + (Real)m.mb_map[3];
-    Real dX = 0, dY = 0;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const Real xp = X - (Real)m.mb_x0[i], yp = Y - (Real)m.mb_y0[i];
-      const Real a = (Real)m.mb_a[i], b = (Real)m.mb_b[i], c = (Real)m.mb_c[i];
-      const Real e = (Real)m.mb_A[i] * exp(a * xp * xp + b * xp * yp + c * yp * yp);
-      dX += e * ((Real)2 * a * xp + b * yp);
-      dY += e * (b * xp + (Real)2 * c * yp);
+  if (k.pot == ABP_POT_DOUBLE_WELL) {
+    dU[0] = (Real)4 * k.dwa * s[0] * (s[0] * s[0] - k.dwb2);
+  } else if (k.pot == ABP_POT_MULLER_BROWN) {
+    Real gx = 0, gy = 0;
+    if (lane < 4) {
+      const Real X = k.mx * s[0] + k.cx, Y = k.my * s[1] + k.cy;
+      const Real xp = X - mt.x0, yp = Y - mt.y0;
+      const Real e = mt.A * exp(mt.a * xp * xp + mt.b * xp * yp + mt.c * yp * yp);
+      gx = e * ((Real)2 * mt.a * xp + mt.b * yp);
+      gy = e * (mt.b * xp + (Real)2 * mt.c * yp);
     }
-    dU[0] = (Real)m.mb_scale * (Real)m.mb_map[0] * dX;
-    dU[1] = (Real)m.mb_scale * (Real)m.mb_map[2] * dY;
+    gx += __shfl_xor_sync(0xffffffffu, gx, 1);
+    gy += __shfl_xor_sync(0xffffffffu, gy, 1);
+    gx += __shfl_xor_sync(0xffffffffu, gx, 2);
+    gy += __shfl_xor_sync(0xffffffffu, gy, 2);
+    dU[0] = k.sx * gx;
+    dU[1] = k.sy * gy;
   }
 }
 

@@ -131,10 +131,12 @@ extern "C" abp_status abp_step_static(int device, void *cuda_stream, const abp_g
   hd.natoms = w->natoms;
   hd.id = -1;
   hd.kwall = w->kwall;
+  hd.kwall_f = (float)w->kwall;
   for (int k = 0; k < d; ++k) {
     if (w->kwall > 0 && !std::isfinite(w->smax[k]))
       return sfail(ABP_ERR_INVALID_ARG, "abp_step_static: smax must be finite when kwall > 0");
     hd.smax[k] = w->kwall > 0 ? w->smax[k] : 0.0;
+    hd.smax_f[k] = (float)hd.smax[k];
   }
   for (int k = 0; k < d; ++k) {
     double sig = w->sigma[k];

@@ -14,10 +14,13 @@ oracle's own quantities at the step (oracle.run(..., error_model=True)):
   floor_i(t) = sum_k |ds_k/dx_i| (sum_j |d(dV_k)/ds_j| u sb_j + 16 u A_k).
 The first term is what a CV error within its rounding bound u sb_j does to
 the interpolated gradient (the slope of the interpolant times the CV
-error); the second is the rounding of the interpolation itself (A_k, the
-interpolation of |dV_k| at the corners, is its scale: the weights, the
-products and the corner sums cost at most 2d + 3 roundings, the force's
-products and sums d + 1 more, the Jacobian a few); a last term of 2^-120
+error); the second is the rounding of the grid and of the interpolation:
+A_k interpolates the gross value of field k at the corners (the sum of the
+absolute values of every hill's contribution there, each computed in FP32
+to a few roundings of its size, where the derivative fields of overlapping
+hills cancel), and the weights, products and corner sums cost at most
+2d + 3 roundings, the force's products and sums d + 1 more, the Jacobian a
+few; a last term of 2^-120
 (FP32; 2^-1000 for FP64) stands for values below the format's normal range,
 which the GPU's products flush (the compact hills of mABP reach e^-160 near
 their support's edge). On a step whose own force
