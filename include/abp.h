@@ -459,15 +459,26 @@ double abp_server_now(void);
 /* ---- allocation-free step -------------------------------------------------- */
 
 /* abp_step_static: one MD step (a1..a5) of one walker, allocating nothing on
- * the device. The paper has no counterpart; it exists for callers that
- * cannot call cudaMalloc (a host routine running while a CUDA graph is being
- * captured, a plugin confined to another program's memory pool, a bias call
- * made where the device allocator must not be touched). It runs the kernels of
- * abp_step_plain and gives the same results, but keeps everything beyond the
- * caller's buffers (the walker description, its atom lists, the Jacobian
- * passed between the kernels, a counter) in one static device array of
- * ABP_STATIC_SCRATCH_BYTES that every GPU loading the library holds until the
- * process exits. No cudaMalloc, cudaFree or other allocating call is made.
+ * the device. The paper has no counterpart. It serves callers for which a
+ * cudaMalloc or cudaFree inside the step is not acceptable:
+ *   - a plugin inside a host MD engine that hands out GPU memory from its own
+ *     pool with a fixed budget: an allocation made around that pool can fail
+ *     once the engine has taken the card's memory, and the engine cannot see
+ *     or account for it;
+ *   - a step loop that keeps several streams busy: cudaFree synchronises the
+ *     whole device, so an allocating bias call would stall the engine's other
+ *     work every time it released scratch;
+ *   - a long run under a per-process memory limit, where the bias must not be
+ *     able to fail for want of memory hours into the run.
+ * It runs the kernels of abp_step_plain and gives the same results, but keeps
+ * everything beyond the caller's buffers (the walker description, its atom
+ * lists, the Jacobian passed between the kernels, a counter) in one static
+ * device array of ABP_STATIC_SCRATCH_BYTES. The CUDA runtime reserves that
+ * array when it loads the library's module on a device (with lazy module
+ * loading: at the first use of one of the library's kernels or symbols there,
+ * which may be this call's first invocation) and holds it until the process
+ * exits; the call itself makes no cudaMalloc, cudaFree or other allocating
+ * call.
  *
  *   device, cuda_stream   the GPU and the cudaStream_t to run on (the caller's
  *                         current device is restored on return)
@@ -479,19 +490,20 @@ double abp_server_now(void);
  *                         {cV, cdV0, cdV1, cdV2}, c = compensation; FP64:
  *                         double {V, dV0} or {V, dV0, dV1, dV2}); zero it
  *                         before the first step (V_b = 0); updated in place
- *   walker_desc           the walker (as for abp_walker_create; host arrays)
+ *   walker_desc           the walker (as for abp_walker_create; host arrays);
+ *                         COM distance, dihedral and coordination-number CVs
+ *                         (an RMSD CV returns ABP_ERR_UNSUPPORTED)
  *   coords_dev, forces_dev  the walker's atoms and its force records
  *   mode, step            as for abp_step_plain
  *
- * The first call on a device looks up the array's device address with that
- * device current; make that first call before any stream capture begins.
  * Every call shares the array and leaves the last call's contents in it; the
- * call rewrites what the kernels read before they run, so calls must not
- * overlap on the GPU: two calls in flight at once (other streams, other host
- * threads) race on the array. The call is asynchronous on cuda_stream; it
- * reports no non-finite coordinates (forces are zeroed, nothing is
- * deposited). A walker whose description, lists and Jacobian need more than
- * ABP_STATIC_SCRATCH_BYTES is rejected with ABP_ERR_INVALID_ARG. */
+ * call copies what the kernels read into it (one cudaMemcpyAsync on
+ * cuda_stream from a host staging image that the call owns) before they run,
+ * so calls must not overlap on the GPU: two calls in flight at once (other
+ * streams, other host threads) race on the array. The call is asynchronous on
+ * cuda_stream; it reports no non-finite coordinates (forces are zeroed,
+ * nothing is deposited). A walker whose description, lists and Jacobian need
+ * more than ABP_STATIC_SCRATCH_BYTES is rejected with ABP_ERR_INVALID_ARG. */
 #define ABP_STATIC_SCRATCH_BYTES (1u << 20)
 abp_status abp_step_static(int device, void *cuda_stream, const abp_grid_desc *grid_desc, void *grid_records_dev,
                            const abp_walker_desc *walker_desc, const void *coords_dev, int coords_dtype,

@@ -26,8 +26,9 @@
  *       (returned to the owner of the atoms, SI "Minimization of
  *       Interprocess Communications").
  *
- * Conventions taken where the paper is silent (each also listed in the
- * design notes):
+ * Conventions taken where the paper is silent (the CUDA library follows
+ * the same ones, written independently; each is the plain reading of the
+ * method where the text leaves a choice open):
  *   - grid nodes: non-periodic axis xi_i = lo + i*D, D = (hi-lo)/(n-1),
  *     i = 0..n-1; periodic axis D = (hi-lo)/n with wrap-around;
  *   - hill centre index i_c = floor(u + 1/2), u = (s - lo)/D (wrapped into

@@ -1,17 +1,18 @@
 // abp_static.cu -- abp_step_static: the plain-form step of one walker for
 // callers that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc at all: a host code that runs inside
-// a CUDA graph being captured, a plugin that lives in another program's
-// memory pool with a fixed footprint, or a bias routine invoked from a
-// context whose allocator must not be touched mid-step. For them this entry
-// point runs the same three plain-form kernels (CV, deposit, interpolation
-// and force) as abp_step_plain, but every piece of state those kernels need
-// beyond the caller's own buffers (the walker's descriptor, its atom lists,
-// the CV Jacobian scratch passed between the kernels, the walker state and a
-// counter) lives in one file-scope static __device__ array of
-// ABP_STATIC_SCRATCH_BYTES. Every GPU that loads the library holds that array
-// until the process exits.
+// Some callers cannot have the bias allocate device memory inside a step: a
+// plugin whose host MD engine hands out GPU memory from its own fixed pool, a
+// step loop that a device-wide cudaFree synchronisation would stall, a long
+// run under a per-process memory limit where the bias must not fail for want
+// of memory. For them this entry point runs the same three plain-form
+// kernels (CV, deposit, interpolation and force) as abp_step_plain, but every
+// piece of state those kernels need beyond the caller's own buffers (the
+// walker's descriptor, its atom lists, the CV Jacobian scratch passed between
+// the kernels, the walker state and a counter) lives in one file-scope static
+// __device__ array of ABP_STATIC_SCRATCH_BYTES. The runtime reserves that
+// array when it loads this module on a device and holds it until the process
+// exits.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -181,6 +182,8 @@ extern "C" abp_status abp_step_static(int device, void *cuda_stream, const abp_g
       if (c.n_a < 1 || c.n_b < 1) return sfail(ABP_ERR_INVALID_ARG, "abp_step_static: CV groups must be non-empty");
     } else if (c.type == ABP_CV_DIHEDRAL) {
       if (c.n_a != 4) return sfail(ABP_ERR_INVALID_ARG, "abp_step_static: a dihedral needs 4 atoms");
+    } else if (c.type == ABP_CV_RMSD) {
+      return sfail(ABP_ERR_UNSUPPORTED, "abp_step_static: RMSD CVs are not built for this entry point");
     } else {
       return sfail(ABP_ERR_INVALID_ARG, "abp_step_static: unknown CV type");
     }

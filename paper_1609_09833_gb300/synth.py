@@ -20,8 +20,11 @@ Walker spec (a dict):
 Units: nm, kJ/mol, rad. Frames are float32 [T, total_atoms, 3]; walker w owns
 atoms offsets[w] .. offsets[w] + natoms - 1 of every frame.
 
-Workload recipes (each a seeded stand-in for the trajectories named in the
-design notes):
+Workload recipes. Each is a seeded stand-in for the MD trajectories the
+paper's runs bias (a ligand in a protein pocket, described by centre-of-mass
+distances, dihedrals, coordination numbers or RMSDs): no trajectory or
+structure data is available, so atoms are drawn from simple geometric
+templates with the same atom counts, CV kinds and grid sizes:
   * ``double_well_com``: 1 walker, two 8-atom groups in a 3 nm box,
     1D grid of 512 nodes on [-2, 2], sigma 0.05, w 1, stride 100, gamma 10.
   * ``mb64``: 64 walkers, COM distance of two 16-atom groups in [0.2, 2.0]
