@@ -393,14 +393,19 @@ abp_status abp_shared_forces(abp_ctx *ctx, abp_walker *const *walkers, int n, vo
 
 /* A request loop over many concurrent simulations (one walker each): every
  * simulation's grid and state stay on the device; callers submit one MD step
- * at a time (host coordinates in, host forces out) from any thread; a worker
- * thread packs the requests that are ready into the next launch of the fused
- * kernel on one of nstreams streams while earlier launches are still in
- * flight (continuous batching), and hands each finished request back through
- * abp_server_poll. A simulation has at most one step in flight: its later
- * requests wait, in order, for the earlier ones (each step depends on the
- * grid after the previous one). A walker's result is the same alone and in
- * any mix of requests. The server owns the context's stream while it runs. */
+ * at a time (host coordinates in, host forces out) from any thread; a
+ * launcher thread packs the requests that are ready into the next launch of
+ * the fused kernel on one of nstreams streams while earlier launches are
+ * still in flight (continuous batching), and a delivery thread hands each
+ * finished request back through abp_server_poll. A simulation's steps run
+ * in order (each depends on the
+ * grid after the previous one): a launch takes at most one request of a
+ * simulation, and when the simulation's previous request is still running
+ * in another launch, the new launch's kernel waits on the device for that
+ * one's kernel, so the host can pack the next launch meanwhile. Results
+ * come back in launch order, so one simulation's results arrive in step
+ * order. A walker's result is the same alone and in any mix of requests.
+ * The server owns the context's stream while it runs. */
 typedef struct abp_server abp_server;
 
 typedef struct {
@@ -443,8 +448,13 @@ abp_status abp_server_submit(abp_server *srv, int64_t sim, int64_t step, const f
                              float *forces_host, uint64_t tag);
 /* n requests in one call: request k is (sims[k], steps[k], tags[k]); its
  * coordinates follow those of request k-1 in coords_host (natoms records of
- * its simulation each) and its forces land at the same offset of
- * forces_host. All are queued together (under one lock), in order. */
+ * its simulation each, copied before the call returns) and its forces land
+ * at the same offset of forces_host. They are queued in order, in chunks of
+ * 2048, so that the first launches start while later chunks are copied; all
+ * carry the call's time as t_submit. Unknown simulations or negative steps
+ * are rejected before anything is queued; a simulation released by another
+ * thread during the call ends it with ABP_ERR_INVALID_ARG after the chunks
+ * before it were queued. */
 abp_status abp_server_submit_many(abp_server *srv, int n, const int64_t *sims, const int64_t *steps,
                                   const float *coords_host, float *forces_host, const uint64_t *tags);
 /* Up to cap finished requests, oldest first; waits up to wait_ms for the
@@ -453,6 +463,14 @@ abp_status abp_server_poll(abp_server *srv, abp_result *out, int cap, int *n_out
 /* Counters: requests submitted, finished, launches, and requests queued now. */
 abp_status abp_server_stats(abp_server *srv, int64_t *submitted, int64_t *finished, int64_t *launches,
                             int64_t *queued);
+/* Seconds the server's two threads have spent, since the server was
+ * created, in each phase: the launcher filling slots from the ready
+ * simulations (under the server lock) and packing and launching them (host
+ * copies into pinned memory, asynchronous copies and the kernel launch); the
+ * deliverer waiting for launched slots to finish on the GPU and delivering
+ * them (forces into the callers' buffers, results queued). Any pointer may
+ * be NULL. */
+abp_status abp_server_times(abp_server *srv, double *fill_s, double *launch_s, double *complete_s, double *wait_s);
 /* Host steady-clock seconds (the clock of abp_result). */
 double abp_server_now(void);
 

@@ -160,6 +160,8 @@ _SIGS = {
     "abp_server_submit_many": [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp],
     "abp_server_poll": [_vp, C.POINTER(Result), C.c_int, C.POINTER(C.c_int), C.c_int],
     "abp_server_stats": [_vp, _i64p, _i64p, _i64p, _i64p],
+    "abp_server_times": [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                         C.POINTER(C.c_double)],
     "abp_server_now": [],
     "abp_fp32_fma_peak": [C.c_int, _vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)],
     "abp_kernel_times": [_vp, C.POINTER(KernelTime), C.c_int, C.POINTER(C.c_int)],
@@ -456,6 +458,12 @@ def abp_server_stats(srv):
     v = [C.c_int64() for _ in range(4)]
     _check(load().abp_server_stats(srv, *[C.byref(x) for x in v]))
     return {"submitted": v[0].value, "finished": v[1].value, "launches": v[2].value, "queued": v[3].value}
+
+
+def abp_server_times(srv):
+    v = [C.c_double() for _ in range(4)]
+    _check(load().abp_server_times(srv, *[C.byref(x) for x in v]))
+    return {"fill": v[0].value, "launch": v[1].value, "complete": v[2].value, "wait": v[3].value}
 
 
 def abp_server_now() -> float:

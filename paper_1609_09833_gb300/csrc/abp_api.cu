@@ -275,6 +275,23 @@ abp_status get_table(abp_ctx *ctx, abp_walker *const *walkers, int n, bool sort_
 // tile of its grid (the rest of ~220 KB / walkers-per-SM). A windowed batch
 // defaults to one 256-thread group per CTA: its two halves run the window
 // pipeline's two stages.
+// The per-step form's shape from the batch's largest group footprint gb
+// (bytes at g threads per group, with tile budget tb): groups per CTA as
+// shared memory allows.
+abp_status step_shape(const abp_ctx *ctx, bool cn, int g, int gb, int tb, int *G, int *gpc, int *group_bytes,
+                      int *tile_budget) {
+  const int smem_max = 227 * 1024;
+  if (gb > smem_max) return fail(ABP_ERR_UNSUPPORTED, "a walker needs %d bytes of shared memory (max %d)", gb, smem_max);
+  int per = 1;
+  if (tb == 0) per = ctx->tune_gpc ? ctx->tune_gpc : (cn ? 2 : 4);
+  while (per > 1 && (per * gb > (ctx->tune_gpc ? smem_max : 100 * 1024) || per * g > 256)) --per;
+  *G = g;
+  *gpc = per;
+  *group_bytes = gb;
+  *tile_budget = tb;
+  return ABP_OK;
+}
+
 abp_status pick_shape(const abp_ctx *ctx, abp_walker *const *walkers, int n, int fp64, int nsteps, bool window,
                       int *G, int *gpc, int *group_bytes, int *tile_budget) {
   bool cn = false;
@@ -293,8 +310,7 @@ abp_status pick_shape(const abp_ctx *ctx, abp_walker *const *walkers, int n, int
     *tile_budget = 0;
     return ABP_OK;
   }
-  int g = ctx->tune_G ? ctx->tune_G : (cn ? 128 : 32);
-  const int smem_max = 227 * 1024;
+  const int g = ctx->tune_G ? ctx->tune_G : (cn ? 128 : 32);
   int fixed = group_fixed_bytes(fp64);
   int tb = 0;
   // Measured on the 64-walker workload, one warp per walker: reloading and
@@ -313,20 +329,12 @@ abp_status pick_shape(const abp_ctx *ctx, abp_walker *const *walkers, int n, int
     gb = std::max(gb, b);
     if (tb > 0 && b > run_group_bytes(walkers[i]->hd, fp64, g, 0, false)) any_tile = true;
   }
-  if (!any_tile) {
+  if (tb > 0 && !any_tile) {
     tb = 0;
     gb = 0;
     for (int i = 0; i < n; ++i) gb = std::max(gb, run_group_bytes(walkers[i]->hd, fp64, g, 0, false));
   }
-  if (gb > smem_max) return fail(ABP_ERR_UNSUPPORTED, "a walker needs %d bytes of shared memory (max %d)", gb, smem_max);
-  int per = 1;
-  if (tb == 0) per = ctx->tune_gpc ? ctx->tune_gpc : (cn ? 2 : 4);
-  while (per > 1 && (per * gb > (ctx->tune_gpc ? smem_max : 100 * 1024) || per * g > 256)) --per;
-  *G = g;
-  *gpc = per;
-  *group_bytes = gb;
-  *tile_budget = tb;
-  return ABP_OK;
+  return step_shape(ctx, cn, g, gb, tb, G, gpc, group_bytes, tile_budget);
 }
 
 }  // namespace
@@ -1629,32 +1637,114 @@ abp_status abp_sync(abp_ctx *ctx) {
 // ===================================================================== serving
 //
 // abp_server: continuous batching of single-step requests from many
-// simulations. A worker thread owns nstreams "slots" (stream, event, pinned
+// simulations. The server owns nstreams "slots" (stream, two events, pinned
 // and device buffers for coordinates, forces, offsets, per-walker steps and
-// the walker table). It fills a free slot with the front request of every
-// ready simulation (FIFO, up to max_batch), launches the fused kernel for one
-// step on the slot's stream and moves on; finished slots are harvested by
-// event query, their forces copied to the callers' buffers, and the
-// simulations made ready again if they have queued requests.
+// the walker table) and two threads:
+//   the launcher fills a free slot with the front request of every
+//   simulation that has one (FIFO, one request per simulation and slot, up
+//   to max_batch), packs it and launches the fused kernel for one step on
+//   the slot's stream. A simulation whose previous request is still on the
+//   GPU in another slot goes into the new slot too: the new slot's kernel
+//   waits on the device for that slot's kernel (an event), so the steps of
+//   one simulation run in order while the host works ahead;
+//   the deliverer takes launched slots in launch order (so one simulation's
+//   results come back in step order), waits for each, copies its forces to
+//   the callers' buffers and frees the slot.
+// Packing the next slot, the GPU and delivering the previous slot overlap.
 
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <functional>
+#include <memory>
 #include <thread>
 #include <unordered_map>
 
 namespace {
 
+// A fixed team of helper threads for the host copies of a large launch:
+// run(fn) calls fn(part, nparts) for every part, part 0 on the calling
+// thread, and returns when all parts are done.
+class CopyTeam {
+ public:
+  explicit CopyTeam(int helpers) : nparts_(helpers + 1) {
+    for (int i = 0; i < helpers; ++i) threads_.emplace_back([this, i] { loop(i + 1); });
+  }
+  ~CopyTeam() {
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      stop_ = true;
+    }
+    cv_.notify_all();
+    for (auto &t : threads_) t.join();
+  }
+  int parts() const { return nparts_; }
+  void run(const std::function<void(int, int)> &fn) {
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      fn_ = &fn;
+      left_ = nparts_ - 1;
+      ++gen_;
+    }
+    cv_.notify_all();
+    fn(0, nparts_);
+    std::unique_lock<std::mutex> lk(mu_);
+    done_.wait(lk, [&] { return left_ == 0; });
+    fn_ = nullptr;
+  }
+
+ private:
+  void loop(int part) {
+    uint64_t seen = 0;
+    for (;;) {
+      const std::function<void(int, int)> *fn;
+      {
+        std::unique_lock<std::mutex> lk(mu_);
+        cv_.wait(lk, [&] { return stop_ || gen_ != seen; });
+        if (stop_) return;
+        seen = gen_;
+        fn = fn_;
+      }
+      (*fn)(part, nparts_);
+      std::lock_guard<std::mutex> lk(mu_);
+      if (--left_ == 0) done_.notify_one();
+    }
+  }
+  const int nparts_;
+  std::vector<std::thread> threads_;
+  std::mutex mu_;
+  std::condition_variable cv_, done_;
+  const std::function<void(int, int)> *fn_ = nullptr;
+  int left_ = 0;
+  uint64_t gen_ = 0;
+  bool stop_ = false;
+};
+
+// Requests [lo, hi) of part p of np, split so that each part copies about
+// the same number of atoms (off: the requests' atom offsets, total atoms).
+void part_range(const long long *off, int n, long long total, int p, int np, int *lo, int *hi) {
+  auto first_at = [&](long long atom) { return (int)(std::lower_bound(off, off + n, atom) - off); };
+  *lo = first_at(total * p / np);
+  *hi = p + 1 == np ? n : first_at(total * (p + 1) / np);
+}
+
+constexpr long long kTeamAtoms = 16384;  // below this a launch is copied by one thread
+
 double steady_now() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
+
+struct SrvSim;
 
 struct SrvRequest {
   int64_t sim = 0, step = 0;
   uint64_t tag = 0;
   float *forces_host = nullptr;
   double t_submit = 0;
-  std::vector<float> coords;
+  std::shared_ptr<std::vector<float>> slab;  // the coordinates' storage (shared by one submit call)
+  const float *coords = nullptr;             // natoms records inside slab
+  int natoms = 0;
+  SrvSim *simp = nullptr;  // stable while the request is queued or in flight
 };
 
 struct SrvSim {
@@ -1662,12 +1752,16 @@ struct SrvSim {
   abp_walker *walker = nullptr;
   int natoms = 0;
   std::deque<SrvRequest> pending;
-  bool busy = false;
+  int inflight = 0;     // requests in slots not yet delivered
+  int last_slot = -1;   // the slot holding its newest request in flight
+  bool in_ready = false;
+  int gb_g[2] = {0, 0}, gb[2] = {0, 0};  // group bytes cached for two group sizes
 };
 
 struct SrvSlot {
   cudaStream_t stream = nullptr;
-  cudaEvent_t done = nullptr;
+  cudaEvent_t kdone = nullptr;  // after the slot's kernel
+  cudaEvent_t done = nullptr;   // after the forces are back in pinned memory
   float *h_in = nullptr, *h_out = nullptr;
   long long *h_off = nullptr, *h_step = nullptr;
   TableEntry *h_table = nullptr;
@@ -1675,6 +1769,10 @@ struct SrvSlot {
   long long *d_off = nullptr, *d_step = nullptr;
   TableEntry *d_table = nullptr;
   std::vector<SrvRequest> reqs;
+  std::vector<abp_walker *> ws;
+  std::vector<int> deps;  // slots whose kernels this slot's kernel waits for
+  bool cn = false;        // a walker with a coordination number is in the slot
+  int G = 0, gb = 0;      // group size and the largest group footprint at G
   bool busy = false;
   int status = ABP_OK;
 };
@@ -1685,15 +1783,24 @@ struct abp_server {
   abp_ctx *ctx = nullptr;
   int max_batch = 4096, max_atoms = 1024, nstreams = 2;
   std::mutex mu;
-  std::condition_variable cv_work, cv_done;
+  std::condition_variable cv_work, cv_done, cv_launched;
   std::unordered_map<int64_t, SrvSim> sims;
   int64_t next_sim = 0;
-  std::deque<int64_t> ready;
+  std::deque<int64_t> ready;  // simulations with pending requests (each once)
   std::deque<abp_result> results;
   std::vector<SrvSlot> slots;
-  std::thread worker;
-  bool stop = false;
+  std::deque<int> launched;  // slots in flight, in launch order
+  std::thread launcher, deliverer;
+  bool stop = false, stop_delivery = false;
   int64_t submitted = 0, finished = 0, launches = 0, queued = 0;
+  // thread seconds by phase (each written under mu by its thread)
+  double t_fill = 0, t_launch = 0, t_complete = 0, t_wait = 0;
+  // coordinate slabs of delivered requests, kept for reuse (their pages
+  // stay mapped: a fresh multi-megabyte copy would fault every page in)
+  std::mutex pool_mu;
+  std::vector<std::vector<float> *> slab_pool;
+  // helper teams for the launcher's packing and the deliverer's unpacking
+  std::unique_ptr<CopyTeam> pack_team, unpack_team;
 };
 
 namespace {
@@ -1712,30 +1819,82 @@ void srv_free_slots(abp_server *s) {
     cudaFree(sl.d_step);
     cudaFree(sl.d_table);
     if (sl.done) cudaEventDestroy(sl.done);
+    if (sl.kdone) cudaEventDestroy(sl.kdone);
     if (sl.stream) cudaStreamDestroy(sl.stream);
   }
   s->slots.clear();
 }
 
-// Launch the requests now in the slot (called without the server lock).
+// A copy of n floats from src in a slab from the pool (the smallest that
+// holds them, else a new one); the slab returns to the pool when the last
+// request using it is gone. Lock order: mu, then pool_mu.
+std::shared_ptr<std::vector<float>> srv_slab(abp_server *s, const float *src, size_t n) {
+  std::vector<float> *v = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(s->pool_mu);
+    size_t best = s->slab_pool.size();
+    for (size_t i = 0; i < s->slab_pool.size(); ++i)
+      if (s->slab_pool[i]->capacity() >= n &&
+          (best == s->slab_pool.size() || s->slab_pool[i]->capacity() < s->slab_pool[best]->capacity()))
+        best = i;
+    if (best < s->slab_pool.size()) {
+      v = s->slab_pool[best];
+      s->slab_pool[best] = s->slab_pool.back();
+      s->slab_pool.pop_back();
+    }
+  }
+  if (!v) v = new std::vector<float>();
+  v->assign(src, src + n);
+  return std::shared_ptr<std::vector<float>>(v, [s](std::vector<float> *p) {
+    // small slabs come from the heap's free lists without faults: only the
+    // large ones (one submit_many chunk) are kept
+    if (p->capacity() * sizeof(float) >= (256u << 10)) {
+      std::lock_guard<std::mutex> lk(s->pool_mu);
+      if (s->slab_pool.size() < 64) {
+        s->slab_pool.push_back(p);
+        return;
+      }
+    }
+    delete p;
+  });
+}
+
+// A simulation's group footprint at g threads per group (cached: the walker
+// does not change while it is admitted).
+int srv_group_bytes(SrvSim &sm, int g) {
+  for (int i = 0; i < 2; ++i)
+    if (sm.gb_g[i] == g) return sm.gb[i];
+  const int b = run_group_bytes(sm.walker->hd, 0, g, 0, false);
+  const int i = sm.gb_g[0] ? 1 : 0;
+  sm.gb_g[i] = g;
+  sm.gb[i] = b;
+  return b;
+}
+
+// Pack and launch the requests now in the slot (launcher thread, without the
+// server lock; the slot's walkers and shape were taken under it).
 int srv_launch(abp_server *s, SrvSlot &sl) {
   const int n = (int)sl.reqs.size();
-  std::vector<abp_walker *> ws(n);
   long long off = 0;
-  {
-    std::lock_guard<std::mutex> lk(s->mu);
-    for (int i = 0; i < n; ++i) ws[i] = s->sims[sl.reqs[i].sim].walker;
-  }
   for (int i = 0; i < n; ++i) {
     const SrvRequest &r = sl.reqs[i];
     sl.h_off[i] = off;
     sl.h_step[i] = r.step;
-    sl.h_table[i] = TableEntry{ws[i]->dd, i, 0};
-    std::memcpy(sl.h_in + off * 4, r.coords.data(), r.coords.size() * sizeof(float));
-    off += ws[i]->hd.natoms;
+    sl.h_table[i] = TableEntry{sl.ws[i]->dd, i, 0};
+    off += r.natoms;
   }
+  auto pack = [&](int p, int np) {
+    int lo, hi;
+    part_range(sl.h_off, n, off, p, np, &lo, &hi);
+    for (int i = lo; i < hi; ++i)
+      std::memcpy(sl.h_in + sl.h_off[i] * 4, sl.reqs[i].coords, (size_t)sl.reqs[i].natoms * 16);
+  };
+  if (off >= kTeamAtoms && s->pack_team)
+    s->pack_team->run(pack);
+  else
+    pack(0, 1);
   RunArgs a{};
-  int st = pick_shape(s->ctx, ws.data(), n, 0, 1, false, &a.G, &a.groups_per_cta, &a.group_bytes, &a.tile_budget);
+  int st = step_shape(s->ctx, sl.cn, sl.G, sl.gb, 0, &a.G, &a.groups_per_cta, &a.group_bytes, &a.tile_budget);
   if (st) return st;
   cudaStream_t stream = sl.stream;
   if (cudaMemcpyAsync(sl.d_in, sl.h_in, (size_t)off * 16, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
@@ -1744,6 +1903,10 @@ int srv_launch(abp_server *s, SrvSlot &sl) {
       cudaMemcpyAsync(sl.d_table, sl.h_table, (size_t)n * sizeof(TableEntry), cudaMemcpyHostToDevice, stream) !=
           cudaSuccess)
     return ABP_ERR_CUDA;
+  // the previous step of a simulation in this slot runs in another slot:
+  // its kernel (grid deposit, walker state) must finish first
+  for (int d : sl.deps)
+    if (cudaStreamWaitEvent(stream, s->slots[d].kdone, 0) != cudaSuccess) return ABP_ERR_CUDA;
   a.table = sl.d_table;
   a.nw = n;
   a.coords = sl.d_in;
@@ -1759,103 +1922,167 @@ int srv_launch(abp_server *s, SrvSlot &sl) {
   a.log = s->ctx->log;
   a.ctr = s->ctx->ctr;
   if (launch_run(a, 0, stream) != cudaSuccess) return ABP_ERR_CUDA;
+  if (cudaEventRecord(sl.kdone, stream) != cudaSuccess) return ABP_ERR_CUDA;
   if (cudaMemcpyAsync(sl.h_out, sl.d_out, (size_t)off * 16, cudaMemcpyDeviceToHost, stream) != cudaSuccess)
     return ABP_ERR_CUDA;
   if (cudaEventRecord(sl.done, stream) != cudaSuccess) return ABP_ERR_CUDA;
   return ABP_OK;
 }
 
-// Deliver a finished slot's requests (called without the server lock).
+// Deliver a finished slot's requests (deliverer thread, without the lock).
 void srv_complete(abp_server *s, SrvSlot &sl) {
   const int n = (int)sl.reqs.size();
-  const double t = steady_now();
-  std::vector<abp_result> res(n);
-  for (int i = 0; i < n; ++i) {
-    SrvRequest &r = sl.reqs[i];
-    if (sl.status == ABP_OK)
-      std::memcpy(r.forces_host, sl.h_out + sl.h_off[i] * 4, r.coords.size() * sizeof(float));
-    res[i] = abp_result{r.sim, r.step, r.tag, r.t_submit, t, sl.status, n};
+  if (sl.status == ABP_OK && n > 0) {
+    const long long total = sl.h_off[n - 1] + sl.reqs[n - 1].natoms;
+    auto unpack = [&](int p, int np) {
+      int lo, hi;
+      part_range(sl.h_off, n, total, p, np, &lo, &hi);
+      for (int i = lo; i < hi; ++i)
+        std::memcpy(sl.reqs[i].forces_host, sl.h_out + sl.h_off[i] * 4, (size_t)sl.reqs[i].natoms * 16);
+    };
+    if (total >= kTeamAtoms && s->unpack_team)
+      s->unpack_team->run(unpack);
+    else
+      unpack(0, 1);
   }
+  const double t = steady_now();  // the forces are in the callers' buffers
   {
     std::lock_guard<std::mutex> lk(s->mu);
     for (int i = 0; i < n; ++i) {
-      s->results.push_back(res[i]);
-      auto it = s->sims.find(sl.reqs[i].sim);
-      if (it != s->sims.end()) {
-        it->second.busy = false;
-        if (!it->second.pending.empty()) s->ready.push_back(sl.reqs[i].sim);
-      }
+      const SrvRequest &r = sl.reqs[i];
+      s->results.push_back(abp_result{r.sim, r.step, r.tag, r.t_submit, t, sl.status, n});
+      --r.simp->inflight;
     }
     s->finished += n;
     sl.reqs.clear();
+    sl.ws.clear();
+    sl.deps.clear();
     sl.busy = false;
   }
   s->cv_done.notify_all();
+  s->cv_work.notify_one();  // a slot is free
 }
 
-void srv_worker(abp_server *s) {
-  cudaSetDevice(s->ctx->device);
-  for (;;) {
-    // harvest
-    bool any_busy = false;
-    for (auto &sl : s->slots) {
-      if (!sl.busy) continue;
-      cudaError_t q = cudaEventQuery(sl.done);
-      if (q == cudaSuccess || (q != cudaErrorNotReady && (sl.status = ABP_ERR_CUDA, true))) {
-        if (q != cudaSuccess) cudaGetLastError();
-        srv_complete(s, sl);
-      } else {
-        any_busy = true;
-      }
-    }
-    // launch
-    SrvSlot *free_slot = nullptr;
-    {
-      std::unique_lock<std::mutex> lk(s->mu);
-      if (s->stop && !any_busy) break;
-      for (auto &sl : s->slots)
-        if (!sl.busy) {
-          free_slot = &sl;
-          break;
-        }
-      if (free_slot && !s->ready.empty() && !s->stop) {
-        int atoms = 0;
-        while (!s->ready.empty() && (int)free_slot->reqs.size() < s->max_batch) {
-          int64_t id = s->ready.front();
-          auto it = s->sims.find(id);
-          if (it == s->sims.end() || it->second.busy || it->second.pending.empty()) {
-            s->ready.pop_front();
-            continue;
-          }
-          if (atoms + it->second.natoms > s->max_batch * s->max_atoms) break;
-          s->ready.pop_front();
-          it->second.busy = true;
-          atoms += it->second.natoms;
-          free_slot->reqs.push_back(std::move(it->second.pending.front()));
-          it->second.pending.pop_front();
-          --s->queued;
-        }
-        free_slot->busy = !free_slot->reqs.empty();
-      } else {
-        free_slot = nullptr;
-        if (!any_busy) {
-          s->cv_work.wait_for(lk, std::chrono::milliseconds(2));
-          continue;
-        }
-      }
-    }
-    if (free_slot && free_slot->busy) {
-      free_slot->status = srv_launch(s, *free_slot);
-      if (free_slot->status != ABP_OK) {
-        cudaGetLastError();
-        srv_complete(s, *free_slot);
-      } else {
-        std::lock_guard<std::mutex> lk(s->mu);
-        ++s->launches;
-      }
+// Fill slot fi from the ready simulations (server lock held): one request
+// per simulation; simulations with more requests stay ready for the next
+// slot.
+void srv_fill(abp_server *s, int fi) {
+  SrvSlot &sl = s->slots[fi];
+  const abp_ctx *ctx = s->ctx;
+  int atoms = 0;
+  std::vector<SrvSim *> again;
+  sl.cn = false;
+  while (!s->ready.empty() && (int)sl.reqs.size() < s->max_batch) {
+    auto it = s->sims.find(s->ready.front());
+    if (it == s->sims.end()) {
+      s->ready.pop_front();
       continue;
     }
-    if (any_busy) std::this_thread::sleep_for(std::chrono::microseconds(5));
+    SrvSim &sm = it->second;
+    if (sm.pending.empty()) {
+      s->ready.pop_front();
+      sm.in_ready = false;
+      continue;
+    }
+    if (atoms + sm.natoms > s->max_batch * s->max_atoms) break;
+    s->ready.pop_front();
+    sm.in_ready = false;
+    if (sm.inflight > 0) sl.deps.push_back(sm.last_slot);
+    ++sm.inflight;
+    sm.last_slot = fi;
+    atoms += sm.natoms;
+    sl.cn = sl.cn || sm.walker->has_cn;
+    sl.reqs.push_back(std::move(sm.pending.front()));
+    sl.ws.push_back(sm.walker);
+    sm.pending.pop_front();
+    --s->queued;
+    if (!sm.pending.empty()) again.push_back(&sm);
+  }
+  for (SrvSim *sm : again) {
+    s->ready.push_back(sm->pending.front().sim);
+    sm->in_ready = true;
+  }
+  std::sort(sl.deps.begin(), sl.deps.end());
+  sl.deps.erase(std::unique(sl.deps.begin(), sl.deps.end()), sl.deps.end());
+  // the launch shape: the per-step form's group size for this mix, and the
+  // largest footprint at that size
+  sl.G = ctx->tune_G ? ctx->tune_G : (sl.cn ? 128 : 32);
+  sl.gb = 0;
+  for (const SrvRequest &r : sl.reqs) sl.gb = std::max(sl.gb, srv_group_bytes(*r.simp, sl.G));
+  sl.busy = !sl.reqs.empty();
+}
+
+void srv_launcher(abp_server *s) {
+  cudaSetDevice(s->ctx->device);
+  double t_fill = 0, t_launch = 0;
+  for (;;) {
+    int fi = -1;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->t_fill = t_fill;
+      s->t_launch = t_launch;
+      auto free_slot = [&] {
+        for (int i = 0; i < (int)s->slots.size(); ++i)
+          if (!s->slots[i].busy) return i;
+        return -1;
+      };
+      s->cv_work.wait(lk, [&] { return s->stop || (!s->ready.empty() && free_slot() >= 0); });
+      if (s->stop) break;
+      const double t0 = steady_now();
+      fi = free_slot();
+      srv_fill(s, fi);
+      t_fill += steady_now() - t0;
+      if (!s->slots[fi].busy) continue;
+    }
+    const double t1 = steady_now();
+    SrvSlot &sl = s->slots[fi];
+    sl.status = srv_launch(s, sl);
+    if (sl.status != ABP_OK) {
+      // the slot still goes to the deliverer in launch order; record its
+      // events so that it and any slot queued after it on the device end
+      cudaGetLastError();
+      cudaEventRecord(sl.kdone, sl.stream);
+      cudaEventRecord(sl.done, sl.stream);
+      cudaGetLastError();
+    }
+    t_launch += steady_now() - t1;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->launched.push_back(fi);
+      ++s->launches;
+    }
+    s->cv_launched.notify_one();
+  }
+}
+
+void srv_deliverer(abp_server *s) {
+  cudaSetDevice(s->ctx->device);
+  double t_complete = 0, t_wait = 0;
+  for (;;) {
+    int fi;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->t_complete = t_complete;
+      s->t_wait = t_wait;
+      s->cv_launched.wait(lk, [&] { return !s->launched.empty() || s->stop_delivery; });
+      if (s->launched.empty()) break;
+      fi = s->launched.front();
+    }
+    SrvSlot &sl = s->slots[fi];
+    const double t0 = steady_now();
+    cudaError_t q = cudaEventSynchronize(sl.done);
+    const double t1 = steady_now();
+    t_wait += t1 - t0;
+    if (q != cudaSuccess) {
+      cudaGetLastError();
+      sl.status = ABP_ERR_CUDA;
+    }
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->launched.pop_front();
+    }
+    srv_complete(s, sl);
+    t_complete += steady_now() - t1;
   }
 }
 
@@ -1891,6 +2118,7 @@ abp_status abp_server_create(abp_ctx *ctx, const abp_server_desc *desc, abp_serv
   for (auto &sl : s->slots) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.kdone, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaHostAlloc(&sl.h_in, rec, cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaHostAlloc(&sl.h_out, rec, cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaHostAlloc(&sl.h_off, (size_t)s->max_batch * 8, cudaHostAllocDefault);
@@ -1908,7 +2136,14 @@ abp_status abp_server_create(abp_ctx *ctx, const abp_server_desc *desc, abp_serv
     delete s;
     return fail(ABP_ERR_OOM, "server buffers: %s", cudaGetErrorString(e));
   }
-  s->worker = std::thread(srv_worker, s);
+  // two helpers each for packing and unpacking where the host has the cores
+  const unsigned hw = std::thread::hardware_concurrency();
+  if (hw >= 8) {
+    s->pack_team.reset(new CopyTeam(2));
+    s->unpack_team.reset(new CopyTeam(2));
+  }
+  s->launcher = std::thread(srv_launcher, s);
+  s->deliverer = std::thread(srv_deliverer, s);
   *out = s;
   return ABP_OK;
 }
@@ -1920,13 +2155,22 @@ void abp_server_destroy(abp_server *s) {
     s->stop = true;
   }
   s->cv_work.notify_all();
-  if (s->worker.joinable()) s->worker.join();
+  if (s->launcher.joinable()) s->launcher.join();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop_delivery = true;  // the deliverer finishes the launched slots first
+  }
+  s->cv_launched.notify_all();
+  if (s->deliverer.joinable()) s->deliverer.join();
   set_device(s->ctx);
   srv_free_slots(s);
   for (auto &kv : s->sims) {
     abp_walker_destroy(kv.second.walker);
     abp_grid_destroy(kv.second.grid);
   }
+  s->sims.clear();  // queued requests return their slabs to the pool
+  for (std::vector<float> *p : s->slab_pool) delete p;
+  s->slab_pool.clear();
   delete s;
 }
 
@@ -1969,7 +2213,7 @@ abp_status abp_server_bias_readout(abp_server *s, int64_t sim, void *dst, int ds
     if (it == s->sims.end()) return fail(ABP_ERR_INVALID_ARG, "unknown simulation %lld", (long long)sim);
     if (!s->cv_done.wait_for(lk, std::chrono::seconds(60), [&] {
           auto jt = s->sims.find(sim);
-          return jt == s->sims.end() || (!jt->second.busy && jt->second.pending.empty());
+          return jt == s->sims.end() || (jt->second.inflight == 0 && jt->second.pending.empty());
         }))
       return fail(ABP_ERR_TIMEOUT, "simulation %lld still has requests after 60 s", (long long)sim);
     it = s->sims.find(sim);
@@ -1988,7 +2232,7 @@ abp_status abp_server_release(abp_server *s, int64_t sim) {
     if (it == s->sims.end()) return fail(ABP_ERR_INVALID_ARG, "unknown simulation %lld", (long long)sim);
     if (!s->cv_done.wait_for(lk, std::chrono::seconds(60), [&] {
           auto jt = s->sims.find(sim);
-          return jt == s->sims.end() || (!jt->second.busy && jt->second.pending.empty());
+          return jt == s->sims.end() || (jt->second.inflight == 0 && jt->second.pending.empty());
         }))
       return fail(ABP_ERR_TIMEOUT, "simulation %lld still has requests after 60 s", (long long)sim);
     it = s->sims.find(sim);
@@ -2013,11 +2257,17 @@ abp_status abp_server_submit(abp_server *s, int64_t sim, int64_t step, const flo
     std::lock_guard<std::mutex> lk(s->mu);
     auto it = s->sims.find(sim);
     if (it == s->sims.end()) return fail(ABP_ERR_INVALID_ARG, "unknown simulation %lld", (long long)sim);
-    r.coords.assign(coords_host, coords_host + (size_t)it->second.natoms * 4);
+    SrvSim &sm = it->second;
+    r.natoms = sm.natoms;
+    r.simp = &sm;
+    r.slab = std::make_shared<std::vector<float>>(coords_host, coords_host + (size_t)sm.natoms * 4);
+    r.coords = r.slab->data();
     r.t_submit = steady_now();
-    bool was_idle = !it->second.busy && it->second.pending.empty();
-    it->second.pending.push_back(std::move(r));
-    if (was_idle) s->ready.push_back(sim);
+    sm.pending.push_back(std::move(r));
+    if (!sm.in_ready) {
+      s->ready.push_back(sim);
+      sm.in_ready = true;
+    }
     ++s->submitted;
     ++s->queued;
   }
@@ -2029,33 +2279,61 @@ abp_status abp_server_submit_many(abp_server *s, int n, const int64_t *sims, con
                                   const float *coords_host, float *forces_host, const uint64_t *tags) {
   if (!s || n < 0 || (n > 0 && (!sims || !steps || !coords_host || !forces_host)))
     return fail(ABP_ERR_INVALID_ARG, "NULL argument");
+  const double t = steady_now();
+  std::vector<int> nat(n);
   {
     std::lock_guard<std::mutex> lk(s->mu);
-    size_t off = 0;
     for (int k = 0; k < n; ++k) {
       auto it = s->sims.find(sims[k]);
       if (it == s->sims.end()) return fail(ABP_ERR_INVALID_ARG, "unknown simulation %lld", (long long)sims[k]);
       if (steps[k] < 0) return fail(ABP_ERR_INVALID_ARG, "step must be >= 0");
+      nat[k] = it->second.natoms;
     }
-    const double t = steady_now();
-    for (int k = 0; k < n; ++k) {
-      SrvSim &sm = s->sims[sims[k]];
-      SrvRequest r;
+  }
+  // queued in chunks, each copied outside the lock, so that the launcher
+  // starts on the first chunk while the later ones are copied
+  constexpr int kChunk = 2048;
+  size_t off = 0;
+  for (int k0 = 0; k0 < n; k0 += kChunk) {
+    const int k1 = std::min(n, k0 + kChunk);
+    size_t total = 0;
+    for (int k = k0; k < k1; ++k) total += (size_t)nat[k];
+    auto slab = srv_slab(s, coords_host + off * 4, total * 4);
+    std::vector<SrvRequest> reqs(k1 - k0);
+    size_t o = 0;
+    for (int k = k0; k < k1; ++k) {
+      SrvRequest &r = reqs[k - k0];
       r.sim = sims[k];
       r.step = steps[k];
       r.tag = tags ? tags[k] : 0;
-      r.forces_host = forces_host + off * 4;
-      r.coords.assign(coords_host + off * 4, coords_host + (off + sm.natoms) * 4);
+      r.forces_host = forces_host + (off + o) * 4;
+      r.natoms = nat[k];
+      r.slab = slab;
+      r.coords = slab->data() + o * 4;
       r.t_submit = t;
-      off += sm.natoms;
-      bool was_idle = !sm.busy && sm.pending.empty();
-      sm.pending.push_back(std::move(r));
-      if (was_idle) s->ready.push_back(sims[k]);
+      o += (size_t)nat[k];
     }
-    s->submitted += n;
-    s->queued += n;
+    off += total;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      for (int k = k0; k < k1; ++k)
+        if (s->sims.find(sims[k]) == s->sims.end())
+          return fail(ABP_ERR_INVALID_ARG, "simulation %lld was released during the call", (long long)sims[k]);
+      for (int k = k0; k < k1; ++k) {
+        SrvSim &sm = s->sims[sims[k]];
+        SrvRequest &r = reqs[k - k0];
+        r.simp = &sm;
+        sm.pending.push_back(std::move(r));
+        if (!sm.in_ready) {
+          s->ready.push_back(sims[k]);
+          sm.in_ready = true;
+        }
+      }
+      s->submitted += k1 - k0;
+      s->queued += k1 - k0;
+    }
+    s->cv_work.notify_one();
   }
-  s->cv_work.notify_one();
   return ABP_OK;
 }
 
@@ -2070,6 +2348,16 @@ abp_status abp_server_poll(abp_server *s, abp_result *out, int cap, int *n_out, 
     s->results.pop_front();
   }
   *n_out = n;
+  return ABP_OK;
+}
+
+abp_status abp_server_times(abp_server *s, double *fill_s, double *launch_s, double *complete_s, double *wait_s) {
+  if (!s) return fail(ABP_ERR_INVALID_ARG, "NULL argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (fill_s) *fill_s = s->t_fill;
+  if (launch_s) *launch_s = s->t_launch;
+  if (complete_s) *complete_s = s->t_complete;
+  if (wait_s) *wait_s = s->t_wait;
   return ABP_OK;
 }
 

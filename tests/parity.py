@@ -35,6 +35,9 @@ FP64. Where the two indices differ, the oracle's u must lie within
 the deposit is counted as a tie and that walker is compared only on what
 does not depend on the choice.
 """
+import json
+import os
+
 import numpy as np
 
 TOL_V = 1e-5
@@ -138,3 +141,16 @@ def check_forces_per_step(F, ref, w, sl, d, tol=TOL_F, unit=U32):
     assert ratio.max() <= 1.0, (w, int(t), int(i), float(err[t, i]), float(scale[t, 0]), float(allow[t, i]))
     rel = (err.max(axis=-1) / np.maximum(scale[:, 0], 1e-300))
     return float(rel.max()), float(ratio.max()), int(np.sum(rel > tol))
+
+
+def record_errors(config, test, worst):
+    """Append one test's worst errors to the JSON-lines file named by the
+    ABP_ERROR_TABLE environment variable (nothing when it is unset): the
+    per-configuration error table is assembled from these records."""
+    path = os.environ.get("ABP_ERROR_TABLE")
+    if not path:
+        return
+    row = {"config": config, "test": test}
+    row.update({k: (float(v) if isinstance(v, (float, np.floating)) else v) for k, v in worst.items()})
+    with open(path, "a") as f:
+        f.write(json.dumps(row) + "\n")

@@ -173,6 +173,8 @@ def test_closed_loop_steps_match_the_oracle_fp32_mueller_brown(abp, ctx):
     worst = check_run(abp, ctx, specs, walkers, frames[:T], 0, F, ref)
     worst["move"] = check_moves(specs, md, streams, frames, X, ref)
     print("worst", worst)
+    P.record_errors("64 walkers, 2 CVs (closed loop, Mueller-Brown)",
+                    "test_closed_loop_steps_match_the_oracle_fp32_mueller_brown", worst)
     # the walkers did move through the potential: the CVs changed
     assert np.ptp(ref["s"][:, :, 0]) > 0.01 and np.ptp(ref["s"][:, :, 1]) > 0.05
 
@@ -193,10 +195,22 @@ def test_closed_loop_steps_match_the_oracle_fp64_double_well(abp, ctx):
     log = abp.abp_deposit_log_readout(ctx.handle, 1 << 16)
     ids = {w.id: i for i, w in enumerate(walkers)}
     assert not P.compare_deposits(specs, log, ref["deposits"], ids, sb=ref["sb"], unit=P.U64)
+    worst = {"V": 0.0, "dV": 0.0, "F": 0.0, "F_step": 0.0, "F_allow": 0.0, "floor_steps": 0}
     for i, w in enumerate(walkers):
-        assert np.all(P.rel_field_err(ctx.bias(w), ref["fields"][i]) < 1e-10)
-        P.check_forces_per_step(F, ref, i, slice(16 * i, 16 * i + 16), 1, tol=1e-9, unit=P.U64)
-    print("worst move", check_moves(specs, md, streams, frames, X, ref, unit=P.U64, tol_f=1e-9))
+        e = P.rel_field_err(ctx.bias(w), ref["fields"][i])
+        assert np.all(e < 1e-10)
+        sl = slice(16 * i, 16 * i + 16)
+        rel, ratio, nfloor = P.check_forces_per_step(F, ref, i, sl, 1, tol=1e-9, unit=P.U64)
+        worst["V"] = max(worst["V"], e[0])
+        worst["dV"] = max(worst["dV"], e[1:].max())
+        worst["F"] = max(worst["F"], P.force_err(F[:, sl], ref["F"][:, sl]))
+        worst["F_step"] = max(worst["F_step"], rel)
+        worst["F_allow"] = max(worst["F_allow"], ratio)
+        worst["floor_steps"] += nfloor
+    worst["move"] = check_moves(specs, md, streams, frames, X, ref, unit=P.U64, tol_f=1e-9)
+    print("worst", worst)
+    P.record_errors("1 walker FP64, double well (closed loop)",
+                    "test_closed_loop_steps_match_the_oracle_fp64_double_well", worst)
 
 
 def test_closed_loop_phased_form_on_a_shared_grid(abp, ctx):
@@ -218,6 +232,8 @@ def test_closed_loop_phased_form_on_a_shared_grid(abp, ctx):
     worst = check_run(abp, ctx, specs, walkers, frames[:T], 0, F, ref)
     worst["move"] = check_moves(specs, md, streams, frames, X, ref)
     print("worst", worst)
+    P.record_errors("shared grid, phased form (closed loop, 4 walkers on 40^3)",
+                    "test_closed_loop_phased_form_on_a_shared_grid", worst)
 
 
 # ---------------------------------------------------------------- the GPU's own closed loop

@@ -73,14 +73,15 @@ def check_run(abp, ctx, specs, walkers, frames, step0, Fg, ref, skip=(), unit=P.
     assert len(ties) <= max(1, len(walkers) // 50), ties
     skip = set(skip) | ties
     off = synth.offsets_of(specs)
-    worst = {"V": 0.0, "F": 0.0, "F_step": 0.0, "F_allow": 0.0, "floor_steps": 0}
+    worst = {"V": 0.0, "dV": 0.0, "F": 0.0, "F_step": 0.0, "F_allow": 0.0, "floor_steps": 0}
     for i, (w, sp) in enumerate(zip(walkers, specs)):
         if i in skip:
             continue
         g = ctx.bias(w)
         e = P.rel_field_err(g, ref["fields"][i])
         assert np.all(e < P.TOL_V), (i, e)
-        worst["V"] = max(worst["V"], float(e.max()))
+        worst["V"] = max(worst["V"], float(e[0]))
+        worst["dV"] = max(worst["dV"], float(e[1:].max()))
         sl = slice(off[i], off[i] + sp["natoms"])
         fe = P.force_err(Fg[:, sl], ref["F"][:, sl])
         assert np.all(fe < P.TOL_F), (i, fe.max())
@@ -137,6 +138,7 @@ def test_replay_parity_two_cv_walkers(abp, ctx):
     _, ref = oracle_replay(specs, frames, 0)
     worst = check_run(abp, ctx, specs, walkers, frames, 0, Fg, ref)
     print("worst errors", worst)
+    P.record_errors("64 walkers, 2 CVs (open-loop frames)", "test_replay_parity_two_cv_walkers", worst)
     # the dihedral did wrap and the deposits did land on both sides of the seam
     assert np.any(np.abs(np.diff(ref["s"][:, :, 1], axis=0)) > math.pi)
 
@@ -330,6 +332,8 @@ def test_uneven_batch_full_size_autotuned_launch(abp, ctx):
     _, ref = oracle_replay(specs, frames, 0)
     worst = check_run(abp, ctx, specs, walkers, frames, 0, Fg, ref)
     print("launch shape", tuned, "worst errors", worst)
+    P.record_errors("uneven 1000 walkers (250 at full size, autotuned launch)",
+                    "test_uneven_batch_full_size_autotuned_launch", worst)
 
 
 # ---------------------------------------------------------------- FP64 end to end
@@ -348,9 +352,14 @@ def test_fp64_single_walker(abp, ctx):
     Fg = gpu_replay(abp, ctx, walkers, frames, 0, dtype=np.float64)
     _, ref = oracle_replay([spec], frames, 0)
     g = ctx.bias(walkers[0])
-    assert np.all(P.rel_field_err(g, ref["fields"][0]) < 1e-10)
-    assert np.all(P.force_err(Fg, ref["F"]) < 1e-9)
-    print("per step", P.check_forces_per_step(Fg, ref, 0, slice(0, 16), 1, tol=1e-9, unit=P.U64))
+    e = P.rel_field_err(g, ref["fields"][0])
+    assert np.all(e < 1e-10)
+    fe = P.force_err(Fg, ref["F"])
+    assert np.all(fe < 1e-9)
+    rel, ratio, nfloor = P.check_forces_per_step(Fg, ref, 0, slice(0, 16), 1, tol=1e-9, unit=P.U64)
+    print("per step", rel, ratio, nfloor)
+    P.record_errors("1 walker FP64, double well (open-loop frames)", "test_fp64_single_walker",
+                    {"V": e[0], "dV": e[1:].max(), "F": fe, "F_step": rel, "F_allow": ratio, "floor_steps": nfloor})
     log = abp.abp_deposit_log_readout(ctx.handle, 4096)
     np.testing.assert_array_equal(log["ic"][:, 0], ref["deposits"]["ic"][:, 0])
     np.testing.assert_allclose(log["height"], ref["deposits"]["height"], rtol=1e-12)

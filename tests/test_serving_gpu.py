@@ -97,6 +97,60 @@ def test_results_alone_and_in_the_mix(abp):
         ctx.close()
 
 
+def test_backlog_pipelines_across_slots_in_order(abp):
+    """Several steps of each simulation queued at once (one submit_many call):
+    consecutive steps of a simulation run in different launches on different
+    streams, ordered on the device, and give the same bits as the same steps
+    submitted one at a time, waiting for each result; the results of a
+    simulation come back in step order."""
+    specs = synth.serve_specs(seed=9, nsim=24, side=(64, 192), stride=(2, 4))
+    tmpl = synth.serve_templates(9, specs)
+    T = 10
+    coords = [_records(_frames(t, 300 + i, T)) for i, t in enumerate(tmpl)]
+    outs = []
+    for nstreams, backlog in ((2, False), (4, True)):
+        ctx = abp.Context(0)
+        srv = abp.abp_server_create(ctx.handle, max_batch=64, max_atoms=256, nstreams=nstreams)
+        try:
+            keep, sims = [], []
+            for sp in specs:
+                desc, k = abp.walker_desc(sp)
+                keep.append(k)
+                sims.append(abp.abp_server_admit(srv, abp.grid_desc(sp["grid"]), desc))
+            if backlog:
+                order = [(i, t) for t in range(T) for i in range(len(specs))]
+                packed = np.ascontiguousarray(np.concatenate([coords[i][t] for i, t in order]))
+                out = np.zeros_like(packed)
+                abp.abp_server_submit_many(srv, [sims[i] for i, _ in order], [t for _, t in order], packed, out)
+                got, deadline = [], time.time() + 60
+                while len(got) < len(order) and time.time() < deadline:
+                    got += abp.abp_server_poll(srv, 4096, wait_ms=50)
+                assert len(got) == len(order) and all(r.status == 0 for r in got)
+                for i in range(len(specs)):
+                    seq = [r.step for r in got if r.sim == sims[i]]
+                    assert seq == list(range(T))
+                res, off = {}, 0
+                for i, t in order:
+                    n = coords[i].shape[1]
+                    res[(i, t)] = out[off:off + n]
+                    off += n
+                st = abp.abp_server_stats(srv)
+                # fewer launches than steps x simulations: the backlog was batched
+                assert st["launches"] < T * len(specs) / 4
+            else:
+                res = {}
+                for t in range(T):  # one step of every simulation, then wait
+                    o, _ = _serve(abp, srv, sims, coords, list(range(T)), [(i, t) for i in range(len(specs))])
+                    res.update(o)
+            outs.append(res)
+        finally:
+            abp.abp_server_destroy(srv)
+            ctx.close()
+    assert any(np.any(v != 0) for v in outs[0].values())
+    for key in outs[0]:
+        assert np.array_equal(outs[0][key], outs[1][key]), key
+
+
 def test_admission_by_hbm_budget(abp):
     ctx = abp.Context(0, budget=40 << 20)
     srv = abp.abp_server_create(ctx.handle, max_batch=64, max_atoms=64, nstreams=2)
@@ -169,6 +223,8 @@ def test_full_size_simulations_against_the_oracle(abp):
         walkers = [_W(i, wid) for i, wid in enumerate(ids)]
         worst = check_run(abp, _Fields(), specs, walkers, frames, 0, Fg, ref, log=log)
         print("sides", [sp["grid"]["n"][0] for sp in specs], "worst", worst)
+        P.record_errors("serving 4096 simulations (the 12 largest grids, 400 steps through the server)",
+                        "test_full_size_simulations_against_the_oracle", worst)
     finally:
         abp.abp_server_destroy(srv)
         ctx.close()
