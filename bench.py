@@ -535,6 +535,7 @@ def bench_shared(abp, synth, torch, dev, sm_mhz, fp32):
                 "kernel_ms_per_md_step": {k: v[1] / max(v[0], 1) for k, v in times.items()},
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                              "frac": achieved / peak, "kernel": "k_big_cn (pair kernel), its own CUDA-event time",
+                             "traffic": captured_traffic("k_big_cn_shared256", nw),
                              "kernel_share_of_step": ms_cn / step_ms if step_ms > 0 else None,
                              "flops_per_pair": CN_PAIR_FLOPS_PBC, "peak_source": fp32.source(sm_mhz)},
                 "deposit_contention": overlap}
@@ -692,12 +693,24 @@ def bench_serve(abp, synth, torch, dev, seconds=2.0, rate=20_000.0):
 # ---------------------------------------------------------------- our arm
 
 
-def kernel_source_hash():
+# The device sources each captured kernel is compiled from (its own file and
+# the headers it includes): a capture stays valid while these are unchanged.
+KERNEL_SOURCES = {
+    "k_md_mb64": ["abp_md.cu", "abp_md.cuh", "abp_window_ops.cuh", "abp_device.cuh", "abp_internal.cuh",
+                  "abp_launch.h"],
+    "k_win_mb64": ["abp_kernels.cu", "abp_window_ops.cuh", "abp_device.cuh", "abp_internal.cuh", "abp_launch.h"],
+    "k_run_uneven1000": ["abp_kernels.cu", "abp_window_ops.cuh", "abp_device.cuh", "abp_internal.cuh",
+                         "abp_launch.h"],
+    "k_big_cn_shared256": ["abp_big.cu", "abp_md.cuh", "abp_device.cuh", "abp_internal.cuh", "abp_launch.h"],
+}
+
+
+def kernel_source_hash(kernel_key):
     import hashlib
 
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1609_09833_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in sorted(KERNEL_SOURCES[kernel_key]):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
@@ -705,13 +718,13 @@ def kernel_source_hash():
 
 def captured_traffic(kernel_key, units_per_launch):
     """DRAM bytes per launch from the committed ncu capture, scaled to this
-    launch's units, or None when the kernel sources changed since."""
+    launch's units, or None when the kernel's sources changed since."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             rec = json.load(f)[kernel_key]
     except (OSError, ValueError, KeyError):
         return None
-    if rec.get("source_hash") != kernel_source_hash():
+    if rec.get("source_hash") != kernel_source_hash(kernel_key):
         return None
     return rec["dram_bytes"] / rec["units"] * units_per_launch
 

@@ -651,10 +651,13 @@ abp_status build_cv(abp_walker *w, const abp_cv_desc &c, int k, int natoms, CvDe
         M += mi;
       }
       std::vector<float> wf(n);
+      bool equal = true;
       for (int i = 0; i < n; ++i) {
         wd[i] = wd[i] / M;
         wf[i] = (float)wd[i];
+        equal = equal && wd[i] == wd[0];
       }
+      (grp ? cv.wc_b : cv.wc_a) = equal ? (float)(wd[0] / (double)wf[0] - 1.0) : 0.f;
       if ((st = upload(w, wf.data(), sizeof(float) * n, &p))) return st;
       (grp ? cv.wb : cv.wa) = static_cast<const float *>(p);
       if ((st = upload(w, wd.data(), sizeof(double) * n, &p))) return st;
@@ -763,6 +766,7 @@ abp_status abp_walker_create(abp_ctx *ctx, abp_grid *grid, const abp_walker_desc
     }
     if (d->cv[k].type == ABP_CV_COORD) w->has_cn = true;
     if (d->cv[k].type == ABP_CV_RMSD) w->has_rmsd = true;
+    if (d->cv[k].type == ABP_CV_DIHEDRAL) hd.cv[k].hp = !fp64 && hd.sigma[k] < kDihedralHpWidth;
   }
   int rsz = fp64 ? 32 : 16;
   // the phased form serves walkers on a shared grid and walkers too large

@@ -345,35 +345,43 @@ __device__ void big_load_desc(const Grp &g, GroupFixed<float> *fx, const WalkerD
 }
 
 // Centre-of-mass distance with compensated arithmetic: each weighted offset
-// w (x - r_G) is split exactly into hi + lo (fma), summed as hi + lo pairs,
-// and |d| is taken in hi + lo. Groups spread over a large box (as a group of
-// environment atoms is) otherwise lose the ~1e-8 relative accuracy a hill a
-// few grid spacings wide needs.
+// w (x - r_G) is split exactly into hi + lo (the difference by two_sum, the
+// product's error by fma; w times the difference's low part, tiny, rounded
+// once), summed as hi + lo pairs, and |d| is taken in hi + lo. Groups spread
+// over a large box (as a group of environment atoms is) otherwise lose the
+// ~1e-8 relative accuracy a hill a few grid spacings wide needs.
 __device__ void cv_com_ff(const Grp &g, GroupFixed<float> *fx, int k, const float4 *xs) {
   const CvDev &c = fx->wd.cv[k];
   const float4 ra = xs[c.ia[0]], rb = xs[c.ib[0]];
   float h[6] = {0, 0, 0, 0, 0, 0}, l[6] = {0, 0, 0, 0, 0, 0};
-  auto acc = [&](int q, float w, float dx) {
-    float p = w * dx;
-    float e = fmaf(w, dx, -p);
+  auto acc = [&](int q, float w, float x, float r) {
+    float dh, dl;
+    two_sum<float>(x, -r, dh, dl);  // x - r exactly
+    float p = __fmul_rn(w, dh);
+    float e = __fmaf_rn(w, dl, __fmaf_rn(w, dh, -p));
     ff_add<float>(h[q], l[q], p, e);
   };
   for (int i = g.t; i < c.na; i += g.G) {
     float w = c.wa[i];
     float4 p = xs[c.ia[i]];
-    acc(0, w, p.x - ra.x);
-    acc(1, w, p.y - ra.y);
-    acc(2, w, p.z - ra.z);
+    acc(0, w, p.x, ra.x);
+    acc(1, w, p.y, ra.y);
+    acc(2, w, p.z, ra.z);
   }
   for (int i = g.t; i < c.nb; i += g.G) {
     float w = c.wb[i];
     float4 p = xs[c.ib[i]];
-    acc(3, w, p.x - rb.x);
-    acc(4, w, p.y - rb.y);
-    acc(5, w, p.z - rb.z);
+    acc(3, w, p.x, rb.x);
+    acc(4, w, p.y, rb.y);
+    acc(5, w, p.z, rb.z);
   }
   for (int q = 0; q < 6; ++q) grp_sum_ff<float>(g, h[q], l[q], fx->red);
   if (g.t != 0) return;
+  // equal masses: the weights' FP32 rounding, one factor per group
+  for (int q = 0; q < 3; ++q) {
+    if (c.wc_a != 0.f) ff_add<float>(h[q], l[q], __fmul_rn(h[q], c.wc_a), 0.f);
+    if (c.wc_b != 0.f) ff_add<float>(h[3 + q], l[3 + q], __fmul_rn(h[3 + q], c.wc_b), 0.f);
+  }
   float dh[3], dl[3];
   const float ra3[3] = {ra.x, ra.y, ra.z}, rb3[3] = {rb.x, rb.y, rb.z};
   for (int q = 0; q < 3; ++q) {

@@ -243,9 +243,13 @@ __device__ __forceinline__ int com_finish_ff(const CvDev &c, const float *ra, co
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
     float rdh, rdl, t, te, s1, e1;
+    float gah = ah[q], gal = al[q], gbh = bh[q], gbl = bl[q];
+    // equal masses: the weights' FP32 rounding, one factor per group
+    if (c.wc_a != 0.f) ff_add<float>(gah, gal, __fmul_rn(gah, c.wc_a), 0.f);
+    if (c.wc_b != 0.f) ff_add<float>(gbh, gbl, __fmul_rn(gbh, c.wc_b), 0.f);
     two_sum<float>(rb[q], -ra[q], rdh, rdl);
-    two_sum<float>(bh[q], -ah[q], t, te);
-    te = __fadd_rn(te, __fsub_rn(bl[q], al[q]));
+    two_sum<float>(gbh, -gah, t, te);
+    te = __fadd_rn(te, __fsub_rn(gbl, gal));
     two_sum<float>(rdh, t, s1, e1);
     e1 = __fadd_rn(e1, __fadd_rn(rdl, te));
     dh[q] = __fadd_rn(s1, e1);
@@ -286,9 +290,12 @@ __device__ __forceinline__ int com_finish_ff(const CvDev &c, const float *ra, co
 // group's weighted sum runs over offsets from the group's first atom, which
 // keeps the rounding at the scale of the group's extent rather than of the
 // absolute coordinates: R_G = r_G + sum_i w_i (x_i - r_G), sum_i w_i = 1.
-// FP32 walkers sum compensated (Kahan per thread, hi + lo across the group)
-// and finish in hi + lo (com_finish_ff): a group of hundreds of atoms spread
-// over nanometres would otherwise lose ~1e-7 nm.
+// FP32 walkers sum every weighted offset exactly as hi + lo (the difference
+// x - r_G split by two_sum, the product's error by fma; the tiny w times the
+// difference's low part rounded once) with two_sum per thread and hi + lo
+// across the group, and finish in hi + lo (com_finish_ff): a group of
+// hundreds of atoms spread over nanometres would otherwise lose ~1e-7 nm,
+// several millionths of a hill a few grid spacings wide.
 template <typename Real>
 __device__ void cv_com(const Grp &g, GroupFixed<Real> *fx, int k, const typename Rec4<Real>::T *xs) {
   const CvDev &c = fx->wd.cv[k];
@@ -297,33 +304,36 @@ __device__ void cv_com(const Grp &g, GroupFixed<Real> *fx, int k, const typename
   const auto ra = xs[ia[0]];
   const auto rb = xs[ib[0]];
   if constexpr (sizeof(Real) == 4) {
-    float h[6] = {0, 0, 0, 0, 0, 0}, cm[6] = {0, 0, 0, 0, 0, 0};
-    auto kahan = [&](int q, float w, float dx) {
-      const float y = __fmaf_rn(w, dx, -cm[q]);
-      const float t = __fadd_rn(h[q], y);
-      cm[q] = __fsub_rn(__fsub_rn(t, h[q]), y);
+    float h[6] = {0, 0, 0, 0, 0, 0}, l[6] = {0, 0, 0, 0, 0, 0};
+    auto acc = [&](int q, float w, float x, float r) {
+      float dh, dl;
+      two_sum<float>(x, -r, dh, dl);  // x - r exactly
+      const float ph = __fmul_rn(w, dh);
+      const float pl = __fmaf_rn(w, dl, __fmaf_rn(w, dh, -ph));
+      float t, e;
+      two_sum<float>(h[q], ph, t, e);
       h[q] = t;
+      l[q] = __fadd_rn(l[q], __fadd_rn(e, pl));
     };
     for (int i = g.t; i < c.na; i += g.G) {
       const float w = wa[i];
       const auto p = xs[ia[i]];
-      kahan(0, w, __fsub_rn(p.x, ra.x));
-      kahan(1, w, __fsub_rn(p.y, ra.y));
-      kahan(2, w, __fsub_rn(p.z, ra.z));
+      acc(0, w, p.x, ra.x);
+      acc(1, w, p.y, ra.y);
+      acc(2, w, p.z, ra.z);
     }
     for (int i = g.t; i < c.nb; i += g.G) {
       const float w = wb[i];
       const auto p = xs[ib[i]];
-      kahan(3, w, __fsub_rn(p.x, rb.x));
-      kahan(4, w, __fsub_rn(p.y, rb.y));
-      kahan(5, w, __fsub_rn(p.z, rb.z));
+      acc(3, w, p.x, rb.x);
+      acc(4, w, p.y, rb.y);
+      acc(5, w, p.z, rb.z);
     }
-    float l[6];
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
-      // the running sum and its compensation as a normalised hi + lo pair
+      // the running sum and its low part as a normalised hi + lo pair
       float s2, e2;
-      two_sum<float>(h[q], -cm[q], s2, e2);
+      two_sum<float>(h[q], l[q], s2, e2);
       h[q] = s2;
       l[q] = e2;
       grp_sum_ff<float>(g, h[q], l[q], fx->red);
@@ -383,12 +393,35 @@ __device__ __forceinline__ Real dot3(const Real *a, const Real *b) {
   return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
 }
 
+// The dihedral angle of FP32 coordinates formed in FP64 (the coordinates
+// and their differences are exact there): for hills so narrow that the FP32
+// angle's rounding, ~1e-7 rad near +-pi, would move them by more than a few
+// millionths of their width.
+__device__ __forceinline__ double dihedral_angle64(const CvDev &c, const float (&x)[4][3]) {
+  double b1[3], b2[3], b3[3], m[3], n[3];
+  for (int q = 0; q < 3; ++q) {
+    b1[q] = (double)x[1][q] - (double)x[0][q];
+    b2[q] = (double)x[2][q] - (double)x[1][q];
+    b3[q] = (double)x[3][q] - (double)x[2][q];
+    if (c.pbc) {
+      b1[q] = min_image<double>(b1[q], c.box[q], c.inv_box[q]);
+      b2[q] = min_image<double>(b2[q], c.box[q], c.inv_box[q]);
+      b3[q] = min_image<double>(b3[q], c.box[q], c.inv_box[q]);
+    }
+  }
+  cross3<double>(b1, b2, m);
+  cross3<double>(b2, b3, n);
+  return atan2(sqrt(dot3<double>(b2, b2)) * dot3<double>(b1, n), dot3<double>(m, n));
+}
+
 // Dihedral of atoms 1-2-3-4: phi = atan2(|b2| b1.(b2 x b3), (b1 x b2).(b2 x b3)),
 // gradient in the Blondel-Karplus form. One thread (the last thread of the
 // group, so that with several warps it overlaps the COM work of warp 0).
+// phi_lo receives the low part of the angle: 0, or with c.hp (FP32 walkers)
+// the FP64 angle's remainder after its FP32 rounding phi.
 template <typename Real>
 __device__ __forceinline__ int dihedral_eval(const CvDev &c, const int32_t *ia, const typename Rec4<Real>::T *xs,
-                                             Real &phi, Real (*grad)[3]) {
+                                             Real &phi, Real (*grad)[3], Real &phi_lo) {
   Real x[4][3];
   for (int a = 0; a < 4; ++a) {
     auto p = xs[ia[a]];
@@ -396,6 +429,7 @@ __device__ __forceinline__ int dihedral_eval(const CvDev &c, const int32_t *ia, 
     x[a][1] = p.y;
     x[a][2] = p.z;
   }
+  phi_lo = 0;
   Real b1[3], b2[3], b3[3], m[3], n[3];
   for (int q = 0; q < 3; ++q) {
     b1[q] = x[1][q] - x[0][q];
@@ -411,7 +445,17 @@ __device__ __forceinline__ int dihedral_eval(const CvDev &c, const int32_t *ia, 
   cross3(b2, b3, n);
   Real b2sq = dot3(b2, b2);
   Real lb2 = sqrt(b2sq);
-  phi = atan2(lb2 * dot3(b1, n), dot3(m, n));
+  if constexpr (sizeof(Real) == 4) {
+    if (c.hp) {
+      const double p64 = dihedral_angle64(c, x);
+      phi = (float)p64;
+      phi_lo = (float)(p64 - (double)phi);
+    } else {
+      phi = atan2(lb2 * dot3(b1, n), dot3(m, n));
+    }
+  } else {
+    phi = atan2(lb2 * dot3(b1, n), dot3(m, n));
+  }
   Real mm = dot3(m, m), nn = dot3(n, n);
   if (!(mm > 0) || !(nn > 0) || !(lb2 > 0)) {
     for (int a = 0; a < 4; ++a)
@@ -435,10 +479,10 @@ __device__ __forceinline__ int dihedral_eval(const CvDev &c, const int32_t *ia, 
 template <typename Real>
 __device__ void cv_dihedral(const Grp &g, GroupFixed<Real> *fx, int k, const typename Rec4<Real>::T *xs) {
   if (g.t != g.G - 1) return;
-  Real phi;
-  int fl = dihedral_eval<Real>(fx->wd.cv[k], fx->ia[k], xs, phi, fx->dih_g[k]);
+  Real phi, phi_lo;
+  int fl = dihedral_eval<Real>(fx->wd.cv[k], fx->ia[k], xs, phi, fx->dih_g[k], phi_lo);
   fx->sh[k] = phi;
-  fx->sl[k] = 0;
+  fx->sl[k] = phi_lo;
   if (fl) fx->flags |= fl;
 }
 

@@ -27,6 +27,11 @@ struct CvDev {
   int pbc;
   double box[3];
   double inv_box[3];
+  int hp;  // DIHEDRAL of an FP32 walker: the angle formed in FP64, carried as hi + lo
+  // COM_DIST: relative error of the FP32 weights when a group's masses are
+  // all equal (W / float(W) - 1, W = 1 / n), else 0; the FP32 finish scales
+  // the group's weighted sum by 1 + wc
+  float wc_a, wc_b;
 };
 
 struct GridDev {
@@ -151,6 +156,11 @@ struct AtomTerm {
 
 constexpr int kWinMax = 32;             // MD steps per window of the windowed form
 constexpr int kAtomTerms = 2 * kMaxCv;  // per atom: up to 2 list entries per CV
+// FP32 walkers form a dihedral's angle in FP64 when its hill (WT: sigma;
+// mABP: a) is narrower than this (rad): the FP32 angle's rounding, up to
+// ~1.2e-7 rad near +-pi, would otherwise move the hill by 2e-6 of its width
+// or more, against a 1e-5 tolerance on the grid fields.
+constexpr double kDihedralHpWidth = 0.06;
 constexpr int kMabpBoxBytes = 96 * 1024;  // windowed mABP: the union of a window's stencil boxes, at most
 constexpr int kWinBytes = 64 * 1024;    // its coordinate double buffer, at most
 constexpr int kWtBoxBytes = 64 * 1024;  // windowed WT: a deposit's stencil box, at most

@@ -232,8 +232,12 @@ __device__ __noinline__ void md_deposit(const Grp &g, GroupFixed<Real> *fx, cons
 //   both run a deposit's stencil and the forces and moves of the atoms.
 //   Named barrier gid + 1 (64 threads) separates the step's phases.
 //   warps 2 and 3, the producers: the Philox noise of the next window of W
-//   steps while the pair runs the current one (two noise buffers); the four
-//   warps meet at window boundaries (named barrier gpc + gid + 1).
+//   steps while the pair runs the current one (two noise buffers); then,
+//   until the pair ends the window, warp 2 prefetches the grid records
+//   around the walker's current cell into L1, so that a4's corner loads
+//   hit there; the four warps meet at window boundaries (named barrier
+//   gpc + gid + 1). A step's finiteness check is made on the coordinates as
+//   the move writes them (the launch's first ones before the first step).
 template <typename Real, int DIM, int UNR>
 __global__ void __launch_bounds__(256, 1) k_md(MdRunArgs a) {
   using R4 = typename Rec4<Real>::T;
@@ -336,14 +340,42 @@ __global__ void __launch_bounds__(256, 1) k_md(MdRunArgs a) {
   long long next_dep = rem == 0 ? 0 : wd.stride - rem;
   int last = -1;        // the last step run
   bool stopped = false;  // non-finite coordinates met (the pair's decision)
-  int pc0 = 0, pc1 = 0;  // warp 1: the previous step's cell (its L1 prefetch)
   Real *dUs = reinterpret_cast<Real *>(dyn + L.ju);  // the step's dU/ds_k (warp 1 -> the force phase)
-  int *badw = reinterpret_cast<int *>(fx->winbad);  // one flag per step-pair warp
+  // [0], [1]: non-finite coordinates seen by each step-pair warp; [2]: the
+  // number of windows the pair has finished (the producers' prefetch stops)
+  int *badw = reinterpret_cast<int *>(fx->winbad);
+  if (tg == 0) badw[2] = 0;
   if (producer && nwin > 0) draw(0);
+  if (!producer) {
+    // the launch's first coordinates; later steps' are checked as they are made
+    int bad = 0;
+    for (int i = g.t; i < natoms; i += 64) bad |= finite_rec<Real>(xs[i]) ? 0 : 1;
+    bad = __any_sync(0xffffffffu, bad);
+    if (lane == 0) badw[g.warp] = bad;
+  }
   gg.sync();
   for (int w = 0; w < nwin; ++w) {
     if (producer) {
       if (w + 1 < nwin) draw(w + 1);
+      if (DIM <= 2 && g.warp == 0) {
+        // until the pair ends the window: L1 prefetch around the walker's
+        // current cell (read while the pair may be writing it; clamped to
+        // the grid), bounded
+        const volatile int *vdone = badw + 2;
+        const volatile int *vi0 = reinterpret_cast<const volatile int *>(st.i0);
+        int l0 = -1, l1 = -1;
+        for (int it = 0; it < (1 << 16) && *vdone != w + 1; ++it) {
+          int c0 = vi0[0], c1 = DIM > 1 ? vi0[DIM > 1 ? 1 : 0] : 0;
+          c0 = c0 < 0 ? 0 : (c0 > wd.g.n[0] - 1 ? wd.g.n[0] - 1 : c0);
+          if (DIM > 1) c1 = c1 < 0 ? 0 : (c1 > wd.g.n[DIM > 1 ? 1 : 0] - 1 ? wd.g.n[DIM > 1 ? 1 : 0] - 1 : c1);
+          if (c0 != l0 || c1 != l1) {
+            prefetch_cell<DIM>(wd.g, c0, c1, lane, 0);
+            l0 = c0;
+            l1 = c1;
+          }
+          __nanosleep(200);
+        }
+      }
     } else {
       const Real *nzw = nzbuf(w);
       const int t0 = w * W, nt = min(W, ra.nsteps - t0);
@@ -352,11 +384,16 @@ __global__ void __launch_bounds__(256, 1) k_md(MdRunArgs a) {
         const long long step = step0 + t;
         const bool dep = t == next_dep;
         if (dep) next_dep += wd.stride;
-        // a1, and each warp's half of the finiteness check
-        int bad = 0;
-        for (int i = g.t; i < natoms; i += 64) bad |= finite_rec<Real>(xs[i]) ? 0 : 1;
-        bad = __any_sync(0xffffffffu, bad);
-        if (lane == 0) badw[g.warp] = bad;
+        if (badw[0] | badw[1]) {
+          // this walker stops here: its state says so, its atoms stay
+          if (g.t == 0) {
+            wd.state->flags = ABP_WFLAG_NONFINITE;
+            atomicAdd(&ra.ctr->nonfinite, 1);
+          }
+          stopped = true;
+          break;
+        }
+        // a1
         if (w0) {
 #pragma unroll
           for (int k = 0; k < DIM; ++k)
@@ -367,8 +404,6 @@ __global__ void __launch_bounds__(256, 1) k_md(MdRunArgs a) {
               if (lane == 0) window_cv_rec<Real>(wd, k, sk, slk, fl, dep, st);
             }
         } else {
-          // the previous step's cell first (its corners likely to be read again)
-          if (t > 0) prefetch_cell<DIM>(wd.g, pc0, pc1, lane, 1);
           int q = 0;
 #pragma unroll
           for (int k = 0; k < DIM; ++k)
@@ -378,15 +413,6 @@ __global__ void __launch_bounds__(256, 1) k_md(MdRunArgs a) {
             }
         }
         psync();
-        if (badw[0] | badw[1]) {
-          // this walker stops here: its state says so, its atoms stay
-          if (g.t == 0) {
-            wd.state->flags = ABP_WFLAG_NONFINITE;
-            atomicAdd(&ra.ctr->nonfinite, 1);
-          }
-          stopped = true;
-          break;
-        }
         if (w0 && lane == 0) step_flags<Real>(DIM, dep, st);
         if (dep) {
           psync();
@@ -404,8 +430,6 @@ __global__ void __launch_bounds__(256, 1) k_md(MdRunArgs a) {
           if (lane == 0)
 #pragma unroll
             for (int k = 0; k < 3; ++k) dUs[k] = dU[k];
-          pc0 = st.i0[0];
-          pc1 = DIM > 1 ? st.i0[DIM > 1 ? 1 : 0] : 0;
         }
         psync();
         // a5 and the move, one atom per thread of the pair: each of the
@@ -420,6 +444,7 @@ __global__ void __launch_bounds__(256, 1) k_md(MdRunArgs a) {
           dvk[k] = k < DIM ? st.dv[k] : (Real)0;
           dtk[k] = dvk[k] + dUs[k];
         }
+        int nbad = 0;
         for (int i = g.t; i < natoms; i += 64) {
           const AtomTerm<Real> *ti = terms + i * kAtomTerms;
           const int ne = cnt[i];
@@ -450,10 +475,15 @@ __global__ void __launch_bounds__(256, 1) k_md(MdRunArgs a) {
           x.y += mc.c1 * f1 + mc.c2 * nz[3 * i + 1];
           x.z += mc.c1 * f2 + mc.c2 * nz[3 * i + 2];
           xs[i] = x;
+          nbad |= finite_rec<Real>(x) ? 0 : 1;
         }
+        // the next step's coordinates: each warp's half of the finiteness check
+        nbad = __any_sync(0xffffffffu, nbad);
+        if (lane == 0) badw[g.warp] = nbad;
         last = t;
         psync();
       }
+      if (g.t == 0) *reinterpret_cast<volatile int *>(badw + 2) = w + 1;  // the pair's thread 0
     }
     gg.sync();
   }

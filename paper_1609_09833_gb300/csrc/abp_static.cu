@@ -196,6 +196,7 @@ extern "C" abp_status abp_step_static(int device, void *cuda_stream, const abp_g
     if (!unique_in_range(c.idx_a, cv.na, w->natoms) || !unique_in_range(c.idx_b, cv.nb, w->natoms))
       return sfail(ABP_ERR_INVALID_ARG, "abp_step_static: atom index lists must be unique and in [0, natoms)");
     cv.pbc = c.pbc != 0;
+    cv.hp = !fp64 && c.type == ABP_CV_DIHEDRAL && hd.sigma[k] < kDihedralHpWidth;
     for (int q = 0; q < 3; ++q) {
       if (cv.pbc && !(c.box[q] > 0)) return sfail(ABP_ERR_INVALID_ARG, "abp_step_static: pbc needs box edges > 0");
       cv.box[q] = cv.pbc ? c.box[q] : 0.0;
@@ -217,10 +218,13 @@ extern "C" abp_status abp_step_static(int device, void *cuda_stream, const abp_g
           wd[i] = mi;
           M += mi;
         }
+        bool equal = true;
         for (int i = 0; i < n; ++i) {
           wd[i] /= M;
           wf[i] = (float)wd[i];
+          equal = equal && wd[i] == wd[0];
         }
+        (grp ? cv.wc_b : cv.wc_a) = equal ? (float)(wd[0] / (double)wf[0] - 1.0) : 0.f;
         (grp ? cv_wb[k] : cv_wa[k]) = put(wf.data(), sizeof(float) * n);
         (grp ? cv_wb64[k] : cv_wa64[k]) = put(wd.data(), sizeof(double) * n);
       }

@@ -331,7 +331,7 @@ __device__ __forceinline__ void window_cv(const GroupFixed<Real> *fx, const type
   if (c.type == ABP_CV_COM_DIST)
     fl = com_thread<Real>(c, fx->ia[k], fx->ib[k], fx->wa[k], fx->wb[k], x, sk, slk, st.jac[k]);
   else if (c.type == ABP_CV_DIHEDRAL)
-    fl = dihedral_eval<Real>(c, fx->ia[k], x, sk, reinterpret_cast<Real(*)[3]>(st.jac[k]));
+    fl = dihedral_eval<Real>(c, fx->ia[k], x, sk, reinterpret_cast<Real(*)[3]>(st.jac[k]), slk);
   else
     fl = rmsd_thread<Real>(c, fx->ia[k], x, sk, st.jac[k]);
   window_cv_rec<Real>(wd, k, sk, slk, fl, dep, st);
