@@ -293,6 +293,24 @@ def cpu_baseline(seconds: float):
 
 # ---------------------------------------------------------------- the other workloads
 
+
+def oracle_rate(step_fn, units_per_call, seconds, what):
+    """The oracle as it stands on a bounded sample of a workload: one pilot
+    call sizes the number of calls to about `seconds` of host time; returns
+    the cpu_baseline record (bias steps/s, host threads, the sample)."""
+    import oracle
+
+    t0 = time.perf_counter()
+    step_fn(0)
+    pilot = time.perf_counter() - t0
+    n = int(max(1, min(1000, seconds / max(pilot, 1e-9))))
+    t0 = time.perf_counter()
+    for i in range(n):
+        step_fn(1 + i)
+    dt = time.perf_counter() - t0
+    return {"value": units_per_call * n / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{n} calls of {what} ({units_per_call * n} bias steps, {dt:.1f} s), FP64 C oracle"}
+
 # Flops of one coordination-number pair as the defined formula has them
 # (s = sum 1 / (1 + q^3), q = r^2 / r0^2, and dCN/dx for both atoms):
 # differences 3, r^2 5, q 1, q^2 and q^3 2, 1 + q^3 1, the reciprocal 1, the
@@ -366,12 +384,35 @@ def bench_double_well(abp, synth, torch, dev):
             so["md"] += T
 
         ms = _time_loop(torch, run, 5)
+        # the plain form on the same frames: three launches per MD step
+        wp = ctx.make_walkers([spec], precision=abp.ABP_PREC_FP64)
+        for t in range(3):
+            abp.abp_step_plain(ctx.handle, wp, rec[t], abp.ABP_F64, offs, F[t], offs, abp.ABP_FORCES_OVERWRITE, t)
+        torch.cuda.synchronize()
+        n_plain = 200
+        t0 = time.perf_counter()
+        for t in range(3, 3 + n_plain):
+            abp.abp_step_plain(ctx.handle, wp, rec[t], abp.ABP_F64, offs, F[t], offs, abp.ABP_FORCES_OVERWRITE, t)
+        torch.cuda.synchronize()
+        plain = n_plain / (time.perf_counter() - t0)
+        import oracle
+
+        ow = [oracle.Walker(spec)]
+        ofield = [ow[0].new_field()]
+        ox = {"x": x0.astype(np.float64)}
+
+        def ostep(i):
+            ox["x"] = oracle.md_run(ow, ox["x"], [0], md, [0], i * 2000, 2000, fields=ofield)["x"]
+
+        cpu = oracle_rate(ostep, 2000, 3.0, "2000 closed-loop MD steps of the walker")
         return {"workload": "1 walker, FP64 end to end, COM distance 2x8 atoms, 512-node grid, stride 100; "
                             "closed loop on U = 5 (s^2-1)^2",
                 "value": T / (ms_closed / 1e3), "unit": "bias steps/s", "us_per_step": 1e3 * ms_closed / T,
                 "md_steps_per_launch": T, "dtype": "f64", "bound": "latency (one walker's dependent step chain)",
                 "open_loop_replay": {"value": T / (ms / 1e3), "us_per_step": 1e3 * ms / T,
-                                     "form": "windowed, recorded random-walk frames"}}
+                                     "form": "windowed, recorded random-walk frames"},
+                "plain": {"value": plain, "form": "3 launches per MD step from a host loop (recorded frames)"},
+                "cpu_baseline": cpu}
     finally:
         torch.cuda.synchronize()
         ctx.close()
@@ -407,13 +448,27 @@ def bench_paper_rmsd(abp, synth, torch, dev):
         per_step = 8 * 16 * 2 + NODE_BYTES + box * NODE_BYTES * 2
         peaks, src = load_peaks()
         achieved = per_step * nw * C / (ms / 1e3) / 1e9
+        import oracle
+
+        ows = [oracle.Walker(sp) for sp in specs]
+        ofields = [w.new_field() for w in ows]
+        ofr = rec[:200].cpu().numpy()[..., :3].astype(np.float64)
+        ooff = synth.offsets_of(specs)
+
+        def ostep(i):
+            t = (i * 10) % 190
+            oracle.run(ows, ofr[t:t + 10], ooff, i * 10, 10, fields=ofields, record_forces=False)
+
+        cpu = oracle_rate(ostep, nw * 10, 3.0, "10 MD steps of the 64 walkers")
+        del ofields
         return {"workload": "64 walkers, 2 RMSD CVs (4 atoms each), 480x480 grid on [0,12] nm, mABP compact hills "
                             "a = 10 spacings, p = 20, b = 0.9, c = 0.001, update every step",
                 "value": nw * C / (ms / 1e3), "unit": "bias steps/s", "ms_per_launch": ms, "md_steps_per_launch": C,
                 "stencil_nodes": box,
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                              "frac": achieved / peaks["hbm_gbs"], "bytes_per_walker_step": per_step,
-                             "kernel": "k_win<float> (windowed form)", "peak_source": src}}
+                             "kernel": "k_win<float> (windowed form)", "peak_source": src},
+                "cpu_baseline": cpu}
     finally:
         torch.cuda.synchronize()
         ctx.close()
@@ -445,9 +500,46 @@ def bench_uneven(abp, synth, torch, dev, sm_mhz, fp32):
         flops = nw * C * 40 * 400 * CN_PAIR_FLOPS
         achieved = flops / (ms / 1e3) / 1e12
         peak = fp32.at(sm_mhz)
+        # the same launch replayed from a CUDA graph
+        s = torch.cuda.Stream()
+        ctx.set_stream(s.cuda_stream)
+        g = torch.cuda.CUDAGraph()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=s):
+            abp.abp_run(ctx.handle, walkers, rec, abp.ABP_F32, offs, A, F, offs, A, abp.ABP_FORCES_OVERWRITE,
+                        10 ** 6, C)
+        ctx.set_stream(torch.cuda.current_stream().cuda_stream)
+        ms_graph = _time_loop(torch, g.replay, 6)
+        # the plain form: three launches per walker per MD step
+        wp = ctx.make_walkers(specs)
+        Fp = torch.zeros_like(rec[0])
+        abp.abp_step_plain(ctx.handle, wp, rec[0], abp.ABP_F32, offs, Fp, offs, abp.ABP_FORCES_OVERWRITE, 0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for t in range(1, 3):
+            abp.abp_step_plain(ctx.handle, wp, rec[t], abp.ABP_F32, offs, Fp, offs, abp.ABP_FORCES_OVERWRITE, t)
+        torch.cuda.synchronize()
+        plain = nw * 2 / (time.perf_counter() - t0)
+        import oracle
+
+        ns = 100
+        ows = [oracle.Walker(sp) for sp in specs[:ns]]
+        ofields = [w.new_field() for w in ows]
+        ofr = rec[:, :synth.offsets_of(specs)[ns]].cpu().numpy()[..., :3].astype(np.float64)
+        ooff = synth.offsets_of(specs[:ns])
+
+        def ostep(i):
+            t = i % C
+            oracle.run(ows, ofr[t:t + 1], ooff, i, 1, fields=ofields, record_forces=False)
+
+        cpu = oracle_rate(ostep, ns, 3.0, f"one MD step of the first {ns} walkers")
         return {"workload": "1000 walkers (40% 1D 1024, 50% 2D 128^2/256^2/512^2, 10% 3D 64^3), CN 40x400, "
                             "jitter frames, one launch per 25 MD steps",
                 "value": nw * C / (ms / 1e3), "unit": "bias steps/s", "ms_per_launch": ms,
+                "graph_replay": {"value": nw * C / (ms_graph / 1e3), "ms_per_launch": ms_graph},
+                "plain": {"value": plain, "ratio": nw * C / (ms / 1e3) / plain,
+                          "form": "3 launches per walker per MD step from a host loop"},
+                "cpu_baseline": cpu,
                 "tuned": tuned["best"],
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                              "frac": achieved / peak, "kernel": "k_run / k_run_lean (per-step form, CN pairs)",
@@ -518,6 +610,19 @@ def bench_shared(abp, synth, torch, dev, sm_mhz, fp32):
             so["md"] += C
 
         ms_open = _time_loop(torch, run, 3)
+        import oracle
+
+        ows = [oracle.Walker(sp) for sp in specs]
+        oshared = ows[0].new_field()
+        ofr = rec.cpu().numpy()[..., :3].astype(np.float64)
+        ooff = synth.offsets_of(specs)
+
+        def ostep(i):
+            t = i % C
+            oracle.run(ows, ofr[t:t + 1], ooff, i, 1, fields=[oshared] * nw, record_forces=False)
+
+        cpu = oracle_rate(ostep, nw, 3.0, "one MD step of the 32 walkers on the shared grid")
+        del oshared
         overlap = None
         if len(log["step"]):
             st0 = log["step"][0]
@@ -538,6 +643,7 @@ def bench_shared(abp, synth, torch, dev, sm_mhz, fp32):
                              "traffic": captured_traffic("k_big_cn_shared256", nw),
                              "kernel_share_of_step": ms_cn / step_ms if step_ms > 0 else None,
                              "flops_per_pair": CN_PAIR_FLOPS_PBC, "peak_source": fp32.source(sm_mhz)},
+                "cpu_baseline": cpu,
                 "deposit_contention": overlap}
     finally:
         torch.cuda.synchronize()
@@ -621,8 +727,11 @@ def bench_serve(abp, synth, torch, dev, seconds=2.0, rate=20_000.0):
         # not enter it; the wall-clock figure seen from Python is kept beside.
         depth = 8
         reps = []
-        tw0 = abp.abp_server_times(srv)
-        for _ in range(5):
+        tw0 = None
+        for rep in range(6):  # the first is a warm-up (its slabs are allocated and faulted in)
+            if rep == 1:
+                reps.clear()
+                tw0 = abp.abp_server_times(srv)
             results.clear()
             order = [i for d in range(depth) for i in range(nsim)]
             sim_ids = np.array([sims[i] for i in order], dtype=np.int64)
@@ -675,6 +784,20 @@ def bench_serve(abp, synth, torch, dev, seconds=2.0, rate=20_000.0):
             plain = np_ * n_plain / (time.perf_counter() - t0)
         finally:
             pctx.close()
+        import oracle
+
+        ns = 32
+        ows = [oracle.Walker(sp) for sp in specs[:ns]]
+        ofields = [w.new_field() for w in ows]
+        ofr = np.concatenate([frames[i][:, :, :3] for i in range(ns)], axis=1).astype(np.float64)
+        ooff = synth.offsets_of(specs[:ns])
+
+        def ostep(i):
+            t = i % nf
+            oracle.run(ows, ofr[t:t + 1], ooff, i, 1, fields=ofields, record_forces=False)
+
+        cpu = oracle_rate(ostep, ns, 3.0, f"one step of {ns} of the simulations")
+        del ofields
         st = abp.abp_server_stats(srv)
         return {"workload": "4096 simulations, 2D grids 64^2..1024^2 FP32+comp, 8..256 atoms, stride 20..500; "
                             "Poisson step requests (host coords in, host forces out)",
@@ -682,6 +805,7 @@ def bench_serve(abp, synth, torch, dev, seconds=2.0, rate=20_000.0):
                 "admitted": len(sims), "hbm_bytes": hbm, "poisson": poisson, "saturation": sat,
                 "plain": {"value": plain, "ratio": sat["throughput"] / plain,
                           "form": "256 of the simulations as plain-form walkers, 3 launches per walker per step"},
+                "cpu_baseline": cpu,
                 "launches": st["launches"]}
     finally:
         if srv is not None:

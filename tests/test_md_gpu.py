@@ -258,6 +258,60 @@ def test_launch_length_does_not_change_the_bits(abp, ctx):
             assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("shared", [False, True])
+def test_closed_loop_under_cuda_graph_capture(abp, ctx, shared):
+    """abp_md_run captured in a CUDA graph (after a direct call has cached
+    the walker table) replays the same steps as direct calls: bit for bit in
+    the fused closed loop on own grids, to FP64 rounding in the phased form
+    on a shared grid (six launches per step; FP64 atomics add a step's hills
+    in any order)."""
+    if shared:
+        nw = 3
+        specs = synth.shared256_specs(nw=nw, n=32, n_lig=16, n_env=200, box=3.0, stride=2, cn_range=(30.0, 130.0))
+        x0 = np.concatenate(synth.shared256_templates(11, nw=nw, n_lig=16, n_env=200, box=3.0)).astype(np.float32)
+        md = synth.md_params(seed=7, mu=0.05)
+    else:
+        nw = 4
+        specs = synth.mb64_specs(nw=nw, stride=3)
+        x0 = synth.SweepFrames(nw, seed=29).frames(0, 1)[0]
+        md = synth.md_muller_brown(seed=7)
+    streams = np.arange(nw) + 5
+    T = 12
+    offs = torch.tensor(synth.offsets_of(specs), dtype=torch.int64, device="cuda")
+    # direct calls: step 0, then steps 1 .. T-1
+    wd = ctx.make_walkers(specs)
+    xd = abp.to_records(x0[None]).cuda()[0]
+    abp.abp_md_run(ctx.handle, wd, xd, abp.ABP_F32, offs, md, streams, step0=0, nsteps=1)
+    abp.abp_md_run(ctx.handle, wd, xd, abp.ABP_F32, offs, md, streams, step0=1, nsteps=T - 1)
+    torch.cuda.synchronize()
+    # step 0 directly (caches the table), steps 1 .. T-1 from a captured graph
+    if shared:
+        for sp in specs:
+            sp["shared"] = "graph"
+    wg = ctx.make_walkers(specs)
+    xg = abp.to_records(x0[None]).cuda()[0]
+    abp.abp_md_run(ctx.handle, wg, xg, abp.ABP_F32, offs, md, streams, step0=0, nsteps=1)
+    torch.cuda.synchronize()
+    st = torch.cuda.Stream()
+    ctx.set_stream(st.cuda_stream)
+    try:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=st):
+            abp.abp_md_run(ctx.handle, wg, xg, abp.ABP_F32, offs, md, streams, step0=1, nsteps=T - 1)
+        g.replay()
+        torch.cuda.synchronize()
+    finally:
+        ctx.set_stream(torch.cuda.current_stream().cuda_stream)
+    assert not torch.equal(xd, abp.to_records(x0[None]).cuda()[0])
+    if shared:
+        assert torch.allclose(xd, xg, rtol=0, atol=1e-6)
+        assert np.all(P.rel_field_err(ctx.bias(wg[0]), ctx.bias(wd[0])) < 1e-9)
+    else:
+        assert torch.equal(xd, xg)
+        for a, b in zip(wd, wg):
+            assert np.array_equal(ctx.bias(a), ctx.bias(b))
+
+
 def test_open_loop_replay_of_the_closed_loop_trajectory(abp, ctx):
     """The windowed form (abp_run) replayed on the GPU's own closed-loop
     trajectory computes the closed loop's bias forces and grids: the two
