@@ -944,6 +944,26 @@ def main():
         state["md"] = md0 + 1
     torch.cuda.synchronize()
     lat = np.array([a.elapsed_time(b) * 1e3 for a, b in evl])
+    # one MD step per call, as a host MD engine calls it: back-to-back calls
+    # (launch overhead included) and the same calls replayed from a CUDA graph
+    n1 = 200
+    t0 = time.perf_counter()
+    for _ in range(n1):
+        md0 = state["md"]
+        abp.abp_md_run(ctx.handle, walkers, x, abp.ABP_F32, offs, md, streams, step0=md0, nsteps=1)
+        state["md"] = md0 + 1
+    torch.cuda.synchronize()
+    one_step = NW * n1 / (time.perf_counter() - t0)
+    gs = torch.cuda.Stream()
+    ctx.set_stream(gs.cuda_stream)
+    g1 = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g1, stream=gs):
+        for k in range(50):
+            abp.abp_md_run(ctx.handle, walkers, x, abp.ABP_F32, offs, md, streams, step0=10 ** 7 + k, nsteps=1)
+    ctx.set_stream(stream.cuda_stream)
+    ms_g1 = _time_loop(torch, g1.replay, 5)
+    one_step_graph = NW * 50 / (ms_g1 / 1e3)
 
     # end to end through the same call with host buffers (pinned), per step:
     # H2D of the walkers' atoms, C closed-loop steps, D2H of the moved atoms
@@ -1072,6 +1092,10 @@ def main():
                       "form": "3 launches per walker per MD step from a host loop (open-loop frames)"},
             "latency_us": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "what": "one closed-loop MD step of all 64 walkers, one call, CUDA events"},
+            "one_step_per_call": {"value": one_step, "graph_replay": one_step_graph, "unit": UNIT,
+                                  "ratio_to_plain": one_step / plain_value,
+                                  "what": "the same walkers, one closed-loop MD step of all 64 per call (as a host MD "
+                                          "engine calls the bias), back to back; and 50 such calls in a CUDA graph"},
             "other_workloads": extra,
         }
         print(json.dumps(line), flush=True)

@@ -60,6 +60,7 @@ typedef int abp_status;
 #define ABP_ERR_NONFINITE (-5)    /* non-finite coordinates were seen; those walkers were left unchanged */
 #define ABP_ERR_TIMEOUT (-6)      /* a bounded device or host wait ran out */
 #define ABP_ERR_UNSUPPORTED (-7)  /* a combination the library does not implement */
+#define ABP_ERR_CANCELLED (-8)    /* a served request was cancelled before it was launched */
 
 /* CV types (step a1). */
 #define ABP_CV_COM_DIST 0 /* |R_B - R_A|, R_G the mass-weighted centre of group G */
@@ -457,6 +458,12 @@ abp_status abp_server_submit(abp_server *srv, int64_t sim, int64_t step, const f
  * before it were queued. */
 abp_status abp_server_submit_many(abp_server *srv, int n, const int64_t *sims, const int64_t *steps,
                                   const float *coords_host, float *forces_host, const uint64_t *tags);
+/* Cancels the requests of simulation `sim` that are still queued (not yet
+ * packed into a launch): each comes back through abp_server_poll with status
+ * ABP_ERR_CANCELLED and its forces_host untouched; requests already launched
+ * finish normally. *n_cancelled (may be NULL) receives how many were
+ * cancelled. The simulation stays admitted; later submits are served. */
+abp_status abp_server_cancel(abp_server *srv, int64_t sim, int64_t *n_cancelled);
 /* Up to cap finished requests, oldest first; waits up to wait_ms for the
  * first one when none is ready (0 = do not wait). */
 abp_status abp_server_poll(abp_server *srv, abp_result *out, int cap, int *n_out, int wait_ms);

@@ -22,7 +22,7 @@ ABP_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "CUDA", -3: "OOM", -4: "ADMISSION", -5: "NONFINITE", -6: "TIMEOUT",
           -7: "UNSUPPORTED"}
 ABP_ERR_INVALID_ARG, ABP_ERR_CUDA, ABP_ERR_OOM, ABP_ERR_ADMISSION = -1, -2, -3, -4
-ABP_ERR_NONFINITE, ABP_ERR_TIMEOUT, ABP_ERR_UNSUPPORTED = -5, -6, -7
+ABP_ERR_NONFINITE, ABP_ERR_TIMEOUT, ABP_ERR_UNSUPPORTED, ABP_ERR_CANCELLED = -5, -6, -7, -8
 CV_TYPES = {"com_dist": 0, "dihedral": 1, "coord": 2, "rmsd": 3}
 ABP_METHOD_WT, ABP_METHOD_MABP = 0, 1
 ABP_PREC_FP32_COMP, ABP_PREC_FP64 = 0, 1
@@ -158,6 +158,7 @@ _SIGS = {
     "abp_server_bias_readout": [_vp, C.c_int64, _vp, C.c_int, C.c_int],
     "abp_server_submit": [_vp, C.c_int64, C.c_int64, _vp, _vp, C.c_uint64],
     "abp_server_submit_many": [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp],
+    "abp_server_cancel": [_vp, C.c_int64, C.POINTER(C.c_int64)],
     "abp_server_poll": [_vp, C.POINTER(Result), C.c_int, C.POINTER(C.c_int), C.c_int],
     "abp_server_stats": [_vp, _i64p, _i64p, _i64p, _i64p],
     "abp_server_times": [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
@@ -445,6 +446,12 @@ def abp_server_submit_many(srv, sims, steps, coords_host, forces_host, tags=None
     tg = None if tags is None else np.ascontiguousarray(tags, dtype=np.uint64)
     _check(load().abp_server_submit_many(srv, len(sims), _ptr(sims), _ptr(steps), _ptr(coords_host),
                                          _ptr(forces_host), _ptr(tg)))
+
+
+def abp_server_cancel(srv, sim) -> int:
+    n = C.c_int64()
+    _check(load().abp_server_cancel(srv, int(sim), C.byref(n)))
+    return int(n.value)
 
 
 def abp_server_poll(srv, cap: int = 4096, wait_ms: int = 0):

@@ -2341,6 +2341,27 @@ abp_status abp_server_submit_many(abp_server *s, int n, const int64_t *sims, con
   return ABP_OK;
 }
 
+abp_status abp_server_cancel(abp_server *s, int64_t sim, int64_t *n_cancelled) {
+  if (!s) return fail(ABP_ERR_INVALID_ARG, "NULL argument");
+  int64_t n = 0;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->sims.find(sim);
+    if (it == s->sims.end()) return fail(ABP_ERR_INVALID_ARG, "unknown simulation %lld", (long long)sim);
+    SrvSim &sm = it->second;
+    const double t = steady_now();
+    for (const SrvRequest &r : sm.pending)
+      s->results.push_back(abp_result{r.sim, r.step, r.tag, r.t_submit, t, ABP_ERR_CANCELLED, 0});
+    n = (int64_t)sm.pending.size();
+    sm.pending.clear();  // the ready queue skips a simulation with nothing pending
+    s->queued -= n;
+    s->finished += n;
+  }
+  if (n) s->cv_done.notify_all();
+  if (n_cancelled) *n_cancelled = n;
+  return ABP_OK;
+}
+
 abp_status abp_server_poll(abp_server *s, abp_result *out, int cap, int *n_out, int wait_ms) {
   if (!s || !n_out || (cap > 0 && !out)) return fail(ABP_ERR_INVALID_ARG, "NULL argument");
   std::unique_lock<std::mutex> lk(s->mu);

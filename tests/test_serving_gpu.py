@@ -151,6 +151,45 @@ def test_backlog_pipelines_across_slots_in_order(abp):
         assert np.array_equal(outs[0][key], outs[1][key]), key
 
 
+def test_cancel_drops_the_queued_requests_of_a_simulation(abp):
+    """50 steps of one simulation queued at once, then cancelled: the steps
+    already launched finish (a prefix, in order, status 0), the rest come back
+    cancelled with their force buffers untouched, and the simulation is
+    served again afterwards."""
+    ctx = abp.Context(0)
+    srv = abp.abp_server_create(ctx.handle, max_batch=64, max_atoms=256, nstreams=2)
+    try:
+        spec = synth.serve_specs(seed=13, nsim=1, side=(256, 256), atoms=(64, 64), stride=(5, 5))[0]
+        desc, keep = abp.walker_desc(spec)
+        sim = abp.abp_server_admit(srv, abp.grid_desc(spec["grid"]), desc)
+        T = 50
+        coords = _records(_frames(synth.serve_templates(13, [spec])[0], 5, T + 1))
+        packed = np.ascontiguousarray(coords[:T].reshape(-1, 4))
+        out = np.full_like(packed, 7.0)
+        abp.abp_server_submit_many(srv, [sim] * T, list(range(T)), packed, out)
+        n = abp.abp_server_cancel(srv, sim)
+        got, deadline = [], time.time() + 60
+        while len(got) < T and time.time() < deadline:
+            got += abp.abp_server_poll(srv, 4096, wait_ms=50)
+        assert len(got) == T
+        done = sorted(r.step for r in got if r.status == 0)
+        cancelled = sorted(r.step for r in got if r.status == abp.ABP_ERR_CANCELLED)
+        assert len(cancelled) == n >= 1
+        assert done == list(range(len(done))) and cancelled == list(range(len(done), T))
+        F = out.reshape(T, -1, 4)
+        assert np.all(F[len(done):] == 7.0)
+        assert all(np.any(F[t] != 7.0) for t in range(len(done)))
+        f = np.zeros_like(coords[0])
+        abp.abp_server_submit(srv, sim, len(done), coords[len(done)], f)
+        r = abp.abp_server_poll(srv, 16, wait_ms=5000)
+        assert len(r) == 1 and r[0].status == 0 and np.any(f != 0)
+        st = abp.abp_server_stats(srv)
+        assert st["finished"] == st["submitted"] == T + 1 and st["queued"] == 0
+    finally:
+        abp.abp_server_destroy(srv)
+        ctx.close()
+
+
 def test_admission_by_hbm_budget(abp):
     ctx = abp.Context(0, budget=40 << 20)
     srv = abp.abp_server_create(ctx.handle, max_batch=64, max_atoms=64, nstreams=2)
