@@ -179,6 +179,37 @@ def test_closed_loop_steps_match_the_oracle_fp32_mueller_brown(abp, ctx):
     assert np.ptp(ref["s"][:, :, 0]) > 0.01 and np.ptp(ref["s"][:, :, 1]) > 0.05
 
 
+def test_closed_loop_full_size_64_walkers(abp, ctx):
+    """The benchmark's closed-loop workload at full size: all 64 walkers
+    (36 atoms, own 256 x 256 grids, Mueller-Brown x 0.1, mu = 0.1, stride
+    50), 120 steps compared with the oracle step by step on the oracle's own
+    trajectory; and the benchmark's launch configuration (one launch of many
+    steps) gives the same bits as one launch per step for all 64 walkers."""
+    nw, T = 64, 120
+    specs = synth.mb64_specs(nw=nw)
+    md = synth.md_muller_brown(seed=2024, mu=0.1, state_f32=True)
+    streams = np.arange(nw)
+    x0 = synth.SweepFrames(nw, seed=2031).frames(0, 1)[0]
+    frames = _oracle_closed_loop(specs, x0, md, streams, T)
+    walkers = ctx.make_walkers(specs)
+    abp.abp_deposit_log_enable(ctx.handle, 1 << 16)
+    X, F = gpu_steps_from(abp, ctx, walkers, frames[:T], md, streams)
+    _, ref = oracle_replay(specs, frames[:T].astype(np.float32), 0)
+    worst = check_run(abp, ctx, specs, walkers, frames[:T], 0, F, ref)
+    worst["move"] = check_moves(specs, md, streams, frames, X, ref)
+    print("worst", worst)
+    P.record_errors("64 walkers, 2 CVs (closed loop, full size, 64 walkers)", "test_closed_loop_full_size_64_walkers",
+                    worst)
+    # one launch of T steps against T one-step launches, all 64 walkers
+    runs = []
+    for chunks in (1, T):
+        w = ctx.make_walkers(specs)
+        runs.append(gpu_run(abp, ctx, w, x0, md, streams, 0, T, chunks=chunks) + ([ctx.bias(v) for v in w],))
+    for a, b in zip(runs[0][:3], runs[1][:3]):
+        assert np.array_equal(a, b)
+    assert all(np.array_equal(a, b) for a, b in zip(runs[0][3], runs[1][3]))
+
+
 def test_closed_loop_steps_match_the_oracle_fp64_double_well(abp, ctx):
     """The one-walker FP64 workload (COM distance of two 8-atom groups on
     U = 5 (s^2 - 1)^2, mu = 1), two walkers, 300 steps, a deposit every 10."""
