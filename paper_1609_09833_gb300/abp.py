@@ -219,9 +219,14 @@ def _ptr(t) -> int:
     return t.data_ptr()
 
 
+def walker_array(ws):
+    """The C array of walker handles a call takes; a caller that calls every
+    MD step can build it once and pass it in place of the list."""
+    return (_vp * max(1, len(ws)))(*[w.handle if hasattr(w, "handle") else w for w in ws])
+
+
 def _walkers(ws):
-    arr = (_vp * max(1, len(ws)))(*[w.handle if hasattr(w, "handle") else w for w in ws])
-    return arr
+    return ws if isinstance(ws, C.Array) else walker_array(ws)
 
 
 # ---------------------------------------------------------------- raw ABI names
@@ -310,7 +315,8 @@ def abp_md_run(ctx, walkers, coords, coords_dtype, coord_offsets, md, streams, t
     """Closed-loop MD steps (coordinates moved in place). md: MdDesc or a
     dynamics dict; streams: one noise stream per walker."""
     desc = md if isinstance(md, MdDesc) else md_desc(md)
-    st = np.ascontiguousarray(np.asarray(streams, dtype=np.uint32))
+    st = streams if (isinstance(streams, np.ndarray) and streams.dtype == np.uint32 and streams.flags.c_contiguous) \
+        else np.ascontiguousarray(np.asarray(streams, dtype=np.uint32))
     _check(load().abp_md_run(ctx, _walkers(walkers), len(walkers), _ptr(coords), coords_dtype, _ptr(coord_offsets),
                              C.byref(desc), st.ctypes.data_as(C.POINTER(C.c_uint32)), _ptr(traj), _ptr(traj_offsets),
                              int(traj_step_stride), _ptr(forces), _ptr(force_offsets), int(force_step_stride),

@@ -585,6 +585,56 @@ abp_status check_indices(const int32_t *idx, int n, int natoms, const char *what
   return ABP_OK;
 }
 
+// COM weights m_i / M of group grp (0: list A, 1: list B) in FP64 (unit
+// masses when none are given); false on a mass that is not finite and > 0.
+bool com_weights(const abp_cv_desc &c, int grp, std::vector<double> &wd) {
+  const int n = grp ? c.n_b : c.n_a;
+  const double *m = grp ? c.mass_b : c.mass_a;
+  wd.assign(n, 0.0);
+  double M = 0;
+  for (int i = 0; i < n; ++i) {
+    const double mi = m ? m[i] : 1.0;
+    if (!(mi > 0) || !std::isfinite(mi)) return false;
+    wd[i] = mi;
+    M += mi;
+  }
+  for (int i = 0; i < n; ++i) wd[i] = wd[i] / M;
+  return true;
+}
+
+// The closed-loop form's a5 term tables, in the order the kernels' own
+// build forms them: per atom its list entries CV by CV, list A before list
+// B; a COM entry carries the weight as the kernels hold it (FP32 walkers:
+// the FP32 weight; list B negated) on the unit separation (offset 12 k), a
+// dihedral or RMSD entry -1 on its atom's gradient row (offset 12 k + 3 i).
+extern "C++" {
+template <typename Real>
+void atom_term_tables(const abp_walker_desc *d, int ncv, std::vector<int> &cnt, std::vector<AtomTerm<Real>> &terms) {
+  cnt.assign(d->natoms, 0);
+  terms.assign((size_t)d->natoms * kAtomTerms, AtomTerm<Real>{(Real)0, 0});
+  for (int k = 0; k < ncv; ++k) {
+    const abp_cv_desc &c = d->cv[k];
+    const bool com = c.type == ABP_CV_COM_DIST;
+    for (int l = 0; l < (com ? 2 : 1); ++l) {
+      const int n = l ? c.n_b : (c.type == ABP_CV_DIHEDRAL ? 4 : c.n_a);
+      const int32_t *list = l ? c.idx_b : c.idx_a;
+      std::vector<double> wd;
+      if (com) com_weights(c, l, wd);
+      for (int i = 0; i < n; ++i) {
+        const int at = list[i];
+        Real wt = (Real)-1;
+        if (com) {
+          wt = sizeof(Real) == 4 ? (Real)(float)wd[i] : (Real)wd[i];
+          if (l) wt = -wt;
+        }
+        terms[(size_t)at * kAtomTerms + cnt[at]] = AtomTerm<Real>{wt, k * 12 + (com ? 0 : 3 * i)};
+        cnt[at] += 1;
+      }
+    }
+  }
+}
+}  // extern "C++"
+
 abp_status build_cv(abp_walker *w, const abp_cv_desc &c, int k, int natoms, CvDev *out) {
   CvDev cv{};
   cv.type = c.type;
@@ -641,19 +691,11 @@ abp_status build_cv(abp_walker *w, const abp_cv_desc &c, int k, int natoms, CvDe
     // weights m_i / M_group, computed once in FP64
     for (int grp = 0; grp < 2; ++grp) {
       int n = grp ? cv.nb : cv.na;
-      const double *m = grp ? c.mass_b : c.mass_a;
-      std::vector<double> wd(n);
-      double M = 0;
-      for (int i = 0; i < n; ++i) {
-        double mi = m ? m[i] : 1.0;
-        if (!(mi > 0) || !std::isfinite(mi)) return fail(ABP_ERR_INVALID_ARG, "CV %d: masses must be > 0", k);
-        wd[i] = mi;
-        M += mi;
-      }
+      std::vector<double> wd;
+      if (!com_weights(c, grp, wd)) return fail(ABP_ERR_INVALID_ARG, "CV %d: masses must be > 0", k);
       std::vector<float> wf(n);
       bool equal = true;
       for (int i = 0; i < n; ++i) {
-        wd[i] = wd[i] / M;
         wf[i] = (float)wd[i];
         equal = equal && wd[i] == wd[0];
       }
@@ -773,6 +815,28 @@ abp_status abp_walker_create(abp_ctx *ctx, abp_grid *grid, const abp_walker_desc
   // for one shared-memory walker group (FP32, at most one CN)
   w->big = grid->desc.shared || run_group_bytes(hd, fp64, 32, 0, false) > 227 * 1024;
   w->win = !w->big && window_eligible(hd, fp64);
+  if (w->win) {
+    // the closed-loop form's a5 term tables (read, not rebuilt, by each launch)
+    std::vector<int> tcnt;
+    void *pc = nullptr, *pt = nullptr;
+    if (fp64) {
+      std::vector<AtomTerm<double>> tt;
+      atom_term_tables<double>(d, ncv, tcnt, tt);
+      st = upload(w, tt.data(), tt.size() * sizeof(AtomTerm<double>), &pt);
+    } else {
+      std::vector<AtomTerm<float>> tt;
+      atom_term_tables<float>(d, ncv, tcnt, tt);
+      st = upload(w, tt.data(), tt.size() * sizeof(AtomTerm<float>), &pt);
+    }
+    if (st == ABP_OK) st = upload(w, tcnt.data(), tcnt.size() * sizeof(int), &pc);
+    if (st) {
+      walker_free(w);
+      delete w;
+      return st;
+    }
+    hd.acnt = static_cast<const int *>(pc);
+    hd.aterms = pt;
+  }
   if ((mabp || w->has_rmsd) && w->big) {
     walker_free(w);
     delete w;

@@ -95,6 +95,11 @@ struct WalkerDev {
   void *fbuf;        // library-owned force records (abp_step -> abp_forces)
   void *jscratch;    // library-owned Jacobian scratch (plain form)
   WalkerState *state;
+  // a5 term tables of the closed-loop form, built at walker creation (or
+  // null): per atom its count and kAtomTerms AtomTerm<Real> records, in CV
+  // order, list A before list B
+  const int *acnt;
+  const void *aterms;
 };
 
 // Closed-loop dynamics of abp_md_run (device copy of abp_md_desc, with the

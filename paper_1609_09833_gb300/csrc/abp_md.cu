@@ -272,20 +272,22 @@ __global__ void __launch_bounds__(256, 1) k_md(MdRunArgs a) {
   GroupFixed<Real> *fx = reinterpret_cast<GroupFixed<Real> *>(base);
   unsigned char *dyn = base + md_fixed_bytes<Real>();
   const TableEntry te = ra.table[slot];
+  // The launch's global reads go out in one wave: the descriptor's copy, and
+  // beside it (read from the global descriptor itself) the CV atom lists and
+  // COM weights, the a5 term tables and the atoms.
+  const WalkerDev *gw = te.wd;
   {
-    const int *s = reinterpret_cast<const int *>(te.wd);
+    const int *s = reinterpret_cast<const int *>(gw);
     int *d = reinterpret_cast<int *>(&fx->wd);
     for (int i = tg; i < (int)(sizeof(WalkerDev) / 4); i += 128) d[i] = s[i];
   }
-  gg.sync();
-  const WalkerDev &wd = fx->wd;
-  const int natoms = wd.natoms;
-  const MdLayout L = md_layout(natoms, wd.cv, DIM, sizeof(Real) == 8);
+  const int natoms = gw->natoms;
+  const MdLayout L = md_layout(natoms, gw->cv, DIM, sizeof(Real) == 8);
   {
     // the CV atom lists (and COM weights) into shared memory
     unsigned char *cur = dyn + L.lists;
     for (int k = 0; k < DIM; ++k) {
-      const CvDev &c = wd.cv[k];
+      const CvDev &c = gw->cv[k];
       int32_t *ia = reinterpret_cast<int32_t *>(cur);
       int32_t *ib = ia + c.na;
       for (int i = tg; i < c.na; i += 128) ia[i] = c.ia[i];
@@ -307,14 +309,21 @@ __global__ void __launch_bounds__(256, 1) k_md(MdRunArgs a) {
       }
     }
   }
-  gg.sync();
   R4 *xs = reinterpret_cast<R4 *>(dyn + L.xs);
   StepRec<Real> &st = *reinterpret_cast<StepRec<Real> *>(dyn + L.st);
   int *cnt = reinterpret_cast<int *>(dyn + L.cnt);
   AtomTerm<Real> *terms = reinterpret_cast<AtomTerm<Real> *>(dyn + L.terms);
-  if (!producer) build_atom_terms<Real>(g, fx, cnt, terms);
+  const bool tables = gw->acnt != nullptr;  // the a5 term tables built at walker creation
+  if (tables) {
+    const AtomTerm<Real> *gt = reinterpret_cast<const AtomTerm<Real> *>(gw->aterms);
+    for (int i = tg; i < natoms; i += 128) cnt[i] = gw->acnt[i];
+    for (int i = tg; i < natoms * kAtomTerms; i += 128) terms[i] = gt[i];
+  }
   R4 *cio = reinterpret_cast<R4 *>(const_cast<void *>(ra.coords)) + ra.coff[te.idx];
   for (int i = tg; i < natoms; i += 128) xs[i] = cio[i];
+  gg.sync();
+  const WalkerDev &wd = fx->wd;
+  if (!tables && !producer) build_atom_terms<Real>(g, fx, cnt, terms);
   R4 *fout = ra.forces ? reinterpret_cast<R4 *>(ra.forces) + ra.foff[te.idx] : reinterpret_cast<R4 *>(wd.fbuf);
   const int fmode = ra.forces ? ra.mode : ABP_FORCES_OVERWRITE;
   R4 *tout = a.traj ? reinterpret_cast<R4 *>(a.traj) + a.toff[te.idx] : nullptr;
