@@ -725,7 +725,7 @@ def bench_serve(abp, synth, torch, dev, seconds=2.0, rate=20_000.0):
         # the moment the last forces were in the caller's buffer
         # (abp_result.t_submit / t_done), so the Python poller's wake-ups do
         # not enter it; the wall-clock figure seen from Python is kept beside.
-        depth = 8
+        depth = 16
         reps = []
         tw0 = None
         for rep in range(6):  # the first is a warm-up (its slabs are allocated and faulted in)
