@@ -481,6 +481,18 @@ abp_status abp_server_times(abp_server *srv, double *fill_s, double *launch_s, d
 /* Host steady-clock seconds (the clock of abp_result). */
 double abp_server_now(void);
 
+/* ---- checked build -------------------------------------------------------- */
+
+/* The library compiled with -DABP_CHECKED (paper_1609_09833_gb300.build,
+ * checked=True) checks every grid node index its kernels read or write:
+ * an index outside its grid is counted here and replaced by node 0, so the
+ * access stays inside the grid's allocation (the substitute for a device
+ * memory checker). Waits for the context stream, then returns the count
+ * since the context was created in *count and whether this library is the
+ * checked build in *checked (the normal build always counts 0). Either
+ * pointer may be NULL. */
+abp_status abp_checked_violations(abp_ctx *ctx, uint64_t *count, int *checked);
+
 /* ---- allocation-free step -------------------------------------------------- */
 
 /* abp_step_static: one MD step (a1..a5) of one walker, allocating nothing on

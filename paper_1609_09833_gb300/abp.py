@@ -164,6 +164,7 @@ _SIGS = {
     "abp_server_times": [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
                          C.POINTER(C.c_double)],
     "abp_server_now": [],
+    "abp_checked_violations": [_vp, C.POINTER(C.c_uint64), C.POINTER(C.c_int)],
     "abp_fp32_fma_peak": [C.c_int, _vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)],
     "abp_kernel_times": [_vp, C.POINTER(KernelTime), C.c_int, C.POINTER(C.c_int)],
     "abp_last_error": [],
@@ -176,7 +177,9 @@ _lib_handle = None
 
 
 def lib_path() -> str:
-    return _build.LIB
+    """The in-tree library; ABP_LIBRARY names another build of it (the
+    checked build, for instance)."""
+    return os.environ.get("ABP_LIBRARY") or _build.LIB
 
 
 def load():
@@ -477,6 +480,13 @@ def abp_server_times(srv):
     v = [C.c_double() for _ in range(4)]
     _check(load().abp_server_times(srv, *[C.byref(x) for x in v]))
     return {"fill": v[0].value, "launch": v[1].value, "complete": v[2].value, "wait": v[3].value}
+
+
+def abp_checked_violations(ctx):
+    """(out-of-grid node indices counted, whether the library is the checked build)."""
+    n, chk = C.c_uint64(), C.c_int()
+    _check(load().abp_checked_violations(ctx, C.byref(n), C.byref(chk)))
+    return int(n.value), bool(chk.value)
 
 
 def abp_server_now() -> float:

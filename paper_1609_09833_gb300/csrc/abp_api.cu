@@ -508,6 +508,7 @@ abp_status abp_create_grid(abp_ctx *ctx, const abp_grid_desc *d, abp_grid **out)
   }
   gd.shared = d->shared ? 1 : 0;
   gd.shadow = nullptr;
+  gd.oob = &ctx->ctr->oob;  // device address of the context's counter
   if (gd.shared) {
     g->shadow_bytes = (size_t)nodes * 4 * sizeof(double);
     void *p = nullptr;
@@ -2402,6 +2403,22 @@ abp_status abp_server_submit_many(abp_server *s, int n, const int64_t *sims, con
     }
     s->cv_work.notify_one();
   }
+  return ABP_OK;
+}
+
+abp_status abp_checked_violations(abp_ctx *ctx, uint64_t *count, int *checked) {
+  if (!ctx) return fail(ABP_ERR_INVALID_ARG, "ctx is NULL");
+  abp_status st = set_device(ctx);
+  if (st) return st;
+  CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  unsigned long long n = 0;
+  CUDA_TRY(cudaMemcpy(&n, &ctx->ctr->oob, sizeof n, cudaMemcpyDeviceToHost));
+  if (count) *count = (uint64_t)n;
+#ifdef ABP_CHECKED
+  if (checked) *checked = 1;
+#else
+  if (checked) *checked = 0;
+#endif
   return ABP_OK;
 }
 

@@ -503,6 +503,7 @@ __global__ void __launch_bounds__(kBigThreads) k_big_cvs(const BigItem *walkers,
         mul *= gd.n[k];
       }
       double v;
+      node = chk_node(gd, node);
       if (gd.shared) {
         v = gd.shadow[node * 4];
       } else {
@@ -593,7 +594,7 @@ __global__ void __launch_bounds__(kBigThreads) k_big_deposit(const BigItem *walk
     if (d > 1) G = G * fx->tabG[1][o1];
     if (d > 2) G = G * fx->tabG[2][o2];
     float d0 = fx->tabD[0][o0], d1 = d > 1 ? fx->tabD[1][o1] : 0.f, d2 = d > 2 ? fx->tabD[2][o2] : 0.f;
-    long long node = j0 + n0 * j1 + n01 * j2;
+    const long long node = chk_node(gd, j0 + n0 * j1 + n01 * j2);
     if (gd.shared) {
       double *p = gd.shadow + node * 4;
       atomicAdd(p, (double)G);
@@ -625,7 +626,7 @@ __global__ void __launch_bounds__(kBigThreads) k_big_refresh(const BigItem *walk
     int j1 = d > 1 ? fx->tabJ[1][o1] : 0;
     int j2 = d > 2 ? fx->tabJ[2][o2] : 0;
     if ((j0 | j1 | j2) < 0) continue;
-    long long node = j0 + n0 * j1 + n01 * j2;
+    const long long node = chk_node(gd, j0 + n0 * j1 + n01 * j2);
     const double *p = gd.shadow + node * 4;
     float hi[4], lo[4];
     for (int q = 0; q < 4; ++q) {
@@ -869,7 +870,7 @@ __global__ void __launch_bounds__(kBigThreads) k_apply_hills(const WalkerDev *sh
     int j1 = d > 1 ? fx->tabJ[1][o1] : 0;
     int j2 = d > 2 ? fx->tabJ[2][o2] : 0;
     if ((j0 | j1 | j2) < 0) continue;
-    long long node = j0 + n0 * j1 + n01 * j2;
+    const long long node = chk_node(gd, j0 + n0 * j1 + n01 * j2);
     double *p = gd.shadow + node * 4;
     if (!refresh) {
       float G = hf * fx->tabG[0][o0];

@@ -179,6 +179,21 @@ __device__ __forceinline__ double rcp_fast<double>(double x) {
 }
 
 // Error-free sum a + b = s + e (two-sum); exact in round-to-nearest.
+// A grid node index about to be read or written. The checked build
+// (compiled with -DABP_CHECKED, the substitute for a memory checker) counts
+// an index outside [0, nodes) in the context's counters and returns node 0,
+// so that the access stays inside the grid; the normal build returns the
+// index unchanged.
+__device__ __forceinline__ long long chk_node(const GridDev &gd, long long node) {
+#ifdef ABP_CHECKED
+  if (node < 0 || node >= gd.nodes) {
+    if (gd.oob) atomicAdd(gd.oob, 1ull);
+    return 0;
+  }
+#endif
+  return node;
+}
+
 template <typename Real>
 __device__ __forceinline__ void two_sum(Real a, Real b, Real &s, Real &e);
 template <>
@@ -998,7 +1013,8 @@ __device__ void tile_load(const Grp &g, GroupFixed<Real> *fx, const GroupLayout 
   for (int r2 = 0; r2 < T2; ++r2) {
     int jj1 = j1;
     for (int r1 = 0; r1 < T1; ++r1) {
-      const unsigned char *row = grid + j2 * plane_stride + jj1 * row_stride;
+      const unsigned char *row =
+          grid + chk_node(gd, (long long)j2 * (gd.d > 1 ? gd.n[1] : 1) * n0 + (long long)jj1 * n0) * rb;
       unsigned char *dst = tile + ((size_t)r2 * T1 + r1) * T0 * rb;
       for (int p = g.t; p < pieces_row; p += g.G) {
         const unsigned char *src =
@@ -1064,7 +1080,8 @@ __device__ __forceinline__ const unsigned char *corner_ptr(const GroupFixed<Real
       mul *= gd.n[k];
     }
   }
-  return (TILE ? tile : reinterpret_cast<const unsigned char *>(gd.rec)) + node * gd.rec_bytes;
+  return TILE ? tile + node * gd.rec_bytes
+              : reinterpret_cast<const unsigned char *>(gd.rec) + chk_node(gd, node) * gd.rec_bytes;
 }
 
 // a2: V_b(s_t) from the grid before the deposit, in FP64, by warp 0's first
@@ -1257,7 +1274,7 @@ __device__ void deposit_stencil(const Grp &g, GroupFixed<Real> *fx, const GroupL
       d0v[u] = fx->tabD[0][o0];
       d1v[u] = d > 1 ? fx->tabD[1][o1] : (Real)0;
       d2v[u] = d > 2 ? fx->tabD[2][o2] : (Real)0;
-      ptr[u] = grid + (j0 + n0 * j1 + n01 * j2) * rb;
+      ptr[u] = grid + chk_node(gd, (long long)j0 + (long long)n0 * j1 + (long long)n01 * j2) * rb;
       if (TILE) {
         int t0 = tile_rel(gd, L, fx->org, 0, j0);
         int t1 = d > 1 ? tile_rel(gd, L, fx->org, 1, j1) : 0;

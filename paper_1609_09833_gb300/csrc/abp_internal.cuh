@@ -52,6 +52,7 @@ struct GridDev {
   void *rec;         // node records (see GridLayout below)
   int shared;        // several walkers deposit per step (see shadow)
   double *shadow;    // shared grids: FP64 accumulator, 4 doubles per node {V, dV0, dV1, dV2}
+  unsigned long long *oob;  // checked builds: the context's count of out-of-grid node indices
 };
 
 // Node record layouts:
@@ -126,7 +127,9 @@ struct DepositLog {
 // Context-wide device counters.
 struct DevCounters {
   int nonfinite;
-  int pad[31];
+  int pad0;
+  unsigned long long oob;  // checked builds (ABP_CHECKED): node indices found outside their grid
+  int pad[28];
 };
 
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }

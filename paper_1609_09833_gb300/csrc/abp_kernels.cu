@@ -291,7 +291,7 @@ __device__ __forceinline__ long long box_node_off(const GridDev &gd, int b0, int
       in = in && j1 >= 0 && j1 < gd.n[1];
     }
   }
-  return in ? (j0 + (DIM > 1 ? (long long)gd.n[0] * j1 : 0)) * rb : -1;
+  return in ? chk_node(gd, j0 + (DIM > 1 ? (long long)gd.n[0] * j1 : 0)) * rb : -1;
 }
 
 // Named barrier `id` of `n` threads: arrive without waiting (after this
@@ -606,7 +606,7 @@ struct WindowCtx {
         node += mul * j;
         mul *= gd.n[k];
       }
-      return rec + node * rb;
+      return rec + chk_node(gd, node) * rb;
     };
     // steps read from the box (bit j), the rest from the grid
     unsigned inbox = 0;

@@ -223,7 +223,7 @@ __device__ __forceinline__ Real corner_weight(const StepRec<Real> &st, int c) {
 
 template <int DIM>
 __device__ __forceinline__ const unsigned char *node_ptr(const GridDev &gd, long long node) {
-  return reinterpret_cast<const unsigned char *>(gd.rec) + node * (DIM > 1 ? 32 : 16);
+  return reinterpret_cast<const unsigned char *>(gd.rec) + chk_node(gd, node) * (DIM > 1 ? 32 : 16);
 }
 
 // a4 of one step, part 1: the 2^d corners' records, loaded together.
