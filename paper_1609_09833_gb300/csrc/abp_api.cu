@@ -1068,6 +1068,7 @@ static abp_status run_common(abp_ctx *ctx, abp_walker *const *walkers, int n, co
     a.log = ctx->log;
     a.ctr = ctx->ctr;
     const char *kname = win ? "k_win" : (a.lean && a.tile_budget == 0 ? "k_run_lean" : "k_run");
+    NvtxRange nv(kname);
     if (ctx->timer) ctx->timer->begin(kname, ctx->stream);
     cudaError_t e = launch_run(a, fp64, ctx->stream);
     if (ctx->timer) ctx->timer->end(kname, ctx->stream);
@@ -1213,6 +1214,7 @@ abp_status abp_md_run(abp_ctx *ctx, abp_walker *const *walkers, int n, void *coo
     a.traj = traj_dev;
     a.toff = reinterpret_cast<const long long *>(traj_offsets_dev);
     a.tstride = traj_step_stride;
+    NvtxRange nv("k_md");
     if (ctx->timer) ctx->timer->begin("k_md", ctx->stream);
     cudaError_t e = launch_md(a, fp64, dim, ctx->stream);
     if (ctx->timer) ctx->timer->end("k_md", ctx->stream);
@@ -1314,6 +1316,7 @@ abp_status abp_step_plain(abp_ctx *ctx, abp_walker *const *walkers, int n, const
   a.step = step;
   a.log = ctx->log;
   a.ctr = ctx->ctr;
+  NvtxRange nv("plain form");
   cudaError_t e = launch_plain(a, fp64, ctx->stream);
   if (e != cudaSuccess) return fail(ABP_ERR_CUDA, "plain launch: %s", cudaGetErrorString(e));
   return ABP_OK;
@@ -1990,7 +1993,10 @@ int srv_launch(abp_server *s, SrvSlot &sl) {
   a.nsteps = 1;
   a.log = s->ctx->log;
   a.ctr = s->ctx->ctr;
-  if (launch_run(a, 0, stream) != cudaSuccess) return ABP_ERR_CUDA;
+  {
+    NvtxRange nv("server launch");
+    if (launch_run(a, 0, stream) != cudaSuccess) return ABP_ERR_CUDA;
+  }
   if (cudaEventRecord(sl.kdone, stream) != cudaSuccess) return ABP_ERR_CUDA;
   if (cudaMemcpyAsync(sl.h_out, sl.d_out, (size_t)off * 16, cudaMemcpyDeviceToHost, stream) != cudaSuccess)
     return ABP_ERR_CUDA;

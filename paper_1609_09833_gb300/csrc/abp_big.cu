@@ -784,10 +784,12 @@ cudaError_t launch_big_step(const BigArgs &a, cudaStream_t st) {
   const int ph = a.phases ? a.phases : 31;
   LaunchTimer *tm = a.timer;
   auto t0 = [&](const char *k) {
+    nvtxRangePushA(k);
     if (tm) tm->begin(k, st);
   };
   auto t1 = [&](const char *k) {
     if (tm) tm->end(k, st);
+    nvtxRangePop();
   };
   cudaError_t e;
   if ((ph & 1) && a.ncn_items > 0) {

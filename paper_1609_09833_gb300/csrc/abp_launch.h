@@ -5,10 +5,21 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "abp_internal.cuh"
 
 namespace abp {
+
+// An NVTX range named after the kernel around each of the library's launches
+// (header-only NVTX: a no-op unless a profiler attaches), so that a timeline
+// or an NVTX-filtered ncu capture finds the launches by name.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Optional per-kernel timing of a context (abp_ctx_tune ABP_TUNE_TIMING): the
 // launchers bracket each kernel launch with begin/end, which record CUDA
