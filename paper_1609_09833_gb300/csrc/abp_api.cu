@@ -160,6 +160,10 @@ struct abp_walker {
   bool big = false;    // runs in the phased form (shared grid, or too large for a walker group)
   bool win = false;    // runs in the windowed form of the fused kernel (COM distance / dihedral CVs)
   bool has_rmsd = false;
+  // the closed-loop kernel's register-fed form applies: FP32, at most 64
+  // atoms of at most two a5 terms each, COM groups of at most 16 atoms, the
+  // other CVs dihedrals
+  bool md_fast = false;
   long long cost = 0;  // rough work estimate used to order batched launches
 };
 
@@ -828,6 +832,12 @@ abp_status abp_walker_create(abp_ctx *ctx, abp_grid *grid, const abp_walker_desc
       std::vector<AtomTerm<float>> tt;
       atom_term_tables<float>(d, ncv, tcnt, tt);
       st = upload(w, tt.data(), tt.size() * sizeof(AtomTerm<float>), &pt);
+      bool fast = d->natoms <= 64;
+      for (int c : tcnt) fast = fast && c <= 2;
+      for (int k = 0; k < ncv; ++k)
+        fast = fast && ((d->cv[k].type == ABP_CV_COM_DIST && d->cv[k].n_a <= 16 && d->cv[k].n_b <= 16) ||
+                        d->cv[k].type == ABP_CV_DIHEDRAL);
+      w->md_fast = fast;
     }
     if (st == ABP_OK) st = upload(w, tcnt.data(), tcnt.size() * sizeof(int), &pc);
     if (st) {
@@ -1214,9 +1224,11 @@ abp_status abp_md_run(abp_ctx *ctx, abp_walker *const *walkers, int n, void *coo
     a.traj = traj_dev;
     a.toff = reinterpret_cast<const long long *>(traj_offsets_dev);
     a.tstride = traj_step_stride;
+    bool fast = !fp64;
+    for (abp_walker *w : lw) fast = fast && w->md_fast;
     NvtxRange nv("k_md");
     if (ctx->timer) ctx->timer->begin("k_md", ctx->stream);
-    cudaError_t e = launch_md(a, fp64, dim, ctx->stream);
+    cudaError_t e = launch_md(a, fp64, dim, fast, ctx->stream);
     if (ctx->timer) ctx->timer->end("k_md", ctx->stream);
     if (e != cudaSuccess) return fail(ABP_ERR_CUDA, "closed-loop launch: %s", cudaGetErrorString(e));
   }

@@ -246,11 +246,16 @@ __device__ __forceinline__ void grp_sum_ff(const Grp &g, Real &h, Real &l, Real 
 
 // The end of an FP32 COM distance in hi + lo arithmetic: d = (r_B - r_A) +
 // (B - A), r_G each group's first atom and G + Gl its weighted offset sum
-// (hi + lo), the first atoms' difference and the sums' difference formed
-// exactly; a minimum image in a periodic box; r^2 = sum d^2 in hi + lo and
-// s = sqrt(r^2) with one Newton correction (sh + sl); u = d / s in FP32. A
-// hill two grid spacings wide on a fine grid needs s to ~1e-6 of its width,
-// below the resolution of one FP32 number near 1 nm.
+// (hi + lo, not necessarily normalised), the first atoms' difference and the
+// sums' difference formed exactly; a minimum image in a periodic box;
+// r^2 = sum d^2 as an FP32 sum S of the squares' high parts plus their
+// exact errors and low terms (Ogita, Rump and Oishi's Sum2 kept unrounded),
+// and s = sh + sl from an approximate root sh = S / sqrt(S) corrected by one
+// Newton step on the residual S + r2l - sh^2 (exact by fma); u = d / s in
+// FP32. A hill two grid spacings wide on a fine grid needs s to ~1e-6 of its
+// width, below the resolution of one FP32 number near 1 nm. The chain is
+// kept short (each value's low part rides beside it unnormalised): it is
+// the longest dependency of a COM-distance step.
 __device__ __forceinline__ int com_finish_ff(const CvDev &c, const float *ra, const float *ah, const float *al,
                                              const float *rb, const float *bh, const float *bl, float &sh, float &sl,
                                              float *u) {
@@ -264,12 +269,15 @@ __device__ __forceinline__ int com_finish_ff(const CvDev &c, const float *ra, co
     if (c.wc_b != 0.f) ff_add<float>(gbh, gbl, __fmul_rn(gbh, c.wc_b), 0.f);
     two_sum<float>(rb[q], -ra[q], rdh, rdl);
     two_sum<float>(gbh, -gah, t, te);
-    te = __fadd_rn(te, __fsub_rn(gbl, gal));
     two_sum<float>(rdh, t, s1, e1);
-    e1 = __fadd_rn(e1, __fadd_rn(rdl, te));
-    dh[q] = __fadd_rn(s1, e1);
-    dl[q] = __fsub_rn(e1, __fsub_rn(dh[q], s1));
+    // every low term is far below s1 unless d itself is (a coincidence of
+    // the two centres, where the direction u carries no information)
+    dh[q] = s1;
+    dl[q] = __fadd_rn(__fadd_rn(e1, te), __fadd_rn(rdl, __fsub_rn(gbl, gal)));
     if (c.pbc) {
+      const float n = __fadd_rn(dh[q], dl[q]);
+      dl[q] = __fsub_rn(dl[q], __fsub_rn(n, dh[q]));
+      dh[q] = n;
       const float shift = __fmul_rn((float)c.box[q], floorf(__fmaf_rn(dh[q], (float)c.inv_box[q], 0.5f)));
       float t2, te2;
       two_sum<float>(dh[q], -shift, t2, te2);
@@ -277,24 +285,29 @@ __device__ __forceinline__ int com_finish_ff(const CvDev &c, const float *ra, co
       dl[q] = __fadd_rn(dl[q], te2);
     }
   }
-  float r2h = 0.f, r2l = 0.f;
+  float p[3], e[3];
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
-    const float p = __fmul_rn(dh[q], dh[q]);
-    const float e = __fmaf_rn(dh[q], dh[q], -p) + 2.f * dh[q] * dl[q];
-    ff_add<float>(r2h, r2l, p, e);
+    p[q] = __fmul_rn(dh[q], dh[q]);
+    e[q] = __fmaf_rn(__fmul_rn(2.f, dh[q]), dl[q], __fmaf_rn(dh[q], dh[q], -p[q]));
   }
-  const float rh = sqrtf(r2h);
-  sh = rh;
-  if (rh > 0.f) {
-    // the correction is a few units in the last place of rh, and u only
-    // needs FP32 accuracy: a fast reciprocal serves both
-    const float ir = __fdividef(1.f, rh);
-    sl = __fmul_rn(__fadd_rn(__fmaf_rn(-rh, rh, r2h), r2l), 0.5f * ir);
+  float S1, c1, S, c2;
+  two_sum<float>(p[0], p[1], S1, c1);
+  two_sum<float>(S1, p[2], S, c2);
+  const float r2l = __fadd_rn(__fadd_rn(c1, c2), __fadd_rn(__fadd_rn(e[0], e[1]), e[2]));
+  if (S > 0.f) {
+    // ir ~ 1 / sqrt(S) to a few units in the last place; the Newton step
+    // makes sh + sl the root of S + r2l to ~2^-44 whatever sh's last bits,
+    // and u only needs FP32 accuracy
+    const float ir = rsqrtf(S);
+    const float rh = __fmul_rn(S, ir);
+    sh = rh;
+    sl = __fmul_rn(__fadd_rn(__fmaf_rn(-rh, rh, S), r2l), __fmul_rn(0.5f, ir));
 #pragma unroll
     for (int q = 0; q < 3; ++q) u[q] = __fmul_rn(dh[q], ir);
     return 0;
   }
+  sh = S == S ? 0.f : S;  // coincident centres: 0; non-finite coordinates: NaN
   sl = 0.f;
 #pragma unroll
   for (int q = 0; q < 3; ++q) u[q] = 0.f;
@@ -429,21 +442,13 @@ __device__ __forceinline__ double dihedral_angle64(const CvDev &c, const float (
   return atan2(sqrt(dot3<double>(b2, b2)) * dot3<double>(b1, n), dot3<double>(m, n));
 }
 
-// Dihedral of atoms 1-2-3-4: phi = atan2(|b2| b1.(b2 x b3), (b1 x b2).(b2 x b3)),
-// gradient in the Blondel-Karplus form. One thread (the last thread of the
-// group, so that with several warps it overlaps the COM work of warp 0).
+// Dihedral of atoms 1-2-3-4 at positions x: phi = atan2(|b2| b1.(b2 x b3),
+// (b1 x b2).(b2 x b3)), gradient in the Blondel-Karplus form, by one thread.
 // phi_lo receives the low part of the angle: 0, or with c.hp (FP32 walkers)
 // the FP64 angle's remainder after its FP32 rounding phi.
 template <typename Real>
-__device__ __forceinline__ int dihedral_eval(const CvDev &c, const int32_t *ia, const typename Rec4<Real>::T *xs,
-                                             Real &phi, Real (*grad)[3], Real &phi_lo) {
-  Real x[4][3];
-  for (int a = 0; a < 4; ++a) {
-    auto p = xs[ia[a]];
-    x[a][0] = p.x;
-    x[a][1] = p.y;
-    x[a][2] = p.z;
-  }
+__device__ __forceinline__ int dihedral_core(const CvDev &c, const Real (&x)[4][3], Real &phi, Real (*grad)[3],
+                                             Real &phi_lo) {
   phi_lo = 0;
   Real b1[3], b2[3], b3[3], m[3], n[3];
   for (int q = 0; q < 3; ++q) {
@@ -489,6 +494,21 @@ __device__ __forceinline__ int dihedral_eval(const CvDev &c, const int32_t *ia, 
     grad[2][q] = -(1 + r) * g4 + p * g1;
   }
   return 0;
+}
+
+// The dihedral of the atoms ia[0..3] of xs (dihedral_core).
+template <typename Real>
+__device__ __forceinline__ int dihedral_eval(const CvDev &c, const int32_t *ia, const typename Rec4<Real>::T *xs,
+                                             Real &phi, Real (*grad)[3], Real &phi_lo) {
+  Real x[4][3];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    auto p = xs[ia[a]];
+    x[a][0] = p.x;
+    x[a][1] = p.y;
+    x[a][2] = p.z;
+  }
+  return dihedral_core<Real>(c, x, phi, grad, phi_lo);
 }
 
 template <typename Real>

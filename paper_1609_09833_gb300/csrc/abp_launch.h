@@ -127,7 +127,7 @@ struct MdRunArgs {
 
 // Closed-loop form of walkers whose CVs a thread evaluates (abp_md.cu).
 int md_group_bytes(const WalkerDev &hd, int fp64);
-cudaError_t launch_md(const MdRunArgs &a, int fp64, int dim, cudaStream_t st);
+cudaError_t launch_md(const MdRunArgs &a, int fp64, int dim, bool fast, cudaStream_t st);
 
 size_t big_scratch_bytes(const WalkerDev &hd);
 // The force phase's per-atom term table of a phased-form walker (host side;

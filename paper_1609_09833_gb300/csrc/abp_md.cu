@@ -72,48 +72,44 @@ __host__ __device__ inline MdLayout md_layout(int natoms, const CvDev *cv, int d
   return L;
 }
 
-// A COM distance by one warp: group A's atoms on lanes 0-15 and group B's on
-// lanes 16-31 (stride 16), each lane's weighted offsets from its group's
-// first atom summed (FP32: compensated, as com_sum), the half-warps' partial
-// sums combined by a butterfly (FP32: in hi + lo), then finished on lane 0
-// (com_finish). Every lane of the warp calls it; lane 0 returns the CV.
+// One weighted offset w (p - p0) added to a lane's COM sum (FP32: Kahan).
 template <typename Real>
-__device__ __forceinline__ int com_warp(const CvDev &c, const int32_t *ia, const int32_t *ib, const Real *wa,
-                                        const Real *wb, const typename Rec4<Real>::T *x, int lane, Real &s, Real &sl,
-                                        Real *u) {
-  const bool gb = lane >= 16;
-  const int32_t *list = gb ? ib : ia;
-  const Real *wts = gb ? wb : wa;
-  const int n = gb ? c.nb : c.na;
-  const auto p0 = x[list[0]];
-  Real h[3] = {0, 0, 0}, l[3] = {0, 0, 0};
-  for (int i = lane & 15; i < n; i += 16) {
-    const Real w = wts[i];
-    const auto p = x[list[i]];
-    const Real d[3] = {sub_rn(p.x, p0.x), sub_rn(p.y, p0.y), sub_rn(p.z, p0.z)};
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      if constexpr (sizeof(Real) == 4) {
-        const Real y = fma_rn(w, d[q], -l[q]);
-        const Real t = add_rn(h[q], y);
-        l[q] = sub_rn(sub_rn(t, h[q]), y);
-        h[q] = t;
-      } else {
-        h[q] = fma_rn(w, d[q], h[q]);
-      }
-    }
-  }
+__device__ __forceinline__ void com_term(Real w, const typename Rec4<Real>::T &p, const typename Rec4<Real>::T &p0,
+                                         Real *h, Real *l) {
+  const Real d[3] = {sub_rn(p.x, p0.x), sub_rn(p.y, p0.y), sub_rn(p.z, p0.z)};
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
     if constexpr (sizeof(Real) == 4) {
-      Real s2, e2;
-      two_sum<Real>(h[q], -l[q], s2, e2);  // Kahan's compensation holds minus the lost part
-      h[q] = s2;
-      l[q] = e2;
+      const Real y = fma_rn(w, d[q], -l[q]);
+      const Real t = add_rn(h[q], y);
+      l[q] = sub_rn(sub_rn(t, h[q]), y);
+      h[q] = t;
+    } else {
+      h[q] = fma_rn(w, d[q], h[q]);
+    }
+  }
+}
+
+// The half-warps' sums of a COM distance combined and finished (com_warp).
+template <typename Real>
+__device__ __forceinline__ int com_warp_end(const CvDev &c, const typename Rec4<Real>::T &p0, Real *h, Real *l,
+                                            int lane, Real &s, Real &sl, Real *u) {
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    if constexpr (sizeof(Real) == 4) {
+      // Kahan's compensation holds minus the lost part. Each level adds the
+      // partner's pair as s = h + oh with its exact error (two_sum) going to
+      // the low part, left unnormalised: the high parts' chain is one add
+      // per level, and both partners form the same bits (a + b and the
+      // exact error of a + b do not depend on the order)
+      l[q] = -l[q];
 #pragma unroll
       for (int o = 8; o > 0; o >>= 1) {
         const Real oh = __shfl_xor_sync(0xffffffffu, h[q], o), ol = __shfl_xor_sync(0xffffffffu, l[q], o);
-        ff_add<Real>(h[q], l[q], oh, ol);
+        Real sq, eq;
+        two_sum<Real>(h[q], oh, sq, eq);
+        h[q] = sq;
+        l[q] = add_rn(add_rn(l[q], ol), eq);
       }
     } else {
 #pragma unroll
@@ -132,6 +128,37 @@ __device__ __forceinline__ int com_warp(const CvDev &c, const int32_t *ia, const
   if (lane != 0) return 0;
   const Real a0[3] = {p0.x, p0.y, p0.z};
   return com_finish<Real>(c, a0, h, l, b0, bh, bl, s, sl, u);
+}
+
+// A COM distance by one warp: group A's atoms on lanes 0-15 and group B's on
+// lanes 16-31 (stride 16), each lane's weighted offsets from its group's
+// first atom summed (FP32: compensated, as com_sum), the half-warps' partial
+// sums combined by a butterfly (FP32: in hi + lo, the low parts unnormalised),
+// then finished on lane 0 (com_finish). Every lane of the warp calls it;
+// lane 0 returns the CV.
+template <typename Real>
+__device__ __forceinline__ int com_warp(const CvDev &c, const int32_t *ia, const int32_t *ib, const Real *wa,
+                                        const Real *wb, const typename Rec4<Real>::T *x, int lane, Real &s, Real &sl,
+                                        Real *u) {
+  const bool gb = lane >= 16;
+  const int32_t *list = gb ? ib : ia;
+  const Real *wts = gb ? wb : wa;
+  const int n = gb ? c.nb : c.na;
+  const auto p0 = x[list[0]];
+  Real h[3] = {0, 0, 0}, l[3] = {0, 0, 0};
+  for (int i = lane & 15; i < n; i += 16) com_term<Real>(wts[i], x[list[i]], p0, h, l);
+  return com_warp_end<Real>(c, p0, h, l, lane, s, sl, u);
+}
+
+// com_warp for groups of at most 16 atoms, the lane's atom (or -1), its
+// weight and its group's first atom held in registers across the launch.
+template <typename Real>
+__device__ __forceinline__ int com_warp_reg(const CvDev &c, int first, int atom, Real w,
+                                            const typename Rec4<Real>::T *x, int lane, Real &s, Real &sl, Real *u) {
+  const auto p0 = x[first];
+  Real h[3] = {0, 0, 0}, l[3] = {0, 0, 0};
+  if (atom >= 0) com_term<Real>(w, x[atom], p0, h, l);
+  return com_warp_end<Real>(c, p0, h, l, lane, s, sl, u);
 }
 
 // The end of a4 in the closed-loop form: V and dV/ds_k (mABP: the nearest
@@ -238,7 +265,7 @@ __device__ __noinline__ void md_deposit(const Grp &g, GroupFixed<Real> *fx, cons
 //   hit there; the four warps meet at window boundaries (named barrier
 //   gpc + gid + 1). A step's finiteness check is made on the coordinates as
 //   the move writes them (the launch's first ones before the first step).
-template <typename Real, int DIM, int UNR>
+template <typename Real, int DIM, int UNR, bool FAST>
 __global__ void __launch_bounds__(256, 1) k_md(MdRunArgs a) {
   using R4 = typename Rec4<Real>::T;
   extern __shared__ __align__(32) unsigned char smem[];
@@ -363,6 +390,58 @@ __global__ void __launch_bounds__(256, 1) k_md(MdRunArgs a) {
     if (lane == 0) badw[g.warp] = bad;
   }
   gg.sync();
+  // FAST (every walker of the launch has COM groups of at most 16 atoms,
+  // dihedrals as its other CVs, and at most 64 atoms of at most two a5
+  // terms each): the step chain's loop invariants in registers -- the
+  // lane's COM atom, weight and group head, the dihedral lane's four atoms,
+  // the thread's atom's a5 terms
+  unsigned com_mask = 0;  // bit k: CV k is a COM distance
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) com_mask |= (wd.cv[k].type == ABP_CV_COM_DIST ? 1u : 0u) << k;
+  int cfirst[DIM], catom[DIM], datom[4] = {0, 0, 0, 0};
+  Real cw[DIM];
+  int tne = 0, to0 = 0, to1 = 0, tk0 = 0, tk1 = 0;
+  Real tw0 = 0, tw1 = 0;
+  if (FAST && !producer) {
+    int q = 0;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      cfirst[k] = catom[k] = 0;
+      cw[k] = 0;
+      if ((com_mask >> k) & 1) {
+        const bool gb = lane >= 16;
+        const int n = gb ? wd.cv[k].nb : wd.cv[k].na;
+        const int32_t *list = gb ? fx->ib[k] : fx->ia[k];
+        const Real *wts = gb ? fx->wb[k] : fx->wa[k];
+        cfirst[k] = list[0];
+        if ((lane & 15) < n) {
+          catom[k] = list[lane & 15];
+          cw[k] = wts[lane & 15];
+        } else {
+          catom[k] = -1;
+        }
+      } else {
+        if (lane == q)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) datom[j] = fx->ia[k][j];
+        ++q;
+      }
+    }
+    if (g.t < natoms) {
+      const AtomTerm<Real> *ti = terms + g.t * kAtomTerms;
+      tne = cnt[g.t];
+      if (tne > 0) {
+        to0 = ti[0].off;
+        tw0 = ti[0].w;
+        tk0 = to0 >= 24 ? 2 : (to0 >= 12 ? 1 : 0);
+      }
+      if (tne > 1) {
+        to1 = ti[1].off;
+        tw1 = ti[1].w;
+        tk1 = to1 >= 24 ? 2 : (to1 >= 12 ? 1 : 0);
+      }
+    }
+  }
   for (int w = 0; w < nwin; ++w) {
     if (producer) {
       if (w + 1 < nwin) draw(w + 1);
@@ -406,18 +485,36 @@ __global__ void __launch_bounds__(256, 1) k_md(MdRunArgs a) {
         if (w0) {
 #pragma unroll
           for (int k = 0; k < DIM; ++k)
-            if (wd.cv[k].type == ABP_CV_COM_DIST) {
+            if ((com_mask >> k) & 1) {
               Real sk, slk;
-              const int fl = com_warp<Real>(wd.cv[k], fx->ia[k], fx->ib[k], fx->wa[k], fx->wb[k], xs, lane, sk,
-                                            slk, st.jac[k]);
+              const int fl =
+                  FAST ? com_warp_reg<Real>(wd.cv[k], cfirst[k], catom[k], cw[k], xs, lane, sk, slk, st.jac[k])
+                       : com_warp<Real>(wd.cv[k], fx->ia[k], fx->ib[k], fx->wa[k], fx->wb[k], xs, lane, sk, slk,
+                                        st.jac[k]);
               if (lane == 0) window_cv_rec<Real>(wd, k, sk, slk, fl, dep, st);
             }
         } else {
           int q = 0;
 #pragma unroll
           for (int k = 0; k < DIM; ++k)
-            if (wd.cv[k].type != ABP_CV_COM_DIST) {
-              if (lane == q) window_cv<Real>(fx, xs, k, dep, st);
+            if (!((com_mask >> k) & 1)) {
+              if (lane == q) {
+                if (FAST) {
+                  Real x4[4][3];
+#pragma unroll
+                  for (int j = 0; j < 4; ++j) {
+                    const R4 p = xs[datom[j]];
+                    x4[j][0] = p.x;
+                    x4[j][1] = p.y;
+                    x4[j][2] = p.z;
+                  }
+                  Real sk, slk;
+                  const int fl = dihedral_core<Real>(wd.cv[k], x4, sk, reinterpret_cast<Real(*)[3]>(st.jac[k]), slk);
+                  window_cv_rec<Real>(wd, k, sk, slk, fl, dep, st);
+                } else {
+                  window_cv<Real>(fx, xs, k, dep, st);
+                }
+              }
               ++q;
             }
         }
@@ -453,38 +550,57 @@ __global__ void __launch_bounds__(256, 1) k_md(MdRunArgs a) {
           dvk[k] = k < DIM ? st.dv[k] : (Real)0;
           dtk[k] = dvk[k] + dUs[k];
         }
-        int nbad = 0;
-        for (int i = g.t; i < natoms; i += 64) {
-          const AtomTerm<Real> *ti = terms + i * kAtomTerms;
-          const int ne = cnt[i];
-          const Real *J = &st.jac[0][0];
-          Real f0 = 0, f1 = 0, f2 = 0, b0 = 0, b1 = 0, b2 = 0;
-          for (int q = 0; q < ne; ++q) {
-            const int off = ti[q].off;
-            const int k = off >= 24 ? 2 : (off >= 12 ? 1 : 0);
-            const Real *v = J + off;
-            const Real wt = ti[q].w * dtk[k];
-            f0 += wt * v[0];
-            f1 += wt * v[1];
-            f2 += wt * v[2];
-            if (keep_f) {
-              const Real wb = ti[q].w * dvk[k];
-              b0 += wb * v[0];
-              b1 += wb * v[1];
-              b2 += wb * v[2];
-            }
-          }
+        const Real *J = &st.jac[0][0];
+        // atom i's force from its terms' sums f (total) and b (bias), the
+        // bias force to the caller, the move
+        auto move = [&](int i, const Real *f, const Real *b) {
           R4 x = xs[i];
           if (tout) tout[(long long)t * a.tstride + i] = x;
           if (keep_f) {
             R4 *fo = fout + (ra.forces ? (long long)t * ra.fstride : 0) + i;
-            store_force<Real>(fo, make_rec<Real>(b0, b1, b2, 0), fmode);
+            store_force<Real>(fo, make_rec<Real>(b[0], b[1], b[2], 0), fmode);
           }
-          x.x += mc.c1 * f0 + mc.c2 * nz[3 * i];
-          x.y += mc.c1 * f1 + mc.c2 * nz[3 * i + 1];
-          x.z += mc.c1 * f2 + mc.c2 * nz[3 * i + 2];
+          x.x = add_rn(x.x, fma_rn(mc.c1, f[0], mul_rn(mc.c2, nz[3 * i])));
+          x.y = add_rn(x.y, fma_rn(mc.c1, f[1], mul_rn(mc.c2, nz[3 * i + 1])));
+          x.z = add_rn(x.z, fma_rn(mc.c1, f[2], mul_rn(mc.c2, nz[3 * i + 2])));
           xs[i] = x;
-          nbad |= finite_rec<Real>(x) ? 0 : 1;
+          return finite_rec<Real>(x) ? 0 : 1;
+        };
+        // one term: CV k's Jacobian row v of weight w
+        auto term = [&](const Real *v, Real w, Real dt, Real dv, Real *f, Real *b) {
+          const Real wt = mul_rn(w, dt);
+#pragma unroll
+          for (int q = 0; q < 3; ++q) f[q] = fma_rn(wt, v[q], f[q]);
+          if (keep_f) {
+            const Real wb = mul_rn(w, dv);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) b[q] = fma_rn(wb, v[q], b[q]);
+          }
+        };
+        int nbad = 0;
+        if (FAST) {
+          if (g.t < natoms) {
+            Real f[3] = {0, 0, 0}, b[3] = {0, 0, 0};
+            if (tne > 0)
+              term(J + to0, tw0, tk0 == 0 ? dtk[0] : (tk0 == 1 ? dtk[1] : dtk[2]),
+                   tk0 == 0 ? dvk[0] : (tk0 == 1 ? dvk[1] : dvk[2]), f, b);
+            if (tne > 1)
+              term(J + to1, tw1, tk1 == 0 ? dtk[0] : (tk1 == 1 ? dtk[1] : dtk[2]),
+                   tk1 == 0 ? dvk[0] : (tk1 == 1 ? dvk[1] : dvk[2]), f, b);
+            nbad = move(g.t, f, b);
+          }
+        } else {
+          for (int i = g.t; i < natoms; i += 64) {
+            const AtomTerm<Real> *ti = terms + i * kAtomTerms;
+            const int ne = cnt[i];
+            Real f[3] = {0, 0, 0}, b[3] = {0, 0, 0};
+            for (int q = 0; q < ne; ++q) {
+              const int off = ti[q].off;
+              const int k = off >= 24 ? 2 : (off >= 12 ? 1 : 0);
+              term(J + off, ti[q].w, dtk[k], dvk[k], f, b);
+            }
+            nbad |= move(i, f, b);
+          }
         }
         // the next step's coordinates: each warp's half of the finiteness check
         nbad = __any_sync(0xffffffffu, nbad);
@@ -520,7 +636,7 @@ int md_group_bytes(const WalkerDev &hd, int fp64) {
   return align32(fixed + md_layout(hd.natoms, hd.cv, hd.g.d, fp64).total);
 }
 
-cudaError_t launch_md(const MdRunArgs &a, int fp64, int dim, cudaStream_t st) {
+cudaError_t launch_md(const MdRunArgs &a, int fp64, int dim, bool fast, cudaStream_t st) {
   const RunArgs &r = a.r;
   if (r.nw == 0) return cudaSuccess;
   const int gpc = r.groups_per_cta;
@@ -529,9 +645,11 @@ cudaError_t launch_md(const MdRunArgs &a, int fp64, int dim, cudaStream_t st) {
   const size_t smem = (size_t)r.group_bytes * gpc;
   void (*k)(MdRunArgs);
   if (fp64)
-    k = dim == 1 ? k_md<double, 1, 4> : dim == 2 ? k_md<double, 2, 4> : k_md<double, 3, 4>;
+    k = dim == 1 ? k_md<double, 1, 4, false> : dim == 2 ? k_md<double, 2, 4, false> : k_md<double, 3, 4, false>;
+  else if (fast)
+    k = dim == 1 ? k_md<float, 1, 7, true> : dim == 2 ? k_md<float, 2, 7, true> : k_md<float, 3, 7, true>;
   else
-    k = dim == 1 ? k_md<float, 1, 7> : dim == 2 ? k_md<float, 2, 7> : k_md<float, 3, 7>;
+    k = dim == 1 ? k_md<float, 1, 7, false> : dim == 2 ? k_md<float, 2, 7, false> : k_md<float, 3, 7, false>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k<<<blocks, threads, smem, st>>>(a);
