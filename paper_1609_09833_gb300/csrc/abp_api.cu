@@ -160,9 +160,9 @@ struct abp_walker {
   bool big = false;    // runs in the phased form (shared grid, or too large for a walker group)
   bool win = false;    // runs in the windowed form of the fused kernel (COM distance / dihedral CVs)
   bool has_rmsd = false;
-  // the closed-loop kernel's register-fed form applies: FP32, at most 64
-  // atoms of at most two a5 terms each, COM groups of at most 16 atoms, the
-  // other CVs dihedrals
+  // the closed-loop kernel's register-fed form applies: FP32 WT walkers of at
+  // most 64 atoms of at most two a5 terms each, COM groups of at most 16
+  // atoms, the other CVs dihedrals
   bool md_fast = false;
   long long cost = 0;  // rough work estimate used to order batched launches
 };
@@ -837,6 +837,7 @@ abp_status abp_walker_create(abp_ctx *ctx, abp_grid *grid, const abp_walker_desc
       for (int k = 0; k < ncv; ++k)
         fast = fast && ((d->cv[k].type == ABP_CV_COM_DIST && d->cv[k].n_a <= 16 && d->cv[k].n_b <= 16) ||
                         d->cv[k].type == ABP_CV_DIHEDRAL);
+      fast = fast && !mabp;
       w->md_fast = fast;
     }
     if (st == ABP_OK) st = upload(w, tcnt.data(), tcnt.size() * sizeof(int), &pc);

@@ -902,6 +902,84 @@ __device__ __forceinline__ AxisSt<Real> axis_eval(const GridDev &gd, int R, int 
   return r;
 }
 
+// One axis's constants of the interpolation state, held in registers by the
+// lane that forms that axis's state every step (the closed-loop form).
+template <typename Real>
+struct AxisC {
+  Real ih, il, u0h, u0l;  // invD and u0 as hi + lo (FP32 grids)
+  int n, periodic;
+};
+
+template <typename Real>
+__device__ __forceinline__ AxisC<Real> axis_consts(const GridDev &gd, int k) {
+  AxisC<Real> c;
+  if constexpr (sizeof(Real) == 4) {
+    c.ih = gd.invD_h[k];
+    c.il = gd.invD_l[k];
+    c.u0h = gd.u0_h[k];
+    c.u0l = gd.u0_l[k];
+  } else {
+    c.ih = gd.invD[k];
+    c.il = 0;
+    c.u0h = gd.u0[k];
+    c.u0l = 0;
+  }
+  c.n = gd.n[k];
+  c.periodic = gd.periodic[k];
+  return c;
+}
+
+// The interpolation part of axis_eval (i0, i1, f, clamped) for a step that
+// deposits nothing, from register constants and with selects in place of
+// the branches of split_u and of the index wrap: the same operations on the
+// same values, so the same bits. FP32 grids.
+__device__ __forceinline__ AxisSt<float> axis_interp_ff(const AxisC<float> &c, float sh, float sl) {
+  AxisSt<float> r;
+  r.da = r.dc = r.ic_log = 0;
+  r.df = 0;
+  float p = sh * c.ih;
+  float pe = fmaf(sh, c.ih, -p);
+  pe = fmaf(sh, c.il, fmaf(sl, c.ih, pe));
+  float t, te;
+  two_sum<float>(p, c.u0h, t, te);
+  te = te + (pe + c.u0l);
+  float uh = t + te, ul = te - (uh - t);
+  const float rn = (float)c.n;
+  if (c.periodic && !(uh >= 0 && uh < rn)) {
+    const float q = floorf(uh / rn);
+    if (!(q == q) || q > 1e6f || q < -1e6f) {
+      uh = 0;
+      ul = 0;
+    } else {
+      ff_add<float>(uh, ul, -q * rn, 0.f);
+    }
+  }
+  const float fa = floorf(uh);
+  int a = (int)fa;
+  float f = (uh - fa) + ul;
+  const bool neg = f < 0, ge1 = f >= 1;
+  a = neg ? a - 1 : (ge1 ? a + 1 : a);
+  f = neg ? f + 1 : (ge1 ? f - 1 : f);
+  if (c.periodic) {
+    a = a >= c.n ? a - c.n : a;
+    a = a < 0 ? a + c.n : a;
+    a = (a < 0 || a >= c.n) ? 0 : a;
+    r.i0 = a;
+    r.i1 = a + 1 == c.n ? 0 : a + 1;
+    r.f = f;
+    r.clamped = 0;
+  } else {
+    const bool below = !(uh >= 0);
+    const bool above = !below && (uh > rn - 1 || (uh == rn - 1 && ul > 0));
+    const bool top = a > c.n - 2;
+    r.i0 = below ? 0 : ((above || top) ? c.n - 2 : a);
+    r.i1 = r.i0 + 1;
+    r.f = below ? 0.f : (above ? 1.f : (top ? f + 1 : f));
+    r.clamped = (below || above) ? 1 : 0;
+  }
+  return r;
+}
+
 // mABP: the nearest node to s on axis k (from the deposit-step split of u),
 // the centre of both the hill and the look-up; wrapped on a periodic axis,
 // limited to the grid on a non-periodic one (a limited axis reports

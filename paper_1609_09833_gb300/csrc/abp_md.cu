@@ -204,6 +204,60 @@ __device__ __forceinline__ void interp_warp(const WalkerDev &wd, StepRec<Real> &
   if (lane == 0) md_finish<Real>(wd, st, acc);
 }
 
+// The register-fed form's a4 (WT walkers): the grid's record pointer and
+// sizes, the wall's constants in registers; the corner weights and the
+// combination as interp_warp's, the clamp bits read from the CV records.
+struct GridC {
+  const unsigned char *rec;
+  int n0, n1;
+};
+
+template <typename Real, int DIM>
+__device__ __forceinline__ void interp_warp_reg(const WalkerDev &wd, const GridC &gc, Real kwall, const Real *smax,
+                                                StepRec<Real> &st, int lane) {
+  constexpr int NC = 1 << DIM;
+  Real acc[4] = {0, 0, 0, 0};
+  if (lane < NC) {
+    long long node = (lane & 1) ? st.i1[0] : st.i0[0];
+    if (DIM > 1) node += (long long)gc.n0 * ((lane & 2) ? st.i1[DIM > 1 ? 1 : 0] : st.i0[DIM > 1 ? 1 : 0]);
+    if (DIM > 2)
+      node += (long long)gc.n0 * gc.n1 * ((lane & 4) ? st.i1[DIM > 2 ? 2 : 0] : st.i0[DIM > 2 ? 2 : 0]);
+    float4 ra, rb;
+    rec_load<DIM>(gc.rec + chk_node(wd.g, node) * (DIM > 1 ? 32 : 16), ra, rb);
+    Real v[4];
+    rec_vals<Real, DIM>(ra, rb, v);
+    const Real wc = corner_weight<Real, DIM>(st, lane);
+#pragma unroll
+    for (int q = 0; q <= DIM; ++q) acc[q] = wc * v[q];
+  }
+#pragma unroll
+  for (int o = 1; o < NC; o <<= 1)
+#pragma unroll
+    for (int q = 0; q <= DIM; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+  if (lane == 0) {
+    st.V = acc[0];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      const Real sk = st.s[k];
+      const Real wall = (kwall > (Real)0 && sk > smax[k]) ? kwall * (sk - smax[k]) : (Real)0;
+      st.dv[k] = (((st.cfl[k] >> 16) & 1) ? (Real)0 : acc[1 + k]) + wall;
+    }
+  }
+}
+
+// The step record's CV k on a step that deposits nothing (register-fed
+// form): the value and the interpolation state (axis_interp_ff).
+__device__ __forceinline__ void cv_rec_reg(const AxisC<float> &c, int k, float sk, float slk, int fl,
+                                           StepRec<float> &st) {
+  st.s[k] = sk;
+  st.sl[k] = slk;
+  const AxisSt<float> ax = axis_interp_ff(c, sk, slk);
+  st.i0[k] = ax.i0;
+  st.i1[k] = ax.i1;
+  st.f[k] = ax.f;
+  st.cfl[k] = fl | (ax.clamped << 16);
+}
+
 // L1 prefetch of the grid records around a cell (lower corner c0 on axis 0,
 // c1 on axis 1): m0 nodes either side along axis 0, m1 rows either side
 // along axis 1 (wrapped on a periodic axis, limited on the others), one
@@ -402,7 +456,19 @@ __global__ void __launch_bounds__(256, 1) k_md(MdRunArgs a) {
   Real cw[DIM];
   int tne = 0, to0 = 0, to1 = 0, tk0 = 0, tk1 = 0;
   Real tw0 = 0, tw1 = 0;
+  AxisC<Real> axc[DIM];
+  GridC gc{nullptr, 0, 0};
+  Real kwall = 0, smax[DIM];
   if (FAST && !producer) {
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      axc[k] = axis_consts<Real>(wd.g, k);
+      smax[k] = wd.smax_f[k];
+    }
+    kwall = wd.kwall_f;
+    gc.rec = reinterpret_cast<const unsigned char *>(wd.g.rec);
+    gc.n0 = wd.g.n[0];
+    gc.n1 = DIM > 1 ? wd.g.n[DIM > 1 ? 1 : 0] : 0;
     int q = 0;
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
@@ -491,7 +557,15 @@ __global__ void __launch_bounds__(256, 1) k_md(MdRunArgs a) {
                   FAST ? com_warp_reg<Real>(wd.cv[k], cfirst[k], catom[k], cw[k], xs, lane, sk, slk, st.jac[k])
                        : com_warp<Real>(wd.cv[k], fx->ia[k], fx->ib[k], fx->wa[k], fx->wb[k], xs, lane, sk, slk,
                                         st.jac[k]);
-              if (lane == 0) window_cv_rec<Real>(wd, k, sk, slk, fl, dep, st);
+              if (lane == 0) {
+                if constexpr (FAST) {
+                  if (!dep) {
+                    cv_rec_reg(axc[k], k, sk, slk, fl, st);
+                    continue;
+                  }
+                }
+                window_cv_rec<Real>(wd, k, sk, slk, fl, dep, st);
+              }
             }
         } else {
           int q = 0;
@@ -499,7 +573,7 @@ __global__ void __launch_bounds__(256, 1) k_md(MdRunArgs a) {
           for (int k = 0; k < DIM; ++k)
             if (!((com_mask >> k) & 1)) {
               if (lane == q) {
-                if (FAST) {
+                if constexpr (FAST) {
                   Real x4[4][3];
 #pragma unroll
                   for (int j = 0; j < 4; ++j) {
@@ -510,7 +584,12 @@ __global__ void __launch_bounds__(256, 1) k_md(MdRunArgs a) {
                   }
                   Real sk, slk;
                   const int fl = dihedral_core<Real>(wd.cv[k], x4, sk, reinterpret_cast<Real(*)[3]>(st.jac[k]), slk);
-                  window_cv_rec<Real>(wd, k, sk, slk, fl, dep, st);
+                  if constexpr (FAST) {
+                    if (dep)
+                      window_cv_rec<Real>(wd, k, sk, slk, fl, dep, st);
+                    else
+                      cv_rec_reg(axc[k], k, sk, slk, fl, st);
+                  }
                 } else {
                   window_cv<Real>(fx, xs, k, dep, st);
                 }
@@ -519,23 +598,30 @@ __global__ void __launch_bounds__(256, 1) k_md(MdRunArgs a) {
             }
         }
         psync();
-        if (w0 && lane == 0) step_flags<Real>(DIM, dep, st);
+        // the step's flags (read after the launch): by warp 0 ahead of a4, or
+        // in the register-fed form by warp 1 beside it
+        if (!FAST && w0 && lane == 0) step_flags<Real>(DIM, dep, st);
         if (dep) {
           psync();
           md_deposit<Real, DIM, UNR>(g, fx, st, step, ra.log);
         }
         if (w0) {
           // a4 by warp 0
-          interp_warp<Real, DIM>(wd, st, lane);
+          if (FAST)
+            interp_warp_reg<Real, DIM>(wd, gc, kwall, smax, st, lane);
+          else
+            interp_warp<Real, DIM>(wd, st, lane);
         } else {
           // beside it, the CV potential's gradient by warp 1
           Real sk[3] = {0, 0, 0}, dU[3];
 #pragma unroll
           for (int k = 0; k < DIM; ++k) sk[k] = st.s[k];
           md_potential_grad_warp<Real>(mc, mt, sk, lane, dU);
-          if (lane == 0)
+          if (lane == 0) {
 #pragma unroll
             for (int k = 0; k < 3; ++k) dUs[k] = dU[k];
+            if (FAST) step_flags<Real>(DIM, dep, st);
+          }
         }
         psync();
         // a5 and the move, one atom per thread of the pair: each of the
@@ -578,7 +664,7 @@ __global__ void __launch_bounds__(256, 1) k_md(MdRunArgs a) {
           }
         };
         int nbad = 0;
-        if (FAST) {
+        if constexpr (FAST) {
           if (g.t < natoms) {
             Real f[3] = {0, 0, 0}, b[3] = {0, 0, 0};
             if (tne > 0)
