@@ -708,7 +708,9 @@ __global__ void __launch_bounds__(256, 1) k_md(MdRunArgs a) {
       ws.dV[k] = k < DIM ? (double)st.dv[k] : 0.0;
     }
     ws.V = (double)st.V;
-    ws.flags = st.flags;
+    // a walker stopped by non-finite coordinates keeps its last completed
+    // step's state and reports the stop
+    ws.flags = stopped ? ABP_WFLAG_NONFINITE : st.flags;
     ws.pad = 0;
     ws.step = step0 + last;
     *wd.state = ws;
@@ -732,8 +734,8 @@ cudaError_t launch_md(const MdRunArgs &a, int fp64, int dim, bool fast, cudaStre
   void (*k)(MdRunArgs);
   if (fp64)
     k = dim == 1 ? k_md<double, 1, 4, false> : dim == 2 ? k_md<double, 2, 4, false> : k_md<double, 3, 4, false>;
-  else if (fast)
-    k = dim == 1 ? k_md<float, 1, 7, true> : dim == 2 ? k_md<float, 2, 7, true> : k_md<float, 3, 7, true>;
+  else if (fast)  // four stencil nodes in flight per thread: measured best for this form's registers
+    k = dim == 1 ? k_md<float, 1, 4, true> : dim == 2 ? k_md<float, 2, 4, true> : k_md<float, 3, 4, true>;
   else
     k = dim == 1 ? k_md<float, 1, 7, false> : dim == 2 ? k_md<float, 2, 7, false> : k_md<float, 3, 7, false>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

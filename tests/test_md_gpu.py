@@ -435,3 +435,29 @@ def test_closed_loop_rejections_and_non_finite_coordinates(abp, ctx):
     assert not torch.equal(buf[36:], before[36:])
     assert ctx.readout(walkers[0])["flags"] == abp.WFLAG_NONFINITE
     assert np.all(ctx.bias(walkers[0]) == 0.0)
+
+
+@pytest.mark.gpu
+def test_closed_loop_walker_that_blows_up_mid_launch_reports_it(abp, ctx):
+    """A walker whose coordinates overflow after some completed steps stops
+    at the first non-finite ones: the call reports it and the walker's state
+    says ABP_WFLAG_NONFINITE (its values are its last completed step's). The
+    double well's force, scaled by 1e30 on the first CV, takes the atoms past
+    the FP32 range within a few steps."""
+    specs = synth.mb64_specs(nw=2, stride=3)
+    walkers = ctx.make_walkers(specs)
+    x0 = synth.SweepFrames(2, seed=2).frames(0, 1)[0]
+    buf = abp.to_records(x0[None]).cuda()[0]
+    offs = torch.tensor([0, 36], dtype=torch.int64, device="cuda")
+    md = synth.md_double_well(seed=4, A=1e30, B=0.1)
+    abp.abp_md_run(ctx.handle, walkers, buf, abp.ABP_F32, offs, md, [0, 1], nsteps=20)
+    with pytest.raises(abp.AbpError) as e:
+        abp.abp_sync(ctx.handle)
+    assert e.value.code == abp.ABP_ERR_NONFINITE
+    x = buf.cpu().numpy()[:, :3]
+    for i, w in enumerate(walkers):
+        r = ctx.readout(w)
+        assert r["flags"] == abp.WFLAG_NONFINITE, r
+        assert not np.all(np.isfinite(x[36 * i:36 * (i + 1)]))
+        # the first step deposited before the blow-up
+        assert np.any(ctx.bias(w)[:, 0] != 0.0)
