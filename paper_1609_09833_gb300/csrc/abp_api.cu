@@ -118,6 +118,30 @@ struct TableCache {
 
 namespace abp {
 abp_status record_error(abp_status code, const char *msg) { return fail(code, "%s", msg); }
+
+cudaError_t smem_attr(const void *fn, size_t bytes) {
+  struct Given {
+    const void *fn;
+    int dev;
+    size_t bytes;
+  };
+  static std::mutex mu;
+  static std::vector<Given> given;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  for (Given &g : given)
+    if (g.fn == fn && g.dev == dev) {
+      if (g.bytes >= bytes) return cudaSuccess;
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      if (e == cudaSuccess) g.bytes = bytes;
+      return e;
+    }
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) given.push_back(Given{fn, dev, bytes});
+  return e;
+}
 }  // namespace abp
 
 struct abp_ctx {
@@ -220,7 +244,8 @@ abp_status check_list(abp_ctx *ctx, abp_walker *const *walkers, int n, int *fp64
   if (n < 0) return fail(ABP_ERR_INVALID_ARG, "negative walker count");
   if (n > 0 && !walkers) return fail(ABP_ERR_INVALID_ARG, "walker list is NULL");
   int prec = -1;
-  std::set<const abp_grid *> grids;
+  thread_local std::vector<const abp_grid *> grids;  // reused: no allocation per call
+  grids.clear();
   *shared = false;
   for (int i = 0; i < n; ++i) {
     const abp_walker *w = walkers[i];
@@ -229,8 +254,10 @@ abp_status check_list(abp_ctx *ctx, abp_walker *const *walkers, int n, int *fp64
     int p = walker_fp64(w);
     if (prec >= 0 && p != prec) return fail(ABP_ERR_INVALID_ARG, "walkers of one call must share a grid precision");
     prec = p;
-    if (!grids.insert(w->grid).second) *shared = true;
+    grids.push_back(w->grid);
   }
+  std::sort(grids.begin(), grids.end());
+  *shared = std::adjacent_find(grids.begin(), grids.end()) != grids.end();
   *fp64 = prec < 0 ? 0 : prec;
   return ABP_OK;
 }
@@ -931,14 +958,19 @@ int32_t abp_walker_id(const abp_walker *w) { return w ? w->hd.id : -1; }
 // caller's index, which selects coordinate and force offsets).
 static abp_status sub_table(abp_ctx *ctx, const std::vector<abp_walker *> &ws, const std::vector<int> &idx,
                             const TableEntry **out, const uint32_t *streams = nullptr) {
-  std::vector<TableEntry> key(ws.size());
-  for (size_t i = 0; i < ws.size(); ++i) key[i] = TableEntry{ws[i]->dd, idx[i], streams ? streams[idx[i]] : 0u};
-  std::vector<long long> cost(ws.size());
-  std::vector<size_t> order(ws.size());
+  // by cost, ties in list order (buffers reused: no allocation per call)
+  thread_local std::vector<size_t> order;
+  thread_local std::vector<TableEntry> sorted;
+  order.resize(ws.size());
   for (size_t i = 0; i < ws.size(); ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return ws[a]->cost > ws[b]->cost; });
-  std::vector<TableEntry> sorted(ws.size());
-  for (size_t i = 0; i < ws.size(); ++i) sorted[i] = key[order[i]];
+  std::sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+    return ws[a]->cost != ws[b]->cost ? ws[a]->cost > ws[b]->cost : a < b;
+  });
+  sorted.resize(ws.size());
+  for (size_t i = 0; i < ws.size(); ++i) {
+    const size_t j = order[i];
+    sorted[i] = TableEntry{ws[j]->dd, idx[j], streams ? streams[idx[j]] : 0u};
+  }
   ++ctx->use_clock;
   TableCache *victim = &ctx->tables[0];
   for (auto &t : ctx->tables) {
@@ -960,7 +992,7 @@ static abp_status sub_table(abp_ctx *ctx, const std::vector<abp_walker *> &ws, c
   }
   CUDA_TRY(cudaMemcpyAsync(victim->dev, sorted.data(), sorted.size() * sizeof(TableEntry), cudaMemcpyHostToDevice,
                            ctx->stream));
-  victim->key = std::move(sorted);
+  victim->key = sorted;
   victim->last_use = ctx->use_clock;
   *out = victim->dev;
   return ABP_OK;
@@ -1175,8 +1207,14 @@ abp_status abp_md_run(abp_ctx *ctx, abp_walker *const *walkers, int n, void *coo
       if (walkers[i]->hd.g.d < 2)
         return fail(ABP_ERR_INVALID_ARG, "walker %d: the Mueller-Brown potential needs two CVs", i);
   // the one-warp form (by grid dimension) and the phased form
-  std::vector<abp_walker *> ww[3], bw;
-  std::vector<int> wi[3], bi;
+  thread_local std::vector<abp_walker *> ww[3], bw;  // reused: no allocation per call
+  thread_local std::vector<int> wi[3], bi;
+  for (int k = 0; k < 3; ++k) {
+    ww[k].clear();
+    wi[k].clear();
+  }
+  bw.clear();
+  bi.clear();
   for (int i = 0; i < n; ++i) {
     if (walkers[i]->big) {
       if (md->potential != ABP_POT_NONE)

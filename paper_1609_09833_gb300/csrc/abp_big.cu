@@ -793,7 +793,7 @@ cudaError_t launch_big_step(const BigArgs &a, cudaStream_t st) {
   };
   cudaError_t e;
   if ((ph & 1) && a.ncn_items > 0) {
-    e = cudaFuncSetAttribute(k_big_cn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.cn_smem);
+    e = smem_attr(reinterpret_cast<const void *>(k_big_cn), a.cn_smem);
     if (e != cudaSuccess) return e;
     t0("k_big_cn");
     k_big_cn<<<a.ncn_items, kBigThreads, a.cn_smem, st>>>(a.cn_items, a.coords, a.coff, a.step_off);

@@ -1029,25 +1029,25 @@ cudaError_t launch_run(const RunArgs &a, int fp64, cudaStream_t st) {
       k = a.window == 1 ? k_win<double, 4, 1> : a.window == 2 ? k_win<double, 4, 2> : k_win<double, 4, 3>;
     else
       k = a.window == 1 ? k_win<float, 7, 1> : a.window == 2 ? k_win<float, 7, 2> : k_win<float, 7, 3>;
-    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = smem_attr(reinterpret_cast<const void *>(k), smem);
     if (e != cudaSuccess) return e;
     k<<<blocks, threads, smem, st>>>(a);
     return cudaGetLastError();
   }
   if (fp64) {
-    e = cudaFuncSetAttribute(k_run<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = smem_attr(reinterpret_cast<const void *>(k_run<double, false>), smem);
     if (e != cudaSuccess) return e;
     k_run<double, false><<<blocks, threads, smem, st>>>(a);
   } else if (a.lean && a.tile_budget == 0) {
-    e = cudaFuncSetAttribute(k_run_lean, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = smem_attr(reinterpret_cast<const void *>(k_run_lean), smem);
     if (e != cudaSuccess) return e;
     k_run_lean<<<blocks, threads, smem, st>>>(a);
   } else if (a.tile_budget > 0) {
-    e = cudaFuncSetAttribute(k_run<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = smem_attr(reinterpret_cast<const void *>(k_run<float, true>), smem);
     if (e != cudaSuccess) return e;
     k_run<float, true><<<blocks, threads, smem, st>>>(a);
   } else {
-    e = cudaFuncSetAttribute(k_run<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = smem_attr(reinterpret_cast<const void *>(k_run<float, false>), smem);
     if (e != cudaSuccess) return e;
     k_run<float, false><<<blocks, threads, smem, st>>>(a);
   }
@@ -1247,15 +1247,15 @@ static cudaError_t plain_one(const PlainArgs &a, int w, cudaStream_t st) {
   const int T = a.threads;
   size_t smem = (size_t)fixed_bytes<Real>() + a.dyn_bytes[w];
   cudaError_t e;
-  e = cudaFuncSetAttribute(k_plain_cv<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = smem_attr(reinterpret_cast<const void *>(k_plain_cv<Real>), smem);
   if (e != cudaSuccess) return e;
   k_plain_cv<Real><<<1, T, smem, st>>>(wd, a.coords, a.coff, w);
   if (a.deposit[w]) {
-    e = cudaFuncSetAttribute(k_plain_deposit<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = smem_attr(reinterpret_cast<const void *>(k_plain_deposit<Real>), smem);
     if (e != cudaSuccess) return e;
     k_plain_deposit<Real><<<1, T, smem, st>>>(wd, a.step, a.log);
   }
-  e = cudaFuncSetAttribute(k_plain_force<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = smem_attr(reinterpret_cast<const void *>(k_plain_force<Real>), smem);
   if (e != cudaSuccess) return e;
   k_plain_force<Real><<<1, T, smem, st>>>(wd, a.forces, a.foff, w, a.mode, a.step, a.ctr);
   return cudaGetLastError();

@@ -159,6 +159,10 @@ cudaError_t launch_run(const RunArgs &a, int fp64, cudaStream_t st);
 cudaError_t launch_plain(const PlainArgs &a, int fp64, cudaStream_t st);
 // Records `msg` as the calling thread's abp_last_error() and returns code.
 abp_status record_error(abp_status code, const char *msg);
+// cudaFuncSetAttribute(fn, MaxDynamicSharedMemorySize, bytes) unless fn was
+// already given at least that many bytes on the current device: a driver
+// call on every launch otherwise.
+cudaError_t smem_attr(const void *fn, size_t bytes);
 cudaError_t launch_deliver(const TableEntry *table, int nw, void *forces, const long long *foff, int mode, int fp64,
                            cudaStream_t st);
 

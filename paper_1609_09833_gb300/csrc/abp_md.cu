@@ -738,7 +738,7 @@ cudaError_t launch_md(const MdRunArgs &a, int fp64, int dim, bool fast, cudaStre
     k = dim == 1 ? k_md<float, 1, 4, true> : dim == 2 ? k_md<float, 2, 4, true> : k_md<float, 3, 4, true>;
   else
     k = dim == 1 ? k_md<float, 1, 7, false> : dim == 2 ? k_md<float, 2, 7, false> : k_md<float, 3, 7, false>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = smem_attr(reinterpret_cast<const void *>(k), smem);
   if (e != cudaSuccess) return e;
   k<<<blocks, threads, smem, st>>>(a);
   return cudaGetLastError();
