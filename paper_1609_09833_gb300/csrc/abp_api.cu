@@ -1801,7 +1801,6 @@ class CopyTeam {
     cv_.notify_all();
     for (auto &t : threads_) t.join();
   }
-  int parts() const { return nparts_; }
   void run(const std::function<void(int, int)> &fn) {
     {
       std::lock_guard<std::mutex> lk(mu_);

@@ -169,7 +169,7 @@ __device__ __forceinline__ void reduce_block_grads(const float (&gi)[4][3], int 
 // One CTA: the A x (one chunk of B) pairs of one walker's CN.
 __global__ void __launch_bounds__(kBigThreads) k_big_cn(const BigItem *items, const void *coords,
                                                         const long long *coff, long long step_off) {
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(32) unsigned char smem[];
   const BigItem it = items[blockIdx.x];
   const WalkerDev *wd = it.wd;
   const int k = big_cn_index(*wd);

@@ -1102,7 +1102,6 @@ __device__ void tile_load(const Grp &g, GroupFixed<Real> *fx, const GroupLayout 
   const int rb = gd.rec_bytes;
   const int T0 = L.T[0], T1 = gd.d > 1 ? L.T[1] : 1, T2 = gd.d > 2 ? L.T[2] : 1;
   const int n0 = gd.n[0];
-  const long long row_stride = (long long)n0 * rb, plane_stride = row_stride * (gd.d > 1 ? gd.n[1] : 1);
   const int o0 = fx->org[0];
   const int first = min(T0, n0 - o0);  // nodes before the wrap of axis 0
   const int pieces_row = T0 * rb / 16, first_pieces = first * rb / 16;
