@@ -991,7 +991,7 @@ def main():
     e2e_s = time.perf_counter() - t0
     e2e = {"value": NW * C * n_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(host_in.numel() * 4),
            "d2h_bytes_per_step": int(host_out.numel() * 4),
-           "what": "per benchmark step: the 64 walkers' atoms from pinned host memory, one 1000-step closed-loop "
+           "what": f"per benchmark step: the {NW} walkers' atoms from pinned host memory, one {C}-step closed-loop "
                    "call, the moved atoms back to pinned host memory; host clock, no L2 flush between steps"}
 
     # the open-loop replay of recorded frames (windowed form, the former
