@@ -461,3 +461,47 @@ def test_closed_loop_walker_that_blows_up_mid_launch_reports_it(abp, ctx):
         assert not np.all(np.isfinite(x[36 * i:36 * (i + 1)]))
         # the first step deposited before the blow-up
         assert np.any(ctx.bias(w)[:, 0] != 0.0)
+
+
+def test_closed_loop_checkpoint_and_resume_is_bit_exact(abp, ctx):
+    """The closed loop's state is the grid, the coordinates and the step
+    counter (the deposit schedule and the Philox counters follow from the
+    step): save the grids after k closed-loop steps (abp_grid_save), restore
+    them into new walkers and continue from the saved coordinates at step k;
+    the coordinates, the bias forces and the grids equal an uninterrupted run
+    bit for bit. Two walker sets: the register-fed form (COM groups of 16,
+    a dihedral) and the generic one (an RMSD CV)."""
+    rmsd = []
+    for sp in synth.mb64_specs(nw=2, stride=3):
+        sp = dict(sp)
+        ref = synth.SweepFrames(1, seed=21).frames(0, 1)[0][32:36].astype(np.float64)
+        sp["cvs"] = [sp["cvs"][0], {"type": "rmsd", "a": np.arange(32, 36), "ref": ref}]
+        sp["grid"] = synth.grid((0.2, 0.0), (2.0, 1.0), (256, 256), (False, False))
+        sp["hill"] = synth.hill(0.5, (0.04, 0.04), 3, 15.0)
+        rmsd.append(sp)
+    md = synth.md_muller_brown(seed=6, mu=0.1)
+    for specs in (synth.mb64_specs(nw=2, stride=3), rmsd):
+        x0 = abp.to_records(synth.SweepFrames(2, seed=17).frames(0, 1)[0][None]).cuda()[0]
+        offs = torch.tensor(synth.offsets_of(specs), dtype=torch.int64, device="cuda")
+        n, k = 40, 23
+        wa = ctx.make_walkers(specs)
+        xa = x0.clone()
+        Fa = torch.zeros(n, xa.shape[0], 4, device="cuda")
+        abp.abp_md_run(ctx.handle, wa, xa, abp.ABP_F32, offs, md, [0, 1], forces=Fa, force_offsets=offs,
+                       force_step_stride=xa.shape[0], step0=0, nsteps=n)
+        wb = ctx.make_walkers(specs)
+        xb = x0.clone()
+        abp.abp_md_run(ctx.handle, wb, xb, abp.ABP_F32, offs, md, [0, 1], step0=0, nsteps=k)
+        torch.cuda.synchronize()
+        saved = [abp.abp_grid_save(ctx.handle, w.grid) for w in wb]
+        wc = ctx.make_walkers(specs)
+        for w, g in zip(wc, saved):
+            abp.abp_grid_restore(ctx.handle, w.grid, g)
+        Fc = torch.zeros(n - k, xb.shape[0], 4, device="cuda")
+        abp.abp_md_run(ctx.handle, wc, xb, abp.ABP_F32, offs, md, [0, 1], forces=Fc, force_offsets=offs,
+                       force_step_stride=xb.shape[0], step0=k, nsteps=n - k)
+        torch.cuda.synchronize()
+        assert torch.equal(xa, xb)
+        assert torch.equal(Fa[k:], Fc)
+        for x, y in zip(wa, wc):
+            assert np.array_equal(ctx.bias(x), ctx.bias(y))
