@@ -505,3 +505,51 @@ def test_closed_loop_checkpoint_and_resume_is_bit_exact(abp, ctx):
         assert torch.equal(Fa[k:], Fc)
         for x, y in zip(wa, wc):
             assert np.array_equal(ctx.bias(x), ctx.bias(y))
+
+
+def _rmsd_spec(seed=21):
+    """A two-CV walker (COM distance + a 4-atom RMSD) that the closed loop
+    runs in its generic form."""
+    sp = dict(synth.mb64_specs(nw=1, stride=3)[0])
+    ref = synth.SweepFrames(1, seed=seed).frames(0, 1)[0][32:36].astype(np.float64)
+    sp["cvs"] = [sp["cvs"][0], {"type": "rmsd", "a": np.arange(32, 36), "ref": ref}]
+    sp["grid"] = synth.grid((0.2, 0.0), (2.0, 1.0), (256, 256), (False, False))
+    sp["hill"] = synth.hill(0.5, (0.04, 0.04), 3, 15.0)
+    return sp
+
+
+def test_register_fed_form_gives_the_generic_forms_bits(abp, ctx):
+    """The register-fed instantiation of the closed-loop kernel (chosen when
+    every walker of a launch qualifies) computes the same operations as the
+    generic one: the same COM-distance / dihedral walkers run alone (the
+    register-fed form) and beside an RMSD walker (which sends the whole
+    launch to the generic form) give the same coordinates, bias forces and
+    grids bit for bit, over 60 steps with deposits every third step."""
+    specs = synth.mb64_specs(nw=3, stride=3)
+    md = synth.md_muller_brown(seed=8, mu=0.1)
+    n = 60
+    x0 = synth.SweepFrames(4, seed=19).frames(0, 1)[0]
+    # alone: the register-fed form
+    wf = ctx.make_walkers(specs)
+    xf = abp.to_records(x0[None, :108]).cuda()[0]
+    of = torch.tensor(synth.offsets_of(specs), dtype=torch.int64, device="cuda")
+    Ff = torch.zeros(n, 108, 4, device="cuda")
+    abp.abp_md_run(ctx.handle, wf, xf, abp.ABP_F32, of, md, [0, 1, 2], forces=Ff, force_offsets=of,
+                   force_step_stride=108, step0=0, nsteps=n)
+    # beside an RMSD walker: the generic form
+    mixed = list(specs) + [_rmsd_spec()]
+    wg = ctx.make_walkers(mixed)
+    xg = abp.to_records(x0[None]).cuda()[0]
+    og = torch.tensor(synth.offsets_of(mixed), dtype=torch.int64, device="cuda")
+    Fg = torch.zeros(n, 144, 4, device="cuda")
+    abp.abp_md_run(ctx.handle, wg, xg, abp.ABP_F32, og, md, [0, 1, 2, 3], forces=Fg, force_offsets=og,
+                   force_step_stride=144, step0=0, nsteps=n)
+    torch.cuda.synchronize()
+    assert not torch.equal(xf, abp.to_records(x0[None, :108]).cuda()[0])
+    assert torch.equal(xf, xg[:108])
+    assert torch.equal(Ff, Fg[:, :108])
+    for a, b in zip(wf, wg[:3]):
+        assert np.array_equal(ctx.bias(a), ctx.bias(b))
+        ra, rb = ctx.readout(a), ctx.readout(b)
+        for key in ("s", "V", "dV", "flags"):
+            assert np.array_equal(np.asarray(ra[key]), np.asarray(rb[key])), key
