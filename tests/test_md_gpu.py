@@ -518,36 +518,64 @@ def _rmsd_spec(seed=21):
     return sp
 
 
-def test_register_fed_form_gives_the_generic_forms_bits(abp, ctx):
+def _equivalence_case(dim):
+    """Walkers of the register-fed form for `dim` CVs, a walker of the same
+    dimension that is not (an RMSD CV), the dynamics, and the atoms per
+    walker."""
+    if dim == 1:
+        fast = [dict(synth.double_well_com_spec(stride=3)) for _ in range(3)]
+        ref = synth.SweepFrames(1, seed=22).frames(0, 1)[0][:4].astype(np.float64)
+        other = {"natoms": 16, "cvs": [{"type": "rmsd", "a": np.arange(0, 4), "ref": ref}],
+                 "grid": synth.grid((0.0,), (2.0,), (512,), (False,)), "hill": synth.hill(0.5, (0.05,), 3, 10.0)}
+        return fast, other, synth.md_params(seed=8, mu=0.1), 16
+    if dim == 2:
+        return synth.mb64_specs(nw=3, stride=3), _rmsd_spec(), synth.md_muller_brown(seed=8, mu=0.1), 36
+    g3 = synth.grid((0.2, -math.pi, 0.0), (2.0, math.pi, 1.5), (24, 24, 24), (False, True, False))
+    h3 = synth.hill(0.5, (0.1, 0.3, 0.1), 3, 15.0)
+    base = synth.mb64_specs(nw=1)[0]
+    fast = []
+    for _ in range(3):
+        sp = dict(base)
+        sp["cvs"] = list(base["cvs"]) + [{"type": "com_dist", "a": np.arange(0, 8), "b": np.arange(8, 16)}]
+        sp["grid"], sp["hill"] = g3, h3
+        fast.append(sp)
+    ref = synth.SweepFrames(1, seed=23).frames(0, 1)[0][16:20].astype(np.float64)
+    other = dict(base)
+    other["cvs"] = list(base["cvs"]) + [{"type": "rmsd", "a": np.arange(16, 20), "ref": ref}]
+    other["grid"], other["hill"] = g3, h3
+    return fast, other, synth.md_muller_brown(seed=8, mu=0.1), 36
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_register_fed_form_gives_the_generic_forms_bits(abp, ctx, dim):
     """The register-fed instantiation of the closed-loop kernel (chosen when
     every walker of a launch qualifies) computes the same operations as the
     generic one: the same COM-distance / dihedral walkers run alone (the
-    register-fed form) and beside an RMSD walker (which sends the whole
-    launch to the generic form) give the same coordinates, bias forces and
-    grids bit for bit, over 60 steps with deposits every third step."""
-    specs = synth.mb64_specs(nw=3, stride=3)
-    md = synth.md_muller_brown(seed=8, mu=0.1)
+    register-fed form) and beside an RMSD walker of the same dimension (which
+    sends the whole launch to the generic form) give the same coordinates,
+    bias forces, grids and walker states bit for bit, over 60 steps with
+    deposits every third step; one, two and three CVs."""
+    specs, other, md, na = _equivalence_case(dim)
     n = 60
-    x0 = synth.SweepFrames(4, seed=19).frames(0, 1)[0]
-    # alone: the register-fed form
+    x0 = synth.SweepFrames(4, seed=19).frames(0, 1)[0].reshape(4, 36, 3)[:, :na].reshape(-1, 3)
+    nf = 3 * na
     wf = ctx.make_walkers(specs)
-    xf = abp.to_records(x0[None, :108]).cuda()[0]
+    xf = abp.to_records(x0[None, :nf]).cuda()[0]
     of = torch.tensor(synth.offsets_of(specs), dtype=torch.int64, device="cuda")
-    Ff = torch.zeros(n, 108, 4, device="cuda")
+    Ff = torch.zeros(n, nf, 4, device="cuda")
     abp.abp_md_run(ctx.handle, wf, xf, abp.ABP_F32, of, md, [0, 1, 2], forces=Ff, force_offsets=of,
-                   force_step_stride=108, step0=0, nsteps=n)
-    # beside an RMSD walker: the generic form
-    mixed = list(specs) + [_rmsd_spec()]
+                   force_step_stride=nf, step0=0, nsteps=n)
+    mixed = list(specs) + [other]
     wg = ctx.make_walkers(mixed)
     xg = abp.to_records(x0[None]).cuda()[0]
     og = torch.tensor(synth.offsets_of(mixed), dtype=torch.int64, device="cuda")
-    Fg = torch.zeros(n, 144, 4, device="cuda")
+    Fg = torch.zeros(n, xg.shape[0], 4, device="cuda")
     abp.abp_md_run(ctx.handle, wg, xg, abp.ABP_F32, og, md, [0, 1, 2, 3], forces=Fg, force_offsets=og,
-                   force_step_stride=144, step0=0, nsteps=n)
+                   force_step_stride=xg.shape[0], step0=0, nsteps=n)
     torch.cuda.synchronize()
-    assert not torch.equal(xf, abp.to_records(x0[None, :108]).cuda()[0])
-    assert torch.equal(xf, xg[:108])
-    assert torch.equal(Ff, Fg[:, :108])
+    assert not torch.equal(xf, abp.to_records(x0[None, :nf]).cuda()[0])
+    assert torch.equal(xf, xg[:nf])
+    assert torch.equal(Ff, Fg[:, :nf])
     for a, b in zip(wf, wg[:3]):
         assert np.array_equal(ctx.bias(a), ctx.bias(b))
         ra, rb = ctx.readout(a), ctx.readout(b)
