@@ -179,6 +179,38 @@ def test_closed_loop_steps_match_the_oracle_fp32_mueller_brown(abp, ctx):
     assert np.ptp(ref["s"][:, :, 0]) > 0.01 and np.ptp(ref["s"][:, :, 1]) > 0.05
 
 
+@pytest.mark.parametrize("dim", [1, 3])
+def test_closed_loop_steps_match_the_oracle_one_and_three_cvs(abp, ctx, dim):
+    """The register-fed closed loop with one CV (COM distance, FP32, under
+    the double well U = 5 (s^2 - 1)^2) and with three (COM distance,
+    dihedral and a second COM distance on a 24^3 grid, under the scaled
+    Mueller-Brown surface of the first two), step by step along the
+    oracle's trajectory: bias forces, deposits and grids within the
+    open-loop tolerances, every move within the error of one FP32 move."""
+    nw, T = 4, 120
+    if dim == 1:
+        specs = [dict(synth.double_well_com_spec(stride=4)) for _ in range(nw)]
+        md = synth.md_double_well(seed=6, state_f32=True, mu=0.2)
+        x0 = np.concatenate([synth.double_well_com_coords(40 + i) for i in range(nw)]).astype(np.float32)
+    else:
+        specs = (_equivalence_case(3)[0] + _equivalence_case(3)[0])[:nw]
+        md = synth.md_muller_brown(seed=6, state_f32=True)
+        x0 = synth.SweepFrames(nw, seed=31).frames(0, 1)[0]
+    streams = np.arange(nw) + 200
+    frames = _oracle_closed_loop(specs, x0, md, streams, T)
+    assert np.array_equal(frames.astype(np.float32).astype(np.float64), frames)
+    walkers = ctx.make_walkers(specs)
+    abp.abp_deposit_log_enable(ctx.handle, 1 << 16)
+    X, F = gpu_steps_from(abp, ctx, walkers, frames[:T], md, streams)
+    _, ref = oracle_replay(specs, frames[:T].astype(np.float32), 0)
+    worst = check_run(abp, ctx, specs, walkers, frames[:T], 0, F, ref)
+    worst["move"] = check_moves(specs, md, streams, frames, X, ref)
+    print("worst", worst)
+    P.record_errors(f"closed loop, {dim} CV{'s' if dim > 1 else ''} (FP32, register-fed form)",
+                    f"test_closed_loop_steps_match_the_oracle_one_and_three_cvs[{dim}]", worst)
+    assert np.ptp(ref["s"][:, :, 0]) > 0.005
+
+
 def test_closed_loop_full_size_64_walkers(abp, ctx):
     """The benchmark's closed-loop workload at full size: all 64 walkers
     (36 atoms, own 256 x 256 grids, Mueller-Brown x 0.1, mu = 0.1, stride
