@@ -92,8 +92,21 @@ def check_mabp(abp, ctx, specs, walkers, Fg, ref, unit=P.U32):
         rel, ratio, _ = P.check_forces_per_step(Fg[keep], sub, i, sl, len(sp["grid"]["n"]), unit=unit)
         worst["F_step"] = max(worst["F_step"], rel)
         worst["F_allow"] = max(worst["F_allow"], ratio)
-    # the tie band is a few 1e-6 wide in u: a small fraction of steps may fall in it
-    assert worst["tie_steps"] <= max(3, 0.005 * Fg.shape[0] * len(walkers)), worst
+    # the tie band is a few 1e-6 wide in u: a small fraction of steps may fall
+    # in it. With uniform fractional parts a step lands there with probability
+    # sum_k 2 band_k, so the count is about Poisson with that total as its
+    # mean: allow the mean plus four standard deviations (and at least 3, or
+    # 0.5 % of the steps)
+    lam = 0.0
+    for i, sp in enumerate(specs):
+        g = sp["grid"]
+        d = len(g["n"])
+        D = np.array([(g["hi"][k] - g["lo"][k]) / (g["n"][k] if g["periodic"][k] else g["n"][k] - 1)
+                      for k in range(d)])
+        band = 4 * unit * ref["sb"][:, i, :d] / D + 1e-6
+        lam += float(np.minimum(1.0, (2 * band).sum(axis=1)).sum())
+    worst["tie_expect"] = lam
+    assert worst["tie_steps"] <= max(3, 0.005 * Fg.shape[0] * len(walkers), lam + 4 * np.sqrt(lam) + 3), worst
     return worst
 
 

@@ -114,7 +114,7 @@ def _potential_floor(md, ref, sl, w, d, unit):
     return np.einsum("tak,tk->ta", Jn, E), np.einsum("tak,tk->ta", Jn, G)
 
 
-def check_moves(specs, md, streams, frames, X, ref, unit=P.U32, tol_f=P.TOL_F):
+def check_moves(specs, md, streams, frames, X, ref, unit=P.U32, tol_f=P.TOL_F, keep=None):
     """The GPU's move of every step and atom against the oracle's next
     frame: the rounding of the position (both sides), the step's force error
     (the per-step force allowance of tests/parity.py for the bias, the
@@ -138,6 +138,8 @@ def check_moves(specs, md, streams, frames, X, ref, unit=P.U32, tol_f=P.TOL_F):
                  + 16 * unit * c2 * np.linalg.norm(xi, axis=-1))
         err = np.linalg.norm(X[:, sl] - xn, axis=-1)
         r = err / allow
+        if keep is not None:  # [T, walkers]: steps to check (mABP: not a look-up tie)
+            r = np.where(keep[:, w, None], r, 0.0)
         t, i = np.unravel_index(np.argmax(r), r.shape)
         assert r.max() <= 1.0, (w, int(t), int(i), float(err[t, i]), float(allow[t, i]))
         worst = max(worst, float(r.max()))
@@ -208,6 +210,37 @@ def test_closed_loop_steps_match_the_oracle_one_and_three_cvs(abp, ctx, dim):
     print("worst", worst)
     P.record_errors(f"closed loop, {dim} CV{'s' if dim > 1 else ''} (FP32, register-fed form)",
                     f"test_closed_loop_steps_match_the_oracle_one_and_three_cvs[{dim}]", worst)
+    assert np.ptp(ref["s"][:, :, 0]) > 0.005
+
+
+def test_closed_loop_mabp_steps_match_the_oracle(abp, ctx):
+    """The paper's own method in the closed loop: mABP with compact S_a^p
+    hills (a = 10 grid spacings, p = 20) at the paper's b = 0.9, c = 0.001,
+    a hill every second step, on COM-distance + dihedral walkers under the
+    scaled Mueller-Brown surface, 150 steps along the oracle's trajectory.
+    Deposits (nearest nodes, fixed heights), grids and forces as in the
+    open-loop mABP tests (a step whose CV sits in the tie band of a half-node
+    may pick the other nearest node, and is left out); every other move
+    within the error of one FP32 move."""
+    from tests.test_mabp_gpu import _lookup_tie_steps, _mabp, check_mabp
+
+    nw, T = 4, 150
+    specs = _mabp(synth.mb64_specs(nw=nw), a_bins=10.0, b=0.9, c=0.001, stride=2)
+    md = synth.md_muller_brown(seed=9, state_f32=True)
+    streams = np.arange(nw) + 300
+    x0 = synth.SweepFrames(nw, seed=41).frames(0, 1)[0]
+    frames = _oracle_closed_loop(specs, x0, md, streams, T)
+    assert np.array_equal(frames.astype(np.float32).astype(np.float64), frames)
+    walkers = ctx.make_walkers(specs)
+    abp.abp_deposit_log_enable(ctx.handle, 1 << 16)
+    X, F = gpu_steps_from(abp, ctx, walkers, frames[:T], md, streams)
+    _, ref = oracle_replay(specs, frames[:T].astype(np.float32), 0)
+    worst = check_mabp(abp, ctx, specs, walkers, F, ref)
+    keep = np.stack([~_lookup_tie_steps(sp, ref["s"][:, i], ref["sb"][:, i]) for i, sp in enumerate(specs)], axis=1)
+    worst["move"] = check_moves(specs, md, streams, frames, X, ref, keep=keep)
+    print("worst", worst)
+    P.record_errors("mABP b = 0.9, c = 0.001, 2 CVs (closed loop, Mueller-Brown)",
+                    "test_closed_loop_mabp_steps_match_the_oracle", worst)
     assert np.ptp(ref["s"][:, :, 0]) > 0.005
 
 
