@@ -244,6 +244,33 @@ def test_closed_loop_mabp_steps_match_the_oracle(abp, ctx):
     assert np.ptp(ref["s"][:, :, 0]) > 0.005
 
 
+def test_closed_loop_range_limit_wall_matches_the_oracle(abp, ctx):
+    """The CV range limit (a harmonic wall above smax on each CV) in the
+    closed loop, register-fed form: walkers that cross the wall on the COM
+    distance, step by step along the oracle's trajectory."""
+    nw, T = 4, 120
+    specs = [dict(sp, hill=synth.with_wall(sp["hill"], [1.5, 3.5], 30.0)) for sp in synth.mb64_specs(nw=nw, stride=4)]
+    md = synth.md_muller_brown(seed=10, state_f32=True)
+    streams = np.arange(nw) + 400
+    x0 = synth.SweepFrames(nw, seed=43).frames(0, 1)[0]
+    frames = _oracle_closed_loop(specs, x0, md, streams, T)
+    walkers = ctx.make_walkers(specs)
+    abp.abp_deposit_log_enable(ctx.handle, 1 << 16)
+    X, F = gpu_steps_from(abp, ctx, walkers, frames[:T], md, streams)
+    _, ref = oracle_replay(specs, frames[:T].astype(np.float32), 0)
+    assert np.any(ref["s"][:, :, 0] > 1.5) and np.any(ref["s"][:, :, 0] < 1.5)
+    # a walker whose dihedral atoms come close to a line has an FP32 angle
+    # whose rounding bound (the oracle's sb) is many times the other walkers':
+    # its hills move by more than the fixed grid target allows, so its grid
+    # and forces are left to the move check, which carries that bound
+    sbmax = ref["sb"].max(axis=0)[:, 1]
+    skip = {i for i in range(nw) if sbmax[i] > 10 * np.median(sbmax)}
+    assert len(skip) < nw // 2, sbmax
+    worst = check_run(abp, ctx, specs, walkers, frames[:T], 0, F, ref, skip=skip)
+    worst["move"] = check_moves(specs, md, streams, frames, X, ref)
+    print("worst", worst, "ill-conditioned walkers", sorted(skip))
+
+
 def test_closed_loop_full_size_64_walkers(abp, ctx):
     """The benchmark's closed-loop workload at full size: all 64 walkers
     (36 atoms, own 256 x 256 grids, Mueller-Brown x 0.1, mu = 0.1, stride
