@@ -271,6 +271,34 @@ def test_closed_loop_range_limit_wall_matches_the_oracle(abp, ctx):
     print("worst", worst, "ill-conditioned walkers", sorted(skip))
 
 
+def test_closed_loop_papers_rmsd_setup_matches_the_oracle(abp, ctx):
+    """The paper's ligand-run shape in the closed loop (generic form): two
+    offset-RMSD CVs of 4 atoms each on the 480 x 480 grid over [0, 12] nm,
+    mABP with compact hills a = 10 spacings, p = 20, b = 0.9, c = 0.001, a
+    hill every step; free overdamped Langevin of the atoms (no CV
+    potential), 150 steps along the oracle's trajectory."""
+    from tests.test_mabp_gpu import _lookup_tie_steps, check_mabp
+
+    nw, T = 4, 150
+    specs = synth.paper_rmsd_specs(nw=nw)
+    md = synth.md_params(seed=12, mu=0.1, state_f32=True)
+    streams = np.arange(nw) + 500
+    x0 = synth.RmsdFrames(specs, seed=7).frames(0, 1)[0]
+    frames = _oracle_closed_loop(specs, x0, md, streams, T)
+    assert np.array_equal(frames.astype(np.float32).astype(np.float64), frames)
+    walkers = ctx.make_walkers(specs)
+    abp.abp_deposit_log_enable(ctx.handle, 1 << 16)
+    X, F = gpu_steps_from(abp, ctx, walkers, frames[:T], md, streams)
+    _, ref = oracle_replay(specs, frames[:T].astype(np.float32), 0)
+    worst = check_mabp(abp, ctx, specs, walkers, F, ref)
+    keep = np.stack([~_lookup_tie_steps(sp, ref["s"][:, i], ref["sb"][:, i]) for i, sp in enumerate(specs)], axis=1)
+    worst["move"] = check_moves(specs, md, streams, frames, X, ref, keep=keep)
+    print("worst", worst)
+    P.record_errors("paper's RMSD setup, mABP b = 0.9, c = 0.001 (closed loop)",
+                    "test_closed_loop_papers_rmsd_setup_matches_the_oracle", worst)
+    assert np.ptp(ref["s"][:, :, 0]) > 0.01
+
+
 def test_closed_loop_full_size_64_walkers(abp, ctx):
     """The benchmark's closed-loop workload at full size: all 64 walkers
     (36 atoms, own 256 x 256 grids, Mueller-Brown x 0.1, mu = 0.1, stride
