@@ -1884,12 +1884,14 @@ struct SrvSlot {
   cudaStream_t stream = nullptr;
   cudaEvent_t kdone = nullptr;  // after the slot's kernel
   cudaEvent_t done = nullptr;   // after the forces are back in pinned memory
+  // h_in / d_in: one upload per launch, the coordinates followed by the
+  // walker table, the offsets and the steps of the batch (contiguous for
+  // the batch's sizes); h_off / h_step / h_table point into h_in for the
+  // batch in the slot
   float *h_in = nullptr, *h_out = nullptr;
   long long *h_off = nullptr, *h_step = nullptr;
   TableEntry *h_table = nullptr;
   float *d_in = nullptr, *d_out = nullptr;
-  long long *d_off = nullptr, *d_step = nullptr;
-  TableEntry *d_table = nullptr;
   std::vector<SrvRequest> reqs;
   std::vector<abp_walker *> ws;
   std::vector<int> deps;  // slots whose kernels this slot's kernel waits for
@@ -1932,14 +1934,8 @@ void srv_free_slots(abp_server *s) {
     if (sl.stream) cudaStreamSynchronize(sl.stream);
     cudaFreeHost(sl.h_in);
     cudaFreeHost(sl.h_out);
-    cudaFreeHost(sl.h_off);
-    cudaFreeHost(sl.h_step);
-    cudaFreeHost(sl.h_table);
     cudaFree(sl.d_in);
     cudaFree(sl.d_out);
-    cudaFree(sl.d_off);
-    cudaFree(sl.d_step);
-    cudaFree(sl.d_table);
     if (sl.done) cudaEventDestroy(sl.done);
     if (sl.kdone) cudaEventDestroy(sl.kdone);
     if (sl.stream) cudaStreamDestroy(sl.stream);
@@ -1997,6 +1993,17 @@ int srv_group_bytes(SrvSim &sm, int g) {
 // server lock; the slot's walkers and shape were taken under it).
 int srv_launch(abp_server *s, SrvSlot &sl) {
   const int n = (int)sl.reqs.size();
+  // the batch's walker table, offsets and steps are written behind its
+  // coordinates in the upload buffer, so that one copy takes them all
+  long long total = 0;
+  for (int i = 0; i < n; ++i) total += sl.reqs[i].natoms;
+  const size_t tab_at = (size_t)total * 16, off_at = tab_at + (size_t)n * sizeof(TableEntry),
+               step_at = off_at + (size_t)n * 8, upload = step_at + (size_t)n * 8;
+  unsigned char *hb = reinterpret_cast<unsigned char *>(sl.h_in);
+  unsigned char *db = reinterpret_cast<unsigned char *>(sl.d_in);
+  sl.h_table = reinterpret_cast<TableEntry *>(hb + tab_at);
+  sl.h_off = reinterpret_cast<long long *>(hb + off_at);
+  sl.h_step = reinterpret_cast<long long *>(hb + step_at);
   long long off = 0;
   for (int i = 0; i < n; ++i) {
     const SrvRequest &r = sl.reqs[i];
@@ -2019,27 +2026,25 @@ int srv_launch(abp_server *s, SrvSlot &sl) {
   int st = step_shape(s->ctx, sl.cn, sl.G, sl.gb, 0, &a.G, &a.groups_per_cta, &a.group_bytes, &a.tile_budget);
   if (st) return st;
   cudaStream_t stream = sl.stream;
-  if (cudaMemcpyAsync(sl.d_in, sl.h_in, (size_t)off * 16, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
-      cudaMemcpyAsync(sl.d_off, sl.h_off, (size_t)n * 8, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
-      cudaMemcpyAsync(sl.d_step, sl.h_step, (size_t)n * 8, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
-      cudaMemcpyAsync(sl.d_table, sl.h_table, (size_t)n * sizeof(TableEntry), cudaMemcpyHostToDevice, stream) !=
-          cudaSuccess)
-    return ABP_ERR_CUDA;
+  if (cudaMemcpyAsync(db, hb, upload, cudaMemcpyHostToDevice, stream) != cudaSuccess) return ABP_ERR_CUDA;
+  const TableEntry *d_table = reinterpret_cast<const TableEntry *>(db + tab_at);
+  const long long *d_off = reinterpret_cast<const long long *>(db + off_at);
+  const long long *d_step = reinterpret_cast<const long long *>(db + step_at);
   // the previous step of a simulation in this slot runs in another slot:
   // its kernel (grid deposit, walker state) must finish first
   for (int d : sl.deps)
     if (cudaStreamWaitEvent(stream, s->slots[d].kdone, 0) != cudaSuccess) return ABP_ERR_CUDA;
-  a.table = sl.d_table;
+  a.table = d_table;
   a.nw = n;
   a.coords = sl.d_in;
-  a.coff = sl.d_off;
+  a.coff = d_off;
   a.cstride = 0;
   a.forces = sl.d_out;
-  a.foff = sl.d_off;
+  a.foff = d_off;
   a.fstride = 0;
   a.mode = ABP_FORCES_OVERWRITE;
   a.step0 = 0;
-  a.wstep = sl.d_step;
+  a.wstep = d_step;
   a.nsteps = 1;
   a.log = s->ctx->log;
   a.ctr = s->ctx->ctr;
@@ -2238,22 +2243,17 @@ abp_status abp_server_create(abp_ctx *ctx, const abp_server_desc *desc, abp_serv
     return st;
   }
   const size_t rec = (size_t)s->max_batch * s->max_atoms * 16;
+  const size_t meta = (size_t)s->max_batch * (sizeof(TableEntry) + 16);  // table, offsets, steps
   s->slots.resize(s->nstreams);
   cudaError_t e = cudaSuccess;
   for (auto &sl : s->slots) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.kdone, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaHostAlloc(&sl.h_in, rec, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc(&sl.h_in, rec + meta, cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaHostAlloc(&sl.h_out, rec, cudaHostAllocDefault);
-    if (e == cudaSuccess) e = cudaHostAlloc(&sl.h_off, (size_t)s->max_batch * 8, cudaHostAllocDefault);
-    if (e == cudaSuccess) e = cudaHostAlloc(&sl.h_step, (size_t)s->max_batch * 8, cudaHostAllocDefault);
-    if (e == cudaSuccess) e = cudaHostAlloc(&sl.h_table, (size_t)s->max_batch * sizeof(TableEntry), cudaHostAllocDefault);
-    if (e == cudaSuccess) e = cudaMalloc(&sl.d_in, rec);
+    if (e == cudaSuccess) e = cudaMalloc(&sl.d_in, rec + meta);
     if (e == cudaSuccess) e = cudaMalloc(&sl.d_out, rec);
-    if (e == cudaSuccess) e = cudaMalloc(&sl.d_off, (size_t)s->max_batch * 8);
-    if (e == cudaSuccess) e = cudaMalloc(&sl.d_step, (size_t)s->max_batch * 8);
-    if (e == cudaSuccess) e = cudaMalloc(&sl.d_table, (size_t)s->max_batch * sizeof(TableEntry));
   }
   if (e != cudaSuccess) {
     cudaGetLastError();
