@@ -1781,6 +1781,7 @@ abp_status abp_sync(abp_ctx *ctx) {
 #include <functional>
 #include <memory>
 #include <thread>
+#include <atomic>
 #include <unordered_map>
 
 namespace {
@@ -1851,6 +1852,7 @@ void part_range(const long long *off, int n, long long total, int p, int np, int
 }
 
 constexpr long long kTeamAtoms = 16384;  // below this a launch is copied by one thread
+constexpr double kLauncherSpin = 50e-6;   // seconds the launcher spins for work before it sleeps
 
 double steady_now() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
@@ -1908,6 +1910,9 @@ struct abp_server {
   int max_batch = 4096, max_atoms = 1024, nstreams = 2;
   std::mutex mu;
   std::condition_variable cv_work, cv_done, cv_launched;
+  // bumped after every change that cv_work announces: the launcher spins on
+  // it for a while before it sleeps
+  std::atomic<unsigned long long> work_seq{0};
   std::unordered_map<int64_t, SrvSim> sims;
   int64_t next_sim = 0;
   std::deque<int64_t> ready;  // simulations with pending requests (each once)
@@ -2090,6 +2095,7 @@ void srv_complete(abp_server *s, SrvSlot &sl) {
     sl.busy = false;
   }
   s->cv_done.notify_all();
+  s->work_seq.fetch_add(1, std::memory_order_release);
   s->cv_work.notify_one();  // a slot is free
 }
 
@@ -2156,7 +2162,18 @@ void srv_launcher(abp_server *s) {
           if (!s->slots[i].busy) return i;
         return -1;
       };
-      s->cv_work.wait(lk, [&] { return s->stop || (!s->ready.empty() && free_slot() >= 0); });
+      auto work = [&] { return s->stop || (!s->ready.empty() && free_slot() >= 0); };
+      if (!work()) {
+        // spin for up to kLauncherSpin seconds before sleeping: a request (or
+        // a freed slot) that comes within it is taken without a thread wake-up
+        const unsigned long long seq0 = s->work_seq.load(std::memory_order_acquire);
+        lk.unlock();
+        const double t_spin = steady_now();
+        for (int it = 0; s->work_seq.load(std::memory_order_acquire) == seq0; ++it)
+          if ((it & 255) == 255 && steady_now() - t_spin > kLauncherSpin) break;
+        lk.lock();
+      }
+      s->cv_work.wait(lk, work);
       if (s->stop) break;
       const double t0 = steady_now();
       fi = free_slot();
@@ -2279,6 +2296,7 @@ void abp_server_destroy(abp_server *s) {
     std::lock_guard<std::mutex> lk(s->mu);
     s->stop = true;
   }
+  s->work_seq.fetch_add(1, std::memory_order_release);
   s->cv_work.notify_all();
   if (s->launcher.joinable()) s->launcher.join();
   {
@@ -2396,6 +2414,7 @@ abp_status abp_server_submit(abp_server *s, int64_t sim, int64_t step, const flo
     ++s->submitted;
     ++s->queued;
   }
+  s->work_seq.fetch_add(1, std::memory_order_release);
   s->cv_work.notify_one();
   return ABP_OK;
 }
@@ -2457,6 +2476,7 @@ abp_status abp_server_submit_many(abp_server *s, int n, const int64_t *sims, con
       s->submitted += k1 - k0;
       s->queued += k1 - k0;
     }
+    s->work_seq.fetch_add(1, std::memory_order_release);
     s->cv_work.notify_one();
   }
   return ABP_OK;
