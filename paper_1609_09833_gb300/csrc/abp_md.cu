@@ -308,9 +308,13 @@ __device__ __noinline__ void md_deposit(const Grp &g, GroupFixed<Real> *fx, cons
 
 // The closed-loop kernel: a group of four warps per walker.
 //   warps 0 and 1, the step pair: each step's chain. Warp 0 evaluates the COM
-//   distances (com_warp), the CV potential's gradient and a4 (lane 0);
-//   warp 1 evaluates the other CVs (one lane per CV) beside warp 0's sums;
-//   both run a deposit's stencil and the forces and moves of the atoms.
+//   distances (com_warp) and a4 (interp_warp); warp 1 evaluates the other
+//   CVs (one lane per CV) beside warp 0's sums and the CV potential's
+//   gradient beside a4; both run a deposit's stencil and the forces and
+//   moves of the atoms. FAST (the register-fed form, chosen on the host for
+//   walkers that fit it): the chain's loop invariants in registers, the
+//   interpolation state of a step without a deposit by selects, the step's
+//   flags on warp 1 beside a4 -- the same operations on the same values.
 //   Named barrier gid + 1 (64 threads) separates the step's phases.
 //   warps 2 and 3, the producers: the Philox noise of the next window of W
 //   steps while the pair runs the current one (two noise buffers); then,
