@@ -406,6 +406,10 @@ abp_status abp_shared_forces(abp_ctx *ctx, abp_walker *const *walkers, int n, vo
  * one's kernel, so the host can pack the next launch meanwhile. Results
  * come back in launch order, so one simulation's results arrive in step
  * order. A walker's result is the same alone and in any mix of requests.
+ * A launch uploads its requests' coordinates and its walker table in one
+ * host-to-device copy. When it runs out of work the launcher thread spins
+ * for up to 50 us before it sleeps, so that a request arriving then is taken
+ * without a thread wake-up (one host core is busy during that spin).
  * The server owns the context's stream while it runs. */
 typedef struct abp_server abp_server;
 
